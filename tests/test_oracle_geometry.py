@@ -1,0 +1,114 @@
+"""Pins for the oracle's unsigned distances (Sec. III-B, d_k of PT and EE pairs).
+
+The distance of a pair is the minimum over the closed primitives; these tests pin the
+oracle's closed-form minimisation against brute-force sampling of that minimum, against
+closed forms of special configurations, and against the stencil it reports."""
+import numpy as np
+import pytest
+
+import oracle
+
+rng = np.random.default_rng(1234)
+
+
+def _tri_samples(t0, t1, t2, n=120):
+    u, v = np.meshgrid(np.linspace(0, 1, n + 1), np.linspace(0, 1, n + 1), indexing="ij")
+    m = (u + v) <= 1.0 + 1e-15
+    u = u[m]; v = v[m]
+    return t0[None] + u[:, None] * (t1 - t0)[None] + v[:, None] * (t2 - t0)[None]
+
+
+def _seg_samples(a, b, n=400):
+    t = np.linspace(0, 1, n + 1)
+    return a[None] + t[:, None] * (b - a)[None]
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_pt_distance_vs_sampling(trial):
+    t = rng.normal(size=(3, 3))
+    # mix of points over the face, near edges and past vertices
+    p = t.mean(0) + rng.normal(size=3) * (0.3 + 1.5 * (trial % 3))
+    d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t.ravel()]))
+    d = np.sqrt(d2)
+    S = _tri_samples(*t)
+    ds = np.sqrt(((S - p) ** 2).sum(1)).min()
+    diam = max(np.linalg.norm(t[0] - t[1]), np.linalg.norm(t[1] - t[2]), np.linalg.norm(t[2] - t[0]))
+    h = 1.0 / 120
+    assert d <= ds + 1e-12
+    assert ds <= d + h * diam
+    # stencil: r = sum c_a x_a has length d
+    X = np.vstack([p, t])
+    r = (c[:, None] * X).sum(0)
+    assert np.isclose(np.linalg.norm(r), d, rtol=1e-12, atol=1e-15)
+    assert abs(c.sum()) < 1e-12
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_ee_distance_vs_sampling(trial):
+    a0, a1, b0, b1 = rng.normal(size=(4, 3))
+    if trial % 4 == 0:      # near-parallel
+        b1 = b0 + (a1 - a0) * 0.8 + rng.normal(size=3) * 1e-4
+    if trial % 8 == 1:      # exactly parallel
+        b1 = b0 + 2.0 * (a1 - a0)
+    d2, reg, c = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+    d = np.sqrt(d2)
+    A = _seg_samples(a0, a1); B = _seg_samples(b0, b1)
+    ds = np.sqrt(((A[:, None] - B[None]) ** 2).sum(2)).min()
+    la = np.linalg.norm(a1 - a0); lb = np.linalg.norm(b1 - b0)
+    assert d <= ds + 1e-12
+    assert ds <= d + (la + lb) / 400
+    X = np.vstack([a0, a1, b0, b1])
+    r = (c[:, None] * X).sum(0)
+    assert np.isclose(np.linalg.norm(r), d, rtol=1e-10, atol=1e-14)
+    assert abs(c.sum()) < 1e-12
+
+
+def test_pt_closed_forms():
+    t0 = np.array([0.0, 0.0, 0.0]); t1 = np.array([1.0, 0.0, 0.0]); t2 = np.array([0.0, 1.0, 0.0])
+    # above the face interior: plane distance
+    p = np.array([0.2, 0.3, 0.7])
+    d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t0, t1, t2]))
+    assert reg == 0 and np.isclose(d2, 0.49, rtol=1e-15)
+    assert np.allclose(c, [1, -0.5, -0.2, -0.3], atol=1e-15)
+    # tilted triangle: n.(p - t0) / |n|
+    T = rng.normal(size=(3, 3))
+    n = np.cross(T[1] - T[0], T[2] - T[0]); n /= np.linalg.norm(n)
+    p = T.mean(0) + 0.05 * n
+    d2, reg, _ = oracle.pair_d2(0, np.concatenate([p, T.ravel()]))
+    assert reg == 0 and np.isclose(np.sqrt(d2), 0.05, rtol=1e-12)
+    # past vertex t1: point-point distance
+    p = np.array([2.0, -1.0, 0.5])
+    d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t0, t1, t2]))
+    assert reg == 5 and np.isclose(d2, 1 + 1 + 0.25)
+    assert np.allclose(c, [1, 0, -1, 0])
+    # beside edge t0-t1: distance to the line
+    p = np.array([0.4, -0.3, 0.4])
+    d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t0, t1, t2]))
+    assert reg == 1 and np.isclose(d2, 0.09 + 0.16)
+
+
+def test_ee_closed_forms():
+    # perpendicular crossing segments separated by 0.3 along z
+    a0, a1 = np.array([-1.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0])
+    b0, b1 = np.array([0.25, -1.0, 0.3]), np.array([0.25, 1.0, 0.3])
+    d2, reg, c = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+    assert reg == 0 and np.isclose(d2, 0.09, rtol=1e-15)
+    assert np.allclose(c, [0.375, 0.625, -0.5, -0.5])
+    # parallel overlapping segments: the distance between the lines
+    b0, b1 = np.array([0.5, 0.2, 0.0]), np.array([3.0, 0.2, 0.0])
+    d2, reg, _ = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+    assert np.isclose(d2, 0.04, rtol=1e-14)
+    # collinear disjoint: endpoint-endpoint
+    b0, b1 = np.array([1.5, 0.0, 0.0]), np.array([3.0, 0.0, 0.0])
+    d2, reg, c = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+    assert np.isclose(d2, 0.25) and reg == 7
+
+
+def test_distance_invariant_under_rigid_motion():
+    for ptype in (0, 1):
+        X = rng.normal(size=(4, 3))
+        d2, _, _ = oracle.pair_d2(ptype, X.ravel())
+        Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        Y = X @ Q.T + rng.normal(size=3)
+        e2, _, _ = oracle.pair_d2(ptype, Y.ravel())
+        assert np.isclose(d2, e2, rtol=1e-12)
