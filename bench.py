@@ -1,0 +1,493 @@
+#!/usr/bin/env python3
+"""Benchmark of the Embedded-IPC contact stage on one GB300 (or N replicas).
+
+Workload: the bubble-grasp scene (noisy sphere body of 100,820 triangles in a 1,584-node
+cage, squeezed by two ellipsoidal membranes of 40,500 triangles in 2,040-node cages,
+dhat = 5e-4 m, kappa = 1e4, lagged friction mu = 0.8) along its 60-iterate closing
+trajectory.  One step is one Newton iteration's contact stage, all through the C ABI:
+  embed x = J q -> LBVH contact set -> (lagged friction state at each time step's first
+  iterate) -> barrier/friction energy, gradient, projected Hessian, reduced by the cage
+  embedding into g_r and the BSR H_r -> CCD step bound along the iterate's search step.
+Metric: active contact pairs evaluated per second over whole steps; CCD candidate pairs
+advanced per second is reported beside it.
+
+Timing: W untimed warm-up steps, then K steps bracketed by barrier + synchronize; each step
+is timed on the device with CUDA events on the launching stream, and a 256 MiB buffer is
+rewritten between steps (outside the events) so every step starts with a cold L2.
+`--impl reference` times the CPU oracle instead (host cores, bounded samples).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contact pairs/s (barrier+grad+Hess into subspace)"
+UNIT = "pairs/s"
+WORKLOAD = "bubble_grasp"
+
+# Algorithmic cost per unit of the kernels the roofline may name:
+#  eval_barrier: FP64 flops per contact pair; ccd_advance: FP64 flops per candidate;
+#  the rest: DRAM bytes per unit (minimum traffic of the kernel's inputs and outputs).
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="small scene (profiling / smoke)")
+    ap.add_argument("--json-out", default="")
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    import torch
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.strip().splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons), samples=len(sm))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# Algorithmic work per unit ("Roofline"):
+#   eval_barrier  FP64 flops per contact pair, counted from the kernel's arithmetic
+#   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
+#   others        DRAM bytes per unit of their minimum input + output traffic
+FP64_FLOPS_PER_PAIR = 7600.0
+FP64_FLOPS_PER_CCD_CAND = 420.0
+# measured DRAM bytes per launch from an ncu capture of the same kernel (None = not captured)
+NCU_TRAFFIC_PER_UNIT = {}
+
+
+def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
+    if launches == 0 or total_ms <= 0:
+        return dict(bound=None, achieved=None, peak=None, unit=None, frac=None, traffic=None, kernel=name)
+    avg_s = total_ms / 1e3 / launches
+    per_step_launches = launches / steps
+    hbm, src = measured_peaks()
+    if name in ("eval_barrier", "ccd_advance"):
+        units = (pairs_per_step if name == "eval_barrier" else cand_per_step) / per_step_launches
+        per = FP64_FLOPS_PER_PAIR if name == "eval_barrier" else FP64_FLOPS_PER_CCD_CAND
+        ach = units * per / avg_s / 1e12
+        peak = FP64_PEAK_TFLOPS
+        tr = NCU_TRAFFIC_PER_UNIT.get(name)
+        return dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                    traffic=(tr * units if tr else None), kernel=name, launch_ms=avg_s * 1e3,
+                    units_per_launch=units, unit_cost=f"{per:.0f} FP64 flop per unit",
+                    peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)")
+    # memory-bound kernels: minimum DRAM bytes per launch
+    nv, ne, nf = sc.Nv, sc.E, sc.F
+    bytes_model = {
+        "bvh_build": 0.5 * (nf + ne) * (24 + 8 + 4 + 4 * 4 * 12 + 64 + 8),
+        "bvh_query": 0.5 * (32 * nv + 72 * ne + 64 * (nf + ne) + 8 * cand_per_step),
+        "narrow_phase": 8 * cand_per_step + 20 * pairs_per_step,
+        "pair_sort": 5 * pairs_per_step * 24 + 20 * pairs_per_step,
+        "hessian_reduce": 0.0,
+        "embed": 32 * nv + 48 * nv,
+    }
+    b = bytes_model.get(name)
+    if not b:
+        return dict(bound="hbm", achieved=None, peak=hbm, unit="GB/s", frac=None, traffic=None, kernel=name,
+                    launch_ms=avg_s * 1e3)
+    ach = b / avg_s / 1e9
+    tr = NCU_TRAFFIC_PER_UNIT.get(name)
+    return dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=tr, kernel=name,
+                launch_ms=avg_s * 1e3, peak_source=src)
+
+
+def build_scene(quick):
+    from paper_2409_16385_gb300 import scenes
+    return scenes.make_config(2, small=quick)
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(sc, t, frac, seed=0):
+    """The oracle's whole contact stage at iterate t restricted to a random fraction of
+    the query primitives (PT queries: vertices; EE queries: edges): brute-force pairs of
+    those queries, lagged friction, evaluation, step bound.  Returns (pairs, seconds,
+    ccd candidates)."""
+    import oracle
+    rng = np.random.default_rng(seed + t)
+    qv = np.sort(rng.choice(sc.Nv, max(1, int(frac * sc.Nv)), replace=False)).astype(np.int32)
+    qe = np.sort(rng.choice(sc.E, max(1, int(frac * sc.E)), replace=False)).astype(np.int32)
+    q, qn = sc.iterate(t), sc.iterate(sc.lag_of(t))
+    t0 = time.perf_counter()
+    x, xn = oracle.embed(sc, q), oracle.embed(sc, qn)
+    pv = oracle.pairs_of(sc, x, 0, qv)
+    pe = oracle.pairs_of(sc, x, 1, qe)
+    prs = dict(type=np.concatenate([np.zeros(len(pv["i"]), np.int32), np.ones(len(pe["i"]), np.int32)]),
+               i=np.concatenate([pv["i"], pe["i"]]), j=np.concatenate([pv["j"], pe["j"]]))
+    pvn = oracle.pairs_of(sc, xn, 0, qv)
+    pen = oracle.pairs_of(sc, xn, 1, qe)
+    prn = dict(type=np.concatenate([np.zeros(len(pvn["i"]), np.int32), np.ones(len(pen["i"]), np.int32)]),
+               i=np.concatenate([pvn["i"], pen["i"]]), j=np.concatenate([pvn["j"], pen["j"]]))
+    lag = oracle.friction_lag(sc, xn, prn)
+    oracle.eval_contact(sc, x, prs, lag)
+    dx = oracle.embed(sc, sc.dq(t), displacement=True)
+    a1 = oracle.accd_of(sc, x, dx, 0, qv)
+    a2 = oracle.accd_of(sc, x, dx, 1, qe)
+    dt = time.perf_counter() - t0
+    return len(prs["type"]), dt, a1["n_candidates"] + a2["n_candidates"]
+
+
+def run_reference(args, ws, rank):
+    """`--impl reference`: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sc = build_scene(args.quick)
+    # size each step's sample so that warm-up + timed steps end within about 3 minutes:
+    # calibrate on a 1/1000 sample, then scale to ~150 s / (steps + warm-up) per step
+    total_steps = args.steps + args.warmup
+    _, t_cal, _ = oracle_sample(sc, 0, 1e-3, seed=999)
+    frac = min(1.0 / 12, 1e-3 * (150.0 / total_steps) / max(t_cal, 1e-3))
+    for k in range(args.warmup):
+        oracle_sample(sc, (7 * k) % sc.n_iterates, frac, seed=k)
+    pairs = 0; secs = 0.0; cand = 0
+    for k in range(args.steps):
+        p, dt, c = oracle_sample(sc, (7 * (k + args.warmup)) % sc.n_iterates, frac, seed=100 + k)
+        pairs += p; secs += dt; cand += c
+    v = pairs / secs if secs > 0 else 0.0
+    cores = oracle.num_threads()
+    sample = f"per step: one iterate, brute-force contact set of {frac:.4f} of the vertices and edges (queries), " \
+             f"lagged friction, evaluation and CCD of those queries"
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * secs / max(1, args.steps), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic (seeded)", impl="reference",
+                config=dict(workload=WORKLOAD, iterates=sc.n_iterates, l2="n/a (host)"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
+                ccd_candidates_per_s=cand / secs if secs > 0 else 0.0)
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2409_16385_gb300 import ContactScene, binding
+
+    dev = torch.device("cuda", local)
+    sc = build_scene(args.quick)
+    n_it = sc.n_iterates
+    cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21)
+    lib = binding.load()
+    Q = torch.tensor(np.stack([sc.iterate(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    DQ = torch.tensor(np.stack([sc.dq(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    lag_of = [sc.lag_of(t) for t in range(n_it)]
+    pairs = cs.new_pairs()
+    lag = cs.new_lag()
+    H = cs.new_bsr()
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros((sc.Ns, 3), dtype=torch.float64, device=dev)
+    x = torch.empty((sc.Nv, 3), dtype=torch.float64, device=dev)
+    dx = torch.empty((sc.Nv, 3), dtype=torch.float64, device=dev)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    ncand = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(t, q, dq):
+        if lag_of[t] == t:
+            cs.build_candidates(q, out=pairs)
+            cs.friction_lag(q, pairs, out=lag)
+        else:
+            cs.build_candidates(q, out=pairs)
+        cs.eval_contact(q, pairs, lag, E=E, g_r=g, H=H)
+        cs.embed(q, out=x)
+        cs.embed(dq, out=dx, displacement=True)
+        cs.accd_toi(x, dx, alpha=alpha, n_candidates=ncand)
+
+    # the lag state of the first timed iterates comes from its time step's first iterate
+    t0 = args.warmup % n_it
+    first = lag_of[t0]
+    cs.build_candidates(Q[first], out=pairs)
+    cs.friction_lag(Q[first], pairs, out=lag)
+
+    # warm-up with every kernel timer on: picks the dominant kernel for the roofline
+    cs.timing_enable(None)
+    start_t = (t0 - args.warmup) % n_it
+    for k in range(args.warmup):
+        t = (start_t + k) % n_it
+        if k == 0 and lag_of[t] != t:
+            cs.build_candidates(Q[lag_of[t]], out=pairs)
+            cs.friction_lag(Q[lag_of[t]], pairs, out=lag)
+        step(t, Q[t], DQ[t])
+    torch.cuda.synchronize()
+    warm = cs.timing_read()
+    dominant = max(warm.items(), key=lambda kv: kv[1][0])[0] if warm else "eval_barrier"
+    cs.timing_enable([dominant])
+    st = cs.status()
+    if st["flags"] & ~64:
+        raise RuntimeError(f"device status after warm-up: {st}")
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    counts = torch.zeros((K, 2), dtype=torch.int64, device=dev)
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    launches0 = lib.eipc_launch_count()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(K):
+        t = (t0 + k) % n_it
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(t, Q[t], DQ[t])
+        evs[k][1].record(stream)
+        counts[k, 0].copy_(pairs.count[0])
+        counts[k, 1].copy_(ncand[0])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = lib.eipc_launch_count() - launches0
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    cnt = counts.cpu().numpy()
+    kt = cs.timing_read()
+    st = cs.status()
+    if st["flags"] & ~64:
+        raise RuntimeError(f"device status after the timed steps: {st}")
+    total_s = step_ms.sum() / 1e3
+    total_pairs = float(cnt[:, 0].sum())
+    total_cand = float(cnt[:, 1].sum())
+    if ws > 1:
+        tt = torch.tensor([total_s, total_pairs, total_cand], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_s_all, total_pairs_all, total_cand_all = float(mx[0]), float(sm[1]), float(sm[2])
+    else:
+        total_s_all, total_pairs_all, total_cand_all = total_s, total_pairs, total_cand
+    value = total_pairs_all / total_s_all
+
+    # ---- roofline of the dominant kernel, from its live event timer
+    dom_ms, dom_n = kt.get(dominant, (0.0, 0))
+    roof = roofline_figure(dominant, dom_ms, dom_n, K, total_pairs / K, total_cand / K, sc)
+
+    # ---- stage-only throughputs (same iterates, pairs precomputed)
+    stage = {}
+    cs.timing_enable([])
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev_ms = 0.0; n_p = 0
+    for k in range(K):
+        t = (t0 + k) % n_it
+        cs.build_candidates(Q[t], out=pairs)
+        n_p += int(pairs.count.item())
+        flush.zero_()
+        ev0.record(stream)
+        cs.eval_contact(Q[t], pairs, lag, E=E, g_r=g, H=H)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ev_ms += ev0.elapsed_time(ev1)
+    stage["eval_pairs_per_s"] = n_p / (ev_ms / 1e3)
+    ac_ms = 0.0; n_c = 0
+    for k in range(K):
+        t = (t0 + k) % n_it
+        cs.embed(Q[t], out=x)
+        cs.embed(DQ[t], out=dx, displacement=True)
+        flush.zero_()
+        ev0.record(stream)
+        cs.accd_toi(x, dx, alpha=alpha, n_candidates=ncand)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ac_ms += ev0.elapsed_time(ev1)
+        n_c += int(ncand.item())
+    stage["ccd_queries_per_s"] = n_c / (ac_ms / 1e3)
+    stage["ccd_queries_per_s_in_step"] = total_cand / total_s
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(cs, sc, Q, DQ, lag_of, t0, K, flush, dev)
+
+    # ---- CPU baseline (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        # about 20 s of oracle work: calibrate on a 1/1000 sample first
+        _, t_cal, _ = oracle_sample(sc, t0, 1e-3, seed=999)
+        frac = 1.0 if args.quick else min(1.0 / 12, 1e-3 * 20.0 / max(t_cal, 1e-3))
+        p, dt, c = oracle_sample(sc, t0, frac)
+        cpu = dict(value=p / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                   sample=f"iterate {t0}: brute-force contact set of a {frac:.4f} fraction of the vertices and edges"
+                          f" (queries), lagged friction, evaluation and CCD of those queries; {p} pairs in {dt:.1f} s")
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=K, warmup=args.warmup,
+                ms_per_step=float(step_ms.mean()), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic (seeded)",
+                config=dict(workload=WORKLOAD + ("_small" if args.quick else ""), iterates=n_it,
+                            triangles=sc.F, vertices=sc.Nv, edges=sc.E, cage_nodes=sc.Ns,
+                            dhat=sc.params["dhat"], mu=sc.params["mu"], parallelism=f"replicas x{ws}",
+                            l2="flushed between steps (256 MiB rewrite)",
+                            pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K),
+                clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
+                ccd_queries_per_s=total_cand_all / total_s_all, stages=stage,
+                e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    cs.close()
+
+
+def run_e2e(cs, sc, Q, DQ, lag_of, t0, K, flush, dev):
+    """Same steps through the public API with pinned host buffers: every step copies q and
+    dq in, runs the stage and reads E, g_r, alpha and the BSR Hessian back."""
+    import torch
+    n_it = sc.n_iterates
+    qh = [Q[t].cpu().pin_memory() for t in range(n_it)]
+    dqh = [DQ[t].cpu().pin_memory() for t in range(n_it)]
+    q = torch.empty_like(Q[0]); dq = torch.empty_like(DQ[0])
+    pairs, lag, H = cs.new_pairs(), cs.new_lag(), cs.new_bsr()
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros((sc.Ns, 3), dtype=torch.float64, device=dev)
+    x = torch.empty((sc.Nv, 3), dtype=torch.float64, device=dev)
+    dx = torch.empty_like(x)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    Eh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    gh = torch.zeros((sc.Ns, 3), dtype=torch.float64).pin_memory()
+    ah = torch.zeros(1, dtype=torch.float64).pin_memory()
+    nh = torch.zeros(1, dtype=torch.int64).pin_memory()
+    rph = torch.zeros(sc.Ns + 1, dtype=torch.int32).pin_memory()
+    colh = torch.zeros(H.col.shape[0], dtype=torch.int32).pin_memory()
+    valh = torch.zeros(H.val.shape, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream()
+    first = lag_of[t0]
+    q.copy_(qh[first], non_blocking=True)
+    cs.build_candidates(q, out=pairs)
+    cs.friction_lag(q, pairs, out=lag)
+    torch.cuda.synchronize()
+    tot_ms, tot_pairs, bi, bo = 0.0, 0, 0, 0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(K):
+        t = (t0 + k) % n_it
+        flush.zero_()
+        ev0.record(stream)
+        q.copy_(qh[t], non_blocking=True)
+        dq.copy_(dqh[t], non_blocking=True)
+        cs.build_candidates(q, out=pairs)
+        if lag_of[t] == t:
+            cs.friction_lag(q, pairs, out=lag)
+        cs.eval_contact(q, pairs, lag, E=E, g_r=g, H=H)
+        cs.embed(q, out=x)
+        cs.embed(dq, out=dx, displacement=True)
+        cs.accd_toi(x, dx, alpha=alpha)
+        Eh.copy_(E, non_blocking=True)
+        gh.copy_(g, non_blocking=True)
+        ah.copy_(alpha, non_blocking=True)
+        nh.copy_(H.nnzb, non_blocking=True)
+        rph.copy_(H.row_ptr, non_blocking=True)
+        stream.synchronize()
+        nb = int(nh[0])
+        colh[:nb].copy_(H.col[:nb], non_blocking=True)
+        valh[:nb].copy_(H.val[:nb], non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        tot_ms += ev0.elapsed_time(ev1)
+        tot_pairs += int(pairs.count.item())
+        bi += 2 * Q[0].numel() * 8
+        bo += 8 + gh.numel() * 8 + 8 + 8 + rph.numel() * 4 + nb * (4 + 72)
+    return dict(value=tot_pairs / (tot_ms / 1e3), unit=UNIT, h2d_bytes_per_step=bi // K, d2h_bytes_per_step=bo // K,
+                ms_per_step=tot_ms / K)
+
+
+def main():
+    args = parse()
+    backend = "gloo" if args.impl == "reference" else "nccl"
+    ws, rank, local = dist_setup(backend)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/* embipc.h -- C ABI of the GB300 contact stage of Embedded IPC (arxiv 2409.16385).
+ *
+ * One Newton iteration's contact work, for a high-resolution collision surface embedded
+ * in a coarse tetrahedral cage (Sec. III-D):
+ *   eipc_embed             x = phi(q) = J q                          (Sec. III-D, Eq. 12)
+ *   eipc_build_candidates  contact set B: PT / EE pairs with 0 < d < dhat (Sec. III-B)
+ *   eipc_friction_lag      lagged friction state at x^n               (Sec. III-B)
+ *   eipc_eval_contact      E = kappa sum b(d_k) + sum D_k, g_r = J^T grad E,
+ *                          H_r = J^T (sum P+(kappa hess b_k) + sum hess D_k) J
+ *                                                   (Eq. IPC_energy, Sec. III-C, Eq. 15)
+ *   eipc_accd_toi          step bound alpha for a straight full-space motion x + t dx,
+ *                          linear in the reduced step because phi is linear (Sec. III-C)
+ *
+ * Conventions
+ *  - Every array passed to a compute call is DEVICE memory owned by the caller, and every
+ *    compute call is asynchronous on the given CUDA stream; nothing synchronises and no
+ *    count is read back to the host, so a sequence of calls can be captured in a CUDA
+ *    graph.  eipc_scene_create takes HOST arrays and copies them to the device.
+ *  - The scene owns its topology copy and a workspace sized at creation; compute calls
+ *    allocate nothing.  A scene may be used from one stream at a time.
+ *  - Host-detectable misuse (null pointer, negative size, capacity too small for the
+ *    scene) returns a negative status synchronously and enqueues nothing.
+ *  - Device-detected conditions (a pair at d <= 0, a full buffer, a non-finite input,
+ *    a CCD pair that hit its iteration cap) set bits of the scene's device status word;
+ *    eipc_status_read synchronises the stream and returns them.  After an overflow the
+ *    outputs of that call are incomplete and the status reports the size needed.
+ *  - Energies and derivatives are the unscaled contact potential; the caller multiplies
+ *    by h^2 as in the incremental potential of Sec. III-B.
+ */
+#ifndef EMBIPC_H
+#define EMBIPC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t eipc_status;
+typedef struct CUstream_st* eipc_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+enum {
+  EIPC_OK = 0,
+  EIPC_ERR_INVALID = -1,      /* bad argument (null pointer, size, capacity)            */
+  EIPC_ERR_CUDA = -2,         /* a CUDA runtime call failed                             */
+  EIPC_ERR_NOMEM = -3,        /* workspace allocation failed at scene creation          */
+  /* device status bits (eipc_status_read) */
+  EIPC_FLAG_PENETRATION = 1,  /* some pair has d <= 0: the configuration is infeasible  */
+  EIPC_FLAG_PAIR_OVERFLOW = 2,/* more contact pairs than the caller's pair capacity     */
+  EIPC_FLAG_CAND_OVERFLOW = 4,/* more broad-phase candidates than the scene workspace   */
+  EIPC_FLAG_REC_OVERFLOW = 8, /* more reduction records than the scene workspace        */
+  EIPC_FLAG_BSR_OVERFLOW = 16,/* more BSR blocks than the caller's block capacity       */
+  EIPC_FLAG_NONFINITE = 32,   /* a non-finite position or displacement was read         */
+  EIPC_FLAG_ACCD_CAP = 64,    /* a CCD pair reached accd_max_iter (alpha still safe)    */
+  EIPC_FLAG_LAG_OVERFLOW = 128,/* more friction pairs than the lag buffer capacity      */
+  EIPC_FLAG_STACK_OVERFLOW = 256 /* a BVH traversal exceeded its 64-entry stack          */
+};
+
+/* Contact parameters.  dhat: barrier activation distance (m); kappa: barrier stiffness;
+ * mu: friction coefficient; eps_v: static-friction velocity threshold (m/s) and h: time
+ * step (s), whose product eps_v*h is the f0/f1 transition; accd_s in (0,1): the CCD
+ * stops advancing once a pair's distance has shrunk to accd_s times its initial value;
+ * accd_max_iter: per-pair cap on CCD advancements. */
+typedef struct {
+  double dhat, kappa, mu, eps_v, h, accd_s;
+  int32_t accd_max_iter;
+  int32_t reserved;
+} eipc_params;
+
+/* Contact pair list, all device arrays owned by the caller.  Pair k is a point-triangle
+ * pair (type 0: i = vertex, j = triangle) or an edge-edge pair (type 1: i < j edge ids),
+ * with unsigned distance d[k].  Lists written by eipc_build_candidates are ordered by
+ * (type, i, j).  *count (device) receives the number of pairs found, which may exceed
+ * capacity (then only capacity entries are written and PAIR_OVERFLOW is raised). */
+typedef struct {
+  int64_t capacity;
+  int32_t* type;
+  int32_t* i;
+  int32_t* j;
+  double* d;
+  int64_t* count;
+} eipc_pairs;
+
+/* Lagged friction state (Sec. III-B), one entry per pair active at x^n, device arrays
+ * owned by the caller: v[4] the stencil's vertices, gamma[4] the closest-point weights
+ * (r = sum_a gamma_a x_a is the vector between the closest points), n[3] the contact
+ * normal r/|r| at x^n, anchor[3] = r at x^n and lambda = kappa |b'(d^n)| the lagged
+ * normal force magnitude.  u(x) is the part of sum_a gamma_a x_a - anchor orthogonal
+ * to n, and D = mu lambda f0(|u|). */
+typedef struct {
+  int64_t capacity;
+  int32_t* v;       /* [capacity,4] */
+  double* gamma;    /* [capacity,4] */
+  double* n;        /* [capacity,3] */
+  double* anchor;   /* [capacity,3] */
+  double* lambda;   /* [capacity]   */
+  int64_t* count;   /* [1]          */
+} eipc_lag;
+
+/* Reduced Hessian in 3x3-block CSR (BSR) form, full symmetric pattern, device arrays
+ * owned by the caller: row_ptr[Ns+1], col[capacity], val[capacity*9] (row-major 3x3),
+ * *nnzb (device) = number of blocks.  Columns are sorted within each row. */
+typedef struct {
+  int64_t capacity;
+  int32_t* row_ptr;
+  int32_t* col;
+  double* val;
+  int64_t* nnzb;
+} eipc_bsr;
+
+typedef struct eipc_scene eipc_scene;
+
+/* Creates a scene from HOST arrays (copied; the caller keeps ownership):
+ *   tris[F*3], edges[E*2] (a < b, unique) vertex ids in [0,Nv);
+ *   cage_idx[Nv*4], w[Nv*4]: containing-tet node ids and barycentric weights of each
+ *     embedded vertex (Sec. III-D); a row with cage_idx[4v] = -1 marks a kinematic vertex
+ *     whose position is x_kin[3v..3v+2] and which has no reduced DoF;
+ *   Ns: number of cage nodes (q has Ns*3 entries);
+ *   cand_capacity: broad-phase candidate buffer entries (<= 0: 48 per primitive);
+ *   rec_capacity: reduction record entries (<= 0: 2^25).
+ * Returns EIPC_ERR_INVALID for inconsistent sizes or out-of-range ids, EIPC_ERR_NOMEM
+ * if the device workspace cannot be allocated. */
+eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, const int32_t* tris,
+                              const int32_t* edges, const int32_t* cage_idx, const double* w,
+                              const double* x_kin, int64_t cand_capacity, int64_t rec_capacity,
+                              eipc_scene** out);
+void eipc_scene_destroy(eipc_scene* scene);
+
+/* x[Nv*3] = J q for q[Ns*3] (Sec. III-D, Eq. 12).  displacement != 0 maps a reduced
+ * displacement instead: kinematic rows are then 0 rather than x_kin. */
+eipc_status eipc_embed(eipc_scene* scene, const double* q, double* x, int32_t displacement,
+                       eipc_stream stream);
+
+/* Contact set B at x = J q (Sec. III-B): every PT and EE pair that is not incident
+ * (shares no vertex), is not made only of kinematic vertices, and has 0 < d < dhat,
+ * found by an LBVH broad phase and an exact FP64 distance test. */
+eipc_status eipc_build_candidates(eipc_scene* scene, const double* q, const eipc_params* p,
+                                  eipc_pairs* out, eipc_stream stream);
+
+/* Lagged friction state at x^n = J q_n for the pairs of pairs_n (Sec. III-B). */
+eipc_status eipc_friction_lag(eipc_scene* scene, const double* q_n, const eipc_pairs* pairs_n,
+                              const eipc_params* p, eipc_lag* out, eipc_stream stream);
+
+/* Contact potential at x = J q over the barrier pairs and (if lag != NULL and mu > 0)
+ * the lagged friction pairs: E (device scalar), g_r[Ns*3] and H_r (BSR).  Each pair's
+ * barrier Hessian is projected to the nearest PSD matrix before the reduction; friction
+ * Hessians are PSD as written.  Reduction is deterministic (bitwise repeatable). */
+eipc_status eipc_eval_contact(eipc_scene* scene, const double* q, const eipc_pairs* pairs,
+                              const eipc_lag* lag, const eipc_params* p, double* E, double* g_r,
+                              eipc_bsr* H_r, eipc_stream stream);
+
+/* Step bound for the straight motion x + t dx, t in [0,1] (x, dx: [Nv*3]): over every
+ * PT / EE pair (not incident, not all kinematic) whose closed swept boxes overlap,
+ * conservative advancement gives a collision-free t_k; alpha = min(1, min_k t_k),
+ * written to the device scalar *alpha and reduced by exact minimum.  *n_candidates
+ * (device, may be NULL) receives the number of pairs advanced. */
+eipc_status eipc_accd_toi(eipc_scene* scene, const double* x, const double* dx,
+                          const eipc_params* p, double* alpha, int64_t* n_candidates,
+                          eipc_stream stream);
+
+/* Synchronises the stream, copies the device status word and clears it.
+ * flags <- OR of EIPC_FLAG_*; needed[0..3] <- pairs, candidates, records, BSR blocks
+ * required by the last overflowing call (0 if none); accd_iters <- total CCD
+ * advancements since the last read.  Any pointer may be NULL. */
+eipc_status eipc_status_read(eipc_scene* scene, eipc_stream stream, int32_t* flags, int64_t* needed,
+                             int64_t* accd_iters);
+
+/* Tracing: per-kernel CUDA-event timers.  Bit k of mask enables timer k (0 embed,
+ * 1 bvh_build, 2 bvh_query, 3 narrow_phase, 4 pair_sort, 5 friction_lag, 6 stencil_nodes,
+ * 7 eval_barrier, 8 eval_friction, 9 hessian_reduce, 10 gradient_reduce, 11 energy_sum,
+ * 12 ccd_advance; eipc_kernel_name(k) names them): each launch is bracketed by two events on
+ * its stream.  eipc_timing_read synchronises, writes the summed milliseconds and launch
+ * counts of the first n timers and resets them. */
+eipc_status eipc_timing_enable(eipc_scene* scene, uint32_t mask);
+eipc_status eipc_timing_read(eipc_scene* scene, double* total_ms, int64_t* launches, int32_t n);
+const char* eipc_kernel_name(int32_t id);
+
+/* Number of kernel launches the library has enqueued in this process (all scenes). */
+int64_t eipc_launch_count(void);
+
+/* Library version string. */
+const char* eipc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMBIPC_H */

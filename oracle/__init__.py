@@ -68,6 +68,8 @@ def lib():
         L.orc_accd.restype = dbl
         L.orc_accd_list.argtypes = [i64, P, P, P, i64, P, P, i64, P, i64, P, dbl, ctypes.c_int, P]
         L.orc_accd_list.restype = dbl
+        L.orc_accd_of.argtypes = [i64, P, P, P, i64, P, i64, P, dbl, ctypes.c_int, ctypes.c_int, i64, P, P, P]
+        L.orc_accd_of.restype = dbl
         L.orc_intersection_free.argtypes = [i64, P, i64, P, i64, P]
         L.orc_intersection_free.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
@@ -246,6 +248,20 @@ def accd(scene, x: np.ndarray, dx: np.ndarray, s: Optional[float] = None, max_it
     a = lib().orc_accd(scene.Nv, _p(_f64(x)), _p(_f64(dx)), _p(_kin(scene)), scene.F, _p(_i32(scene.tris)),
                        scene.E, _p(_i32(scene.edges)), float(s), int(max_iter), _p(nc), _p(it), _p(cp))
     return dict(alpha=a, n_candidates=int(nc[0]), iters=int(it[0]), capped=bool(cp[0]))
+
+
+def accd_of(scene, x, dx, ptype: int, queries, s=None, max_iter=None):
+    """Step bound over the pairs having one of `queries` (vertices if ptype == 0, edges if
+    ptype == 1) as a side: a bounded sample of `accd`."""
+    p = scene.params
+    s = p["accd_s"] if s is None else s
+    max_iter = p["accd_max_iter"] if max_iter is None else max_iter
+    q = _i32(queries)
+    nc = np.zeros(1, np.int64); it = np.zeros(1, np.int64)
+    a = lib().orc_accd_of(scene.Nv, _p(_f64(x)), _p(_f64(dx)), _p(_kin(scene)), scene.F, _p(_i32(scene.tris)),
+                          scene.E, _p(_i32(scene.edges)), float(s), int(max_iter), int(ptype), len(q), _p(q),
+                          _p(nc), _p(it))
+    return dict(alpha=a, n_candidates=int(nc[0]), iters=int(it[0]))
 
 
 def accd_list(scene, x, dx, cand, s=None, max_iter=None):

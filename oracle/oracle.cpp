@@ -675,6 +675,52 @@ double orc_accd(int64_t nv, const double* x, const double* dx, const uint8_t* ki
   return alpha;
 }
 
+// Step bound restricted to the pairs that have one of the given query primitives as a
+// side (type 0: query vertices against all triangles; type 1: query edges against all
+// other edges) -- a bounded sample of orc_accd's work.
+double orc_accd_of(int64_t nv, const double* x, const double* dx, const uint8_t* kin, int64_t nf,
+                   const int32_t* tris, int64_t ne, const int32_t* edges, double s, int max_iter, int type,
+                   int64_t nq, const int32_t* queries, int64_t* n_candidates, int64_t* total_iters) {
+  std::vector<double> x1(3 * nv);
+  for (int64_t i = 0; i < 3 * nv; ++i) x1[i] = x[i] + dx[i];
+  Mesh m0{nv, nf, ne, x, tris, edges, kin};
+  Mesh m1{nv, nf, ne, x1.data(), tris, edges, kin};
+  auto swept = [&](int t, int64_t i, bool side_a) {
+    Box a = prim_box(m0, t, i, side_a, x), b = prim_box(m1, t, i, side_a, x1.data());
+    for (int k = 0; k < 3; ++k) { a.lo[k] = std::min(a.lo[k], b.lo[k]); a.hi[k] = std::max(a.hi[k], b.hi[k]); }
+    return a;
+  };
+  int64_t nb = type == 0 ? nf : ne;
+  std::vector<Box> other(nb);
+  for (int64_t b = 0; b < nb; ++b) other[b] = swept(type, b, type == 1);
+  double alpha = 1.0;
+  int64_t ncand = 0, iters = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : alpha) reduction(+ : ncand, iters)
+  for (int64_t qi = 0; qi < nq; ++qi) {
+    int64_t a = queries[qi];
+    Box ba = swept(type, a, true);
+    for (int64_t b = 0; b < nb; ++b) {
+      if (type == 1 && b == a) continue;
+      if (!overlap(ba, other[b], 0.0)) continue;
+      int64_t i = a, j = b;
+      if (type == 1 && j < i) std::swap(i, j);
+      int32_t st[4];
+      stencil(m0, type, i, j, st);
+      if (incident(type, st) || all_kinematic(m0, st)) continue;
+      double x4[12], dx4[12];
+      gather4(x, st, x4);
+      gather4(dx, st, dx4);
+      int n; bool c;
+      double t = ca_pair(type, x4, dx4, s, max_iter, &n, &c);
+      ++ncand; iters += n;
+      if (t < alpha) alpha = t;
+    }
+  }
+  if (n_candidates) *n_candidates = ncand;
+  if (total_iters) *total_iters = iters;
+  return alpha;
+}
+
 // Step bound over a given candidate list (the CPU-baseline stage timing feeds the same
 // candidates the GPU found); returns alpha and accumulates iterations.
 double orc_accd_list(int64_t nc, const int32_t* type, const int32_t* pi, const int32_t* pj,

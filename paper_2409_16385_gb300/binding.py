@@ -1,0 +1,324 @@
+"""ctypes binding of libembipc.so (include/embipc.h): argument marshalling only.
+
+Device memory comes from torch CUDA tensors and every call is enqueued on torch's current
+CUDA stream; all arithmetic runs in the library's kernels.  Importing works without a GPU;
+constructing a `ContactScene` requires the compiled library and a CUDA device and raises
+otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+EIPC_OK = 0
+FLAGS = {1: "PENETRATION", 2: "PAIR_OVERFLOW", 4: "CAND_OVERFLOW", 8: "REC_OVERFLOW", 16: "BSR_OVERFLOW",
+         32: "NONFINITE", 64: "ACCD_CAP", 128: "LAG_OVERFLOW", 256: "STACK_OVERFLOW"}
+EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_candidates", "eipc_friction_lag",
+           "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
+                ("eps_v", ctypes.c_double), ("h", ctypes.c_double), ("accd_s", ctypes.c_double),
+                ("accd_max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Pairs(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("type", ctypes.c_void_p), ("i", ctypes.c_void_p),
+                ("j", ctypes.c_void_p), ("d", ctypes.c_void_p), ("count", ctypes.c_void_p)]
+
+
+class _Lag(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("v", ctypes.c_void_p), ("gamma", ctypes.c_void_p),
+                ("n", ctypes.c_void_p), ("anchor", ctypes.c_void_p), ("lam", ctypes.c_void_p),
+                ("count", ctypes.c_void_p)]
+
+
+class _Bsr(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("nnzb", ctypes.c_void_p)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libembipc.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libembipc.so is not built ({_build.LIB}); run paper_2409_16385_gb300.build.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    L.eipc_scene_create.argtypes = [i64, i64, i64, i64, P, P, P, P, P, i64, i64, ctypes.POINTER(P)]
+    L.eipc_scene_create.restype = i32
+    L.eipc_scene_destroy.argtypes = [P]
+    L.eipc_embed.argtypes = [P, P, P, i32, P]
+    L.eipc_embed.restype = i32
+    L.eipc_build_candidates.argtypes = [P, P, ctypes.POINTER(Params), ctypes.POINTER(_Pairs), P]
+    L.eipc_build_candidates.restype = i32
+    L.eipc_friction_lag.argtypes = [P, P, ctypes.POINTER(_Pairs), ctypes.POINTER(Params), ctypes.POINTER(_Lag), P]
+    L.eipc_friction_lag.restype = i32
+    L.eipc_eval_contact.argtypes = [P, P, ctypes.POINTER(_Pairs), ctypes.POINTER(_Lag), ctypes.POINTER(Params), P, P,
+                                    ctypes.POINTER(_Bsr), P]
+    L.eipc_eval_contact.restype = i32
+    L.eipc_accd_toi.argtypes = [P, P, P, ctypes.POINTER(Params), P, P, P]
+    L.eipc_accd_toi.restype = i32
+    L.eipc_status_read.argtypes = [P, P, ctypes.POINTER(i32), P, P]
+    L.eipc_status_read.restype = i32
+    L.eipc_version.restype = ctypes.c_char_p
+    L.eipc_timing_enable.argtypes = [P, ctypes.c_uint32]
+    L.eipc_timing_enable.restype = i32
+    L.eipc_timing_read.argtypes = [P, P, P, i32]
+    L.eipc_timing_read.restype = i32
+    L.eipc_kernel_name.argtypes = [i32]
+    L.eipc_kernel_name.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != EIPC_OK:
+        raise RuntimeError(f"{what} failed with status {rc}")
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def make_params(p: dict) -> Params:
+    return Params(float(p["dhat"]), float(p["kappa"]), float(p.get("mu", 0.0)), float(p.get("eps_v", 1e-3)),
+                  float(p.get("h", 1e-2)), float(p.get("accd_s", 0.1)), int(p.get("accd_max_iter", 10000)), 0)
+
+
+@dataclass
+class PairList:
+    type: "object"
+    i: "object"
+    j: "object"
+    d: "object"
+    count: "object"   # int64[1] device
+
+    def n(self) -> int:
+        return int(self.count.item())
+
+    def host(self):
+        n = min(self.n(), self.type.shape[0])
+        return dict(type=self.type[:n].cpu().numpy(), i=self.i[:n].cpu().numpy(), j=self.j[:n].cpu().numpy(),
+                    d=self.d[:n].cpu().numpy())
+
+    def _c(self) -> _Pairs:
+        return _Pairs(self.type.shape[0], _ptr(self.type), _ptr(self.i), _ptr(self.j), _ptr(self.d), _ptr(self.count))
+
+
+@dataclass
+class LagState:
+    v: "object"
+    gamma: "object"
+    n: "object"
+    anchor: "object"
+    lam: "object"
+    count: "object"
+
+    def host(self):
+        k = min(int(self.count.item()), self.v.shape[0])
+        return dict(v=self.v[:k].cpu().numpy(), gamma=self.gamma[:k].cpu().numpy(), n=self.n[:k].cpu().numpy(),
+                    anchor=self.anchor[:k].cpu().numpy(), lam=self.lam[:k].cpu().numpy())
+
+    def _c(self) -> _Lag:
+        return _Lag(self.v.shape[0], _ptr(self.v), _ptr(self.gamma), _ptr(self.n), _ptr(self.anchor), _ptr(self.lam),
+                    _ptr(self.count))
+
+
+@dataclass
+class BSR:
+    row_ptr: "object"
+    col: "object"
+    val: "object"
+    nnzb: "object"
+
+    def host(self):
+        k = min(int(self.nnzb.item()), self.col.shape[0])
+        return dict(row_ptr=self.row_ptr.cpu().numpy(), col=self.col[:k].cpu().numpy(),
+                    val=self.val[:k].cpu().numpy().reshape(-1, 3, 3))
+
+    def _c(self) -> _Bsr:
+        return _Bsr(self.col.shape[0], _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), _ptr(self.nnzb))
+
+
+class ContactScene:
+    """One scene on the device: topology + embedding copied at creation, workspace sized
+    once.  Methods map 1:1 to the C ABI calls and enqueue on torch's current stream."""
+
+    def __init__(self, scene, pair_capacity: int = 1 << 20, bsr_capacity: int = 1 << 22,
+                 cand_capacity: int = 0, rec_capacity: int = 0, device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ContactScene needs a CUDA device: the contact stage has no CPU path")
+        self.lib = load()
+        self.device = torch.device(device)
+        self.scene = scene
+        self.params = make_params(scene.params)
+        h = ctypes.c_void_p()
+        tris = np.ascontiguousarray(scene.tris, np.int32)
+        edges = np.ascontiguousarray(scene.edges, np.int32)
+        idx = np.ascontiguousarray(scene.cage_idx, np.int32)
+        w = np.ascontiguousarray(scene.w, np.float64)
+        xk = np.ascontiguousarray(scene.x_kin, np.float64)
+        rc = self.lib.eipc_scene_create(scene.Nv, scene.F, scene.E, scene.Ns, tris.ctypes.data, edges.ctypes.data,
+                                        idx.ctypes.data, w.ctypes.data, xk.ctypes.data, int(cand_capacity),
+                                        int(rec_capacity), ctypes.byref(h))
+        _check(rc, "eipc_scene_create")
+        self.handle = h
+        self.Ns, self.Nv = scene.Ns, scene.Nv
+        self.pair_capacity = int(pair_capacity)
+        self.bsr_capacity = int(bsr_capacity)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.eipc_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- buffers
+    def new_pairs(self, capacity: Optional[int] = None) -> PairList:
+        import torch
+        c = self.pair_capacity if capacity is None else int(capacity)
+        dev = self.device
+        return PairList(torch.empty(c, dtype=torch.int32, device=dev), torch.empty(c, dtype=torch.int32, device=dev),
+                        torch.empty(c, dtype=torch.int32, device=dev), torch.empty(c, dtype=torch.float64, device=dev),
+                        torch.zeros(1, dtype=torch.int64, device=dev))
+
+    def new_lag(self, capacity: Optional[int] = None) -> LagState:
+        import torch
+        c = self.pair_capacity if capacity is None else int(capacity)
+        dev = self.device
+        return LagState(torch.empty((c, 4), dtype=torch.int32, device=dev), torch.empty((c, 4), dtype=torch.float64, device=dev),
+                        torch.empty((c, 3), dtype=torch.float64, device=dev), torch.empty((c, 3), dtype=torch.float64, device=dev),
+                        torch.empty(c, dtype=torch.float64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+
+    def new_bsr(self, capacity: Optional[int] = None) -> BSR:
+        import torch
+        c = self.bsr_capacity if capacity is None else int(capacity)
+        dev = self.device
+        return BSR(torch.zeros(self.Ns + 1, dtype=torch.int32, device=dev), torch.empty(c, dtype=torch.int32, device=dev),
+                   torch.empty((c, 9), dtype=torch.float64, device=dev), torch.zeros(1, dtype=torch.int64, device=dev))
+
+    # -- calls
+    def embed(self, q, out=None, displacement: bool = False):
+        import torch
+        x = out if out is not None else torch.empty((self.Nv, 3), dtype=torch.float64, device=self.device)
+        _check(self.lib.eipc_embed(self.handle, _ptr(q), _ptr(x), 1 if displacement else 0, _stream()), "eipc_embed")
+        return x
+
+    def build_candidates(self, q, out: Optional[PairList] = None) -> PairList:
+        pr = out if out is not None else self.new_pairs()
+        c = pr._c()
+        _check(self.lib.eipc_build_candidates(self.handle, _ptr(q), ctypes.byref(self.params), ctypes.byref(c), _stream()),
+               "eipc_build_candidates")
+        return pr
+
+    def friction_lag(self, q_n, pairs_n: PairList, out: Optional[LagState] = None) -> LagState:
+        lag = out if out is not None else self.new_lag()
+        pc, lc = pairs_n._c(), lag._c()
+        _check(self.lib.eipc_friction_lag(self.handle, _ptr(q_n), ctypes.byref(pc), ctypes.byref(self.params),
+                                          ctypes.byref(lc), _stream()), "eipc_friction_lag")
+        return lag
+
+    def eval_contact(self, q, pairs: PairList, lag: Optional[LagState] = None, E=None, g_r=None, H: Optional[BSR] = None):
+        import torch
+        E = E if E is not None else torch.zeros(1, dtype=torch.float64, device=self.device)
+        g_r = g_r if g_r is not None else torch.zeros((self.Ns, 3), dtype=torch.float64, device=self.device)
+        H = H if H is not None else self.new_bsr()
+        pc, hc = pairs._c(), H._c()
+        lp = ctypes.byref(lag._c()) if lag is not None else None
+        _check(self.lib.eipc_eval_contact(self.handle, _ptr(q), ctypes.byref(pc), lp, ctypes.byref(self.params), _ptr(E),
+                                          _ptr(g_r), ctypes.byref(hc), _stream()), "eipc_eval_contact")
+        return E, g_r, H
+
+    def accd_toi(self, x, dx, alpha=None, n_candidates=None):
+        import torch
+        alpha = alpha if alpha is not None else torch.zeros(1, dtype=torch.float64, device=self.device)
+        nc = _ptr(n_candidates) if n_candidates is not None else None
+        _check(self.lib.eipc_accd_toi(self.handle, _ptr(x), _ptr(dx), ctypes.byref(self.params), _ptr(alpha), nc,
+                                      _stream()), "eipc_accd_toi")
+        return alpha
+
+    N_TIMERS = 13
+
+    def timing_enable(self, names=None):
+        """Brackets every launch of the named kernels (all if None, none if []) with CUDA
+        events on the launching stream."""
+        mask = 0
+        for k in range(self.N_TIMERS):
+            if names is None or self.lib.eipc_kernel_name(k).decode() in names:
+                mask |= 1 << k
+        _check(self.lib.eipc_timing_enable(self.handle, mask), "eipc_timing_enable")
+
+    def timing_read(self) -> dict:
+        ms = np.zeros(self.N_TIMERS)
+        n = np.zeros(self.N_TIMERS, np.int64)
+        _check(self.lib.eipc_timing_read(self.handle, ms.ctypes.data, n.ctypes.data, self.N_TIMERS), "eipc_timing_read")
+        return {self.lib.eipc_kernel_name(k).decode(): (float(ms[k]), int(n[k])) for k in range(self.N_TIMERS) if n[k]}
+
+    def status(self) -> dict:
+        flags = ctypes.c_int32(0)
+        need = np.zeros(4, np.int64)
+        it = np.zeros(1, np.int64)
+        _check(self.lib.eipc_status_read(self.handle, _stream(), ctypes.byref(flags), need.ctypes.data, it.ctypes.data),
+               "eipc_status_read")
+        names = [n for b, n in FLAGS.items() if flags.value & b]
+        return dict(flags=int(flags.value), names=names, needed=need.tolist(), accd_iters=int(it[0]))
+
+
+# -------------------------------------------------------------- functional front end
+_scene_cache: dict = {}
+
+
+def _scene_for(scene) -> ContactScene:
+    key = id(scene)
+    cs = _scene_cache.get(key)
+    if cs is None or cs.scene is not scene:
+        cs = ContactScene(scene)
+        _scene_cache[key] = cs
+    return cs
+
+
+def build_candidates(scene, q):
+    """Contact pairs of `scene` at reduced coordinates q (torch CUDA f64 [Ns,3])."""
+    return _scene_for(scene).build_candidates(q)
+
+
+def eval_contact(q, scene, lag=None, pairs=None):
+    """(E, g_r, H_r) at reduced coordinates q.  `scene` carries W (cage_idx, w), the
+    surface (tris, edges) and dhat, kappa, mu in scene.params."""
+    cs = _scene_for(scene)
+    pr = pairs if pairs is not None else cs.build_candidates(q)
+    return cs.eval_contact(q, pr, lag)
+
+
+def accd_toi(scene, x, dx):
+    """Step bound alpha for the full-space motion x + t dx (torch CUDA f64 [Nv,3])."""
+    return _scene_for(scene).accd_toi(x, dx)

@@ -1,0 +1,270 @@
+// C ABI entry points (include/embipc.h): argument checks, scene creation and workspace
+// sizing, and the enqueueing of each call's kernels on the caller's stream.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "scene.cuh"
+#include "sort.cuh"
+
+using namespace eipc;
+
+namespace {
+
+template <class T>
+cudaError_t dalloc(T** p, int64_t n) {
+  if (n < 1) n = 1;
+  return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)n);
+}
+
+void free_scene(eipc_scene* s) {
+  if (!s) return;
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->x4, s->dx4,
+                  s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim,
+                  s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
+                  s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes,
+                  s->edge_bvh.parent, s->edge_bvh.leaf_prim, s->edge_bvh.leaf_box, s->edge_bvh.refit_flag,
+                  s->edge_bvh.keys, s->edge_bvh.vals, s->edge_bvh.keys_alt, s->edge_bvh.vals_alt, s->bounds_ws,
+                  s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
+                  s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
+                  s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start,
+                  s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec, s->gseg_flag, s->gseg_id,
+                  s->gseg_start, s->row_count, s->scan_partial, s->sum_partial, s->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->timers) {
+    s->timers->destroy();
+    delete s->timers;
+  }
+  delete s;
+}
+
+cudaError_t alloc_bvh(Bvh& t, int64_t n) {
+  t.n = n;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+  ok(dalloc(&t.n_dev, 1));
+  ok(dalloc(&t.nodes, n > 1 ? n - 1 : 1));
+  ok(dalloc(&t.parent, 2 * n));
+  ok(dalloc(&t.leaf_prim, n));
+  ok(dalloc(&t.leaf_box, 6 * n));
+  ok(dalloc(&t.refit_flag, n));
+  ok(dalloc(&t.keys, n));
+  ok(dalloc(&t.vals, n));
+  ok(dalloc(&t.keys_alt, n));
+  ok(dalloc(&t.vals_alt, n));
+  if (e == cudaSuccess) e = cudaMemcpy(t.n_dev, &n, sizeof(int64_t), cudaMemcpyHostToDevice);
+  return e;
+}
+
+bool params_ok(const eipc_params* p) {
+  return p && p->dhat > 0.0 && p->kappa > 0.0 && p->mu >= 0.0 && p->eps_v > 0.0 && p->h > 0.0 && p->accd_s > 0.0 &&
+         p->accd_s < 1.0 && p->accd_max_iter > 0;
+}
+
+bool pairs_ok(const eipc_pairs* p) {
+  return p && p->capacity >= 0 && p->capacity < (1ll << 31) && p->count &&
+         (p->capacity == 0 || (p->type && p->i && p->j && p->d));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* eipc_version(void) { return "embipc 0.1 (sm_103a)"; }
+
+eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, const int32_t* tris,
+                              const int32_t* edges, const int32_t* cage_idx, const double* w, const double* x_kin,
+                              int64_t cand_capacity, int64_t rec_capacity, eipc_scene** out) {
+  if (!out) return EIPC_ERR_INVALID;
+  *out = nullptr;
+  if (Nv <= 0 || F < 0 || E < 0 || Ns < 0 || Nv >= (1ll << 30) || F >= (1ll << 30) || E >= (1ll << 30) ||
+      Ns >= (1ll << 24))
+    return EIPC_ERR_INVALID;
+  if ((F > 0 && !tris) || (E > 0 && !edges) || !cage_idx || !w || !x_kin) return EIPC_ERR_INVALID;
+  // host-side validation of ids
+  for (int64_t k = 0; k < 3 * F; ++k)
+    if (tris[k] < 0 || tris[k] >= Nv) return EIPC_ERR_INVALID;
+  for (int64_t k = 0; k < E; ++k)
+    if (edges[2 * k] < 0 || edges[2 * k] >= Nv || edges[2 * k + 1] < 0 || edges[2 * k + 1] >= Nv ||
+        edges[2 * k] >= edges[2 * k + 1])
+      return EIPC_ERR_INVALID;
+  std::vector<uint8_t> vkin(Nv), ekin(E > 0 ? E : 1), fkin(F > 0 ? F : 1);
+  for (int64_t v = 0; v < Nv; ++v) {
+    bool kin = cage_idx[4 * v] < 0;
+    vkin[v] = kin;
+    for (int s = 0; s < 4; ++s) {
+      int32_t id = cage_idx[4 * v + s];
+      if (kin ? (id != -1) : (id < 0 || id >= Ns)) return EIPC_ERR_INVALID;
+    }
+  }
+  for (int64_t e = 0; e < E; ++e) ekin[e] = vkin[edges[2 * e]] && vkin[edges[2 * e + 1]];
+  for (int64_t f = 0; f < F; ++f) fkin[f] = vkin[tris[3 * f]] && vkin[tris[3 * f + 1]] && vkin[tris[3 * f + 2]];
+  std::vector<double> xk4(4 * Nv, 0.0);
+  for (int64_t v = 0; v < Nv; ++v)
+    for (int k = 0; k < 3; ++k) xk4[4 * v + k] = vkin[v] ? x_kin[3 * v + k] : 0.0;
+
+  auto* s = new eipc_scene;
+  std::memset(s, 0, sizeof(eipc_scene));
+  s->timers = new Timers();
+  s->nv = Nv; s->nf = F; s->ne = E; s->ns = Ns;
+  if (cand_capacity <= 0) cand_capacity = 48 * (Nv + E);
+  if (cand_capacity >= (1ll << 31)) cand_capacity = (1ll << 31) - 1;
+  if (rec_capacity <= 0) rec_capacity = 1ll << 25;
+  if (rec_capacity >= (1ll << 31)) rec_capacity = (1ll << 31) - 1;
+  s->cand_cap = cand_capacity;
+  s->item_cap = cand_capacity;
+  s->rec_cap = rec_capacity;
+  s->gcap = rec_capacity;
+  cudaError_t e = cudaSuccess;
+  auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+  ok(dalloc(&s->tris, 3 * F)); ok(dalloc(&s->edges, 2 * E)); ok(dalloc(&s->cage_idx, 4 * Nv));
+  ok(dalloc(&s->w, 4 * Nv)); ok(dalloc(&s->x_kin4, 4 * Nv));
+  ok(dalloc(&s->vkin, Nv)); ok(dalloc(&s->ekin, E)); ok(dalloc(&s->fkin, F));
+  ok(dalloc(&s->x4, 4 * Nv)); ok(dalloc(&s->dx4, 4 * Nv));
+  ok(alloc_bvh(s->tri_bvh, F));
+  ok(alloc_bvh(s->edge_bvh, E));
+  ok(dalloc(&s->bounds_ws, 8));
+  ok(dalloc(&s->sort_hist, (int64_t)sort_hist_entries()));
+  ok(dalloc(&s->cand, s->cand_cap));
+  ok(dalloc(&s->counters, kCntN));
+  ok(dalloc(&s->skeys, s->cand_cap)); ok(dalloc(&s->skeys_alt, s->cand_cap));
+  ok(dalloc(&s->svals, s->cand_cap)); ok(dalloc(&s->svals_alt, s->cand_cap)); ok(dalloc(&s->sd, s->cand_cap));
+  ok(dalloc(&s->item_nodes, 16 * s->item_cap)); ok(dalloc(&s->item_n, s->item_cap));
+  ok(dalloc(&s->rc_h, s->item_cap)); ok(dalloc(&s->ro_h, s->item_cap));
+  ok(dalloc(&s->rc_g, s->item_cap)); ok(dalloc(&s->ro_g, s->item_cap)); ok(dalloc(&s->item_E, s->item_cap));
+  ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
+  ok(dalloc(&s->hvals, s->rec_cap)); ok(dalloc(&s->hvals_alt, s->rec_cap)); ok(dalloc(&s->hrec, 9 * s->rec_cap));
+  ok(dalloc(&s->seg_flag, s->rec_cap)); ok(dalloc(&s->seg_id, s->rec_cap)); ok(dalloc(&s->seg_start, s->rec_cap));
+  ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
+  ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, 3 * s->gcap));
+  ok(dalloc(&s->gseg_flag, s->gcap)); ok(dalloc(&s->gseg_id, s->gcap)); ok(dalloc(&s->gseg_start, s->gcap));
+  ok(dalloc(&s->row_count, Ns + 1));
+  ok(dalloc(&s->scan_partial, kScanBlocks + 1)); ok(dalloc(&s->sum_partial, kScanBlocks));
+  ok(dalloc(&s->status, 1));
+  if (e != cudaSuccess) {
+    free_scene(s);
+    cudaGetLastError();
+    return EIPC_ERR_NOMEM;
+  }
+  ok(cudaMemcpy(s->tris, tris, sizeof(int32_t) * 3 * F, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->edges, edges, sizeof(int32_t) * 2 * E, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->cage_idx, cage_idx, sizeof(int32_t) * 4 * Nv, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->w, w, sizeof(double) * 4 * Nv, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->x_kin4, xk4.data(), sizeof(double) * 4 * Nv, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->vkin, vkin.data(), Nv, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->ekin, ekin.data(), E, cudaMemcpyHostToDevice));
+  ok(cudaMemcpy(s->fkin, fkin.data(), F, cudaMemcpyHostToDevice));
+  ok(cudaMemset(s->counters, 0, sizeof(int64_t) * kCntN));
+  ok(cudaMemset(s->status, 0, sizeof(DevStatus)));
+  ok(cudaMemset(s->x4, 0, sizeof(double) * 4 * Nv));
+  ok(cudaMemset(s->dx4, 0, sizeof(double) * 4 * Nv));
+  if (e != cudaSuccess) {
+    free_scene(s);
+    cudaGetLastError();
+    return EIPC_ERR_CUDA;
+  }
+  Topo& T = s->topo;
+  T.nv = Nv; T.ne = E; T.nf = F;
+  T.tris = s->tris; T.edges = s->edges; T.vkin = s->vkin; T.ekin = s->ekin; T.fkin = s->fkin;
+  T.bits_i = bits_for((uint64_t)(Nv > E ? Nv : E));
+  T.bits_j = bits_for((uint64_t)(F > E ? F : E));
+  s->bits_h = bits_for((uint64_t)Ns * (uint64_t)Ns);
+  s->bits_g = bits_for((uint64_t)Ns);
+  *out = s;
+  return EIPC_OK;
+}
+
+void eipc_scene_destroy(eipc_scene* scene) {
+  if (!scene) return;
+  cudaDeviceSynchronize();
+  free_scene(scene);
+}
+
+eipc_status eipc_embed(eipc_scene* sc, const double* q, double* x, int32_t displacement, eipc_stream stream) {
+  if (!sc || (!q && sc->ns > 0) || !x) return EIPC_ERR_INVALID;
+  embed_launch(sc, q, x, 0, displacement, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_build_candidates(eipc_scene* sc, const double* q, const eipc_params* p, eipc_pairs* out,
+                                  eipc_stream stream) {
+  if (!sc || (!q && sc->ns > 0) || !params_ok(p) || !pairs_ok(out)) return EIPC_ERR_INVALID;
+  pairs_launch(sc, q, *p, *out, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_friction_lag(eipc_scene* sc, const double* q_n, const eipc_pairs* pairs_n, const eipc_params* p,
+                              eipc_lag* out, eipc_stream stream) {
+  if (!sc || (!q_n && sc->ns > 0) || !params_ok(p) || !pairs_ok(pairs_n) || !out || !out->count ||
+      out->capacity < 0 || (out->capacity > 0 && (!out->v || !out->gamma || !out->n || !out->anchor || !out->lambda)))
+    return EIPC_ERR_INVALID;
+  lag_launch(sc, q_n, *pairs_n, *p, *out, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_eval_contact(eipc_scene* sc, const double* q, const eipc_pairs* pairs, const eipc_lag* lag,
+                              const eipc_params* p, double* E, double* g_r, eipc_bsr* H, eipc_stream stream) {
+  if (!sc || (!q && sc->ns > 0) || !params_ok(p) || !pairs_ok(pairs) || !E || !g_r || !H || !H->row_ptr ||
+      !H->nnzb || H->capacity < 0 || (H->capacity > 0 && (!H->col || !H->val)))
+    return EIPC_ERR_INVALID;
+  if (lag && (!lag->count || lag->capacity < 0 || (lag->capacity > 0 && (!lag->v || !lag->gamma || !lag->n ||
+                                                                          !lag->anchor || !lag->lambda))))
+    return EIPC_ERR_INVALID;
+  eval_launch(sc, q, *pairs, lag, *p, E, g_r, *H, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_accd_toi(eipc_scene* sc, const double* x, const double* dx, const eipc_params* p, double* alpha,
+                          int64_t* n_candidates, eipc_stream stream) {
+  if (!sc || !x || !dx || !params_ok(p) || !alpha) return EIPC_ERR_INVALID;
+  accd_launch(sc, x, dx, *p, alpha, n_candidates, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_status_read(eipc_scene* sc, eipc_stream stream, int32_t* flags, int64_t* needed,
+                             int64_t* accd_iters) {
+  if (!sc) return EIPC_ERR_INVALID;
+  DevStatus h;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&h, sc->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return EIPC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return EIPC_ERR_CUDA;
+  if (cudaMemsetAsync(sc->status, 0, sizeof(DevStatus), s) != cudaSuccess) return EIPC_ERR_CUDA;
+  if (flags) *flags = h.flags;
+  if (needed) {
+    needed[0] = h.need_pairs; needed[1] = h.need_cand; needed[2] = h.need_rec; needed[3] = h.need_bsr;
+  }
+  if (accd_iters) *accd_iters = (int64_t)h.accd_iters;
+  return EIPC_OK;
+}
+
+eipc_status eipc_timing_enable(eipc_scene* sc, uint32_t mask) {
+  if (!sc) return EIPC_ERR_INVALID;
+  if (mask) sc->timers->create();
+  sc->timers->mask = mask;
+  return EIPC_OK;
+}
+
+eipc_status eipc_timing_read(eipc_scene* sc, double* total_ms, int64_t* launches, int32_t n) {
+  if (!sc || n < 0 || (n > 0 && (!total_ms || !launches))) return EIPC_ERR_INVALID;
+  for (int k = 0; k < kKNum; ++k) sc->timers->drain(k);
+  for (int k = 0; k < n && k < kKNum; ++k) {
+    total_ms[k] = sc->timers->total_ms[k];
+    launches[k] = sc->timers->launches[k];
+    sc->timers->total_ms[k] = 0.0;
+    sc->timers->launches[k] = 0;
+  }
+  return EIPC_OK;
+}
+
+int64_t eipc_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char* eipc_kernel_name(int32_t id) {
+  static const char* names[kKNum] = {"embed", "bvh_build", "bvh_query", "narrow_phase", "pair_sort", "friction_lag",
+                                     "stencil_nodes", "eval_barrier", "eval_friction", "hessian_reduce",
+                                     "gradient_reduce", "energy_sum", "ccd_advance"};
+  return (id >= 0 && id < kKNum) ? names[id] : "";
+}
+
+}  // extern "C"

@@ -1,0 +1,314 @@
+// LBVH build (Morton sort, Karras hierarchy, bottom-up refit) and traversal.
+#include "bvh.cuh"
+#include "sort.cuh"
+
+namespace eipc {
+namespace {
+
+// order-preserving map float -> int for atomic min / max
+__device__ __forceinline__ int32_t f2ord(float f) {
+  int32_t i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float ord2f(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+__global__ void k_bounds_init(int32_t* b) {
+  if (threadIdx.x < 3) b[threadIdx.x] = 0x7fffffff;
+  else if (threadIdx.x < 6) b[threadIdx.x] = (int32_t)0x80000000;
+}
+
+// scene box over all vertex positions (and their swept ends)
+__global__ void __launch_bounds__(kBlock) k_bounds(const double* __restrict__ x4, const double* __restrict__ dx4,
+                                                   int64_t nv, int32_t* __restrict__ b) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
+    V3 p = load_x(x4, (int32_t)v);
+    double c[3] = {p.x, p.y, p.z};
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], __double2float_rd(c[k]));
+      hi[k] = fmaxf(hi[k], __double2float_ru(c[k]));
+    }
+    if (dx4) {
+      V3 d = load_x(dx4, (int32_t)v);
+      double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(lo[k], __double2float_rd(e[k]));
+        hi[k] = fmaxf(hi[k], __double2float_ru(e[k]));
+      }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&b[k], f2ord(lo[k]));
+      atomicMax(&b[3 + k], f2ord(hi[k]));
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// FP32 box of one primitive from FP64 positions, rounded outward; swept over x + dx if
+// dx4 != null; grown by pad (FP64, before rounding).
+__device__ __forceinline__ void prim_box(PrimKind kind, int64_t i, const Topo& T, const double* x4,
+                                         const double* dx4, double pad, float lo[3], float hi[3]) {
+  int32_t v[3];
+  int nvx;
+  if (kind == kVertex) { v[0] = (int32_t)i; nvx = 1; }
+  else if (kind == kEdge) { v[0] = T.edges[2 * i]; v[1] = T.edges[2 * i + 1]; nvx = 2; }
+  else { v[0] = T.tris[3 * i]; v[1] = T.tris[3 * i + 1]; v[2] = T.tris[3 * i + 2]; nvx = 3; }
+  double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int a = 0; a < nvx; ++a) {
+    V3 p = load_x(x4, v[a]);
+    double c[3] = {p.x, p.y, p.z};
+    for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
+    if (dx4) {
+      V3 d = load_x(dx4, v[a]);
+      double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
+      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = __double2float_rd(__dsub_rd(dlo[k], pad));
+    hi[k] = __double2float_ru(__dadd_ru(dhi[k], pad));
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Topo T, const double* __restrict__ x4,
+                                                   const double* __restrict__ dx4, const int32_t* __restrict__ b,
+                                                   float* __restrict__ leaf_box, uint64_t* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals) {
+  float blo[3], bext[3];
+  for (int k = 0; k < 3; ++k) {
+    blo[k] = ord2f(b[k]);
+    float e = ord2f(b[3 + k]) - blo[k];
+    bext[k] = e > 0.f ? e : 1.f;
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride()) {
+    float lo[3], hi[3];
+    prim_box(kind, i, T, x4, dx4, 0.0, lo, hi);
+    uint32_t code = 0;
+    for (int k = 0; k < 3; ++k) {
+      float c = (0.5f * (lo[k] + hi[k]) - blo[k]) / bext[k];
+      c = fminf(fmaxf(c, 0.f), 1.f);
+      uint32_t q = (uint32_t)fminf(c * 1024.f, 1023.f);
+      code |= spread10(q) << (2 - k);
+    }
+    for (int k = 0; k < 3; ++k) { leaf_box[6 * i + k] = lo[k]; leaf_box[6 * i + 3 + k] = hi[k]; }
+    keys[i] = code;
+    vals[i] = (uint32_t)i;
+  }
+}
+
+__device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = k[i], b = k[j];
+  if (a == b) return 64 + __clzll((unsigned long long)(i ^ j));
+  return __clzll((unsigned long long)(a ^ b));
+}
+
+// Karras 2012: internal node i covers a key range; its split is the highest differing bit.
+__global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict__ keys, int64_t n,
+                                                     BvhNode* __restrict__ nodes, int32_t* __restrict__ parent) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1; i += grid_stride()) {
+    int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(keys, n, i, i - dir);
+    int64_t lmax = 2;
+    while (delta(keys, n, i, i + lmax * dir) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+      if (delta(keys, n, i, i + (l + t) * dir) > dmin) l += t;
+    int64_t j = i + l * dir;
+    int dnode = delta(keys, n, i, j);
+    int64_t s = 0;
+    for (int64_t div = 2;; div *= 2) {
+      int64_t t = (l + div - 1) / div;
+      if (delta(keys, n, i, i + (s + t) * dir) > dnode) s += t;
+      if (t == 1) break;
+    }
+    int64_t gamma = i + s * dir + (dir < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int32_t c0 = (lo == gamma) ? ~(int32_t)gamma : (int32_t)gamma;
+    int32_t c1 = (hi == gamma + 1) ? ~(int32_t)(gamma + 1) : (int32_t)(gamma + 1);
+    nodes[i].c0 = c0;
+    nodes[i].c1 = c1;
+    parent[c0 >= 0 ? c0 : (n - 1 + ~c0)] = (int32_t)i;
+    parent[c1 >= 0 ? c1 : (n - 1 + ~c1)] = (int32_t)i;
+  }
+}
+
+__device__ __forceinline__ uint8_t prim_kin(PrimKind kind, const Topo& T, int64_t p) {
+  return kind == kTri ? T.fkin[p] : (kind == kEdge ? T.ekin[p] : T.vkin[p]);
+}
+
+__device__ __forceinline__ void write_child(BvhNode* nd, int slot, const float lo[3], const float hi[3], int kin) {
+  float* l = slot ? nd->lo1 : nd->lo0;
+  float* h = slot ? nd->hi1 : nd->hi0;
+  for (int k = 0; k < 3; ++k) { __stcg(&l[k], lo[k]); __stcg(&h[k], hi[k]); }
+  if (kin) atomicOr(&nd->kin, 1 << slot);
+}
+
+// Bottom-up refit: the second child to finish a node unions both child boxes and
+// carries on upward; the first one stops.  No thread ever waits on another.
+__global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo T, const uint32_t* __restrict__ sorted,
+                                                  const float* __restrict__ leaf_box, BvhNode* nodes,
+                                                  const int32_t* __restrict__ parent, int32_t* leaf_prim,
+                                                  int32_t* flag) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
+    int32_t prim = (int32_t)sorted[l];
+    leaf_prim[l] = prim;
+    if (n == 1) continue;
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
+    int kin = prim_kin(kind, T, prim);
+    int32_t node = parent[n - 1 + l];
+    int slot = (nodes[node].c0 == ~(int32_t)l) ? 0 : 1;
+    write_child(&nodes[node], slot, lo, hi, kin);
+    __threadfence();
+    if (atomicAdd(&flag[node], 1) == 0) continue;
+    for (int64_t step = 0; step < n; ++step) {   // a root path has at most n-1 nodes
+      __threadfence();
+      const BvhNode* nd = &nodes[node];
+      for (int k = 0; k < 3; ++k) {
+        lo[k] = fminf(__ldcg(&nd->lo0[k]), __ldcg(&nd->lo1[k]));
+        hi[k] = fmaxf(__ldcg(&nd->hi0[k]), __ldcg(&nd->hi1[k]));
+      }
+      int kk = atomicOr(&nodes[node].kin, 0);
+      kin = (kk & 3) == 3;
+      if (node == 0) break;
+      int32_t p = parent[node];
+      slot = (nodes[p].c0 == node) ? 0 : 1;
+      write_child(&nodes[p], slot, lo, hi, kin);
+      __threadfence();
+      if (atomicAdd(&flag[p], 1) == 0) break;
+      node = p;
+    }
+  }
+}
+
+__device__ __forceinline__ bool box_overlap(const float* lo, const float* hi, const float qlo[3], const float qhi[3]) {
+  return !(lo[0] > qhi[0] || qlo[0] > hi[0] || lo[1] > qhi[1] || qlo[1] > hi[1] || lo[2] > qhi[2] ||
+           qlo[2] > hi[2]);
+}
+
+__device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
+  uint32_t mask = __activemask();
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(mask) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(reinterpret_cast<unsigned long long*>(n_cand), (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  int64_t pos = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+  if (pos < cap) {
+    cand[pos] = key;
+  } else {
+    raise_flag(st, EIPC_FLAG_CAND_OVERFLOW);
+    raise_need(st, &st->need_cand, pos + 1);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_query(Bvh t, PrimKind qkind, Topo T, const double* __restrict__ x4,
+                                               const double* __restrict__ dx4, double pad, uint64_t* cand,
+                                               int64_t* n_cand, int64_t cap, DevStatus* st) {
+  const int64_t nq = qkind == kVertex ? T.nv : T.ne;
+  const int type = qkind == kVertex ? 0 : 1;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += grid_stride()) {
+    float qlo[3], qhi[3];
+    prim_box(qkind, q, T, x4, dx4, pad, qlo, qhi);
+    int32_t qa, qb;
+    if (qkind == kVertex) { qa = (int32_t)q; qb = (int32_t)q; }
+    else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
+    const bool qkin = prim_kin(qkind, T, q);
+    auto leaf = [&](int32_t lpos) {
+      int32_t p = t.leaf_prim[lpos];
+      if (type == 0) {
+        const int32_t* f = T.tris + 3 * (int64_t)p;
+        if (f[0] == qa || f[1] == qa || f[2] == qa) return;
+        if (qkin && T.fkin[p]) return;
+        // tight leaf box against the inflated query box was already tested by the parent
+        emit(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
+      } else {
+        if (p <= q) return;
+        int32_t pa = T.edges[2 * (int64_t)p], pb = T.edges[2 * (int64_t)p + 1];
+        if (pa == qa || pa == qb || pb == qa || pb == qb) return;
+        if (qkin && T.ekin[p]) return;
+        emit(pair_key(1, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
+      }
+    };
+    if (t.n == 1) {
+      const float* b = t.leaf_box + 6 * (int64_t)t.leaf_prim[0];
+      if (box_overlap(b, b + 3, qlo, qhi)) leaf(0);
+      continue;
+    }
+    int32_t stack[64];
+    int sp = 0;
+    stack[sp++] = 0;
+    // a tree of n leaves has n-1 internal nodes, each popped at most once
+    int64_t visits = 0;
+    while (sp > 0) {
+      if (++visits > t.n) {
+        raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+        break;
+      }
+      int32_t node = stack[--sp];
+      const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
+      float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+      int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
+      float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+      float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+      int32_t c0 = f3.x, c1 = f3.y, kin = f3.z;
+      bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1));
+      bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2));
+      if (o0) {
+        if (c0 < 0) leaf(~c0);
+        else if (sp < 64) stack[sp++] = c0;
+        else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+      }
+      if (o1) {
+        if (c1 < 0) leaf(~c1);
+        else if (sp < 64) stack[sp++] = c1;
+        else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, int32_t* bounds_ws,
+               uint32_t* sort_hist, cudaStream_t s) {
+  if (t.n <= 0) return;
+  launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
+  launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, dx4, topo.nv, bounds_ws);
+  launch(k_leaves, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, x4, dx4, bounds_ws, t.leaf_box, t.keys, t.vals);
+  int which = radix_sort_u64(t.keys, t.vals, t.keys_alt, t.vals_alt, t.n_dev, t.n, 30, sort_hist, s);
+  const uint64_t* sk = which ? t.keys_alt : t.keys;
+  const uint32_t* sv = which ? t.vals_alt : t.vals;
+  cudaMemsetAsync(t.nodes, 0, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1), s);
+  cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
+  if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent);
+  launch(k_refit, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv, t.leaf_box, t.nodes, t.parent, t.leaf_prim,
+                                              t.refit_flag);
+}
+
+void bvh_query(const Bvh& t, PrimKind qkind, const Topo& topo, const double* x4, const double* dx4, double pad,
+               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s) {
+  if (t.n <= 0) return;
+  int64_t nq = qkind == kVertex ? topo.nv : topo.ne;
+  if (nq <= 0) return;
+  launch(k_query, blocks_for(nq, 16, 128), 128, 0, s, t, qkind, topo, x4, dx4, pad, cand, n_cand, cap, st);
+}
+
+}  // namespace eipc

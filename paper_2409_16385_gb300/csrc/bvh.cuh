@@ -1,0 +1,64 @@
+// Linear BVH over the surface primitives (Karras 2012 construction on 30-bit Morton
+// codes) and the traversal that produces candidate pairs for the contact set and for the
+// CCD step bound.  Boxes are FP32 rounded outward from the FP64 positions, so a box test
+// never rejects a pair that the exact FP64 test would keep.
+#pragma once
+#include "common.cuh"
+
+namespace eipc {
+
+// One internal node holds the boxes of both children so a traversal step is one 64-byte
+// fetch.  Child ids: >= 0 internal node, < 0 leaf ~position in Morton order.
+struct alignas(16) BvhNode {
+  float lo0[3], hi0[3];
+  float lo1[3], hi1[3];
+  int32_t c0, c1;
+  int32_t kin;   // bit 0 / bit 1: every primitive under child 0 / 1 is kinematic
+  int32_t pad;
+};
+
+struct Bvh {
+  int64_t n;             // primitives (static per scene)
+  int64_t* n_dev;        // [1] device copy of n (element count for the Morton sort)
+  BvhNode* nodes;        // [n-1]
+  int32_t* parent;       // [2n-1]: internal i at i, leaf l at n-1+l
+  int32_t* leaf_prim;    // [n]
+  float* leaf_box;       // [6n], by primitive id (lo xyz, hi xyz)
+  int32_t* refit_flag;   // [n]
+  uint64_t* keys;        // [n] Morton keys (sorted in place)
+  uint32_t* vals;        // [n]
+  uint64_t* keys_alt;    // [n]
+  uint32_t* vals_alt;    // [n]
+};
+
+enum PrimKind { kVertex = 0, kEdge = 1, kTri = 2 };
+
+// Static topology needed by the broad and narrow phases.
+struct Topo {
+  int64_t nv, ne, nf;
+  const int32_t* tris;   // [nf*3]
+  const int32_t* edges;  // [ne*2]
+  const uint8_t* vkin;   // [nv]
+  const uint8_t* ekin;   // [ne] both ends kinematic
+  const uint8_t* fkin;   // [nf] all three kinematic
+  int bits_i, bits_j;    // pair key packing
+};
+
+// Pair key: type << (bi+bj) | i << bj | j, ordered like (type, i, j).
+__host__ __device__ __forceinline__ uint64_t pair_key(int type, uint32_t i, uint32_t j, int bi, int bj) {
+  return ((uint64_t)type << (bi + bj)) | ((uint64_t)i << bj) | (uint64_t)j;
+}
+
+// Build the tree over primitives of `kind` from positions x4 (padded), optionally swept
+// by dx4 (CCD); `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
+void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4,
+               int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s);
+
+// Traverse: queries of `qkind` (vertices against a triangle tree -> PT, edges against an
+// edge tree -> EE with j > i), query boxes inflated by `pad` (contact) or swept by dx4
+// (CCD).  Candidates (non-incident, not all kinematic) are appended as pair keys to
+// cand[0..cap) with the running count in *n_cand; overflow raises CAND_OVERFLOW.
+void bvh_query(const Bvh& t, PrimKind qkind, const Topo& topo, const double* x4, const double* dx4,
+               double pad, uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s);
+
+}  // namespace eipc

@@ -1,0 +1,693 @@
+// Per-pair contact potentials and their reduction into the subspace.
+//
+// Barrier (Eq. IPC_energy): E_k = kappa b(d), b = -(d - dhat)^2 log(d / dhat).
+// With s = d^2 the partial minimum min_beta |r(x,beta)|^2 (geometry.cuh):
+//   grad s   = 2 c (x) r
+//   hess s   = 2 (c c^T) (x) I3 - G M^-1 G^T,  G_j = 2 (c (x) v_j + a_j (x) r),
+//              v_j = sum_a a_j[a] x_a, M = 2 [v_j . v_l]
+// (Schur complement of the inner minimisation), so
+//   hess E = kappa [(b'' - b'/d) (c c^T) (x) (r^ r^T) + (b'/d) (c c^T) (x) I3]
+//            - (kappa b' / (2d)) G M^-1 G^T.
+// Every term lies in the span of {c^ (x) e_x, c^ (x) e_y, c^ (x) e_z, a^_1 (x) r^, a^_2 (x) r^}
+// (a^_j: a_j orthonormalised against c), an orthonormal basis Q of at most 5 columns.  The
+// 12x12 Hessian is Q K Q^T with K (<= 5x5) in closed form; its projection onto the PSD cone
+// (projected Newton, Sec. III-C) is Q K+ Q^T with K+ from a 5x5 Jacobi eigensolve -- the
+// same matrix as projecting the 12x12 itself, because P+ acts on eigenpairs and the
+// complement of span(Q) is the zero eigenspace.
+//
+// Reduction (Eq. 15): g_r = J^T g, H_r = J^T H J.  J restricted to a stencil maps the
+// stencil's unique cage nodes I to the 4 vertices with weights w_aI, so Q's columns map to
+// per-node scalars omega_I = sum_a c^_a w_aI, alpha_jI = sum_a a^_j[a] w_aI, and
+//   block(I, J) = A_I K+ A_J^T,   A_I = [omega_I I3 | alpha_1I r^ | alpha_2I r^]  (3x5).
+// Friction (Sec. III-B, lagged): D = mu lambda f0(|u|), u = (I - n n^T)(sum gamma_a x_a - anchor),
+//   grad = mu lambda f1(y)/y gamma (x) u,   hess = (gamma gamma^T) (x) F,
+//   F = mu lambda [(f1/y)(I - n n^T) + (f1' - f1/y) u^ u^T]   (PSD as written).
+// Records (key = I * Ns + J, 3x3 block) are written at per-pair offsets, sorted stably by
+// key and summed per key in pair order: the result is bitwise repeatable.
+#include "geometry.cuh"
+#include "scene.cuh"
+#include "sort.cuh"
+
+namespace eipc {
+namespace {
+
+constexpr int kMaxNodes = 16;
+constexpr int kEvalThreads = 128;
+
+// stencil vertex ids of pair (type, i, j)
+__device__ __forceinline__ void stencil_vertices(const Topo& T, int type, int32_t i, int32_t j, int32_t v[4]) {
+  if (type == 0) {
+    v[0] = i;
+    v[1] = T.tris[3 * (int64_t)j]; v[2] = T.tris[3 * (int64_t)j + 1]; v[3] = T.tris[3 * (int64_t)j + 2];
+  } else {
+    v[0] = T.edges[2 * (int64_t)i]; v[1] = T.edges[2 * (int64_t)i + 1];
+    v[2] = T.edges[2 * (int64_t)j]; v[3] = T.edges[2 * (int64_t)j + 1];
+  }
+}
+
+// item k < P: barrier pair k; P <= k < P + L: friction pair k - P
+__device__ __forceinline__ bool item_vertices(const Topo& T, const eipc_pairs& pr, int64_t P, const int32_t* lag_v,
+                                              int64_t L, int64_t k, int32_t v[4]) {
+  if (k < P) {
+    stencil_vertices(T, pr.type[k], pr.i[k], pr.j[k], v);
+    return true;
+  }
+  if (k < P + L) {
+    const int4 q = reinterpret_cast<const int4*>(lag_v)[k - P];
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    return true;
+  }
+  return false;
+}
+
+// unique cage nodes of each item (kinematic vertices carry none), record counts
+__global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, const int32_t* lag_v,
+                                                       const int64_t* lag_count, int64_t lag_cap,
+                                                       const int32_t* __restrict__ cage_idx, int64_t item_cap,
+                                                       int32_t* __restrict__ item_nodes, int32_t* __restrict__ item_n,
+                                                       int64_t* __restrict__ rc_h, int64_t* __restrict__ rc_g,
+                                                       int64_t* n_items, DevStatus* st) {
+  const int64_t P = clamp_count(pr.count, pr.capacity);
+  const int64_t L = lag_v ? clamp_count(lag_count, lag_cap) : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int64_t n = P + L;
+    if (n > item_cap) {
+      raise_flag(st, EIPC_FLAG_REC_OVERFLOW);
+      n = item_cap;
+    }
+    *n_items = n;
+  }
+  const int64_t n = (P + L) < item_cap ? (P + L) : item_cap;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
+    int32_t v[4];
+    item_vertices(T, pr, P, lag_v, L, k, v);
+    int32_t nodes[kMaxNodes];
+    int cnt = 0;
+    for (int a = 0; a < 4; ++a) {
+      const int4 id = __ldg(reinterpret_cast<const int4*>(cage_idx) + v[a]);
+      if (id.x < 0) continue;
+      const int32_t ids[4] = {id.x, id.y, id.z, id.w};
+      for (int s = 0; s < 4; ++s) {
+        bool seen = false;
+        for (int u = 0; u < cnt; ++u) seen |= (nodes[u] == ids[s]);
+        if (!seen) nodes[cnt++] = ids[s];
+      }
+    }
+    for (int u = 0; u < cnt; ++u) item_nodes[kMaxNodes * k + u] = nodes[u];
+    item_n[k] = cnt;
+    rc_h[k] = (int64_t)cnt * cnt;
+    rc_g[k] = cnt;
+  }
+}
+
+// per-node weights of a stencil basis: out[u] = sum over (a, slot) with idx == node_u of
+// coef[a] * w[a][slot]
+__device__ __forceinline__ void node_weights(const int32_t v[4], const int32_t* __restrict__ cage_idx,
+                                             const double* __restrict__ w, const int32_t* nodes, int n,
+                                             const double coef[3][4], int ncoef, double out[kMaxNodes][3]) {
+  for (int u = 0; u < n; ++u)
+    for (int c = 0; c < 3; ++c) out[u][c] = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    const int4 id = __ldg(reinterpret_cast<const int4*>(cage_idx) + v[a]);
+    if (id.x < 0) continue;
+    const int ids[4] = {id.x, id.y, id.z, id.w};
+    const double2 w01 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a]);
+    const double2 w23 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a] + 1);
+    const double ws[4] = {w01.x, w01.y, w23.x, w23.y};
+    for (int s = 0; s < 4; ++s) {
+      int u = 0;
+      while (u < n - 1 && nodes[u] != ids[s]) ++u;
+      for (int c = 0; c < ncoef; ++c) out[u][c] += coef[c][a] * ws[s];
+    }
+  }
+}
+
+// Cyclic Jacobi on a symmetric N x N matrix held in registers; A becomes diagonal
+// (eigenvalues), V accumulates the rotations (columns = eigenvectors).
+template <int N>
+__device__ __forceinline__ void jacobi(double A[N][N], double V[N][N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  double fro = 0.0;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) fro += A[i][j] * A[i][j];
+  const double tol = 1e-34 * fro;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    double off = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; ++p)
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) off += A[p][q] * A[p][q];
+    if (off <= tol) break;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) {
+        const double apq = A[p][q];
+        if (apq != 0.0) {
+          const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+          const double at = fabs(theta);
+          double t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
+          t = theta < 0.0 ? -t : t;
+          const double c = rsqrt(t * t + 1.0);
+          const double s = t * c;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const double akp = A[k][p], akq = A[k][q];
+            A[k][p] = c * akp - s * akq;
+            A[k][q] = s * akp + c * akq;
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const double apk = A[p][k], aqk = A[q][k];
+            A[p][k] = c * apk - s * aqk;
+            A[q][k] = s * apk + c * aqk;
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const double vkp = V[k][p], vkq = V[k][q];
+            V[k][p] = c * vkp - s * vkq;
+            V[k][q] = s * vkp + c * vkq;
+          }
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void write_block(double* __restrict__ rec, int64_t pos, const double B[3][3]) {
+  double* p = rec + 9 * pos;   // 72-byte records: 8-byte aligned, stored as scalars
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) p[3 * a + b] = B[a][b];
+}
+
+struct EvalArgs {
+  Topo T;
+  eipc_pairs pr;
+  const int32_t* cage_idx;
+  const double* w;
+  const double* x4;
+  int64_t ns;
+  double dhat, kappa;
+  const int32_t* item_nodes;
+  const int32_t* item_n;
+  const int64_t* ro_h;
+  const int64_t* ro_g;
+  const int64_t* n_items;
+  int64_t rec_cap, gcap;
+  uint64_t* hkeys;
+  uint32_t* hvals;
+  double* hrec;
+  uint64_t* gkeys;
+  uint32_t* gvals;
+  double* grec;
+  double* item_E;
+  DevStatus* st;
+};
+
+__global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
+  const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
+  const int64_t nit = *A.n_items;
+  const int64_t np = P < nit ? P : nit;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < np; k += grid_stride()) {
+    int32_t v[4];
+    const int type = A.pr.type[k];
+    stencil_vertices(A.T, type, A.pr.i[k], A.pr.j[k], v);
+    V3 X[4];
+    for (int a = 0; a < 4; ++a) X[a] = load_x(A.x4, v[a]);
+    // positions relative to the first vertex (distance and derivatives are translation
+    // invariant; this keeps the differences exact-ish)
+    V3 Y[4];
+    for (int a = 0; a < 4; ++a) Y[a] = X[a] - X[0];
+    Stencil S;
+    if (type == 0) pt_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    const int n = A.item_n[k];
+    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+    const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+    double E = 0.0;
+    double Kp[5][5];
+    double cn = 0.0, b1 = 0.0;
+    V3 rh = {0.0, 0.0, 0.0};
+    double basis[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // c^, a^_1, a^_2
+    bool active = false;
+    if (!(S.d2 > 0.0)) {
+      raise_flag(A.st, EIPC_FLAG_PENETRATION);
+    } else {
+      const double d = sqrt(S.d2);
+      active = d < A.dhat;
+      if (active) {
+        const double dh = A.dhat;
+        const double lg = log(d / dh);
+        const double m = d - dh;
+        const double b = -m * m * lg;
+        b1 = -2.0 * m * lg - m * m / d;
+        const double b2 = -2.0 * lg - 4.0 * m / d + (m * m) / (d * d);
+        E = A.kappa * b;
+        // r and r^
+        V3 r = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 4; ++a) r = r + Y[a] * S.c[a];
+        const double rn = sqrt(dot(r, r));
+        rh = r * (1.0 / rn);
+        // orthonormal 4-vectors c^, a^_1, a^_2
+        cn = sqrt(S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3]);
+        for (int a = 0; a < 4; ++a) basis[0][a] = S.c[a] / cn;
+        for (int j = 0; j < 2; ++j) {
+          if (j < S.m) {
+            double t[4];
+            for (int a = 0; a < 4; ++a) t[a] = S.a[j][a];
+            for (int i = 0; i <= j; ++i) {
+              double pr = 0.0;
+              for (int a = 0; a < 4; ++a) pr += basis[i][a] * t[a];
+              for (int a = 0; a < 4; ++a) t[a] -= pr * basis[i][a];
+            }
+            double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+            for (int a = 0; a < 4; ++a) basis[1 + j][a] = t[a] / tn;
+          } else {
+            for (int a = 0; a < 4; ++a) basis[1 + j][a] = 0.0;
+          }
+        }
+        // v_j, M = 2 [v_j . v_l], g_j = Q^T G_j
+        V3 vj[2];
+        for (int j = 0; j < 2; ++j) {
+          vj[j] = {0.0, 0.0, 0.0};
+          for (int a = 0; a < 4; ++a) vj[j] = vj[j] + Y[a] * S.a[j][a];
+        }
+        double K[5][5];
+        const double kb = A.kappa * cn * cn;
+        const double rr = A.kappa * (b2 - b1 / d);
+        const double rhv[3] = {rh.x, rh.y, rh.z};
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) K[p][q] = cn * cn * (rr * rhv[p] * rhv[q]) + (p == q ? kb * b1 / d : 0.0);
+        for (int p = 0; p < 5; ++p)
+          for (int q = 3; q < 5; ++q) { K[p][q] = 0.0; K[q][p] = 0.0; }
+        if (S.m > 0) {
+          double g[2][5];
+          for (int j = 0; j < S.m; ++j) {
+            double ca = 0.0;
+            for (int a = 0; a < 4; ++a) ca += basis[0][a] * S.a[j][a];
+            const double vv[3] = {vj[j].x, vj[j].y, vj[j].z};
+            for (int p = 0; p < 3; ++p) g[j][p] = 2.0 * cn * vv[p] + 2.0 * d * ca * rhv[p];
+            for (int l = 0; l < 2; ++l) {
+              double al = 0.0;
+              for (int a = 0; a < 4; ++a) al += basis[1 + l][a] * S.a[j][a];
+              g[j][3 + l] = 2.0 * d * al;
+            }
+          }
+          double Mi[2][2];
+          if (S.m == 1) {
+            Mi[0][0] = 1.0 / (2.0 * dot(vj[0], vj[0]));
+          } else {
+            const double m00 = 2.0 * dot(vj[0], vj[0]), m01 = 2.0 * dot(vj[0], vj[1]), m11 = 2.0 * dot(vj[1], vj[1]);
+            const double det = m00 * m11 - m01 * m01;
+            Mi[0][0] = m11 / det; Mi[1][1] = m00 / det; Mi[0][1] = Mi[1][0] = -m01 / det;
+          }
+          const double beta = -A.kappa * b1 / (2.0 * d);
+          for (int p = 0; p < 5; ++p)
+            for (int q = 0; q < 5; ++q) {
+              double s = 0.0;
+              for (int j = 0; j < S.m; ++j)
+                for (int l = 0; l < S.m; ++l) s += g[j][p] * Mi[j][l] * g[l][q];
+              K[p][q] += beta * s;
+            }
+        }
+        // symmetrise against rounding, then project
+        for (int p = 0; p < 5; ++p)
+          for (int q = p + 1; q < 5; ++q) { const double s = 0.5 * (K[p][q] + K[q][p]); K[p][q] = s; K[q][p] = s; }
+        double V[5][5];
+        jacobi<5>(K, V);
+        for (int p = 0; p < 5; ++p)
+          for (int q = 0; q < 5; ++q) {
+            double s = 0.0;
+            for (int e = 0; e < 5; ++e) s += (K[e][e] > 0.0 ? V[p][e] * K[e][e] * V[q][e] : 0.0);
+            Kp[p][q] = s;
+          }
+      }
+    }
+    A.item_E[k] = E;
+    // per-node scalars omega, alpha_1, alpha_2
+    double nw[kMaxNodes][3];
+    if (active) {
+      node_weights(v, A.cage_idx, A.w, nodes, n, basis, 3, nw);
+    } else {
+      for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
+    }
+    // gradient records: kappa b' |c| omega_I r^
+    for (int u = 0; u < n; ++u) {
+      const int64_t pos = og + u;
+      if (pos < A.gcap) {
+        const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
+        A.gkeys[pos] = (uint64_t)nodes[u];
+        A.gvals[pos] = (uint32_t)pos;
+        A.grec[3 * pos] = s * rh.x; A.grec[3 * pos + 1] = s * rh.y; A.grec[3 * pos + 2] = s * rh.z;
+      }
+    }
+    // Hessian records: block(u,v) = A_u K+ A_v^T
+    const double rhv[3] = {rh.x, rh.y, rh.z};
+    for (int u = 0; u < n; ++u) {
+      double Bu[3][5];
+      if (active) {
+        double t[5];
+        for (int q = 0; q < 5; ++q) t[q] = nw[u][1] * Kp[3][q] + nw[u][2] * Kp[4][q];
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 5; ++q) Bu[p][q] = nw[u][0] * Kp[p][q] + rhv[p] * t[q];
+      }
+      for (int w2 = 0; w2 < n; ++w2) {
+        const int64_t pos = oh + (int64_t)u * n + w2;
+        if (pos >= A.rec_cap) continue;
+        double B[3][3];
+        if (active) {
+          for (int p = 0; p < 3; ++p) {
+            const double s = nw[w2][1] * Bu[p][3] + nw[w2][2] * Bu[p][4];
+            for (int q = 0; q < 3; ++q) B[p][q] = nw[w2][0] * Bu[p][q] + s * rhv[q];
+          }
+        } else {
+          for (int p = 0; p < 3; ++p)
+            for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
+        }
+        A.hkeys[pos] = (uint64_t)nodes[u] * (uint64_t)A.ns + (uint64_t)nodes[w2];
+        A.hvals[pos] = (uint32_t)pos;
+        write_block(A.hrec, pos, B);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc_lag lag, double mu, double eps) {
+  const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
+  const int64_t nit = *A.n_items;
+  const int64_t L = nit - P;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < L; f += grid_stride()) {
+    const int64_t k = P + f;
+    const int4 q4 = reinterpret_cast<const int4*>(lag.v)[f];
+    const int32_t v[4] = {q4.x, q4.y, q4.z, q4.w};
+    double gam[4];
+    for (int a = 0; a < 4; ++a) gam[a] = lag.gamma[4 * f + a];
+    const V3 nrm = {lag.n[3 * f], lag.n[3 * f + 1], lag.n[3 * f + 2]};
+    const V3 anc = {lag.anchor[3 * f], lag.anchor[3 * f + 1], lag.anchor[3 * f + 2]};
+    const double ml = mu * lag.lambda[f];
+    V3 vs = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) vs = vs + load_x(A.x4, v[a]) * gam[a];
+    vs = vs - anc;
+    const V3 u = vs - nrm * dot(nrm, vs);
+    const double y2 = dot(u, u);
+    double f0, f1y, f1p_minus;   // f0(y), f1(y)/y, f1'(y) - f1(y)/y
+    if (y2 == 0.0) {
+      f0 = eps / 3.0; f1y = 2.0 / eps; f1p_minus = 0.0;
+    } else {
+      const double y = sqrt(y2);
+      if (y < eps) {
+        f0 = -y2 * y / (3.0 * eps * eps) + y2 / eps + eps / 3.0;
+        f1y = 2.0 / eps - y / (eps * eps);
+        f1p_minus = -y / (eps * eps);   // (2/eps - 2y/eps^2) - (2/eps - y/eps^2)
+      } else {
+        f0 = y; f1y = 1.0 / y; f1p_minus = -1.0 / y;
+      }
+    }
+    A.item_E[k] = ml * f0;
+    const double uu[3] = {u.x, u.y, u.z};
+    const double nn[3] = {nrm.x, nrm.y, nrm.z};
+    double F[3][3];
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) {
+        double s = f1y * ((p == q ? 1.0 : 0.0) - nn[p] * nn[q]);
+        if (y2 > 0.0) s += f1p_minus * uu[p] * uu[q] / y2;
+        F[p][q] = ml * s;
+      }
+    const int n = A.item_n[k];
+    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+    const double coef[3][4] = {{gam[0], gam[1], gam[2], gam[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    double nw[kMaxNodes][3];
+    node_weights(v, A.cage_idx, A.w, nodes, n, coef, 1, nw);
+    const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+    for (int a = 0; a < n; ++a) {
+      const int64_t pos = og + a;
+      if (pos < A.gcap) {
+        const double s = ml * f1y * nw[a][0];
+        A.gkeys[pos] = (uint64_t)nodes[a];
+        A.gvals[pos] = (uint32_t)pos;
+        A.grec[3 * pos] = s * u.x; A.grec[3 * pos + 1] = s * u.y; A.grec[3 * pos + 2] = s * u.z;
+      }
+      for (int b = 0; b < n; ++b) {
+        const int64_t pos2 = oh + (int64_t)a * n + b;
+        if (pos2 >= A.rec_cap) continue;
+        double B[3][3];
+        const double ww = nw[a][0] * nw[b][0];
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) B[p][q] = ww * F[p][q];
+        A.hkeys[pos2] = (uint64_t)nodes[a] * (uint64_t)A.ns + (uint64_t)nodes[b];
+        A.hvals[pos2] = (uint32_t)pos2;
+        write_block(A.hrec, pos2, B);
+      }
+    }
+  }
+}
+
+// record totals -> overflow flags and clamped sort counts
+__global__ void k_rec_check(const int64_t* rh_total, const int64_t* rg_total, int64_t rec_cap, int64_t gcap,
+                            int64_t* n_rh, int64_t* n_rg, DevStatus* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t a = *rh_total, b = *rg_total;
+    if (a > rec_cap || b > gcap) {
+      raise_flag(st, EIPC_FLAG_REC_OVERFLOW);
+      raise_need(st, &st->need_rec, a > b ? a : b);
+    }
+    *n_rh = a < rec_cap ? a : rec_cap;
+    *n_rg = b < gcap ? b : gcap;
+  }
+}
+
+// segment heads of a sorted key array
+__global__ void __launch_bounds__(kBlock) k_seg_flags(const uint64_t* __restrict__ keys, const int64_t* n_dev,
+                                                      int64_t cap, int64_t* __restrict__ flag) {
+  const int64_t n = clamp_count(n_dev, cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride())
+    flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_seg_starts(const int64_t* __restrict__ flag, const int64_t* __restrict__ id,
+                                                       const int64_t* n_dev, int64_t cap, int64_t* __restrict__ start) {
+  const int64_t n = clamp_count(n_dev, cap);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride())
+    if (flag[i]) start[id[i]] = i;
+}
+
+// BSR blocks: segment s sums its records in sorted (= pair) order
+__global__ void __launch_bounds__(kBlock) k_seg_sum_h(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                      const double* __restrict__ rec, const int64_t* __restrict__ start,
+                                                      const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
+                                                      int64_t ns, eipc_bsr H, int64_t* __restrict__ row_count,
+                                                      DevStatus* st) {
+  const int64_t R = clamp_count(n_rec, cap);
+  const int64_t S = *n_seg;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *H.nnzb = S;
+    if (S > H.capacity) {
+      raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
+      raise_need(st, &st->need_bsr, S);
+    }
+  }
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+    const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
+    double acc[9];
+    for (int c = 0; c < 9; ++c) acc[c] = 0.0;
+    for (int64_t r = b; r < e; ++r) {
+      const double* p = rec + 9 * (int64_t)vals[r];
+      for (int c = 0; c < 9; ++c) acc[c] += p[c];
+    }
+    const uint64_t key = keys[b];
+    const int64_t row = (int64_t)(key / (uint64_t)ns), col = (int64_t)(key % (uint64_t)ns);
+    atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
+    if (s < H.capacity) {
+      H.col[s] = (int32_t)col;
+      for (int c = 0; c < 9; ++c) H.val[9 * s + c] = acc[c];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                                      const double* __restrict__ rec, const int64_t* __restrict__ start,
+                                                      const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
+                                                      double* __restrict__ g) {
+  const int64_t R = clamp_count(n_rec, cap);
+  const int64_t S = *n_seg;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+    const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t r = b; r < e; ++r) {
+      const double* p = rec + 3 * (int64_t)vals[r];
+      for (int c = 0; c < 3; ++c) acc[c] += p[c];
+    }
+    const int64_t node = (int64_t)keys[b];
+    for (int c = 0; c < 3; ++c) g[3 * node + c] = acc[c];
+  }
+}
+
+__global__ void k_rowptr(const int64_t* __restrict__ row_off, int64_t ns, int32_t* __restrict__ row_ptr) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= ns; i += grid_stride())
+    row_ptr[i] = (int32_t)row_off[i];
+}
+
+// deterministic sum: fixed chunk per block, fixed in-block tree, partials summed in order
+__global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict__ x, const int64_t* n_dev,
+                                                        int64_t cap, double* __restrict__ partial) {
+  const int64_t n = clamp_count(n_dev, cap);
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t b = blockIdx.x * per, e = (b + per < n) ? b + per : n;
+  double s = 0.0;
+  for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) s += x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double ws[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_final(const double* __restrict__ partial, int nb, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += partial[b];
+    *out = t;
+  }
+}
+
+// ------------------------------------------------------------------ friction lag
+__global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __restrict__ x4, eipc_pairs pr,
+                                                      double dhat, double kappa, eipc_lag out, DevStatus* st) {
+  const int64_t P = clamp_count(pr.count, pr.capacity);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *out.count = P < out.capacity ? P : out.capacity;
+    if (P > out.capacity) raise_flag(st, EIPC_FLAG_LAG_OVERFLOW);
+  }
+  const int64_t n = P < out.capacity ? P : out.capacity;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
+    int32_t v[4];
+    const int type = pr.type[k];
+    stencil_vertices(T, type, pr.i[k], pr.j[k], v);
+    V3 X[4], Y[4];
+    for (int a = 0; a < 4; ++a) X[a] = load_x(x4, v[a]);
+    for (int a = 0; a < 4; ++a) Y[a] = X[a] - X[0];
+    Stencil S;
+    if (type == 0) pt_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    const double d = sqrt(S.d2);
+    double b1 = 0.0;
+    if (d > 0.0 && d < dhat) {
+      const double lg = log(d / dhat), m = d - dhat;
+      b1 = -2.0 * m * lg - m * m / d;
+    }
+    V3 rrel = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) rrel = rrel + Y[a] * S.c[a];
+    const double rn = sqrt(dot(rrel, rrel));
+    // anchor with the same arithmetic the evaluation uses for sum_a gamma_a x_a
+    V3 anc = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) anc = anc + X[a] * S.c[a];
+    reinterpret_cast<int4*>(out.v)[k] = make_int4(v[0], v[1], v[2], v[3]);
+    for (int a = 0; a < 4; ++a) out.gamma[4 * k + a] = S.c[a];
+    out.n[3 * k] = rrel.x / rn; out.n[3 * k + 1] = rrel.y / rn; out.n[3 * k + 2] = rrel.z / rn;
+    out.anchor[3 * k] = anc.x; out.anchor[3 * k + 1] = anc.y; out.anchor[3 * k + 2] = anc.z;
+    out.lambda[k] = kappa * fabs(b1);
+  }
+}
+
+__global__ void k_set_count(int64_t* c, int64_t v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *c = v;
+}
+
+}  // namespace
+
+int bits_for(uint64_t maxval) {
+  int b = 1;
+  while (b < 63 && (1ull << b) <= maxval) ++b;
+  return b;
+}
+
+void lag_launch(eipc_scene* sc, const double* q_n, const eipc_pairs& pr, const eipc_params& p, const eipc_lag& out,
+                cudaStream_t s) {
+  EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q_n, sc->x4, 1, 0, s));
+  EIPC_TIMED(sc, kKLag, s,
+             (launch(k_lag, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, sc->topo, sc->x4, pr, p.dhat,
+                                                                                      p.kappa, out, sc->status)));
+}
+
+void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
+                 double* E, double* g_r, const eipc_bsr& H, cudaStream_t s) {
+  EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
+  const bool fr = lag && p.mu > 0.0;
+  int64_t* cnt = sc->counters;
+  cudaMemsetAsync(cnt + kCntItems, 0, 5 * sizeof(int64_t), s);
+  const int64_t item_cap = sc->item_cap;
+  sc->timers->start(kKItems, s);
+  launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
+                                                           fr ? lag->capacity : 0, sc->cage_idx, item_cap,
+                                                           sc->item_nodes, sc->item_n, sc->rc_h, sc->rc_g,
+                                                           cnt + kCntItems, sc->status);
+  int64_t* tot_h = cnt + 9;
+  int64_t* tot_g = cnt + 10;
+  exclusive_scan_i64(sc->rc_h, sc->ro_h, cnt + kCntItems, item_cap, tot_h, sc->scan_partial, s);
+  exclusive_scan_i64(sc->rc_g, sc->ro_g, cnt + kCntItems, item_cap, tot_g, sc->scan_partial, s);
+  launch(k_rec_check, 1, 32, 0, s, tot_h, tot_g, sc->rec_cap, sc->gcap, cnt + kCntRecH, cnt + kCntRecG, sc->status);
+  sc->timers->stop(kKItems, s);
+  EvalArgs A;
+  A.T = sc->topo; A.pr = pr; A.cage_idx = sc->cage_idx; A.w = sc->w; A.x4 = sc->x4; A.ns = sc->ns;
+  A.dhat = p.dhat; A.kappa = p.kappa; A.item_nodes = sc->item_nodes; A.item_n = sc->item_n;
+  A.ro_h = sc->ro_h; A.ro_g = sc->ro_g; A.n_items = cnt + kCntItems; A.rec_cap = sc->rec_cap; A.gcap = sc->gcap;
+  A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
+  A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
+  EIPC_TIMED(sc, kKEvalBarrier, s,
+             (launch(k_eval_barrier, blocks_for(pr.capacity, 16, kEvalThreads), kEvalThreads, 0, s, A)));
+  if (fr)
+    EIPC_TIMED(sc, kKEvalFriction, s,
+               (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
+                                                                                                    p.eps_v * p.h)));
+  // Hessian: stable sort by (I, J), segmented sum, row pointers
+  sc->timers->start(kKHReduce, s);
+  int wh = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, cnt + kCntRecH, sc->rec_cap, sc->bits_h,
+                          sc->sort_hist, s);
+  const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
+  const uint32_t* hv = wh ? sc->hvals_alt : sc->hvals;
+  launch(k_seg_flags, blocks_for(sc->rec_cap), kBlock, 0, s, hk, cnt + kCntRecH, sc->rec_cap, sc->seg_flag);
+  exclusive_scan_i64(sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap, cnt + kCntSegH, sc->scan_partial, s);
+  launch(k_seg_starts, blocks_for(sc->rec_cap), kBlock, 0, s, sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap,
+                                                           sc->seg_start);
+  cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
+  launch(k_seg_sum_h, blocks_for(sc->rec_cap), kBlock, 0, s, hk, hv, sc->hrec, sc->seg_start, cnt + kCntRecH,
+                                                          cnt + kCntSegH, sc->rec_cap, sc->ns, H, sc->row_count,
+                                                          sc->status);
+  int64_t* nrow = cnt + 11;
+  launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
+  exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);
+  launch(k_rowptr, blocks_for(sc->ns + 1), kBlock, 0, s, sc->row_count, sc->ns, H.row_ptr);
+  sc->timers->stop(kKHReduce, s);
+  // gradient
+  sc->timers->start(kKGReduce, s);
+  int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap, sc->bits_g,
+                          sc->sort_hist, s);
+  const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
+  const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
+  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
+  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
+  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
+                                                        sc->gseg_start);
+  cudaMemsetAsync(g_r, 0, sizeof(double) * 3 * sc->ns, s);
+  launch(k_seg_sum_g, blocks_for(sc->gcap), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG, cnt + kCntSegG,
+                                                       sc->gcap, g_r);
+  sc->timers->stop(kKGReduce, s);
+  // energy
+  sc->timers->start(kKEnergy, s);
+  launch(k_sum_partial, kScanBlocks, kBlock, 0, s, sc->item_E, cnt + kCntItems, item_cap, sc->sum_partial);
+  launch(k_sum_final, 1, 32, 0, s, sc->sum_partial, kScanBlocks, E);
+  sc->timers->stop(kKEnergy, s);
+}
+
+}  // namespace eipc

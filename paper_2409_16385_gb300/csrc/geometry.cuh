@@ -1,0 +1,141 @@
+// Device-side unsigned distance of point-triangle (PT) and edge-edge (EE) stencils
+// (Sec. III-B, d_k(x)) with the closest-feature stencil needed by the closed-form
+// derivatives.
+//
+// A stencil's squared distance is a partial minimum s(x) = min_beta |r(x, beta)|^2 with
+// r = sum_a c_a(beta) x_a affine in beta (beta: barycentric / segment parameters of the
+// closest feature).  For each region we report
+//   c[4]      the coefficients at the minimiser (r = sum c_a x_a),
+//   m         the number of free parameters of that feature (0, 1 or 2),
+//   a[j][4]   dc/dbeta_j (constant per region),
+// from which eval.cu builds the exact gradient and Hessian of s by the Schur complement of
+// the inner minimisation.  Region choice: PT -- projection inside the triangle, else the
+// nearest of the three edges (t0t1, t1t2, t2t0); EE -- unconstrained segment-parameter
+// minimiser inside [0,1]^2 (and the segments not parallel to within 1e-20 relative),
+// else the nearest of (a0, seg b), (a1, seg b), (b0, seg a), (b1, seg a); ties keep the
+// first in that order.
+#pragma once
+#include "common.cuh"
+
+namespace eipc {
+
+struct Stencil {
+  double c[4];
+  double a[2][4];
+  int m;
+  double d2;
+};
+
+// |p - (e0 + t (e1 - e0))|^2 over t in [0,1]
+__device__ __forceinline__ double seg_point_d2(V3 p, V3 e0, V3 e1, double* t_out) {
+  V3 e = e1 - e0, w = p - e0;
+  double t = dot(w, e) / dot(e, e);
+  t = fmin(fmax(t, 0.0), 1.0);
+  V3 r = w - e * t;
+  *t_out = t;
+  return dot(r, r);
+}
+
+__device__ __forceinline__ void set_zero(Stencil& S) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) { S.c[k] = 0.0; S.a[0][k] = 0.0; S.a[1][k] = 0.0; }
+}
+
+// closest feature on segment (ia, ib) at parameter t, seen from a fixed point slot `ip`
+// with sign +1 (point on side A) -- used for PT edges and EE endpoint cases
+__device__ __forceinline__ void point_segment_stencil(Stencil& S, int ip, double sp, int ia, int ib,
+                                                      double t) {
+  set_zero(S);
+  S.c[ip] = sp;
+  if (t <= 0.0) {
+    S.c[ia] = -sp; S.m = 0;
+  } else if (t >= 1.0) {
+    S.c[ib] = -sp; S.m = 0;
+  } else {
+    S.c[ia] = -sp * (1.0 - t);
+    S.c[ib] = -sp * t;
+    S.a[0][ia] = sp;
+    S.a[0][ib] = -sp;
+    S.m = 1;
+  }
+}
+
+template <bool kStencil>
+__device__ __forceinline__ double pt_distance(V3 p, V3 t0, V3 t1, V3 t2, Stencil* S) {
+  V3 e1 = t1 - t0, e2 = t2 - t0, w = p - t0;
+  V3 n = cross(e1, e2);
+  double nn = dot(n, n);
+  // barycentric coordinates of the projection: beta1 = ((w x e2) . n)/nn, etc.
+  double b1 = dot(cross(w, e2), n) / nn;
+  double b2 = dot(cross(e1, w), n) / nn;
+  if (b1 >= 0.0 && b2 >= 0.0 && b1 + b2 <= 1.0) {
+    double h = dot(w, n);
+    double d2 = h * h / nn;
+    if (kStencil) {
+      set_zero(*S);
+      S->c[0] = 1.0; S->c[1] = -(1.0 - b1 - b2); S->c[2] = -b1; S->c[3] = -b2;
+      S->a[0][1] = 1.0; S->a[0][2] = -1.0;
+      S->a[1][1] = 1.0; S->a[1][3] = -1.0;
+      S->m = 2;
+      S->d2 = d2;
+    }
+    return d2;
+  }
+  double ta, tb, tc;
+  double da = seg_point_d2(p, t0, t1, &ta);
+  double db = seg_point_d2(p, t1, t2, &tb);
+  double dc = seg_point_d2(p, t2, t0, &tc);
+  int k = 0;
+  double best = da, tbest = ta;
+  if (db < best) { best = db; tbest = tb; k = 1; }
+  if (dc < best) { best = dc; tbest = tc; k = 2; }
+  if (kStencil) {
+    point_segment_stencil(*S, 0, 1.0, 1 + k, 1 + (k + 1) % 3, tbest);
+    S->d2 = best;
+  }
+  return best;
+}
+
+template <bool kStencil>
+__device__ __forceinline__ double ee_distance(V3 a0, V3 a1, V3 b0, V3 b1, Stencil* S) {
+  V3 ea = a1 - a0, eb = b1 - b0, w = a0 - b0;
+  double A = dot(ea, ea), B = dot(ea, eb), C = dot(eb, eb);
+  double D = dot(ea, w), E = dot(eb, w);
+  V3 n = cross(ea, eb);
+  double nn = dot(n, n);
+  if (nn > 1e-20 * A * C) {
+    double s = (B * E - C * D) / nn;
+    double t = (A * E - B * D) / nn;
+    if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {
+      double h = dot(w, n);
+      double d2 = h * h / nn;
+      if (kStencil) {
+        set_zero(*S);
+        S->c[0] = 1.0 - s; S->c[1] = s; S->c[2] = -(1.0 - t); S->c[3] = -t;
+        S->a[0][0] = -1.0; S->a[0][1] = 1.0;
+        S->a[1][2] = 1.0; S->a[1][3] = -1.0;
+        S->m = 2;
+        S->d2 = d2;
+      }
+      return d2;
+    }
+  }
+  double t0, t1, t2, t3;
+  double d0 = seg_point_d2(a0, b0, b1, &t0);
+  double d1 = seg_point_d2(a1, b0, b1, &t1);
+  double d2 = seg_point_d2(b0, a0, a1, &t2);
+  double d3 = seg_point_d2(b1, a0, a1, &t3);
+  int k = 0;
+  double best = d0, tb = t0;
+  if (d1 < best) { best = d1; tb = t1; k = 1; }
+  if (d2 < best) { best = d2; tb = t2; k = 2; }
+  if (d3 < best) { best = d3; tb = t3; k = 3; }
+  if (kStencil) {
+    if (k < 2) point_segment_stencil(*S, k, 1.0, 2, 3, tb);      // a_k - point on b
+    else point_segment_stencil(*S, k, -1.0, 0, 1, tb);          // point on a - b_{k-2}
+    S->d2 = best;
+  }
+  return best;
+}
+
+}  // namespace eipc

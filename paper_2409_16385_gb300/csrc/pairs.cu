@@ -1,0 +1,163 @@
+// Embedding x = J q (Sec. III-D) and the contact set B (Sec. III-B): LBVH candidates,
+// exact FP64 distance filter 0 < d < dhat, canonical (type, i, j) order.
+#include "geometry.cuh"
+#include "scene.cuh"
+#include "sort.cuh"
+
+namespace eipc {
+namespace {
+
+// x_k = sum_j w_kj q_{idx_kj}; kinematic rows take x_kin (or 0 for a displacement).
+// One thread per vertex; writes either the padded internal layout or a caller [Nv,3] array.
+__global__ void __launch_bounds__(kBlock) k_embed(int64_t nv, const int32_t* __restrict__ idx,
+                                                  const double* __restrict__ w, const double* __restrict__ xk4,
+                                                  const double* __restrict__ q, double* __restrict__ out,
+                                                  int padded, int displacement, DevStatus* st) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
+    const int4 id = __ldg(reinterpret_cast<const int4*>(idx) + v);
+    double r[3];
+    if (id.x < 0) {
+      for (int k = 0; k < 3; ++k) r[k] = displacement ? 0.0 : xk4[4 * v + k];
+    } else {
+      const double2 w01 = __ldg(reinterpret_cast<const double2*>(w) + 2 * v);
+      const double2 w23 = __ldg(reinterpret_cast<const double2*>(w) + 2 * v + 1);
+      const int ids[4] = {id.x, id.y, id.z, id.w};
+      const double ws[4] = {w01.x, w01.y, w23.x, w23.y};
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s += ws[j] * __ldg(q + 3 * (int64_t)ids[j] + k);
+        r[k] = s;
+      }
+      if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) raise_flag(st, EIPC_FLAG_NONFINITE);
+    }
+    if (padded) {
+      reinterpret_cast<double2*>(out)[2 * v] = make_double2(r[0], r[1]);
+      reinterpret_cast<double2*>(out)[2 * v + 1] = make_double2(r[2], 0.0);
+    } else {
+      for (int k = 0; k < 3; ++k) out[3 * v + k] = r[k];
+    }
+  }
+}
+
+__device__ __forceinline__ void unpack(uint64_t key, int bi, int bj, int* type, int32_t* i, int32_t* j) {
+  *j = (int32_t)(key & ((1ull << bj) - 1));
+  *i = (int32_t)((key >> bj) & ((1ull << bi) - 1));
+  *type = (int)(key >> (bi + bj));
+}
+
+__device__ __forceinline__ double stencil_d2(const Topo& T, const double* __restrict__ x4, int type, int32_t i,
+                                             int32_t j) {
+  if (type == 0) {
+    const int32_t* f = T.tris + 3 * (int64_t)j;
+    return pt_distance<false>(load_x(x4, i), load_x(x4, f[0]), load_x(x4, f[1]), load_x(x4, f[2]), nullptr);
+  }
+  const int32_t* ea = T.edges + 2 * (int64_t)i;
+  const int32_t* eb = T.edges + 2 * (int64_t)j;
+  return ee_distance<false>(load_x(x4, ea[0]), load_x(x4, ea[1]), load_x(x4, eb[0]), load_x(x4, eb[1]), nullptr);
+}
+
+// Exact filter of the broad-phase candidates: keep 0 < d < dhat, flag d <= 0.
+__global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restrict__ x4,
+                                                   const uint64_t* __restrict__ cand, const int64_t* n_cand,
+                                                   int64_t cand_cap, double dhat, uint64_t* __restrict__ skeys,
+                                                   uint32_t* __restrict__ svals, double* __restrict__ sd,
+                                                   int64_t* n_surv, DevStatus* st) {
+  const int64_t n = clamp_count(n_cand, cand_cap);
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
+    const int64_t k = base + threadIdx.x;
+    bool keep = false;
+    uint64_t key = 0;
+    double d = 0.0;
+    if (k < n) {
+      key = cand[k];
+      int type; int32_t i, j;
+      unpack(key, T.bits_i, T.bits_j, &type, &i, &j);
+      double d2 = stencil_d2(T, x4, type, i, j);
+      if (!(d2 > 0.0)) {
+        raise_flag(st, EIPC_FLAG_PENETRATION);
+      } else {
+        d = sqrt(d2);
+        keep = d < dhat;
+      }
+    }
+    uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (mask) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(n_surv), (unsigned long long)__popc(mask));
+      b = __shfl_sync(0xffffffffu, b, 0);
+      if (keep) {
+        int64_t pos = (int64_t)b + __popc(mask & ((1u << lane) - 1u));
+        // survivors never outnumber candidates, so pos < cand_cap
+        skeys[pos] = key;
+        svals[pos] = (uint32_t)pos;
+        sd[pos] = d;
+      }
+    }
+  }
+}
+
+// Sorted survivors -> caller's pair arrays.
+__global__ void __launch_bounds__(kBlock) k_emit_pairs(Topo T, const uint64_t* __restrict__ keys,
+                                                       const uint32_t* __restrict__ vals, const double* __restrict__ sd,
+                                                       const int64_t* n_surv, int64_t cand_cap, eipc_pairs out,
+                                                       DevStatus* st) {
+  const int64_t n = clamp_count(n_surv, cand_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *out.count = n;
+    if (n > out.capacity) {
+      raise_flag(st, EIPC_FLAG_PAIR_OVERFLOW);
+      raise_need(st, &st->need_pairs, n);
+    }
+  }
+  const int64_t m = n < out.capacity ? n : out.capacity;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += grid_stride()) {
+    int type; int32_t i, j;
+    unpack(keys[k], T.bits_i, T.bits_j, &type, &i, &j);
+    out.type[k] = type;
+    out.i[k] = i;
+    out.j[k] = j;
+    out.d[k] = sd[vals[k]];
+  }
+}
+
+}  // namespace
+
+void embed_launch(const eipc_scene* sc, const double* q, double* out, int out_padded, int displacement,
+                  cudaStream_t s) {
+  launch(k_embed, blocks_for(sc->nv), kBlock, 0, s, sc->nv, sc->cage_idx, sc->w, sc->x_kin4, q, out, out_padded,
+                                                 displacement, sc->status);
+}
+
+void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const eipc_pairs& out, cudaStream_t s) {
+  EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
+  int64_t* n_cand = sc->counters + kCntCand;
+  int64_t* n_surv = sc->counters + kCntSurv;
+  cudaMemsetAsync(sc->counters + kCntCand, 0, 2 * sizeof(int64_t), s);
+  // PT: every vertex (box grown by dhat) against the triangle tree
+  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+  EIPC_TIMED(sc, kKQuery, s,
+             bvh_query(sc->tri_bvh, kVertex, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
+                       sc->status, s));
+  // EE: every edge (box grown by dhat) against the edge tree, j > i
+  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+  EIPC_TIMED(sc, kKQuery, s,
+             bvh_query(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
+                       sc->status, s));
+  EIPC_TIMED(sc, kKNarrow, s,
+             (launch(k_narrow, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, sc->x4, sc->cand, n_cand,
+                                                                        sc->cand_cap, p.dhat, sc->skeys, sc->svals,
+                                                                        sc->sd, n_surv, sc->status)));
+  sc->timers->start(kKPairSort, s);
+  int bits = 1 + sc->topo.bits_i + sc->topo.bits_j;
+  int which = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, n_surv, sc->cand_cap, bits,
+                             sc->sort_hist, s);
+  const uint64_t* k = which ? sc->skeys_alt : sc->skeys;
+  const uint32_t* v = which ? sc->svals_alt : sc->svals;
+  launch(k_emit_pairs, blocks_for(out.capacity, 8), kBlock, 0, s, sc->topo, k, v, sc->sd, n_surv, sc->cand_cap, out,
+                                                               sc->status);
+  sc->timers->stop(kKPairSort, s);
+}
+
+}  // namespace eipc

@@ -1,0 +1,93 @@
+// Scene object behind the opaque eipc_scene handle: static topology, embedding weights and
+// the device workspace every compute call reuses (sized once at creation).
+#pragma once
+#include "bvh.cuh"
+#include "common.cuh"
+#include "timing.cuh"
+
+struct eipc_scene {
+  int64_t nv, nf, ne, ns;
+  // topology and embedding (device)
+  int32_t* tris;
+  int32_t* edges;
+  int32_t* cage_idx;     // [nv*4], -1 rows kinematic
+  double* w;             // [nv*4]
+  double* x_kin4;        // [nv*4] padded kinematic positions
+  uint8_t* vkin;
+  uint8_t* ekin;
+  uint8_t* fkin;
+  eipc::Topo topo;
+  // positions (padded, 4 doubles per vertex)
+  double* x4;
+  double* dx4;
+  // broad phase
+  eipc::Bvh tri_bvh, edge_bvh;
+  int32_t* bounds_ws;
+  uint32_t* sort_hist;
+  int64_t cand_cap;
+  uint64_t* cand;
+  int64_t* counters;     // [16] device counters (see kCnt*)
+  // narrow phase survivors
+  uint64_t* skeys;
+  uint64_t* skeys_alt;
+  uint32_t* svals;
+  uint32_t* svals_alt;
+  double* sd;
+  // reduction workspace
+  int64_t item_cap;      // pairs + friction items per eval
+  int32_t* item_nodes;   // [item_cap*16]
+  int32_t* item_n;       // [item_cap]
+  int64_t* rc_h;         // [item_cap] record counts, then offsets
+  int64_t* ro_h;
+  int64_t* rc_g;
+  int64_t* ro_g;
+  double* item_E;        // [item_cap]
+  int64_t rec_cap;
+  uint64_t* hkeys;
+  uint64_t* hkeys_alt;
+  uint32_t* hvals;
+  uint32_t* hvals_alt;
+  double* hrec;          // [rec_cap*9]
+  int64_t* seg_flag;     // [rec_cap]
+  int64_t* seg_id;       // [rec_cap]
+  int64_t* seg_start;    // [rec_cap]
+  int64_t gcap;          // gradient records
+  uint64_t* gkeys;
+  uint64_t* gkeys_alt;
+  uint32_t* gvals;
+  uint32_t* gvals_alt;
+  double* grec;          // [gcap*3]
+  int64_t* gseg_flag;
+  int64_t* gseg_id;
+  int64_t* gseg_start;
+  int64_t* row_count;    // [ns+1]
+  int64_t* scan_partial; // [kScanBlocks+1]
+  double* sum_partial;   // [kScanBlocks]
+  int bits_h, bits_g;    // key widths of the reduction sorts
+  eipc::DevStatus* status;
+  eipc::Timers* timers;   // host-side event timers (off unless enabled)
+};
+
+namespace eipc {
+// device counters
+enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
+       kCntAccd = 7, kCntZero = 8, kCntN = 16 };
+
+#define EIPC_TIMED(sc, id, s, ...)        \
+  do {                                    \
+    (sc)->timers->start((id), (s));       \
+    __VA_ARGS__;                          \
+    (sc)->timers->stop((id), (s));        \
+  } while (0)
+
+void embed_launch(const eipc_scene* sc, const double* q, double* out, int out_padded, int displacement,
+                  cudaStream_t s);
+void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const eipc_pairs& out, cudaStream_t s);
+void lag_launch(eipc_scene* sc, const double* q_n, const eipc_pairs& pr, const eipc_params& p, const eipc_lag& out,
+                cudaStream_t s);
+void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
+                 double* E, double* g_r, const eipc_bsr& H, cudaStream_t s);
+int bits_for(uint64_t maxval);
+void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_params& p, double* alpha,
+                 int64_t* n_candidates, cudaStream_t s);
+}  // namespace eipc

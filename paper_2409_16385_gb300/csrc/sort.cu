@@ -1,0 +1,217 @@
+// Stable LSD radix sort and exclusive scan with device-resident element counts.
+//
+// Radix pass (8-bit digit): each of kSortBlocks blocks owns one contiguous chunk of the
+// input.  (1) per-block digit histograms, (2) one block turns them into exclusive output
+// offsets in digit-major order, (3) each block scatters its chunk tile by tile: warp peers
+// with equal digits are found with __match_any_sync, per-warp digit counts are prefix-
+// summed across the block's 8 warps, so every element lands at a position that preserves
+// input order among equal digits (stability is what makes the sort-and-reduce of the
+// reduced Hessian deterministic).
+#include "common.cuh"
+#include "sort.cuh"
+
+namespace eipc {
+namespace {
+
+__device__ __forceinline__ void chunk_range(int64_t n, int64_t* beg, int64_t* end) {
+  int64_t per = (n + kSortBlocks - 1) / kSortBlocks;
+  per = (per + kSortThreads - 1) / kSortThreads * kSortThreads;
+  *beg = (int64_t)blockIdx.x * per;
+  int64_t e = *beg + per;
+  *end = e < n ? e : n;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restrict__ keys,
+                                                       const int64_t* n_dev, int64_t cap, int shift,
+                                                       uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  chunk_range(n, &beg, &end);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
+    atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * kSortBlocks + blockIdx.x] = h[d];
+}
+
+// exclusive scan of 256 * kSortBlocks counters in one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_hist_scan(uint32_t* hist) {
+  constexpr int N = 256 * kSortBlocks;
+  constexpr int PER = (N + 1023) / 1024;
+  __shared__ uint32_t part[1024];
+  int t = threadIdx.x;
+  int beg = t * PER;
+  uint32_t s = 0;
+  for (int k = 0; k < PER; ++k)
+    if (beg + k < N) s += hist[beg + k];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = (t >= off) ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = part[t] - s;  // exclusive prefix of this thread's range
+  for (int k = 0; k < PER; ++k)
+    if (beg + k < N) {
+      uint32_t c = hist[beg + k];
+      hist[beg + k] = run;
+      run += c;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __restrict__ kin,
+                                                          const uint32_t* __restrict__ vin,
+                                                          uint64_t* __restrict__ kout,
+                                                          uint32_t* __restrict__ vout,
+                                                          const int64_t* n_dev, int64_t cap, int shift,
+                                                          const uint32_t* __restrict__ offs) {
+  constexpr int W = kSortThreads / 32;
+  __shared__ uint32_t base[256];
+  __shared__ uint32_t wcnt[W][257];
+  __shared__ uint32_t total[256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  chunk_range(n, &beg, &end);
+  for (int d = t; d < 256; d += blockDim.x) base[d] = offs[d * kSortBlocks + blockIdx.x];
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (int64_t tile = beg; tile < end; tile += kSortThreads) {
+    for (int d = lane; d < 257; d += 32) wcnt[warp][d] = 0;
+    __syncthreads();
+    int64_t i = tile + t;
+    bool valid = i < end;
+    uint64_t key = valid ? kin[i] : 0;
+    uint32_t val = valid ? vin[i] : 0;
+    uint32_t digit = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+    uint32_t peers = __match_any_sync(0xffffffffu, digit);
+    uint32_t rank = __popc(peers & lt_mask);
+    if (rank == 0) wcnt[warp][digit] = __popc(peers);
+    __syncthreads();
+    if (t < 256) {
+      uint32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        uint32_t c = wcnt[w][t];
+        wcnt[w][t] = run;
+        run += c;
+      }
+      total[t] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = base[digit] + wcnt[warp][digit] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    if (t < 256) base[t] += total[t];
+  }
+}
+
+// ---------------------------------------------------------------- exclusive scan
+__device__ __forceinline__ void scan_range(int64_t n, int64_t* beg, int64_t* end) {
+  int64_t per = (n + kScanBlocks - 1) / kScanBlocks;
+  *beg = (int64_t)blockIdx.x * per;
+  int64_t e = *beg + per;
+  *end = e < n ? e : n;
+}
+
+__device__ int64_t block_sum_i64(int64_t v) {
+  __shared__ int64_t ws[32];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) ws[warp] = v;
+  __syncthreads();
+  int64_t r = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += ws[w];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_scan_partial(const int64_t* __restrict__ in, const int64_t* n_dev,
+                                                      int64_t cap, int64_t* __restrict__ partial) {
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t s = 0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) s += in[i];
+  s = block_sum_i64(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_scan_partials(int64_t* partial, int64_t* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t run = 0;
+    for (int b = 0; b < kScanBlocks; ++b) {
+      int64_t c = partial[b];
+      partial[b] = run;
+      run += c;
+    }
+    partial[kScanBlocks] = run;
+    if (total) *total = run;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                                    const int64_t* n_dev, int64_t cap,
+                                                    const int64_t* __restrict__ partial) {
+  __shared__ int64_t tile_sum[256];
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t run = partial[blockIdx.x];
+  const int t = threadIdx.x;
+  for (int64_t tile = beg; tile < end; tile += 256) {
+    int64_t i = tile + t;
+    int64_t v = (i < end) ? in[i] : 0;
+    tile_sum[t] = v;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      int64_t u = (t >= off) ? tile_sum[t - off] : 0;
+      __syncthreads();
+      tile_sum[t] += u;
+      __syncthreads();
+    }
+    if (i < end) out[i] = run + tile_sum[t] - v;
+    int64_t tot = tile_sum[255];
+    __syncthreads();
+    run += tot;
+  }
+}
+
+}  // namespace
+
+int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s) {
+  int which = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    uint64_t* ki = which ? keys_alt : keys;
+    uint32_t* vi = which ? vals_alt : vals;
+    uint64_t* ko = which ? keys : keys_alt;
+    uint32_t* vo = which ? vals : vals_alt;
+    launch(k_hist, kSortBlocks, kSortThreads, 0, s, ki, n, cap, shift, hist);
+    launch(k_hist_scan, 1, 1024, 0, s, hist);
+    launch(k_scatter, kSortBlocks, kSortThreads, 0, s, ki, vi, ko, vo, n, cap, shift, hist);
+    which ^= 1;
+  }
+  return which;
+}
+
+void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64_t cap, int64_t* total,
+                        int64_t* partial, cudaStream_t s) {
+  launch(k_scan_partial, kScanBlocks, 256, 0, s, in, n, cap, partial);
+  launch(k_scan_partials, 1, 32, 0, s, partial, total);
+  launch(k_scan_apply, kScanBlocks, 256, 0, s, in, out, n, cap, partial);
+}
+
+}  // namespace eipc

@@ -1,0 +1,27 @@
+// Sorting and scan primitives whose element counts live in device memory, so that they
+// can run inside a captured CUDA graph without any host read-back.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eipc {
+
+constexpr int kSortBlocks = 304;   // 2 per SM; each block owns one contiguous chunk
+constexpr int kSortThreads = 256;  // 8 warps, one element per thread per tile
+
+// Scratch: 256 * kSortBlocks digit counters.
+inline size_t sort_hist_entries() { return 256u * kSortBlocks; }
+
+// Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), on key bits [0, bits).
+// Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns 0 if the sorted
+// result ends in (keys, vals), 1 if it ends in the alternate buffers.
+int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
+                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s);
+
+// out[i] = sum_{k<i} in[k] for i < min(*n, cap); *total = the full sum.
+// partial needs kScanBlocks + 1 entries.
+constexpr int kScanBlocks = 304;
+void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64_t cap,
+                        int64_t* total, int64_t* partial, cudaStream_t s);
+
+}  // namespace eipc

@@ -456,7 +456,8 @@ def bubble_grasp(seed: int = 0, n_body: int = 71, n_mem: int = 45,
     extreme y, and they flatten slightly.  Every iterate, and every straight path between
     consecutive iterates, keeps the bodies on opposite sides of the planes y = +-(ymax +
     g/2), so the trajectory is intersection-free by construction.  The CCD direction dq(t)
-    overshoots the next iterate three-fold so that the step bound is active."""
+    is the motion to the next iterate plus a push of the membranes by 1.5 gaps toward the
+    body, so that the step bound is active."""
     params = dict(DEFAULT_PARAMS, dhat=5e-4, mu=0.8)
     dhat = params["dhat"]
     R = 0.05
@@ -520,10 +521,18 @@ def bubble_grasp(seed: int = 0, n_body: int = 71, n_mem: int = 45,
         q[sl_bot] = mb_
         return q
 
+    def dq_at(t: int) -> np.ndarray:
+        # next-iterate motion plus a push of both membranes toward the body by 1.5 gaps,
+        # so the step bound cuts the step at about two thirds
+        d = q_at(float(t) + 1.0) - q_at(float(t))
+        d[sl_top, 1] -= 1.5 * gap[t]
+        d[sl_bot, 1] += 1.5 * gap[t]
+        return d
+
     sc.n_iterates = n_it
     sc.iterate = lambda t: q_at(float(t))
     sc.lag_of = lambda t: (t // iters_per_step) * iters_per_step
-    sc.dq = lambda t: 3.0 * (q_at(float(t) + 1.0) - q_at(float(t)))
+    sc.dq = dq_at
     return sc
 
 
@@ -575,10 +584,17 @@ def plate_in_rack(seed: int = 0, plate_cells=(150, 100), n_tines: int = 10,
         q[:, 2] += z_off - lower_per_iter * t
         return q
 
+    def dq_at(t: int) -> np.ndarray:
+        # next lowering step plus a sideways push of 0.75 dhat toward one tine row (the
+        # gap is 0.5 dhat, so contact comes at two thirds of the step)
+        d = q_at(float(t) + 1.0) - q_at(float(t))
+        d[:, 1] += 0.75 * dhat
+        return d
+
     sc.n_iterates = n_iters
     sc.iterate = lambda t: q_at(float(t))
     sc.lag_of = lambda t: (t // 5) * 5
-    sc.dq = lambda t: 3.0 * (q_at(float(t) + 1.0) - q_at(float(t)))
+    sc.dq = dq_at
     return sc
 
 

@@ -1,0 +1,66 @@
+"""The C-ABI library loads and exports every entry point include/embipc.h declares (no
+GPU needed: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2409_16385_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(eipc_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for n in ("eipc_build_candidates", "eipc_eval_contact", "eipc_accd_toi", "eipc_scene_create",
+              "eipc_friction_lag", "eipc_embed", "eipc_status_read"):
+        assert n in d
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    build.build()
+    lib = ctypes.CDLL(build.LIB)
+    for n in _declared():
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+    assert set(binding.EXPORTS) <= set(_declared())
+
+
+def test_version_string():
+    lib = binding.load()
+    assert b"embipc" in lib.eipc_version()
+
+
+def test_scene_create_rejects_bad_input_without_gpu_work():
+    """Host-side validation: out-of-range ids are refused before any device call."""
+    import numpy as np
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    tris = np.array([[0, 1, 5]], np.int32)          # vertex 5 does not exist
+    edges = np.array([[0, 1], [0, 5], [1, 5]], np.int32)
+    idx = np.full((3, 4), -1, np.int32)
+    w = np.zeros((3, 4)); xk = np.zeros((3, 3))
+    rc = lib.eipc_scene_create(3, 1, 3, 0, tris.ctypes.data, edges.ctypes.data, idx.ctypes.data, w.ctypes.data,
+                               xk.ctypes.data, 0, 0, ctypes.byref(h))
+    assert rc == -1 and not h.value
+    rc = lib.eipc_scene_create(0, 0, 0, 0, None, None, None, None, None, 0, 0, ctypes.byref(h))
+    assert rc == -1
+
+
+def test_binding_refuses_to_run_without_cuda():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2409_16385_gb300 import ContactScene, scenes
+    with pytest.raises(RuntimeError):
+        ContactScene(scenes.make_config(1))

@@ -1,0 +1,111 @@
+"""GPU edge cases: empty contact set, a touching pair (d = 0), undersized caller buffers,
+non-finite input and the CCD iteration cap.  Each condition is reported through the
+device status word; none faults the device."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_16385_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _two_triangle_scene(gap):
+    """Kinematic triangle at z = 0 and an embedded triangle `gap` above it (each embedded
+    vertex is its own cage node)."""
+    verts = np.array([[0, 0, 0], [1e-2, 0, 0], [0, 1e-2, 0],
+                      [2e-3, 2e-3, gap], [6e-3, 2e-3, gap], [2e-3, 6e-3, gap]], float)
+    tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    idx = np.full((6, 4), -1, np.int32)
+    w = np.zeros((6, 4))
+    for v in range(3, 6):
+        idx[v] = v - 3
+        w[v, 0] = 1.0
+    xk = verts.copy(); xk[3:] = 0
+    sc = scenes.Scene(name="two_tris", tris=tris, edges=scenes.edges_of(tris), cage_idx=idx, w=w, x_kin=xk, Ns=3,
+                      cage_tets=np.zeros((0, 4), np.int32), q_rest=verts[3:].copy(), body=np.array([0, 0, 0, 1, 1, 1], np.int32),
+                      params=dict(scenes.DEFAULT_PARAMS))
+    return sc, verts[3:].copy()
+
+
+def test_empty_contact_set():
+    from paper_2409_16385_gb300 import ContactScene
+    sc, q = _two_triangle_scene(5e-3)          # farther than dhat = 1e-3
+    cs = ContactScene(sc, pair_capacity=64, bsr_capacity=64)
+    qd = _t(q)
+    pr = cs.build_candidates(qd)
+    E, g, H = cs.eval_contact(qd, pr, None)
+    torch.cuda.synchronize()
+    assert pr.n() == 0 and E.item() == 0.0 and float(g.abs().max()) == 0.0
+    assert int(H.nnzb.item()) == 0 and int(H.row_ptr.abs().max()) == 0
+    assert cs.status()["flags"] == 0
+    # three PT pairs at exactly the known gap, and matching the oracle
+    sc2, q2 = _two_triangle_scene(4e-4)
+    cs2 = ContactScene(sc2, pair_capacity=64, bsr_capacity=64)
+    pr2 = cs2.build_candidates(_t(q2)).host()
+    x = oracle.embed(sc2, q2)
+    po = oracle.pairs(sc2, x)
+    assert pr2["type"].tolist() == po["type"].tolist() and pr2["i"].tolist() == po["i"].tolist()
+    assert np.allclose(pr2["d"], 4e-4, rtol=1e-12)
+
+
+def test_touching_pair_raises_penetration_flag():
+    from paper_2409_16385_gb300 import ContactScene
+    sc, q = _two_triangle_scene(0.0)           # the upper triangle lies in the lower one's plane
+    q[:, 2] = 0.0
+    q[0] = [2e-3, 2e-3, 0.0]                    # and vertex 3 lies on the lower triangle
+    q[1:, 2] = 1e-3
+    cs = ContactScene(sc, pair_capacity=64, bsr_capacity=64)
+    cs.build_candidates(_t(q))
+    torch.cuda.synchronize()
+    st = cs.status()
+    assert "PENETRATION" in st["names"]
+    assert cs.status()["flags"] == 0           # reading clears the word
+
+
+def test_pair_and_bsr_capacity_overflow_reported():
+    from paper_2409_16385_gb300 import ContactScene
+    sc = scenes.make_config(1)
+    cs = ContactScene(sc, pair_capacity=16, bsr_capacity=8)
+    q = _t(sc.iterate(0))
+    pr = cs.build_candidates(q)
+    torch.cuda.synchronize()
+    st = cs.status()
+    assert "PAIR_OVERFLOW" in st["names"] and st["needed"][0] > 16
+    assert pr.n() == st["needed"][0]           # the true count is still reported
+    E, g, H = cs.eval_contact(q, pr, None)
+    torch.cuda.synchronize()
+    st = cs.status()
+    assert "BSR_OVERFLOW" in st["names"] and st["needed"][3] > 8
+
+
+def test_nonfinite_input_flag():
+    from paper_2409_16385_gb300 import ContactScene
+    sc = scenes.make_config(1)
+    cs = ContactScene(sc, pair_capacity=1 << 12, bsr_capacity=1 << 12)
+    q = sc.iterate(0).copy()
+    q[sc.cage_idx[0, 0], 1] = np.nan            # a cage node the first surface vertex uses
+    cs.build_candidates(_t(q))
+    torch.cuda.synchronize()
+    assert "NONFINITE" in cs.status()["names"]
+
+
+def test_accd_iteration_cap_keeps_alpha_safe():
+    from paper_2409_16385_gb300 import ContactScene
+    sc = scenes.make_config(1)
+    sc.params = dict(sc.params, accd_max_iter=1)
+    cs = ContactScene(sc, pair_capacity=1 << 12, bsr_capacity=1 << 12)
+    q = sc.iterate(0)
+    x = cs.embed(_t(q))
+    dx = cs.embed(_t(sc.dq(0)), displacement=True)
+    a = cs.accd_toi(x, dx).item()
+    torch.cuda.synchronize()
+    st = cs.status()
+    ao = oracle.accd(sc, oracle.embed(sc, q), oracle.embed(sc, sc.dq(0), displacement=True), max_iter=1)
+    assert ao["capped"] and "ACCD_CAP" in st["names"]
+    assert a <= ao["alpha"] and ao["alpha"] - a <= 1e-6

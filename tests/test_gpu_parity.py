@@ -1,0 +1,175 @@
+"""GPU parity: the CUDA contact stage (through the C ABI) against the CPU oracle, element
+by element on the same seeded inputs.
+
+Bars (all stated against the oracle's values):
+  contact set   identical (type, i, j) lists, except pairs with |d - dhat| <= 1e-12 dhat;
+                d within 1e-10 relative
+  E             |dE| <= 1e-9 |E|
+  g_r           max |dg| <= 1e-9 max |g|
+  H_r           identical block pattern, max |dH| <= 1e-9 max |H|
+  alpha         alpha_gpu <= alpha_oracle and alpha_oracle - alpha_gpu <= 1e-6
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_16385_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def _t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@functools.lru_cache(maxsize=None)
+def _scene(k, small):
+    return scenes.make_config(k, small=small)
+
+
+_cs_cache = {}
+
+
+def _cs(sc):
+    from paper_2409_16385_gb300 import ContactScene
+    key = id(sc)
+    if key not in _cs_cache:
+        _cs_cache[key] = ContactScene(sc, pair_capacity=1 << 20, bsr_capacity=1 << 21)
+    return _cs_cache[key]
+
+
+def check_pairs(g, o, dhat):
+    kg = list(zip(g["type"].tolist(), g["i"].tolist(), g["j"].tolist()))
+    ko = list(zip(o["type"].tolist(), o["i"].tolist(), o["j"].tolist()))
+    assert kg == sorted(kg), "GPU pair list not in (type, i, j) order"
+    sg, so = set(kg), set(ko)
+    dg = dict(zip(kg, g["d"].tolist()))
+    do = dict(zip(ko, o["d"].tolist()))
+    for k in sg ^ so:
+        d = dg.get(k, do.get(k))
+        assert abs(d - dhat) <= 1e-12 * dhat, f"pair {k} (d={d!r}) differs outside the dhat band"
+    common = sg & so
+    if common:
+        err = max(abs(dg[k] - do[k]) / do[k] for k in common)
+        assert err <= 1e-10, err
+    return len(common)
+
+
+def bsr_dict(H, ns):
+    rp, col, val = H["row_ptr"], H["col"], H["val"]
+    out = {}
+    for r in range(ns):
+        for k in range(rp[r], rp[r + 1]):
+            out[(r, int(col[k]))] = val[k]
+    return out
+
+
+def check_eval(E, g, H, ro, ns):
+    Eg = float(E)
+    assert abs(Eg - ro["E"]) <= TOL * abs(ro["E"]) + 1e-300, (Eg, ro["E"])
+    gs = np.abs(ro["g"]).max()
+    assert np.abs(g - ro["g"]).max() <= TOL * gs + 1e-300
+    hg = bsr_dict(H, ns)
+    ho = {(int(i), int(j)): v for i, j, v in zip(ro["I"], ro["J"], ro["V"])}
+    assert set(hg) == set(ho), "reduced Hessian block patterns differ"
+    hs = max((np.abs(v).max() for v in ho.values()), default=0.0)
+    err = max((np.abs(hg[k] - ho[k]).max() for k in ho), default=0.0)
+    assert err <= TOL * hs + 1e-300, (err, hs)
+    # rows sorted, full symmetric pattern
+    rp, col = H["row_ptr"], H["col"]
+    for r in range(ns):
+        assert np.all(np.diff(col[rp[r]:rp[r + 1]]) > 0)
+    return err / hs if hs else 0.0
+
+
+def run_iterate(sc, t, lag_t=None, check_alpha=True):
+    """Full pipeline at iterate t on both sides; returns the GPU outputs."""
+    cs = _cs(sc)
+    p = sc.params
+    q = sc.iterate(t)
+    lag_t = sc.lag_of(t) if lag_t is None else lag_t
+    qn = sc.iterate(lag_t)
+    qd, qnd = _t(q), _t(qn)
+    # GPU
+    pairs_n = cs.build_candidates(qnd, out=cs.new_pairs())
+    lag = cs.friction_lag(qnd, pairs_n) if p["mu"] > 0 else None
+    pairs = cs.build_candidates(qd)
+    E, g, H = cs.eval_contact(qd, pairs, lag)
+    torch.cuda.synchronize()
+    st = cs.status()
+    assert st["flags"] == 0, st
+    # oracle
+    x, xn = oracle.embed(sc, q), oracle.embed(sc, qn)
+    po, pon = oracle.pairs(sc, x), oracle.pairs(sc, xn)
+    lo = oracle.friction_lag(sc, xn, pon) if p["mu"] > 0 else None
+    ro = oracle.eval_contact(sc, x, po, lo)
+    ncommon = check_pairs(pairs.host(), po, p["dhat"])
+    check_pairs(pairs_n.host(), pon, p["dhat"])
+    if lo is not None:
+        lg = lag.host()
+        assert len(lg["lam"]) == len(lo["lam"])
+        assert np.array_equal(lg["v"], lo["v"])
+        assert np.allclose(lg["lam"], lo["lam"], rtol=1e-9, atol=0)
+        assert np.allclose(lg["gamma"], lo["gamma"], atol=1e-9)
+        assert np.allclose(lg["n"], lo["n"], atol=1e-9)
+    rel = check_eval(E.item(), g.cpu().numpy(), H.host(), ro, sc.Ns)
+    alpha = None
+    if check_alpha:
+        dq = sc.dq(t)
+        xg = cs.embed(qd)
+        dxg = cs.embed(_t(dq), displacement=True)
+        a = cs.accd_toi(xg, dxg).item()
+        ao = oracle.accd(sc, x, oracle.embed(sc, dq, displacement=True))
+        assert a <= ao["alpha"], (a, ao)
+        assert ao["alpha"] - a <= 1e-6, (a, ao)
+        alpha = (a, ao["alpha"])
+        assert cs.status()["flags"] == 0
+    return dict(pairs=ncommon, rel=rel, alpha=alpha, E=ro["E"])
+
+
+def test_config1_sphere_on_pad():
+    sc = _scene(1, False)
+    r = run_iterate(sc, 0)
+    assert r["pairs"] > 100 and 0 < r["alpha"][1] < 1
+    # second evaluation at q0 + alpha/2 dq: friction now sees tangential motion
+    sc2 = scenes.with_second_iterate(sc, r["alpha"][1])
+    r2 = run_iterate(sc2, 1, lag_t=0, check_alpha=False)
+    assert r2["pairs"] > 0
+
+
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("t", [0, 7, 13])
+def test_small_trajectories(k, t):
+    sc = _scene(k, True)
+    t = min(t, sc.n_iterates - 2)
+    r = run_iterate(sc, t)
+    assert r["pairs"] > 0
+
+
+@pytest.mark.parametrize("k,t", [(2, 30), (3, 40)])
+def test_full_size_iterate(k, t):
+    """Benchmark-size scenes, whole outputs (the oracle enumerates all pairs)."""
+    oracle.set_threads(max(1, oracle.num_threads()))
+    sc = _scene(k, False)
+    r = run_iterate(sc, t)
+    assert r["pairs"] > 1000
+
+
+def test_bitwise_repeatable():
+    sc = _scene(2, True)
+    cs = _cs(sc)
+    q = _t(sc.iterate(9))
+    qn = _t(sc.iterate(sc.lag_of(9)))
+    lag = cs.friction_lag(qn, cs.build_candidates(qn, out=cs.new_pairs()))
+    outs = []
+    for _ in range(3):
+        pr = cs.build_candidates(q)
+        E, g, H = cs.eval_contact(q, pr, lag)
+        h = H.host()
+        outs.append((E.cpu().numpy().tobytes(), g.cpu().numpy().tobytes(), h["val"].tobytes(), h["col"].tobytes()))
+    assert outs[0] == outs[1] == outs[2]
