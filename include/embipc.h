@@ -44,6 +44,7 @@ enum {
   EIPC_ERR_INVALID = -1,      /* bad argument (null pointer, size, capacity)            */
   EIPC_ERR_CUDA = -2,         /* a CUDA runtime call failed                             */
   EIPC_ERR_NOMEM = -3,        /* workspace allocation failed at scene creation          */
+  EIPC_ERR_TOO_LARGE = -4,    /* a size exceeds a fixed maximum of the call             */
   /* device status bits (eipc_status_read) */
   EIPC_FLAG_PENETRATION = 1,  /* some pair has d <= 0: the configuration is infeasible  */
   EIPC_FLAG_PAIR_OVERFLOW = 2,/* more contact pairs than the caller's pair capacity     */
@@ -53,7 +54,8 @@ enum {
   EIPC_FLAG_NONFINITE = 32,   /* a non-finite position or displacement was read         */
   EIPC_FLAG_ACCD_CAP = 64,    /* a CCD pair reached accd_max_iter (alpha still safe)    */
   EIPC_FLAG_LAG_OVERFLOW = 128,/* more friction pairs than the lag buffer capacity      */
-  EIPC_FLAG_STACK_OVERFLOW = 256 /* a BVH traversal exceeded its 64-entry stack          */
+  EIPC_FLAG_STACK_OVERFLOW = 256,/* a BVH traversal exceeded its 64-entry stack         */
+  EIPC_FLAG_BAD_INDEX = 512   /* a caller-supplied candidate names an out-of-range id   */
 };
 
 /* Contact parameters.  dhat: barrier activation distance (m); kappa: barrier stiffness;
@@ -177,6 +179,36 @@ const char* eipc_kernel_name(int32_t id);
 
 /* Number of kernel launches the library has enqueued in this process (all scenes). */
 int64_t eipc_launch_count(void);
+
+/* CCD step bound without any device allocation.  The paper has no counterpart: this
+ * exists for callers that cannot call cudaMalloc -- code running under another framework's
+ * device-memory allocator or pool that must own every allocation, or a control loop that
+ * cannot afford the implicit device synchronisation of an allocation -- and so cannot
+ * create an eipc_scene, whose workspace is allocated at creation.
+ *
+ * Same arithmetic as eipc_accd_toi, over a candidate list the caller supplies instead of
+ * the LBVH search: for k < n_cand, pair (cand_type[k], cand_i[k], cand_j[k]) is a PT pair
+ * (type 0: vertex i, triangle j) or an EE pair (type 1: edges i, j).  Candidates whose
+ * closed FP64 swept boxes over [x, x + dx] do not overlap, and incident ones, are skipped,
+ * so any superset of the overlapping pairs gives the same alpha.  Inputs (device, caller-
+ * owned): x[Nv*3], dx[Nv*3], tris[F*3], edges[E*2], the three candidate arrays.  Outputs
+ * (device, caller-owned): *alpha; *flags (EIPC_FLAG_PENETRATION / NONFINITE / ACCD_CAP /
+ * BAD_INDEX, may be NULL); *n_advanced (candidates whose boxes overlap, may be NULL).
+ * Scratch: a fixed device array inside the library holding two padded copies of the
+ * positions, for at most eipc_accd_static_max_vertices() = 131,072 vertices (8 MiB plus a
+ * 256-byte header, resident on every device that loads the library until the process
+ * exits).  Nv above that returns EIPC_ERR_TOO_LARGE before anything is enqueued.
+ * The first call on a device looks up that array's device address with the device
+ * current (cudaGetSymbolAddress); make that first call before any stream capture.  Every
+ * call re-initialises the scratch it needs, but all calls share the one array, so calls
+ * whose work overlaps on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller. */
+eipc_status eipc_accd_toi_static(int64_t Nv, int64_t F, int64_t E, const double* x, const double* dx,
+                                 const int32_t* tris, const int32_t* edges, int64_t n_cand,
+                                 const int32_t* cand_type, const int32_t* cand_i, const int32_t* cand_j,
+                                 const eipc_params* p, double* alpha, int32_t* flags, int64_t* n_advanced,
+                                 eipc_stream stream);
+int64_t eipc_accd_static_max_vertices(void);
 
 /* Library version string. */
 const char* eipc_version(void);
