@@ -2,12 +2,12 @@
  *
  * One Newton iteration's contact work, for a high-resolution collision surface embedded
  * in a coarse tetrahedral cage (Sec. III-D):
- *   eipc_embed             x = phi(q) = J q                          (Sec. III-D, Eq. 12)
+ *   eipc_embed             x = phi(q) = J q                          (Sec. III-D, Eq. 14)
  *   eipc_build_candidates  contact set B: PT / EE pairs with 0 < d < dhat (Sec. III-B)
  *   eipc_friction_lag      lagged friction state at x^n               (Sec. III-B)
  *   eipc_eval_contact      E = kappa sum b(d_k) + sum D_k, g_r = J^T grad E,
  *                          H_r = J^T (sum P+(kappa hess b_k) + sum hess D_k) J
- *                                                   (Eq. IPC_energy, Sec. III-C, Eq. 15)
+ *                                                   (Eq. 7-8, Sec. III-C, Eq. 17)
  *   eipc_accd_toi          step bound alpha for a straight full-space motion x + t dx,
  *                          linear in the reduced step because phi is linear (Sec. III-C)
  *
@@ -119,7 +119,7 @@ typedef struct eipc_scene eipc_scene;
  *     whose position is x_kin[3v..3v+2] and which has no reduced DoF;
  *   Ns: number of cage nodes (q has Ns*3 entries);
  *   cand_capacity: broad-phase candidate buffer entries (<= 0: 48 per primitive);
- *   rec_capacity: reduction record entries (<= 0: 2^25).
+ *   rec_capacity: reduction record entries (<= 0: 2^24).
  * Returns EIPC_ERR_INVALID for inconsistent sizes or out-of-range ids, EIPC_ERR_NOMEM
  * if the device workspace cannot be allocated. */
 eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, const int32_t* tris,
@@ -128,7 +128,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
                               eipc_scene** out);
 void eipc_scene_destroy(eipc_scene* scene);
 
-/* x[Nv*3] = J q for q[Ns*3] (Sec. III-D, Eq. 12).  displacement != 0 maps a reduced
+/* x[Nv*3] = J q for q[Ns*3] (Sec. III-D, Eq. 14).  displacement != 0 maps a reduced
  * displacement instead: kinematic rows are then 0 rather than x_kin. */
 eipc_status eipc_embed(eipc_scene* scene, const double* q, double* x, int32_t displacement,
                        eipc_stream stream);

@@ -151,7 +151,7 @@ T ee_d2(const V3<T>& a0, const V3<T>& a1, const V3<T>& b0, const V3<T>& b1, int*
   return d2[k];
 }
 
-// IPC log barrier, Eq. (IPC_energy): b(d) = -(d - dhat)^2 log(d / dhat) on (0, dhat), else 0.
+// IPC log barrier, Eq. 7: b(d) = -(d - dhat)^2 log(d / dhat) on (0, dhat), else 0.
 template <class T>
 T barrier(const T& d, double dhat) {
   if (val(d) <= 0.0 || val(d) >= dhat) return T(0.0);
@@ -160,7 +160,7 @@ T barrier(const T& d, double dhat) {
 }
 
 // f0 of the lagged friction (Sec. III-B): f0(y) = integral_{eps}^{y} f1 + eps with f1 of
-// Eq. (f1); for y < eps this is -y^3/(3 eps^2) + y^2/eps + eps/3, and y otherwise.
+// Eq. 9; for y < eps this is -y^3/(3 eps^2) + y^2/eps + eps/3, and y otherwise.
 template <class T>
 T friction_f0(const T& y, double eps) {
   if (val(y) >= eps) return y;

@@ -1,14 +1,14 @@
 // Test infrastructure: the CPU oracle of the Embedded-IPC contact stage.
 //
 // A plain, slow FP64 implementation written straight from the paper (arxiv 2409.16385):
-//   * embedding x = phi(q) = J q, x_k = sum_j w^k_j q_{i^j(k)}          (Sec. III-D, Eq. 12)
+//   * embedding x = phi(q) = J q, x_k = sum_j w^k_j q_{i^j(k)}          (Sec. III-D, Eq. 14)
 //   * contact set B: every point-triangle and edge-edge pair with 0 < d_k < dhat,
 //     enumerated by brute force over all pairs                            (Sec. III-B)
-//   * barrier kappa * b(d_k) with b of Eq. (IPC_energy); lagged friction
+//   * barrier kappa * b(d_k) with b of Eq. 7; lagged friction
 //     D_k = mu lambda_k^n f0(|u_k|) with f0, f1 of Sec. III-B
 //   * exact gradient / Hessian by forward-mode AD (ad.hpp), per-pair barrier Hessian
 //     projected to the nearest PSD matrix (projected Newton, Sec. III-C) by cyclic Jacobi
-//   * reduced gradient / Hessian  grad_q = J^T grad_x,  hess_q = J^T hess_x J   (Eq. 15)
+//   * reduced gradient / Hessian  grad_q = J^T grad_x,  hess_q = J^T hess_x J   (Eq. 17)
 //   * step bound by conservative advancement over every pair whose swept boxes overlap
 //     (the CCD clamp of Sec. III-C; x = J q is linear so a reduced step is a straight
 //     full-space motion)

@@ -27,7 +27,7 @@ void free_scene(eipc_scene* s) {
                   s->edge_bvh.keys, s->edge_bvh.vals, s->edge_bvh.keys_alt, s->edge_bvh.vals_alt, s->bounds_ws,
                   s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
                   s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
-                  s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start,
+                  s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->ublk, s->seg_flag, s->seg_id, s->seg_start,
                   s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec, s->gseg_flag, s->gseg_id,
                   s->gseg_start, s->row_count, s->scan_partial, s->sum_partial, s->status};
   for (void* p : ptrs)
@@ -110,7 +110,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   s->nv = Nv; s->nf = F; s->ne = E; s->ns = Ns;
   if (cand_capacity <= 0) cand_capacity = 48 * (Nv + E);
   if (cand_capacity >= (1ll << 31)) cand_capacity = (1ll << 31) - 1;
-  if (rec_capacity <= 0) rec_capacity = 1ll << 25;
+  if (rec_capacity <= 0) rec_capacity = 1ll << 24;
   if (rec_capacity >= (1ll << 31)) rec_capacity = (1ll << 31) - 1;
   s->cand_cap = cand_capacity;
   s->item_cap = cand_capacity;
@@ -135,6 +135,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->rc_g, s->item_cap)); ok(dalloc(&s->ro_g, s->item_cap)); ok(dalloc(&s->item_E, s->item_cap));
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
   ok(dalloc(&s->hvals, s->rec_cap)); ok(dalloc(&s->hvals_alt, s->rec_cap)); ok(dalloc(&s->hrec, 9 * s->rec_cap));
+  ok(dalloc(&s->ublk, 9 * s->rec_cap));
   ok(dalloc(&s->seg_flag, s->rec_cap)); ok(dalloc(&s->seg_id, s->rec_cap)); ok(dalloc(&s->seg_start, s->rec_cap));
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, 3 * s->gcap));

@@ -224,7 +224,10 @@ __global__ void __launch_bounds__(128) k_query(Bvh t, PrimKind qkind, Topo T, co
                                                int64_t* n_cand, int64_t cap, DevStatus* st) {
   const int64_t nq = qkind == kVertex ? T.nv : T.ne;
   const int type = qkind == kVertex ? 0 : 1;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += grid_stride()) {
+  for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += grid_stride()) {
+    // edge queries run against the edge tree in its Morton order: neighbouring threads
+    // then take similar paths
+    const int64_t q = (qkind == kEdge) ? (int64_t)t.leaf_prim[qi] : qi;
     float qlo[3], qhi[3];
     prim_box(qkind, q, T, x4, dx4, pad, qlo, qhi);
     int32_t qa, qb;

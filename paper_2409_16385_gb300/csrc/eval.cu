@@ -1,6 +1,6 @@
 // Per-pair contact potentials and their reduction into the subspace.
 //
-// Barrier (Eq. IPC_energy): E_k = kappa b(d), b = -(d - dhat)^2 log(d / dhat).
+// Barrier (Eq. 7): E_k = kappa b(d), b = -(d - dhat)^2 log(d / dhat).
 // With s = d^2 the partial minimum min_beta |r(x,beta)|^2 (geometry.cuh):
 //   grad s   = 2 c (x) r
 //   hess s   = 2 (c c^T) (x) I3 - G M^-1 G^T,  G_j = 2 (c (x) v_j + a_j (x) r),
@@ -15,7 +15,7 @@
 // same matrix as projecting the 12x12 itself, because P+ acts on eigenpairs and the
 // complement of span(Q) is the zero eigenspace.
 //
-// Reduction (Eq. 15): g_r = J^T g, H_r = J^T H J.  J restricted to a stencil maps the
+// Reduction (Eq. 17): g_r = J^T g, H_r = J^T H J.  J restricted to a stencil maps the
 // stencil's unique cage nodes I to the 4 vertices with weights w_aI, so Q's columns map to
 // per-node scalars omega_I = sum_a c^_a w_aI, alpha_jI = sum_a a^_j[a] w_aI, and
 //   block(I, J) = A_I K+ A_J^T,   A_I = [omega_I I3 | alpha_1I r^ | alpha_2I r^]  (3x5).
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
     }
     for (int u = 0; u < cnt; ++u) item_nodes[kMaxNodes * k + u] = nodes[u];
     item_n[k] = cnt;
-    rc_h[k] = (int64_t)cnt * cnt;
+    rc_h[k] = (int64_t)cnt * (cnt + 1) / 2;
     rc_g[k] = cnt;
   }
 }
@@ -122,20 +122,69 @@ __device__ __forceinline__ void node_weights(const int32_t v[4], const int32_t* 
   }
 }
 
-// Cyclic Jacobi on a symmetric N x N matrix held in registers; A becomes diagonal
-// (eigenvalues), V accumulates the rotations (columns = eigenvectors).
+// Fixed number of cyclic Jacobi sweeps in FP32 (62x the FP64 rate on this part): a cheap
+// approximate eigenbasis V of the symmetric matrix A (scaled to unit norm beforehand).
 template <int N>
-__device__ __forceinline__ void jacobi(double A[N][N], double V[N][N]) {
+__device__ __forceinline__ void jacobi_f32(float A[N][N], float V[N][N], int sweeps) {
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+#pragma unroll
+      for (int q = p + 1; q < N; ++q) {
+        const float apq = A[p][q];
+        if (fabsf(apq) > 1e-30f) {
+          const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
+          const float at = fabsf(theta);
+          float t = at > 1e18f ? 0.5f / at : 1.f / (at + sqrtf(at * at + 1.f));
+          t = theta < 0.f ? -t : t;
+          const float c = 1.f / sqrtf(t * t + 1.f);
+          const float s = t * c;
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float akp = A[k][p], akq = A[k][q];
+            A[k][p] = c * akp - s * akq;
+            A[k][q] = s * akp + c * akq;
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float apk = A[p][k], aqk = A[q][k];
+            A[p][k] = c * apk - s * aqk;
+            A[q][k] = s * apk + c * aqk;
+          }
+#pragma unroll
+          for (int k = 0; k < N; ++k) {
+            const float vkp = V[k][p], vkq = V[k][q];
+            V[k][p] = c * vkp - s * vkq;
+            V[k][q] = s * vkp + c * vkq;
+          }
+        }
+      }
+    }
+  }
+}
+
+// Cyclic Jacobi on a symmetric N x N matrix held in registers; A becomes diagonal
+// (eigenvalues), V accumulates the rotations (columns = eigenvectors).  V is taken as the
+// starting basis when `seeded` (the caller has already rotated A into it).
+template <int N>
+__device__ __forceinline__ void jacobi(double A[N][N], double V[N][N], bool seeded = false) {
+  if (!seeded) {
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+      for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  }
   double fro = 0.0;
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < N; ++j) fro += A[i][j] * A[i][j];
-  const double tol = 1e-34 * fro;
+  // stop once the off-diagonal norm is below 1e-13 of the matrix norm
+  const double tol = 1e-26 * fro;
   for (int sweep = 0; sweep < 12; ++sweep) {
     double off = 0.0;
 #pragma unroll
@@ -179,14 +228,6 @@ __device__ __forceinline__ void jacobi(double A[N][N], double V[N][N]) {
   }
 }
 
-__device__ __forceinline__ void write_block(double* __restrict__ rec, int64_t pos, const double B[3][3]) {
-  double* p = rec + 9 * pos;   // 72-byte records: 8-byte aligned, stored as scalars
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) p[3 * a + b] = B[a][b];
-}
-
 struct EvalArgs {
   Topo T;
   eipc_pairs pr;
@@ -210,6 +251,95 @@ struct EvalArgs {
   double* item_E;
   DevStatus* st;
 };
+
+// Eigen-decomposition of the symmetric 5x5 K: an FP32 Jacobi pre-diagonalisation of K/|K|,
+// its eigenvectors re-orthonormalised in FP64 (modified Gram-Schmidt), K rotated into that
+// basis in FP64, then FP64 Jacobi sweeps to full precision (quadratic convergence from the
+// ~1e-7 residual leaves one or two sweeps).  On return K is diagonal, V its eigenvectors.
+__device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
+  double fro = 0.0;
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) fro += K[p][q] * K[p][q];
+  if (fro == 0.0) {
+#pragma unroll
+    for (int p = 0; p < 5; ++p)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) V[p][q] = (p == q) ? 1.0 : 0.0;
+    return;
+  }
+  const double inv = rsqrt(fro);
+  float Af[5][5], Vf[5][5];
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Af[p][q] = (float)(K[p][q] * inv);
+  jacobi_f32<5>(Af, Vf, 4);
+  // FP64 orthonormal basis from the FP32 eigenvectors (columns)
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+#pragma unroll
+    for (int p = 0; p < 5; ++p) V[p][j] = (double)Vf[p][j];
+#pragma unroll
+    for (int i = 0; i < j; ++i) {
+      double pr = 0.0;
+#pragma unroll
+      for (int p = 0; p < 5; ++p) pr += V[p][i] * V[p][j];
+#pragma unroll
+      for (int p = 0; p < 5; ++p) V[p][j] -= pr * V[p][i];
+    }
+    double nn = 0.0;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) nn += V[p][j] * V[p][j];
+    const double r = rsqrt(nn);
+#pragma unroll
+    for (int p = 0; p < 5; ++p) V[p][j] *= r;
+  }
+  // K <- V^T K V
+  double T[5][5];
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) s += K[p][q] * V[q][j];
+      T[p][j] = s;
+    }
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = i; j < 5; ++j) {
+      double s = 0.0;
+#pragma unroll
+      for (int p = 0; p < 5; ++p) s += V[p][i] * T[p][j];
+      K[i][j] = s;
+      K[j][i] = s;
+    }
+  jacobi<5>(K, V, true);
+}
+
+// one upper-triangle record: key (min, max) of the two cage nodes, block transposed when
+// the first node is the larger one
+__device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32_t Iu, int32_t Iv,
+                                           const double B[3][3]) {
+  double* p = A.hrec + 9 * pos;
+  if (Iu <= Iv) {
+    A.hkeys[pos] = (uint64_t)Iu * (uint64_t)A.ns + (uint64_t)Iv;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p[3 * a + b] = B[a][b];
+  } else {
+    A.hkeys[pos] = (uint64_t)Iv * (uint64_t)A.ns + (uint64_t)Iu;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) p[3 * a + b] = B[b][a];
+  }
+  A.hvals[pos] = (uint32_t)pos;
+}
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
@@ -321,7 +451,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
         for (int p = 0; p < 5; ++p)
           for (int q = p + 1; q < 5; ++q) { const double s = 0.5 * (K[p][q] + K[q][p]); K[p][q] = s; K[q][p] = s; }
         double V[5][5];
-        jacobi<5>(K, V);
+        eigen5(K, V);
         for (int p = 0; p < 5; ++p)
           for (int q = 0; q < 5; ++q) {
             double s = 0.0;
@@ -348,8 +478,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
         A.grec[3 * pos] = s * rh.x; A.grec[3 * pos + 1] = s * rh.y; A.grec[3 * pos + 2] = s * rh.z;
       }
     }
-    // Hessian records: block(u,v) = A_u K+ A_v^T
+    // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
+    // (min(I_u, I_v), max(I_u, I_v)) and transposed when I_u > I_v
     const double rhv[3] = {rh.x, rh.y, rh.z};
+    int64_t pos = oh;
     for (int u = 0; u < n; ++u) {
       double Bu[3][5];
       if (active) {
@@ -358,8 +490,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 5; ++q) Bu[p][q] = nw[u][0] * Kp[p][q] + rhv[p] * t[q];
       }
-      for (int w2 = 0; w2 < n; ++w2) {
-        const int64_t pos = oh + (int64_t)u * n + w2;
+      for (int w2 = u; w2 < n; ++w2, ++pos) {
         if (pos >= A.rec_cap) continue;
         double B[3][3];
         if (active) {
@@ -371,9 +502,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
           for (int p = 0; p < 3; ++p)
             for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
         }
-        A.hkeys[pos] = (uint64_t)nodes[u] * (uint64_t)A.ns + (uint64_t)nodes[w2];
-        A.hvals[pos] = (uint32_t)pos;
-        write_block(A.hrec, pos, B);
+        emit_upper(A, pos, nodes[u], nodes[w2], B);
       }
     }
   }
@@ -426,6 +555,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
     double nw[kMaxNodes][3];
     node_weights(v, A.cage_idx, A.w, nodes, n, coef, 1, nw);
     const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+    int64_t pos2 = oh;
     for (int a = 0; a < n; ++a) {
       const int64_t pos = og + a;
       if (pos < A.gcap) {
@@ -434,16 +564,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
         A.gvals[pos] = (uint32_t)pos;
         A.grec[3 * pos] = s * u.x; A.grec[3 * pos + 1] = s * u.y; A.grec[3 * pos + 2] = s * u.z;
       }
-      for (int b = 0; b < n; ++b) {
-        const int64_t pos2 = oh + (int64_t)a * n + b;
+      for (int b = a; b < n; ++b, ++pos2) {
         if (pos2 >= A.rec_cap) continue;
         double B[3][3];
         const double ww = nw[a][0] * nw[b][0];
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] = ww * F[p][q];
-        A.hkeys[pos2] = (uint64_t)nodes[a] * (uint64_t)A.ns + (uint64_t)nodes[b];
-        A.hvals[pos2] = (uint32_t)pos2;
-        write_block(A.hrec, pos2, B);
+        emit_upper(A, pos2, nodes[a], nodes[b], B);
       }
     }
   }
@@ -478,35 +605,102 @@ __global__ void __launch_bounds__(kBlock) k_seg_starts(const int64_t* __restrict
     if (flag[i]) start[id[i]] = i;
 }
 
-// BSR blocks: segment s sums its records in sorted (= pair) order
+// Segment sums, one warp per segment: lane l adds records b+l, b+l+32, ... in order and a
+// fixed shuffle tree combines the lanes, so the result depends only on the sorted order.
+template <int W>
+__device__ __forceinline__ void warp_tree_sum(double acc[W]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
+}
+
+// upper-triangle blocks: segment s -> (ukey[s], ublk[s])
 __global__ void __launch_bounds__(kBlock) k_seg_sum_h(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                                       const double* __restrict__ rec, const int64_t* __restrict__ start,
                                                       const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
-                                                      int64_t ns, eipc_bsr H, int64_t* __restrict__ row_count,
-                                                      DevStatus* st) {
+                                                      uint64_t* __restrict__ ukey, double* __restrict__ ublk) {
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *H.nnzb = S;
-    if (S > H.capacity) {
-      raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
-      raise_need(st, &st->need_bsr, S);
-    }
-  }
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
     double acc[9];
+#pragma unroll
     for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-    for (int64_t r = b; r < e; ++r) {
+    for (int64_t r = b + lane; r < e; r += 32) {
       const double* p = rec + 9 * (int64_t)vals[r];
+#pragma unroll
       for (int c = 0; c < 9; ++c) acc[c] += p[c];
     }
-    const uint64_t key = keys[b];
+    warp_tree_sum<9>(acc);
+    if (lane == 0) {
+      ukey[s] = keys[b];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) ublk[9 * s + c] = acc[c];
+    }
+  }
+}
+
+// every upper block (I, J) becomes the full-pattern entry (I, J) and, off the diagonal,
+// the transposed entry (J, I); diagonal blocks get a sentinel twin that sorts last
+__global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restrict__ ukey, const int64_t* n_seg,
+                                                         int64_t ns, uint64_t sentinel, int64_t cap,
+                                                         uint64_t* __restrict__ fkey, uint32_t* __restrict__ fval,
+                                                         int64_t* n_full_sort, int64_t* n_diag, DevStatus* st) {
+  const int64_t S0 = *n_seg;
+  const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_full_sort = 2 * S;
+    if (S < S0) raise_flag(st, EIPC_FLAG_REC_OVERFLOW);
+  }
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+    const uint64_t key = ukey[s];
+    const uint64_t I = key / (uint64_t)ns, J = key % (uint64_t)ns;
+    fkey[2 * s] = key;
+    fval[2 * s] = (uint32_t)(s << 1);
+    if (I != J) {
+      fkey[2 * s + 1] = J * (uint64_t)ns + I;
+      fval[2 * s + 1] = (uint32_t)((s << 1) | 1);
+    } else {
+      fkey[2 * s + 1] = sentinel;
+      fval[2 * s + 1] = 0;
+      atomicAdd(reinterpret_cast<unsigned long long*>(n_diag), 1ull);
+    }
+  }
+}
+
+// sorted full entries -> BSR columns and values, row counts
+__global__ void __launch_bounds__(kBlock) k_emit_bsr(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
+                                                     const double* __restrict__ ublk, const int64_t* n_full_sort,
+                                                     const int64_t* n_diag, int64_t ns, eipc_bsr H,
+                                                     int64_t* __restrict__ row_count, DevStatus* st) {
+  const int64_t nnzb = *n_full_sort - *n_diag;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *H.nnzb = nnzb;
+    if (nnzb > H.capacity) {
+      raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
+      raise_need(st, &st->need_bsr, nnzb);
+    }
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzb; e += grid_stride()) {
+    const uint64_t key = fkey[e];
     const int64_t row = (int64_t)(key / (uint64_t)ns), col = (int64_t)(key % (uint64_t)ns);
     atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
-    if (s < H.capacity) {
-      H.col[s] = (int32_t)col;
-      for (int c = 0; c < 9; ++c) H.val[9 * s + c] = acc[c];
+    if (e < H.capacity) {
+      const uint32_t v = fval[e];
+      const double* b = ublk + 9 * (int64_t)(v >> 1);
+      H.col[e] = (int32_t)col;
+      if (v & 1u) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) H.val[9 * e + 3 * a + c] = b[3 * c + a];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) H.val[9 * e + c] = b[c];
+      }
     }
   }
 }
@@ -517,15 +711,22 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict
                                                       double* __restrict__ g) {
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
     const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int64_t r = b; r < e; ++r) {
+    for (int64_t r = b + lane; r < e; r += 32) {
       const double* p = rec + 3 * (int64_t)vals[r];
+#pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] += p[c];
     }
-    const int64_t node = (int64_t)keys[b];
-    for (int c = 0; c < 3; ++c) g[3 * node + c] = acc[c];
+    warp_tree_sum<3>(acc);
+    if (lane == 0) {
+      const int64_t node = (int64_t)keys[b];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) g[3 * node + c] = acc[c];
+    }
   }
 }
 
@@ -660,10 +861,25 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   exclusive_scan_i64(sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap, cnt + kCntSegH, sc->scan_partial, s);
   launch(k_seg_starts, blocks_for(sc->rec_cap), kBlock, 0, s, sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap,
                                                            sc->seg_start);
+  // upper blocks; seg_flag is free again after k_seg_starts and holds their keys
+  uint64_t* ukey = reinterpret_cast<uint64_t*>(sc->seg_flag);
+  launch(k_seg_sum_h, blocks_for(sc->rec_cap, 16), kBlock, 0, s, hk, hv, sc->hrec, sc->seg_start, cnt + kCntRecH,
+         cnt + kCntSegH, sc->rec_cap, ukey, sc->ublk);
+  // full symmetric pattern: each off-diagonal upper block also lands transposed at (J, I)
+  int64_t* n_full = cnt + 13;
+  int64_t* n_diag = cnt + 14;
+  cudaMemsetAsync(n_diag, 0, sizeof(int64_t), s);
+  const uint64_t sentinel = (1ull << sc->bits_h) - 1;
+  launch(k_full_entries, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const uint64_t*>(ukey),
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->ns, sentinel, sc->rec_cap, sc->hkeys, sc->hvals, n_full, n_diag,
+         sc->status);
+  int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_full, sc->rec_cap, sc->bits_h,
+                          sc->sort_hist, s);
+  const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
+  const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
   cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
-  launch(k_seg_sum_h, blocks_for(sc->rec_cap), kBlock, 0, s, hk, hv, sc->hrec, sc->seg_start, cnt + kCntRecH,
-                                                          cnt + kCntSegH, sc->rec_cap, sc->ns, H, sc->row_count,
-                                                          sc->status);
+  launch(k_emit_bsr, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const double*>(sc->ublk),
+         static_cast<const int64_t*>(n_full), static_cast<const int64_t*>(n_diag), sc->ns, H, sc->row_count, sc->status);
   int64_t* nrow = cnt + 11;
   launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
   exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);
@@ -680,7 +896,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
                                                         sc->gseg_start);
   cudaMemsetAsync(g_r, 0, sizeof(double) * 3 * sc->ns, s);
-  launch(k_seg_sum_g, blocks_for(sc->gcap), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG, cnt + kCntSegG,
+  launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG, cnt + kCntSegG,
                                                        sc->gcap, g_r);
   sc->timers->stop(kKGReduce, s);
   // energy

@@ -48,6 +48,7 @@ struct eipc_scene {
   uint32_t* hvals;
   uint32_t* hvals_alt;
   double* hrec;          // [rec_cap*9]
+  double* ublk;          // [rec_cap*9] reduced upper-triangle blocks
   int64_t* seg_flag;     // [rec_cap]
   int64_t* seg_id;       // [rec_cap]
   int64_t* seg_start;    // [rec_cap]

@@ -1,8 +1,9 @@
 // Stable LSD radix sort and exclusive scan with device-resident element counts.
 //
 // Radix pass (8-bit digit): each of kSortBlocks blocks owns one contiguous chunk of the
-// input.  (1) per-block digit histograms, (2) one block turns them into exclusive output
-// offsets in digit-major order, (3) each block scatters its chunk tile by tile: warp peers
+// input.  (1) per-block digit histograms, (2) one warp per digit turns its counts into
+// exclusive per-block prefixes and a digit total, (3) each block scans the 256 digit totals
+// for its digit bases and scatters its chunk tile by tile: warp peers
 // with equal digits are found with __match_any_sync, per-warp digit counts are prefix-
 // summed across the block's 8 warps, so every element lands at a position that preserves
 // input order among equal digits (stability is what makes the sort-and-reduce of the
@@ -37,31 +38,27 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restric
   for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * kSortBlocks + blockIdx.x] = h[d];
 }
 
-// exclusive scan of 256 * kSortBlocks counters in one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_hist_scan(uint32_t* hist) {
-  constexpr int N = 256 * kSortBlocks;
-  constexpr int PER = (N + 1023) / 1024;
-  __shared__ uint32_t part[1024];
-  int t = threadIdx.x;
-  int beg = t * PER;
-  uint32_t s = 0;
-  for (int k = 0; k < PER; ++k)
-    if (beg + k < N) s += hist[beg + k];
-  part[t] = s;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = (t >= off) ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  uint32_t run = part[t] - s;  // exclusive prefix of this thread's range
-  for (int k = 0; k < PER; ++k)
-    if (beg + k < N) {
-      uint32_t c = hist[beg + k];
-      hist[beg + k] = run;
-      run += c;
+// One warp per digit: exclusive prefix of that digit's counts over the blocks (in place)
+// and the digit's total, stored after the 256 * kSortBlocks counters.
+__global__ void __launch_bounds__(256) k_hist_digits(uint32_t* hist) {
+  const int lane = threadIdx.x & 31;
+  const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (d >= 256) return;
+  uint32_t* row = hist + (size_t)d * kSortBlocks;
+  uint32_t run = 0;
+  for (int b0 = 0; b0 < kSortBlocks; b0 += 32) {
+    const int b = b0 + lane;
+    const uint32_t c = b < kSortBlocks ? row[b] : 0u;
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    if (b < kSortBlocks) row[b] = run + x - c;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) hist[256 * kSortBlocks + d] = run;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __restrict__ kin,
@@ -79,7 +76,25 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __rest
   if (n > cap) n = cap;
   int64_t beg, end;
   chunk_range(n, &beg, &end);
-  for (int d = t; d < 256; d += blockDim.x) base[d] = offs[d * kSortBlocks + blockIdx.x];
+  // digit bases: exclusive scan of the 256 digit totals, plus this block's prefix
+  if (t < 256) total[t] = offs[256 * kSortBlocks + t];
+  __syncthreads();
+  if (t < 32) {
+    uint32_t run = 0;
+    for (int d0 = 0; d0 < 256; d0 += 32) {
+      const uint32_t c = total[d0 + t];
+      uint32_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (t >= o) x += y;
+      }
+      base[d0 + t] = run + x - c;
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+  }
+  __syncthreads();
+  for (int d = t; d < 256; d += blockDim.x) base[d] += offs[d * kSortBlocks + blockIdx.x];
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (int64_t tile = beg; tile < end; tile += kSortThreads) {
     for (int d = lane; d < 257; d += 32) wcnt[warp][d] = 0;
@@ -200,7 +215,7 @@ int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t*
     uint64_t* ko = which ? keys : keys_alt;
     uint32_t* vo = which ? vals : vals_alt;
     launch(k_hist, kSortBlocks, kSortThreads, 0, s, ki, n, cap, shift, hist);
-    launch(k_hist_scan, 1, 1024, 0, s, hist);
+    launch(k_hist_digits, 32, 256, 0, s, hist);
     launch(k_scatter, kSortBlocks, kSortThreads, 0, s, ki, vi, ko, vo, n, cap, shift, hist);
     which ^= 1;
   }

@@ -9,8 +9,8 @@ namespace eipc {
 constexpr int kSortBlocks = 304;   // 2 per SM; each block owns one contiguous chunk
 constexpr int kSortThreads = 256;  // 8 warps, one element per thread per tile
 
-// Scratch: 256 * kSortBlocks digit counters.
-inline size_t sort_hist_entries() { return 256u * kSortBlocks; }
+// Scratch: 256 * kSortBlocks digit counters followed by 256 digit totals.
+inline size_t sort_hist_entries() { return 256u * kSortBlocks + 256u; }
 
 // Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), on key bits [0, bits).
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns 0 if the sorted

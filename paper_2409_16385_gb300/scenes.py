@@ -12,7 +12,7 @@ Layout of a `Scene` (all numpy, C-contiguous):
   edges    int32 [E,2]   unique undirected edges (a < b), sorted lexicographically
   cage_idx int32 [Nv,4]  cage-node ids of the containing tet (Sec. III-D, i^j(k)); -1 row
                          for a kinematic vertex (prescribed, no reduced DoF)
-  w        f64   [Nv,4]  barycentric weights omega^k_j of Eq. (embedding map)
+  w        f64   [Nv,4]  barycentric weights omega^k_j of Eq. 13-14
   x_kin    f64   [Nv,3]  positions of kinematic vertices (zero rows for embedded ones)
   Ns       number of cage nodes; q has shape [Ns,3]
   body     int32 [Nv]    body id of each vertex (informational)

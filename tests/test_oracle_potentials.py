@@ -1,5 +1,5 @@
 """Pins for the oracle's barrier, friction mollifier, per-pair derivatives and PSD
-projection (Sec. III-B Eq. IPC_energy, f0/f1; Sec. III-C projected Newton)."""
+projection (Sec. III-B Eq. 7, Eqs. 8-9; Sec. III-C projected Newton)."""
 import json
 import os
 
@@ -46,7 +46,7 @@ def test_f0_matches_integral_of_f1():
     pp = _paper_params()["bubble_gripper"]
     eps = pp["eps_v"] * 0.01
 
-    def f1(y):   # Eq. (f1)
+    def f1(y):   # Eq. 9
         return -y * y / (eps * eps) + 2 * y / eps if y < eps else mp.mpf(1)
 
     for y in [0.0, 1e-8, 0.3 * eps, 0.9 * eps, eps, 1.7 * eps, 5 * eps]:

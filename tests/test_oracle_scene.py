@@ -1,5 +1,5 @@
 """Scene-level pins of the oracle: contact-set enumeration, reduction through the
-embedding (Eq. 15: grad_q = J^T grad_x, hess_q = J^T hess_x J), its special cases
+embedding (Eq. 17: grad_q = J^T grad_x, hess_q = J^T hess_x J), its special cases
 (identity embedding = full-space IPC), invariances, and the CCD step bound."""
 import functools
 
