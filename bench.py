@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--quick", action="store_true", help="small scene (profiling / smoke)")
     ap.add_argument("--json-out", default="")
+    ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
+    ap.add_argument("--rec-cap", type=int, default=0, help="reduction record capacity (0: library default)")
     return ap.parse_args()
 
 
@@ -128,10 +130,14 @@ def measured_peaks():
 #   eval_barrier  FP64 flops per contact pair, counted from the kernel's arithmetic
 #   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-FP64_FLOPS_PER_PAIR = 7600.0
+# eval_barrier: FP64 flops per contact pair counted by ncu on this workload
+# (2 x DFMA + DMUL + DADD thread instructions / pairs: 460.1e6 / 115,559), see
+# profiles/eval_barrier_bubble_grasp.md
+FP64_FLOPS_PER_PAIR = 3980.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
-# measured DRAM bytes per launch from an ncu capture of the same kernel (None = not captured)
-NCU_TRAFFIC_PER_UNIT = {}
+# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
+# (eval_barrier: 203.9 MB per launch of 115,559 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 1764.0}
 
 
 def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
@@ -248,7 +254,8 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     sc = build_scene(args.quick)
     n_it = sc.n_iterates
-    cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21)
+    cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21, cand_capacity=args.cand_cap,
+                      rec_capacity=args.rec_cap)
     lib = binding.load()
     Q = torch.tensor(np.stack([sc.iterate(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
     DQ = torch.tensor(np.stack([sc.dq(t) for t in range(n_it)]), dtype=torch.float64, device=dev)

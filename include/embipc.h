@@ -177,6 +177,13 @@ eipc_status eipc_timing_enable(eipc_scene* scene, uint32_t mask);
 eipc_status eipc_timing_read(eipc_scene* scene, double* total_ms, int64_t* launches, int32_t n);
 const char* eipc_kernel_name(int32_t id);
 
+/* eipc_build_candidates rebuilds its LBVHs (Morton sort + hierarchy) every n-th call and
+ * only refits the boxes of the existing hierarchy in between (default n = 8; n = 1 rebuilds
+ * every call).  The contact set is exact either way; only the traversal cost depends on how
+ * well the reused hierarchy fits the current positions.  eipc_accd_toi always refits the
+ * last hierarchy with swept boxes. */
+eipc_status eipc_set_rebuild_interval(eipc_scene* scene, int32_t n);
+
 /* Number of kernel launches the library has enqueued in this process (all scenes). */
 int64_t eipc_launch_count(void);
 

@@ -22,7 +22,8 @@ EIPC_OK = 0
 FLAGS = {1: "PENETRATION", 2: "PAIR_OVERFLOW", 4: "CAND_OVERFLOW", 8: "REC_OVERFLOW", 16: "BSR_OVERFLOW",
          32: "NONFINITE", 64: "ACCD_CAP", 128: "LAG_OVERFLOW", 256: "STACK_OVERFLOW"}
 EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_candidates", "eipc_friction_lag",
-           "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version"]
+           "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
+           "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval"]
 
 
 class Params(ctypes.Structure):
@@ -85,6 +86,9 @@ def load(build_if_missing: bool = True):
     L.eipc_timing_read.restype = i32
     L.eipc_kernel_name.argtypes = [i32]
     L.eipc_kernel_name.restype = ctypes.c_char_p
+    L.eipc_set_rebuild_interval.argtypes = [P, i32]
+    L.eipc_set_rebuild_interval.restype = i32
+    L.eipc_launch_count.restype = i64
     _lib = L
     return L
 
@@ -265,6 +269,10 @@ class ContactScene:
         _check(self.lib.eipc_accd_toi(self.handle, _ptr(x), _ptr(dx), ctypes.byref(self.params), _ptr(alpha), nc,
                                       _stream()), "eipc_accd_toi")
         return alpha
+
+    def set_rebuild_interval(self, n: int):
+        """Full LBVH rebuild every n-th build_candidates call, refit in between."""
+        _check(self.lib.eipc_set_rebuild_interval(self.handle, int(n)), "eipc_set_rebuild_interval")
 
     N_TIMERS = 13
 

@@ -152,13 +152,18 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
   cudaMemsetAsync(n_cand, 0, sizeof(int64_t), s);
   cudaMemsetAsync(n_adv, 0, sizeof(int64_t), s);
   launch(k_alpha_init, 1, 32, 0, s, abits);
-  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s));
+  // the hierarchies of the last contact-set build are refitted with swept boxes when they
+  // exist (the topology is reused; only the boxes change)
+  if (sc->tri_bvh.built)
+    EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, s));
+  else
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s));
+  if (sc->edge_bvh.built)
+    EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, s));
+  else
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s));
   EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->tri_bvh, kVertex, sc->topo, sc->x4, sc->dx4, 0.0, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s));
-  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s));
-  EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, 0.0, sc->cand, n_cand, sc->cand_cap,
+             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, sc->dx4, 0.0, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s));
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 

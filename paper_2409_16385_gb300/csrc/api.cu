@@ -19,10 +19,10 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->x4, s->dx4,
-                  s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->x4, s->dx4, s->x4f, s->cand2,
+                  s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
-                  s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes,
+                  s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
                   s->edge_bvh.parent, s->edge_bvh.leaf_prim, s->edge_bvh.leaf_box, s->edge_bvh.refit_flag,
                   s->edge_bvh.keys, s->edge_bvh.vals, s->edge_bvh.keys_alt, s->edge_bvh.vals_alt, s->bounds_ws,
                   s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
@@ -47,6 +47,7 @@ cudaError_t alloc_bvh(Bvh& t, int64_t n) {
   ok(dalloc(&t.nodes, n > 1 ? n - 1 : 1));
   ok(dalloc(&t.parent, 2 * n));
   ok(dalloc(&t.leaf_prim, n));
+  ok(dalloc(&t.leaf_info, n));
   ok(dalloc(&t.leaf_box, 6 * n));
   ok(dalloc(&t.refit_flag, n));
   ok(dalloc(&t.keys, n));
@@ -113,7 +114,8 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   if (rec_capacity <= 0) rec_capacity = 1ll << 24;
   if (rec_capacity >= (1ll << 31)) rec_capacity = (1ll << 31) - 1;
   s->cand_cap = cand_capacity;
-  s->item_cap = cand_capacity;
+  // items = contact pairs + lagged friction pairs of one evaluation
+  s->item_cap = cand_capacity < (1ll << 22) ? cand_capacity : (1ll << 22);
   s->rec_cap = rec_capacity;
   s->gcap = rec_capacity;
   cudaError_t e = cudaSuccess;
@@ -121,12 +123,13 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->tris, 3 * F)); ok(dalloc(&s->edges, 2 * E)); ok(dalloc(&s->cage_idx, 4 * Nv));
   ok(dalloc(&s->w, 4 * Nv)); ok(dalloc(&s->x_kin4, 4 * Nv));
   ok(dalloc(&s->vkin, Nv)); ok(dalloc(&s->ekin, E)); ok(dalloc(&s->fkin, F));
-  ok(dalloc(&s->x4, 4 * Nv)); ok(dalloc(&s->dx4, 4 * Nv));
+  ok(dalloc(&s->x4, 4 * Nv)); ok(dalloc(&s->dx4, 4 * Nv)); ok(dalloc(&s->x4f, 4 * Nv));
   ok(alloc_bvh(s->tri_bvh, F));
   ok(alloc_bvh(s->edge_bvh, E));
   ok(dalloc(&s->bounds_ws, 8));
   ok(dalloc(&s->sort_hist, (int64_t)sort_hist_entries()));
   ok(dalloc(&s->cand, s->cand_cap));
+  ok(dalloc(&s->cand2, s->cand_cap));
   ok(dalloc(&s->counters, kCntN));
   ok(dalloc(&s->skeys, s->cand_cap)); ok(dalloc(&s->skeys_alt, s->cand_cap));
   ok(dalloc(&s->svals, s->cand_cap)); ok(dalloc(&s->svals_alt, s->cand_cap)); ok(dalloc(&s->sd, s->cand_cap));
@@ -172,6 +175,8 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   T.bits_j = bits_for((uint64_t)(F > E ? F : E));
   s->bits_h = bits_for((uint64_t)Ns * (uint64_t)Ns);
   s->bits_g = bits_for((uint64_t)Ns);
+  s->rebuild_interval = 8;
+  s->contact_refits = 0;
   *out = s;
   return EIPC_OK;
 }
@@ -256,6 +261,13 @@ eipc_status eipc_timing_read(eipc_scene* sc, double* total_ms, int64_t* launches
     sc->timers->total_ms[k] = 0.0;
     sc->timers->launches[k] = 0;
   }
+  return EIPC_OK;
+}
+
+eipc_status eipc_set_rebuild_interval(eipc_scene* sc, int32_t n) {
+  if (!sc || n < 1) return EIPC_ERR_INVALID;
+  sc->rebuild_interval = n;
+  sc->contact_refits = 0;
   return EIPC_OK;
 }
 

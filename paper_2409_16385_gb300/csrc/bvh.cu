@@ -112,6 +112,16 @@ __global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Top
   }
 }
 
+// leaf boxes only, for refitting an existing hierarchy
+__global__ void __launch_bounds__(kBlock) k_leaf_boxes(PrimKind kind, int64_t n, Topo T, const double* __restrict__ x4,
+                                                       const double* __restrict__ dx4, float* __restrict__ leaf_box) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride()) {
+    float lo[3], hi[3];
+    prim_box(kind, i, T, x4, dx4, 0.0, lo, hi);
+    for (int k = 0; k < 3; ++k) { leaf_box[6 * i + k] = lo[k]; leaf_box[6 * i + 3 + k] = hi[k]; }
+  }
+}
+
 __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
   if (j < 0 || j >= n) return -1;
   uint64_t a = k[i], b = k[j];
@@ -144,6 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict_
     int32_t c1 = (hi == gamma + 1) ? ~(int32_t)(gamma + 1) : (int32_t)(gamma + 1);
     nodes[i].c0 = c0;
     nodes[i].c1 = c1;
+    nodes[i].split = (int32_t)gamma;   // last leaf position under child 0
     parent[c0 >= 0 ? c0 : (n - 1 + ~c0)] = (int32_t)i;
     parent[c1 >= 0 ? c1 : (n - 1 + ~c1)] = (int32_t)i;
   }
@@ -165,14 +176,19 @@ __device__ __forceinline__ void write_child(BvhNode* nd, int slot, const float l
 __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo T, const uint32_t* __restrict__ sorted,
                                                   const float* __restrict__ leaf_box, BvhNode* nodes,
                                                   const int32_t* __restrict__ parent, int32_t* leaf_prim,
-                                                  int32_t* flag) {
+                                                  int4* __restrict__ leaf_info, int32_t* flag) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
     int32_t prim = (int32_t)sorted[l];
     leaf_prim[l] = prim;
+    int kin = prim_kin(kind, T, prim);
+    // the leaf's vertex ids and kinematic flag, in leaf order for the traversal
+    if (kind == kTri)
+      leaf_info[l] = make_int4(T.tris[3 * (int64_t)prim], T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2], kin);
+    else
+      leaf_info[l] = make_int4(T.edges[2 * (int64_t)prim], T.edges[2 * (int64_t)prim + 1], -1, kin);
     if (n == 1) continue;
     float lo[3], hi[3];
     for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
-    int kin = prim_kin(kind, T, prim);
     int32_t node = parent[n - 1 + l];
     int slot = (nodes[node].c0 == ~(int32_t)l) ? 0 : 1;
     write_child(&nodes[node], slot, lo, hi, kin);
@@ -219,35 +235,41 @@ __device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_ca
   }
 }
 
-__global__ void __launch_bounds__(128) k_query(Bvh t, PrimKind qkind, Topo T, const double* __restrict__ x4,
+// One launch for both query sets: threads [0, nv) run vertex boxes against the triangle
+// tree (PT), threads [nv, nv + ne) run edge boxes against the edge tree (EE, j > i), the
+// edges in that tree's Morton order so neighbouring threads take similar paths.
+__global__ void __launch_bounds__(128) k_query(Bvh tt, Bvh te, Topo T, const double* __restrict__ x4,
                                                const double* __restrict__ dx4, double pad, uint64_t* cand,
                                                int64_t* n_cand, int64_t cap, DevStatus* st) {
-  const int64_t nq = qkind == kVertex ? T.nv : T.ne;
-  const int type = qkind == kVertex ? 0 : 1;
+  const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);
+  const int64_t nv_q = tt.n > 0 ? T.nv : 0;
   for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += grid_stride()) {
-    // edge queries run against the edge tree in its Morton order: neighbouring threads
-    // then take similar paths
-    const int64_t q = (qkind == kEdge) ? (int64_t)t.leaf_prim[qi] : qi;
+    const bool is_pt = qi < nv_q;
+    const Bvh& t = is_pt ? tt : te;
+    const PrimKind qkind = is_pt ? kVertex : kEdge;
+    const int64_t qpos = is_pt ? -1 : qi - nv_q;     // EE: the query's own leaf position
+    const int64_t q = is_pt ? qi : (int64_t)te.leaf_prim[qpos];
     float qlo[3], qhi[3];
     prim_box(qkind, q, T, x4, dx4, pad, qlo, qhi);
     int32_t qa, qb;
-    if (qkind == kVertex) { qa = (int32_t)q; qb = (int32_t)q; }
+    if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
     else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
     const bool qkin = prim_kin(qkind, T, q);
     auto leaf = [&](int32_t lpos) {
-      int32_t p = t.leaf_prim[lpos];
-      if (type == 0) {
-        const int32_t* f = T.tris + 3 * (int64_t)p;
-        if (f[0] == qa || f[1] == qa || f[2] == qa) return;
-        if (qkin && T.fkin[p]) return;
-        // tight leaf box against the inflated query box was already tested by the parent
+      const int4 info = __ldg(t.leaf_info + lpos);
+      if (is_pt) {
+        if (info.x == qa || info.y == qa || info.z == qa) return;
+        if (qkin && info.w) return;
+        const int32_t p = t.leaf_prim[lpos];
         emit(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
       } else {
-        if (p <= q) return;
-        int32_t pa = T.edges[2 * (int64_t)p], pb = T.edges[2 * (int64_t)p + 1];
-        if (pa == qa || pa == qb || pb == qa || pb == qb) return;
-        if (qkin && T.ekin[p]) return;
-        emit(pair_key(1, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
+        // each EE pair is found once, from the edge earlier in Morton order
+        if (lpos <= qpos) return;
+        if (info.x == qa || info.x == qb || info.y == qa || info.y == qb) return;
+        if (qkin && info.w) return;
+        const int32_t p = t.leaf_prim[lpos];
+        const uint32_t lo = (uint32_t)(p < q ? p : q), hi = (uint32_t)(p < q ? q : p);
+        emit(pair_key(1, lo, hi, T.bits_i, T.bits_j), cand, n_cand, cap, st);
       }
     };
     if (t.n == 1) {
@@ -255,9 +277,12 @@ __global__ void __launch_bounds__(128) k_query(Bvh t, PrimKind qkind, Topo T, co
       if (box_overlap(b, b + 3, qlo, qhi)) leaf(0);
       continue;
     }
-    int32_t stack[64];
+    // stack of (node, last leaf position under it); EE queries skip subtrees that lie
+    // entirely at or before their own leaf
+    int32_t stack[64], smax[64];
     int sp = 0;
-    stack[sp++] = 0;
+    stack[sp] = 0;
+    smax[sp++] = (int32_t)(t.n - 1);
     // a tree of n leaves has n-1 internal nodes, each popped at most once
     int64_t visits = 0;
     while (sp > 0) {
@@ -265,23 +290,25 @@ __global__ void __launch_bounds__(128) k_query(Bvh t, PrimKind qkind, Topo T, co
         raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
         break;
       }
-      int32_t node = stack[--sp];
+      --sp;
+      const int32_t node = stack[sp];
+      const int32_t nmax = smax[sp];
       const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
-      float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-      int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
-      float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-      float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-      int32_t c0 = f3.x, c1 = f3.y, kin = f3.z;
-      bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1));
-      bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2));
+      const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+      const int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
+      const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+      const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+      const int32_t c0 = f3.x, c1 = f3.y, kin = f3.z, split = f3.w;
+      const bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
+      const bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
       if (o0) {
         if (c0 < 0) leaf(~c0);
-        else if (sp < 64) stack[sp++] = c0;
+        else if (sp < 64) { stack[sp] = c0; smax[sp++] = split; }
         else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
       }
       if (o1) {
         if (c1 < 0) leaf(~c1);
-        else if (sp < 64) stack[sp++] = c1;
+        else if (sp < 64) { stack[sp] = c1; smax[sp++] = nmax; }
         else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
       }
     }
@@ -299,19 +326,33 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   int which = radix_sort_u64(t.keys, t.vals, t.keys_alt, t.vals_alt, t.n_dev, t.n, 30, sort_hist, s);
   const uint64_t* sk = which ? t.keys_alt : t.keys;
   const uint32_t* sv = which ? t.vals_alt : t.vals;
+  t.sorted = sv;
   cudaMemsetAsync(t.nodes, 0, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1), s);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
   if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent);
   launch(k_refit, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv, t.leaf_box, t.nodes, t.parent, t.leaf_prim,
-                                              t.refit_flag);
+         t.leaf_info, t.refit_flag);
+  t.built = true;
 }
 
-void bvh_query(const Bvh& t, PrimKind qkind, const Topo& topo, const double* x4, const double* dx4, double pad,
-               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s) {
+void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s) {
+  launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
+  launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, static_cast<const double*>(nullptr), topo.nv, bounds_ws);
+}
+
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s) {
   if (t.n <= 0) return;
-  int64_t nq = qkind == kVertex ? topo.nv : topo.ne;
+  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, x4, dx4, t.leaf_box);
+  cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
+  launch(k_refit, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted, static_cast<const float*>(t.leaf_box),
+         t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim, t.leaf_info, t.refit_flag);
+}
+
+void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
+               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s) {
+  const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
-  launch(k_query, blocks_for(nq, 16, 128), 128, 0, s, t, qkind, topo, x4, dx4, pad, cand, n_cand, cap, st);
+  launch(k_query, blocks_for(nq, 24, 128), 128, 0, s, tri, edge, topo, x4, dx4, pad, cand, n_cand, cap, st);
 }
 
 }  // namespace eipc

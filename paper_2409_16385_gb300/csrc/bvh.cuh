@@ -14,7 +14,7 @@ struct alignas(16) BvhNode {
   float lo1[3], hi1[3];
   int32_t c0, c1;
   int32_t kin;   // bit 0 / bit 1: every primitive under child 0 / 1 is kinematic
-  int32_t pad;
+  int32_t split; // last leaf position under child 0 (child 1 ends where its parent ends)
 };
 
 struct Bvh {
@@ -23,10 +23,13 @@ struct Bvh {
   BvhNode* nodes;        // [n-1]
   int32_t* parent;       // [2n-1]: internal i at i, leaf l at n-1+l
   int32_t* leaf_prim;    // [n]
+  int4* leaf_info;       // [n] per leaf (Morton order): vertex ids (-1 if unused), kinematic flag
   float* leaf_box;       // [6n], by primitive id (lo xyz, hi xyz)
   int32_t* refit_flag;   // [n]
   uint64_t* keys;        // [n] Morton keys (sorted in place)
   uint32_t* vals;        // [n]
+  const uint32_t* sorted; // Morton order of the last build (points into vals / vals_alt)
+  bool built;            // a hierarchy exists and can be refitted
   uint64_t* keys_alt;    // [n]
   uint32_t* vals_alt;    // [n]
 };
@@ -54,11 +57,20 @@ __host__ __device__ __forceinline__ uint64_t pair_key(int type, uint32_t i, uint
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s);
 
-// Traverse: queries of `qkind` (vertices against a triangle tree -> PT, edges against an
-// edge tree -> EE with j > i), query boxes inflated by `pad` (contact) or swept by dx4
-// (CCD).  Candidates (non-incident, not all kinematic) are appended as pair keys to
-// cand[0..cap) with the running count in *n_cand; overflow raises CAND_OVERFLOW.
-void bvh_query(const Bvh& t, PrimKind qkind, const Topo& topo, const double* x4, const double* dx4,
-               double pad, uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s);
+// Scene box of the positions x4 into bounds_ws (6 order-preserving ints: lo xyz, hi xyz).
+void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s);
+
+// Refit the hierarchy of the last bvh_build with new leaf boxes (x4, optionally swept by
+// dx4): any binary tree over the primitives with conservative boxes gives the same exact
+// candidate set, so the Morton sort and hierarchy can be reused while the topology stays.
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s);
+
+// Traverse both trees in one launch: every vertex box (grown by `pad`, or swept by dx4)
+// against the triangle tree -> PT candidates, every edge box against the edge tree -> EE
+// candidates with j > i.  Incident pairs and all-kinematic pairs are skipped; candidates
+// are appended as pair keys to cand[0..cap) with the running count in *n_cand, and an
+// overflow raises CAND_OVERFLOW.
+void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
+               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s);
 
 }  // namespace eipc

@@ -138,4 +138,72 @@ __device__ __forceinline__ double ee_distance(V3 a0, V3 a1, V3 b0, V3 b1, Stenci
   return best;
 }
 
+// ---------------------------------------------------------------- FP32 screen
+// "Certainly farther than r" tests in FP32 only (62x the FP64 rate on GB300), on an FP32
+// copy of the positions (absolute coordinates within a 0.25 m scene: each coordinate is off
+// by <= 1.5e-8 m, each difference by <= 3e-8 m).  A pair is declared far only if its FP32
+// squared distance exceeds r^2 (1 + 4e-3), i.e. d > r (1 + 2e-3), a margin of >= 4e-7 m
+// for r >= 2e-4 m against distance errors of order 1e-7 m.  Misclassifying the closest
+// region can only (a) report a lower bound (plane / line distance when the projection is
+// wrongly found inside), or (b) report a boundary value whose excess is bounded by the
+// curvature times the squared parameter error.  Stencils whose parameter solve is not
+// well conditioned (|n|^2 <= 0.1 |e1|^2 |e2|^2: skinny triangles, edges within 18 degrees
+// of parallel) are never screened.  Every pair not screened goes through the exact FP64
+// test, so the kept set is unchanged.
+struct F3 {
+  float x, y, z;
+};
+__device__ __forceinline__ F3 load_xf(const float* __restrict__ x4f, int32_t v) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(x4f) + v);
+  return {a.x, a.y, a.z};
+}
+__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ F3 operator*(F3 a, float s) { return {a.x * s, a.y * s, a.z * s}; }
+__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ F3 fcross(F3 a, F3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+// |w - t e|^2 over t in [0,1] (w relative to the segment start)
+__device__ __forceinline__ float fseg_d2(F3 w, F3 e) {
+  float t = fdot(w, e) / fdot(e, e);
+  t = fminf(fmaxf(t, 0.f), 1.f);
+  const F3 r = w - e * t;
+  return fdot(r, r);
+}
+
+__device__ __forceinline__ bool pt_far_f32(F3 p, F3 t0, F3 t1, F3 t2, float r2m) {
+  const F3 e1 = t1 - t0, e2 = t2 - t0, w = p - t0;
+  const F3 n = fcross(e1, e2);
+  const float nn = fdot(n, n);
+  if (!(nn > 0.1f * fdot(e1, e1) * fdot(e2, e2))) return false;
+  const float b1 = fdot(fcross(w, e2), n) / nn;
+  const float b2 = fdot(fcross(e1, w), n) / nn;
+  float d2;
+  if (b1 >= 0.f && b2 >= 0.f && b1 + b2 <= 1.f) {
+    const float h = fdot(w, n);
+    d2 = h * h / nn;
+  } else {
+    d2 = fminf(fseg_d2(w, e1), fminf(fseg_d2(w - e1, e2 - e1), fseg_d2(w, e2)));
+  }
+  return d2 > r2m;
+}
+
+__device__ __forceinline__ bool ee_far_f32(F3 a0, F3 a1, F3 b0, F3 b1, float r2m) {
+  const F3 ea = a1 - a0, eb = b1 - b0, w = a0 - b0;
+  const float A = fdot(ea, ea), C = fdot(eb, eb);
+  const F3 n = fcross(ea, eb);
+  const float nn = fdot(n, n);
+  if (!(nn > 0.1f * A * C)) return false;
+  const float B = fdot(ea, eb), D = fdot(ea, w), E = fdot(eb, w);
+  const float s = (B * E - C * D) / nn, t = (A * E - B * D) / nn;
+  float d2;
+  if (s >= 0.f && s <= 1.f && t >= 0.f && t <= 1.f) {
+    const float h = fdot(w, n);
+    d2 = h * h / nn;
+  } else {
+    d2 = fminf(fminf(fseg_d2(w, eb), fseg_d2(a1 - b0, eb)), fminf(fseg_d2(b0 - a0, ea), fseg_d2(b1 - a0, ea)));
+  }
+  return d2 > r2m;
+}
+
 }  // namespace eipc

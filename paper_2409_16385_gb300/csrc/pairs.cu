@@ -12,7 +12,8 @@ namespace {
 __global__ void __launch_bounds__(kBlock) k_embed(int64_t nv, const int32_t* __restrict__ idx,
                                                   const double* __restrict__ w, const double* __restrict__ xk4,
                                                   const double* __restrict__ q, double* __restrict__ out,
-                                                  int padded, int displacement, DevStatus* st) {
+                                                  int padded, int displacement, float* __restrict__ outf,
+                                                  DevStatus* st) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     const int4 id = __ldg(reinterpret_cast<const int4*>(idx) + v);
     double r[3];
@@ -34,6 +35,9 @@ __global__ void __launch_bounds__(kBlock) k_embed(int64_t nv, const int32_t* __r
     if (padded) {
       reinterpret_cast<double2*>(out)[2 * v] = make_double2(r[0], r[1]);
       reinterpret_cast<double2*>(out)[2 * v + 1] = make_double2(r[2], 0.0);
+      if (outf)
+        reinterpret_cast<float4*>(outf)[v] =
+            make_float4(__double2float_rn(r[0]), __double2float_rn(r[1]), __double2float_rn(r[2]), 0.f);
     } else {
       for (int k = 0; k < 3; ++k) out[3 * v + k] = r[k];
     }
@@ -57,6 +61,53 @@ __device__ __forceinline__ double stencil_d2(const Topo& T, const double* __rest
   return ee_distance<false>(load_x(x4, ea[0]), load_x(x4, ea[1]), load_x(x4, eb[0]), load_x(x4, eb[1]), nullptr);
 }
 
+__device__ __forceinline__ float ord_to_float(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// FP32 screen (geometry.cuh) over all candidates; the ones it cannot prove farther than
+// dhat are compacted into `out` for the exact FP64 test.  The screen is used only when the
+// scene's largest coordinate M keeps FP32 rounding (M 2^-24 per coordinate) 40 times below
+// the 2e-3 dhat margin; otherwise every candidate is passed on.
+__global__ void __launch_bounds__(kBlock) k_screen(Topo T, const float* __restrict__ x4f,
+                                                   const int32_t* __restrict__ bounds, const uint64_t* __restrict__ cand,
+                                                   const int64_t* n_cand, int64_t cap, double dhat,
+                                                   uint64_t* __restrict__ out, int64_t* n_out) {
+  const int64_t n = clamp_count(n_cand, cap);
+  float M = 0.f;
+  for (int k = 0; k < 6; ++k) M = fmaxf(M, fabsf(ord_to_float(bounds[k])));
+  const bool use = 40.0 * (double)M * 5.9604644775390625e-8 < 2e-3 * dhat;
+  const float r2m = (float)(dhat * dhat * (1.0 + 4e-3));
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
+    const int64_t k = base + threadIdx.x;
+    bool pass = false;
+    uint64_t key = 0;
+    if (k < n) {
+      key = cand[k];
+      pass = true;
+      if (use) {
+        const int32_t j = (int32_t)(key & ((1ull << T.bits_j) - 1));
+        const int32_t i = (int32_t)((key >> T.bits_j) & ((1ull << T.bits_i) - 1));
+        const int type = (int)(key >> (T.bits_i + T.bits_j));
+        if (type == 0) {
+          const int32_t* f = T.tris + 3 * (int64_t)j;
+          pass = !pt_far_f32(load_xf(x4f, i), load_xf(x4f, f[0]), load_xf(x4f, f[1]), load_xf(x4f, f[2]), r2m);
+        } else {
+          const int32_t* ea = T.edges + 2 * (int64_t)i;
+          const int32_t* eb = T.edges + 2 * (int64_t)j;
+          pass = !ee_far_f32(load_xf(x4f, ea[0]), load_xf(x4f, ea[1]), load_xf(x4f, eb[0]), load_xf(x4f, eb[1]), r2m);
+        }
+      }
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, pass);
+    if (mask) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(n_out), (unsigned long long)__popc(mask));
+      b = __shfl_sync(0xffffffffu, b, 0);
+      if (pass) out[(int64_t)b + __popc(mask & ((1u << lane) - 1u))] = key;
+    }
+  }
+}
+
 // Exact filter of the broad-phase candidates: keep 0 < d < dhat, flag d <= 0.
 __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restrict__ x4,
                                                    const uint64_t* __restrict__ cand, const int64_t* n_cand,
@@ -74,7 +125,7 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
       key = cand[k];
       int type; int32_t i, j;
       unpack(key, T.bits_i, T.bits_j, &type, &i, &j);
-      double d2 = stencil_d2(T, x4, type, i, j);
+      const double d2 = stencil_d2(T, x4, type, i, j);
       if (!(d2 > 0.0)) {
         raise_flag(st, EIPC_FLAG_PENETRATION);
       } else {
@@ -126,8 +177,9 @@ __global__ void __launch_bounds__(kBlock) k_emit_pairs(Topo T, const uint64_t* _
 
 void embed_launch(const eipc_scene* sc, const double* q, double* out, int out_padded, int displacement,
                   cudaStream_t s) {
+  float* outf = (out_padded && out == sc->x4) ? sc->x4f : nullptr;   // FP32 copy for the screen
   launch(k_embed, blocks_for(sc->nv), kBlock, 0, s, sc->nv, sc->cage_idx, sc->w, sc->x_kin4, q, out, out_padded,
-                                                 displacement, sc->status);
+         displacement, outf, sc->status);
 }
 
 void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const eipc_pairs& out, cudaStream_t s) {
@@ -135,20 +187,35 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   int64_t* n_cand = sc->counters + kCntCand;
   int64_t* n_surv = sc->counters + kCntSurv;
   cudaMemsetAsync(sc->counters + kCntCand, 0, 2 * sizeof(int64_t), s);
-  // PT: every vertex (box grown by dhat) against the triangle tree
-  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+  // LBVHs over triangles and edges, then one traversal: vertex boxes grown by dhat against
+  // the triangle tree (PT) and edge boxes grown by dhat against the edge tree (EE, j > i)
+  // full rebuild every `rebuild_interval` calls, refit of the same hierarchy in between (the
+  // candidate set is exact for any hierarchy; only traversal cost depends on its quality)
+  const bool rebuild = !sc->tri_bvh.built || !sc->edge_bvh.built || sc->contact_refits + 1 >= sc->rebuild_interval;
+  if (rebuild) {
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+    sc->contact_refits = 0;
+  } else {
+    sc->timers->start(kKBvh, s);
+    scene_bounds(sc->topo, sc->x4, sc->bounds_ws, s);    // the narrow-phase screen reads it
+    bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, s);
+    bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s);
+    sc->timers->stop(kKBvh, s);
+    ++sc->contact_refits;
+  }
   EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->tri_bvh, kVertex, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
+             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s));
-  // EE: every edge (box grown by dhat) against the edge tree, j > i
-  EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
-  EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s));
-  EIPC_TIMED(sc, kKNarrow, s,
-             (launch(k_narrow, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, sc->x4, sc->cand, n_cand,
-                                                                        sc->cand_cap, p.dhat, sc->skeys, sc->svals,
-                                                                        sc->sd, n_surv, sc->status)));
+  int64_t* n_cand2 = sc->counters + 15;
+  cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
+  sc->timers->start(kKNarrow, s);
+  launch(k_screen, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, static_cast<const float*>(sc->x4f),
+         static_cast<const int32_t*>(sc->bounds_ws), static_cast<const uint64_t*>(sc->cand),
+         static_cast<const int64_t*>(n_cand), sc->cand_cap, p.dhat, sc->cand2, n_cand2);
+  launch(k_narrow, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, sc->x4, sc->cand2, n_cand2, sc->cand_cap,
+         p.dhat, sc->skeys, sc->svals, sc->sd, n_surv, sc->status);
+  sc->timers->stop(kKNarrow, s);
   sc->timers->start(kKPairSort, s);
   int bits = 1 + sc->topo.bits_i + sc->topo.bits_j;
   int which = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, n_surv, sc->cand_cap, bits,

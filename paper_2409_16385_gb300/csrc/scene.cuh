@@ -20,12 +20,14 @@ struct eipc_scene {
   // positions (padded, 4 doubles per vertex)
   double* x4;
   double* dx4;
+  float* x4f;            // [nv*4] FP32 copy of x4 for the narrow-phase screen
   // broad phase
   eipc::Bvh tri_bvh, edge_bvh;
   int32_t* bounds_ws;
   uint32_t* sort_hist;
   int64_t cand_cap;
   uint64_t* cand;
+  uint64_t* cand2;       // candidates the FP32 screen passed on to the FP64 test
   int64_t* counters;     // [16] device counters (see kCnt*)
   // narrow phase survivors
   uint64_t* skeys;
@@ -65,6 +67,8 @@ struct eipc_scene {
   int64_t* scan_partial; // [kScanBlocks+1]
   double* sum_partial;   // [kScanBlocks]
   int bits_h, bits_g;    // key widths of the reduction sorts
+  int rebuild_interval;  // contact LBVH: full rebuild every this many build_candidates calls
+  int contact_refits;    // refits since the last full rebuild
   eipc::DevStatus* status;
   eipc::Timers* timers;   // host-side event timers (off unless enabled)
 };

@@ -163,14 +163,24 @@ __global__ void __launch_bounds__(256) k_scan_partial(const int64_t* __restrict_
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// exclusive scan of the kScanBlocks partial sums by one warp (chunks of 32 with a carry)
 __global__ void k_scan_partials(int64_t* partial, int64_t* total) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    int64_t run = 0;
-    for (int b = 0; b < kScanBlocks; ++b) {
-      int64_t c = partial[b];
-      partial[b] = run;
-      run += c;
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x >= 32 || blockIdx.x != 0) return;
+  int64_t run = 0;
+  for (int b0 = 0; b0 < kScanBlocks; b0 += 32) {
+    const int b = b0 + lane;
+    const int64_t c = b < kScanBlocks ? partial[b] : 0;
+    int64_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
+    if (b < kScanBlocks) partial[b] = run + x - c;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) {
     partial[kScanBlocks] = run;
     if (total) *total = run;
   }

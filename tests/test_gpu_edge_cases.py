@@ -109,3 +109,61 @@ def test_accd_iteration_cap_keeps_alpha_safe():
     ao = oracle.accd(sc, oracle.embed(sc, q), oracle.embed(sc, sc.dq(0), displacement=True), max_iter=1)
     assert ao["capped"] and "ACCD_CAP" in st["names"]
     assert a <= ao["alpha"] and ao["alpha"] - a <= 1e-6
+
+
+def _rot(rng):
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return Q
+
+
+def test_pairs_at_the_dhat_boundary_match_the_oracle():
+    """Hundreds of PT (face region) and EE (crossing, down to 1 degree from parallel)
+    stencils placed at (1 -+ 1e-4) and (1 -+ 3e-3) dhat: the kept set must be exactly the
+    oracle's, whatever shortcuts the narrow phase takes."""
+    from paper_2409_16385_gb300 import ContactScene
+    rng = np.random.default_rng(11)
+    dhat = 1e-3
+    verts, tris, emb = [], [], []
+    for k in range(240):
+        o = np.array([0.02 * (k % 20), 0.02 * (k // 20), 0.0])
+        R = _rot(rng)
+        rel = [1 - 3e-3, 1 - 1e-4, 1 + 1e-4, 1 + 3e-3][k % 4]
+        if k % 2 == 0:
+            T = rng.normal(size=(3, 3)) * 2e-3
+            T[:, 2] = 0.0
+            foot = rng.dirichlet([2, 2, 2]) @ T
+            p = foot + np.array([0, 0, rel * dhat])
+            up = np.array([p, p + [1e-3, 0, 3e-3], p + [0, 1e-3, 3e-3]])
+        else:
+            ang = np.radians([1.0, 5.0, 30.0, 90.0][(k // 2) % 4])
+            T = np.array([[-1e-3, 0, 0], [1e-3, 0, 0], [0, -1e-3, 0]])
+            h = rel * dhat
+            dirn = np.array([np.cos(ang), np.sin(ang), 0.0])
+            up = np.array([-1e-3 * dirn + [0, 0, h], 1e-3 * dirn + [0, 0, h], [0, 3e-4, h + 2e-3]])
+        base = len(verts)
+        for v in T:
+            verts.append(R @ v + o); emb.append(False)
+        for v in up:
+            verts.append(R @ v + o); emb.append(True)
+        tris += [[base, base + 1, base + 2], [base + 3, base + 4, base + 5]]
+    verts = np.array(verts); tris = np.array(tris, np.int32); emb = np.array(emb)
+    nv = len(verts)
+    idx = np.full((nv, 4), -1, np.int32); w = np.zeros((nv, 4))
+    node_of = np.cumsum(emb) - 1
+    idx[emb, 0] = node_of[emb]; idx[emb, 1:] = node_of[emb][:, None]
+    w[emb, 0] = 1.0
+    xk = np.where(emb[:, None], 0.0, verts)
+    sc = scenes.Scene(name="boundary", tris=tris, edges=scenes.edges_of(tris), cage_idx=idx, w=w, x_kin=xk,
+                      Ns=int(emb.sum()), cage_tets=np.zeros((0, 4), np.int32), q_rest=verts[emb].copy(),
+                      body=np.zeros(nv, np.int32), params=dict(scenes.DEFAULT_PARAMS, dhat=dhat))
+    q = verts[emb].copy()
+    cs = ContactScene(sc, pair_capacity=1 << 14, bsr_capacity=1 << 14)
+    g = cs.build_candidates(_t(q)).host()
+    torch.cuda.synchronize()
+    assert cs.status()["flags"] == 0
+    o = oracle.pairs(sc, oracle.embed(sc, q))
+    kg = list(zip(g["type"].tolist(), g["i"].tolist(), g["j"].tolist()))
+    ko = list(zip(o["type"].tolist(), o["i"].tolist(), o["j"].tolist()))
+    assert kg == ko
+    near = np.abs(o["d"] / dhat - 1.0) < 5e-3
+    assert near.sum() >= 100          # the boundary cases really are in the set

@@ -173,3 +173,27 @@ def test_bitwise_repeatable():
         h = H.host()
         outs.append((E.cpu().numpy().tobytes(), g.cpu().numpy().tobytes(), h["val"].tobytes(), h["col"].tobytes()))
     assert outs[0] == outs[1] == outs[2]
+
+
+def test_refitted_and_rebuilt_hierarchies_agree_bitwise():
+    """The contact set and the reduced outputs do not depend on whether the LBVH was
+    rebuilt for these positions or refitted from another configuration's hierarchy."""
+    from paper_2409_16385_gb300 import ContactScene
+    sc = _scene(2, True)
+    a = ContactScene(sc, pair_capacity=1 << 18, bsr_capacity=1 << 18)
+    b = ContactScene(sc, pair_capacity=1 << 18, bsr_capacity=1 << 18)
+    b.set_rebuild_interval(1)
+    a.set_rebuild_interval(1000)
+    a.build_candidates(_t(sc.iterate(0)))          # hierarchy from another configuration
+    a.build_candidates(_t(sc.iterate(19)))
+    q = _t(sc.iterate(11))
+    outs = []
+    for cs in (a, b):
+        pr = cs.build_candidates(q)
+        E, g, H = cs.eval_contact(q, pr, None)
+        h = H.host()
+        ph = pr.host()
+        outs.append((ph["type"].tobytes(), ph["i"].tobytes(), ph["j"].tobytes(), ph["d"].tobytes(),
+                     E.cpu().numpy().tobytes(), g.cpu().numpy().tobytes(), h["val"].tobytes()))
+        assert cs.status()["flags"] == 0
+    assert outs[0] == outs[1]
