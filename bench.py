@@ -34,7 +34,7 @@ METRIC = "contact pairs/s (barrier+grad+Hess into subspace)"
 UNIT = "pairs/s"
 WORKLOAD = "bubble_grasp"
 
-# Algorithmic cost per unit of the kernels the roofline may name (see DESIGN.md):
+# Algorithmic cost per unit of the kernels the roofline may name:
 #  eval_barrier: FP64 flops per contact pair; ccd_advance: FP64 flops per candidate;
 #  the rest: DRAM bytes per unit (minimum traffic of the kernel's inputs and outputs).
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--json-out", default="")
     ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
     ap.add_argument("--rec-cap", type=int, default=0, help="reduction record capacity (0: library default)")
+    ap.add_argument("--workload", choices=["bubble_grasp", "batched"], default="bubble_grasp",
+                    help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step")
+    ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain per-scene comparison")
+    ap.add_argument("--retune", action="store_true", help="batched: ignore the autotuner cache")
     return ap.parse_args()
 
 
@@ -126,13 +130,11 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# Algorithmic work per unit ("Roofline"):
-#   eval_barrier  FP64 flops per contact pair, counted from the kernel's arithmetic
+# Algorithmic work per unit:
+#   eval_barrier  FP64 flops per contact pair, counted by ncu on the bubble-grasp workload
+#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 460.1e6 / 115,559)
 #   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-# eval_barrier: FP64 flops per contact pair counted by ncu on this workload
-# (2 x DFMA + DMUL + DADD thread instructions / pairs: 460.1e6 / 115,559), see
-# profiles/eval_barrier_bubble_grasp.md
 FP64_FLOPS_PER_PAIR = 3980.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
@@ -483,12 +485,343 @@ def run_e2e(cs, sc, Q, DQ, lag_of, t0, K, flush, dev):
                 ms_per_step=tot_ms / K)
 
 
+# --------------------------------------------------------------------------- batched
+
+BATCH_WORKLOAD = "batched_grasp_256"
+
+
+def _grow(caps, need):
+    """Capacities after an overflow: at least 1.3x what the device reported as needed."""
+    names = ("pair", "cand", "rec", "bsr")
+    out = dict(caps)
+    for n, v in zip(names, need):
+        if v > 0:
+            out[n] = max(out[n], int(1.3 * v) + 1024)
+    return out
+
+
+class _Stage:
+    """One contact stage of a (batched) scene through the C ABI, on preallocated buffers so
+    that it can be captured in a CUDA graph: static inputs q, dq; outputs E, g_r, H_r,
+    per-group energy, alpha and per-group alpha."""
+
+    def __init__(self, sc, caps, groups, dev):
+        import torch
+        from paper_2409_16385_gb300 import ContactScene
+        self.sc, self.caps = sc, caps
+        self.cs = ContactScene(sc, pair_capacity=caps["pair"], bsr_capacity=caps["bsr"], cand_capacity=caps["cand"],
+                               rec_capacity=caps["rec"])
+        ng = 1
+        if groups is not None:
+            self.cs.set_groups(groups[0], groups[1])
+            ng = groups[1]
+        f64 = dict(dtype=torch.float64, device=dev)
+        self.q = torch.zeros((sc.Ns, 3), **f64)
+        self.dq = torch.zeros((sc.Ns, 3), **f64)
+        self.pairs, self.lag, self.H = self.cs.new_pairs(), self.cs.new_lag(), self.cs.new_bsr()
+        self.E = torch.zeros(1, **f64)
+        self.g = torch.zeros((sc.Ns, 3), **f64)
+        self.Eg = torch.zeros(ng, **f64)
+        self.ag = torch.zeros(ng, **f64)
+        self.x = torch.zeros((sc.Nv, 3), **f64)
+        self.dx = torch.zeros((sc.Nv, 3), **f64)
+        self.alpha = torch.zeros(1, **f64)
+        self.ncand = torch.zeros(1, dtype=torch.int64, device=dev)
+
+    def __call__(self, lag_step):
+        cs = self.cs
+        cs.build_candidates(self.q, out=self.pairs)
+        if lag_step:
+            cs.friction_lag(self.q, self.pairs, out=self.lag)
+        cs.eval_contact(self.q, self.pairs, self.lag, E=self.E, g_r=self.g, H=self.H)
+        cs.group_energy(out=self.Eg)
+        cs.embed(self.q, out=self.x)
+        cs.embed(self.dq, out=self.dx, displacement=True)
+        cs.accd_toi(self.x, self.dx, alpha=self.alpha, n_candidates=self.ncand)
+        cs.group_alpha(out=self.ag)
+
+
+def _sized_stage(sc, caps, groups, dev, Q, DQ, lag_of, ts):
+    """A _Stage whose capacities hold every iterate in `ts` (grown and rebuilt on overflow)."""
+    import torch
+    for _ in range(4):
+        st = _Stage(sc, caps, groups, dev)
+        need = [0, 0, 0, 0]
+        bad = 0
+        for t in ts:
+            st.q.copy_(Q[lag_of[t]])
+            st(True)
+            st.q.copy_(Q[t]); st.dq.copy_(DQ[t])
+            st(False)
+            torch.cuda.synchronize()
+            s = st.cs.status()
+            bad |= s["flags"] & ~64
+            need = [max(a, b) for a, b in zip(need, s["needed"])]
+        if not bad:
+            return st
+        if bad & ~(2 | 4 | 8 | 16 | 128):
+            raise RuntimeError(f"device status {s}")
+        st.cs.close()
+        del st
+        caps = _grow(caps, need)
+        if need[0] == 0 and bad & 128:
+            caps["pair"] *= 2
+    raise RuntimeError("capacities did not converge")
+
+
+def run_batched(args, ws, rank, local):
+    """256 independent grasp scenes (surface sizes log-uniform in [2k, 50k] triangles, own
+    closing phase each) in one scene with one group per scene.  One step is one CUDA graph
+    replay of the whole contact stage of all scenes; the plain per-scene path (one
+    ContactScene per scene, called scene after scene, eager) runs the same iterates beside
+    it.  Metric: contact pairs evaluated per second over whole steps."""
+    import torch
+    import torch.distributed as dist
+    from paper_2409_16385_gb300 import autotune, binding, scenes
+
+    dev = torch.device("cuda", local)
+    lib = binding.load()
+    t_gen = time.perf_counter()
+    b = scenes.make_config(4, small=args.quick)
+    gen_s = time.perf_counter() - t_gen
+    G, n_it = b.n_scenes, b.n_iterates
+    lag_of = [b.lag_of(t) for t in range(n_it)]
+    Q = torch.tensor(np.stack([b.iterate(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    DQ = torch.tensor(np.stack([b.dq(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    K, W = args.steps, args.warmup
+    t0 = W % n_it
+    size_ts = sorted({t0, (t0 + 3) % n_it, (t0 + 29) % n_it, (t0 + 47) % n_it})
+    caps = dict(pair=1 << 22, bsr=1 << 21, cand=args.cand_cap, rec=args.rec_cap or (1 << 27))
+    if args.quick:
+        caps = dict(pair=1 << 20, bsr=1 << 20, cand=args.cand_cap, rec=args.rec_cap or (1 << 24))
+    st = _sized_stage(b, caps, (b.body, G), dev, Q, DQ, lag_of, size_ts)
+
+    # ---- autotuned launch shapes (cached per device and workload)
+    def tune_stage():
+        st(False)
+    st.q.copy_(Q[t0]); st.dq.copy_(DQ[t0])
+    tuned = autotune.tune(st.cs, tune_stage, f"{BATCH_WORKLOAD if not args.quick else 'batched_grasp_16'}",
+                          force=args.retune)
+
+    # ---- one graph per (lag step, hierarchy rebuild) combination
+    R = 8
+    graphs, kernels_per_graph = {}, {}
+    side = torch.cuda.Stream()
+    for lag_step in (False, True):
+        for rebuild in (True, False):
+            st.cs.set_rebuild_interval(1 if rebuild else 1 << 30)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                st(lag_step)                      # warm-up on the side stream
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            n0 = lib.eipc_launch_count()
+            with torch.cuda.graph(g):
+                st(lag_step)
+            kernels_per_graph[(lag_step, rebuild)] = lib.eipc_launch_count() - n0
+            graphs[(lag_step, rebuild)] = g
+    torch.cuda.synchronize()
+
+    def replay(k, t):
+        st.q.copy_(Q[t]); st.dq.copy_(DQ[t])
+        key = (lag_of[t] == t, k % R == 0)
+        graphs[key].replay()
+        return kernels_per_graph[key]
+
+    # lag state of the first timed iterates, then warm-up replays
+    start_t = (t0 - W) % n_it
+    st.q.copy_(Q[lag_of[start_t]])
+    st(True)
+    for k in range(W):
+        replay(k, (start_t + k) % n_it)
+    torch.cuda.synchronize()
+    s0 = st.cs.status()
+    if s0["flags"] & ~64:
+        raise RuntimeError(f"device status after warm-up: {s0}")
+
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    counts = torch.zeros((K, 2), dtype=torch.int64, device=dev)
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    launches = 0
+    for k in range(K):
+        t = (t0 + k) % n_it
+        flush.zero_()
+        evs[k][0].record(stream)
+        launches += replay(W + k, t)
+        evs[k][1].record(stream)
+        counts[k, 0].copy_(st.pairs.count[0])
+        counts[k, 1].copy_(st.ncand[0])
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    s1 = st.cs.status()
+    if s1["flags"] & ~64:
+        raise RuntimeError(f"device status after the timed steps: {s1}")
+    step_ms = np.array([a.elapsed_time(c) for a, c in evs])
+    cnt = counts.cpu().numpy()
+    total_s, total_pairs, total_cand = step_ms.sum() / 1e3, float(cnt[:, 0].sum()), float(cnt[:, 1].sum())
+    if ws > 1:
+        tt = torch.tensor([total_s, total_pairs, total_cand], dtype=torch.float64, device=dev)
+        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        total_s_all, total_pairs_all, total_cand_all = float(mx[0]), float(sm[1]), float(sm[2])
+    else:
+        total_s_all, total_pairs_all, total_cand_all = total_s, total_pairs, total_cand
+    value = total_pairs_all / total_s_all
+    Eg_last = st.Eg.cpu().numpy()
+    ag_last = st.ag.cpu().numpy()
+
+    # ---- dominant kernel and its roofline: the same steps eagerly, kernel timers on
+    st.cs.set_rebuild_interval(R)
+    st.cs.timing_enable(None)
+    st.q.copy_(Q[lag_of[t0]]); st(True)
+    for k in range(K):
+        t = (t0 + k) % n_it
+        st.q.copy_(Q[t]); st.dq.copy_(DQ[t])
+        flush.zero_()
+        st(lag_of[t] == t)
+    torch.cuda.synchronize()
+    kt = st.cs.timing_read()
+    st.cs.timing_enable([])
+    dominant = max(kt.items(), key=lambda kv: kv[1][0])[0]
+    dom_ms, dom_n = kt[dominant]
+    roof = roofline_figure(dominant, dom_ms, dom_n, K, total_pairs / K, total_cand / K, b)
+    roof["timed"] = "eager replay of the timed steps with per-kernel CUDA-event timers"
+
+    # ---- end to end: pinned host q, dq in; E per scene, alpha per scene, g_r out
+    e2e = None
+    if not args.no_e2e:
+        qh = [Q[t].cpu().pin_memory() for t in range(n_it)]
+        dqh = [DQ[t].cpu().pin_memory() for t in range(n_it)]
+        Egh = torch.zeros(G, dtype=torch.float64).pin_memory()
+        agh = torch.zeros(G, dtype=torch.float64).pin_memory()
+        gh = torch.zeros((b.Ns, 3), dtype=torch.float64).pin_memory()
+        st.q.copy_(Q[lag_of[t0]]); st(True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot_ms, tot_pairs = 0.0, 0
+        for k in range(K):
+            t = (t0 + k) % n_it
+            flush.zero_()
+            ev0.record(stream)
+            st.q.copy_(qh[t], non_blocking=True)
+            st.dq.copy_(dqh[t], non_blocking=True)
+            graphs[(lag_of[t] == t, k % R == 0)].replay()
+            Egh.copy_(st.Eg, non_blocking=True)
+            agh.copy_(st.ag, non_blocking=True)
+            gh.copy_(st.g, non_blocking=True)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += ev0.elapsed_time(ev1)
+            tot_pairs += int(st.pairs.count.item())
+        e2e = dict(value=tot_pairs / (tot_ms / 1e3), unit=UNIT, h2d_bytes_per_step=2 * b.Ns * 3 * 8,
+                   d2h_bytes_per_step=2 * G * 8 + b.Ns * 3 * 8, ms_per_step=tot_ms / K,
+                   api="q, dq from pinned host memory; per-scene E and alpha and g_r back to pinned host memory")
+
+    # ---- the plain per-scene path on the same iterates
+    plain = None
+    if not args.no_plain:
+        parts = [b.part_scene(s) for s in range(G)]
+        stages = []
+        for s, one in enumerate(parts):
+            n0, ns = b.node_ranges[s]
+            pc = dict(pair=max(1 << 14, 4 * one.Nv), bsr=max(1 << 14, 64 * one.Ns), cand=0,
+                      rec=max(1 << 18, 96 * one.Nv))
+            Qs, DQs = Q[:, n0:n0 + ns], DQ[:, n0:n0 + ns]
+            stages.append((_sized_stage(one, pc, None, dev, Qs, DQs, lag_of, size_ts), Qs, DQs))
+        for stg, Qs, _ in stages:
+            stg.cs.set_rebuild_interval(R)
+            stg.q.copy_(Qs[lag_of[start_t]]); stg(True)
+        for k in range(W):
+            t = (start_t + k) % n_it
+            for stg, Qs, DQs in stages:
+                stg.q.copy_(Qs[t]); stg.dq.copy_(DQs[t]); stg(lag_of[t] == t)
+        torch.cuda.synchronize()
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        pcount = torch.zeros((K, G), dtype=torch.int64, device=dev)
+        l0 = lib.eipc_launch_count()
+        for k in range(K):
+            t = (t0 + k) % n_it
+            flush.zero_()
+            pev[k][0].record(stream)
+            for s, (stg, Qs, DQs) in enumerate(stages):
+                stg.q.copy_(Qs[t]); stg.dq.copy_(DQs[t])
+                stg(lag_of[t] == t)
+                pcount[k, s].copy_(stg.pairs.count[0])
+            pev[k][1].record(stream)
+        torch.cuda.synchronize()
+        pl = lib.eipc_launch_count() - l0
+        pms = np.array([a.elapsed_time(c) for a, c in pev])
+        ppairs = float(pcount.sum().item())
+        for stg, _, _ in stages:
+            if stg.cs.status()["flags"] & ~64:
+                raise RuntimeError("plain path overflowed")
+        # the last iterate's per-scene energy and step bound, against the batch's
+        same_E = all(stg.Eg.item() == Eg_last[s] for s, (stg, _, _) in enumerate(stages))
+        same_a = all(stg.alpha.item() == ag_last[s] for s, (stg, _, _) in enumerate(stages))
+        plain = dict(value=ppairs / (pms.sum() / 1e3), unit=UNIT, ms_per_step=float(pms.mean()),
+                     launches_per_step=pl / K, pairs_per_step=ppairs / K,
+                     last_step_bitwise_equal=dict(energy_per_scene=bool(same_E), alpha_per_scene=bool(same_a)))
+        for stg, _, _ in stages:
+            stg.cs.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        _, t_cal, _ = oracle_sample(b, t0, 1e-4, seed=999)
+        frac = min(1.0 / 12, 1e-4 * 20.0 / max(t_cal, 1e-3))
+        p, dt, c = oracle_sample(b, t0, frac)
+        cpu = dict(value=p / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                   sample=f"iterate {t0}: brute-force contact set of a {frac:.5f} fraction of the batch's vertices "
+                          f"and edges (queries), lagged friction, evaluation and CCD of those queries; "
+                          f"{p} pairs in {dt:.1f} s")
+
+    sizes = [sc.F for sc, _ in b.parts]
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=K, warmup=W,
+                ms_per_step=float(step_ms.mean()), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic (seeded)",
+                config=dict(workload=BATCH_WORKLOAD if not args.quick else "batched_grasp_16", scenes=G,
+                            triangles=b.F, vertices=b.Nv, edges=b.E, cage_nodes=b.Ns,
+                            triangles_per_scene=[int(min(sizes)), int(np.median(sizes)), int(max(sizes))],
+                            dhat=b.params["dhat"], mu=b.params["mu"], parallelism=f"replicas x{ws}",
+                            l2="flushed between steps (256 MiB rewrite)", pairs_per_step=total_pairs / K,
+                            ccd_candidates_per_step=total_cand / K, rebuild_interval=R,
+                            graph="one CUDA graph replay per step (4 graphs: lag step x hierarchy rebuild)"),
+                clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
+                ccd_queries_per_s=total_cand_all / total_s_all, e2e=e2e, cpu_baseline=cpu,
+                plain_per_scene=plain, speedup_vs_plain=(value / plain["value"]) if plain else None,
+                autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"])
+                          for k, v in tuned.items()},
+                kernels_per_graph={f"lag={a},rebuild={c}": int(n) for (a, c), n in kernels_per_graph.items()},
+                capacities=st.caps, scene_generation_s=gen_s,
+                kernel_ms_eager={k: v[0] for k, v in kt.items()})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    st.cs.close()
+
+
 def main():
     args = parse()
     backend = "gloo" if args.impl == "reference" else "nccl"
     ws, rank, local = dist_setup(backend)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "batched":
+        run_batched(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -119,7 +119,8 @@ typedef struct eipc_scene eipc_scene;
  *     whose position is x_kin[3v..3v+2] and which has no reduced DoF;
  *   Ns: number of cage nodes (q has Ns*3 entries);
  *   cand_capacity: broad-phase candidate buffer entries (<= 0: 48 per primitive);
- *   rec_capacity: reduction record entries (<= 0: 2^24).
+ *   rec_capacity: reduction record entries (<= 0: 2^24).  The evaluation holds up to
+ *     min(cand_capacity, max(2^22, rec_capacity / 4)) items (contact + friction pairs).
  * Returns EIPC_ERR_INVALID for inconsistent sizes or out-of-range ids, EIPC_ERR_NOMEM
  * if the device workspace cannot be allocated. */
 eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, const int32_t* tris,
@@ -183,6 +184,30 @@ const char* eipc_kernel_name(int32_t id);
  * well the reused hierarchy fits the current positions.  eipc_accd_toi always refits the
  * last hierarchy with swept boxes. */
 eipc_status eipc_set_rebuild_interval(eipc_scene* scene, int32_t n);
+
+/* Batched scenes.  Several independent scenes concatenated into one eipc_scene (disjoint
+ * vertex and cage-node ranges) run through one set of launches per call; vertex_group[v]
+ * (HOST array [Nv], values in [0, n_groups)) names the scene of each vertex.  Every
+ * triangle and edge must lie inside one group (EIPC_ERR_INVALID otherwise), and pairs
+ * across groups are never formed.  Each scene's g_r and H_r are the rows and columns of its
+ * own cage nodes.  Its energy and step bound come from:
+ *   eipc_group_energy: after eipc_eval_contact, E_groups[g] (device, [n_groups]) is group g's
+ *     share of E, summed in an order fixed by the group's own pairs, so it is bitwise the
+ *     value the same scene gives on its own;
+ *   eipc_group_alpha: after eipc_accd_toi, alpha_groups[g] (device) is group g's step bound.
+ * The scene keeps one group (all of it) until eipc_scene_set_groups is called; the call
+ * synchronises (host-side validation). */
+eipc_status eipc_scene_set_groups(eipc_scene* scene, const int32_t* vertex_group, int32_t n_groups);
+eipc_status eipc_group_energy(eipc_scene* scene, double* E_groups, eipc_stream stream);
+eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_stream stream);
+
+/* Launch shape of a tunable kernel (the autotuner's knobs).  kernel: 0 = per-pair barrier
+ * evaluation, 1 = BVH traversal.  threads per block: 64, 128 (eval) or 64, 128, 256
+ * (traversal); blocks_per_sm: cap on the grid as a multiple of the 152 SMs (1..64);
+ * variant (eval only): 2 = no register cap, 3 = at most 170 registers (3 blocks of 128 per
+ * SM).  Results never depend on the shape. */
+eipc_status eipc_set_launch(eipc_scene* scene, int32_t kernel, int32_t threads, int32_t blocks_per_sm,
+                            int32_t variant);
 
 /* Number of kernel launches the library has enqueued in this process (all scenes). */
 int64_t eipc_launch_count(void);

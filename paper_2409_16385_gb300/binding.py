@@ -20,10 +20,11 @@ _lib = None
 
 EIPC_OK = 0
 FLAGS = {1: "PENETRATION", 2: "PAIR_OVERFLOW", 4: "CAND_OVERFLOW", 8: "REC_OVERFLOW", 16: "BSR_OVERFLOW",
-         32: "NONFINITE", 64: "ACCD_CAP", 128: "LAG_OVERFLOW", 256: "STACK_OVERFLOW"}
+         32: "NONFINITE", 64: "ACCD_CAP", 128: "LAG_OVERFLOW", 256: "STACK_OVERFLOW", 512: "BAD_INDEX"}
 EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_candidates", "eipc_friction_lag",
            "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
-           "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval"]
+           "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
+           "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch"]
 
 
 class Params(ctypes.Structure):
@@ -89,6 +90,14 @@ def load(build_if_missing: bool = True):
     L.eipc_set_rebuild_interval.argtypes = [P, i32]
     L.eipc_set_rebuild_interval.restype = i32
     L.eipc_launch_count.restype = i64
+    L.eipc_scene_set_groups.argtypes = [P, P, i32]
+    L.eipc_scene_set_groups.restype = i32
+    L.eipc_group_energy.argtypes = [P, P, P]
+    L.eipc_group_energy.restype = i32
+    L.eipc_group_alpha.argtypes = [P, P, P]
+    L.eipc_group_alpha.restype = i32
+    L.eipc_set_launch.argtypes = [P, i32, i32, i32, i32]
+    L.eipc_set_launch.restype = i32
     _lib = L
     return L
 
@@ -273,6 +282,39 @@ class ContactScene:
     def set_rebuild_interval(self, n: int):
         """Full LBVH rebuild every n-th build_candidates call, refit in between."""
         _check(self.lib.eipc_set_rebuild_interval(self.handle, int(n)), "eipc_set_rebuild_interval")
+
+    def set_groups(self, vertex_group, n_groups: int):
+        """Split the scene into n_groups independent scenes: vertex_group (host int32 [Nv])
+        holds each vertex's scene id.  Pairs never join two groups, and E and alpha are
+        reported per group by group_energy / group_alpha."""
+        vg = np.ascontiguousarray(vertex_group, np.int32)
+        if vg.shape != (self.Nv,):
+            raise ValueError("vertex_group must have one entry per vertex")
+        _check(self.lib.eipc_scene_set_groups(self.handle, vg.ctypes.data, int(n_groups)), "eipc_scene_set_groups")
+        self.n_groups = int(n_groups)
+
+    def group_energy(self, out=None):
+        """Per-group energy of the last eval_contact call (device f64 [n_groups])."""
+        import torch
+        out = out if out is not None else torch.zeros(getattr(self, "n_groups", 1), dtype=torch.float64,
+                                                      device=self.device)
+        _check(self.lib.eipc_group_energy(self.handle, _ptr(out), _stream()), "eipc_group_energy")
+        return out
+
+    def group_alpha(self, out=None):
+        """Per-group step bound of the last accd_toi call (device f64 [n_groups])."""
+        import torch
+        out = out if out is not None else torch.zeros(getattr(self, "n_groups", 1), dtype=torch.float64,
+                                                      device=self.device)
+        _check(self.lib.eipc_group_alpha(self.handle, _ptr(out), _stream()), "eipc_group_alpha")
+        return out
+
+    LAUNCH_KERNELS = {"eval_barrier": 0, "bvh_query": 1}
+
+    def set_launch(self, kernel: str, threads: int, blocks_per_sm: int, variant: int = 2):
+        """Launch shape of a tunable kernel; results do not depend on it."""
+        _check(self.lib.eipc_set_launch(self.handle, self.LAUNCH_KERNELS[kernel], int(threads), int(blocks_per_sm),
+                                        int(variant)), "eipc_set_launch")
 
     N_TIMERS = 13
 

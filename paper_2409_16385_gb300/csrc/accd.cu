@@ -36,8 +36,10 @@ __global__ void __launch_bounds__(kBlock) k_pad(const double* __restrict__ x, co
   }
 }
 
-__global__ void k_alpha_init(unsigned long long* bits) {
+__global__ void k_alpha_init(unsigned long long* bits, unsigned long long* group_bits, int32_t ng) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *bits = __double_as_longlong(1.0);
+  for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+    group_bits[g] = __double_as_longlong(1.0);
 }
 
 __device__ __forceinline__ double pair_distance(int type, const V3 p[4]) {
@@ -50,7 +52,9 @@ __device__ __forceinline__ double pair_distance(int type, const V3 p[4]) {
 __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __restrict__ x4,
                                                      const double* __restrict__ dx4, const uint64_t* __restrict__ cand,
                                                      const int64_t* n_cand, int64_t cap, double s, int max_iter,
-                                                     unsigned long long* alpha_bits, int64_t* n_adv, DevStatus* st) {
+                                                     unsigned long long* alpha_bits,
+                                                     unsigned long long* __restrict__ group_bits, int64_t* n_adv,
+                                                     DevStatus* st) {
   const int64_t n = clamp_count(n_cand, cap);
   const int lane = threadIdx.x & 31;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
@@ -121,7 +125,11 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
             }
           }
         }
-        if (t < 1.0) atomicMin(alpha_bits, (unsigned long long)__double_as_longlong(t * kMargin));
+        if (t < 1.0) {
+          const unsigned long long tb = (unsigned long long)__double_as_longlong(t * kMargin);
+          atomicMin(alpha_bits, tb);
+          atomicMin(group_bits + T.vgroup[v[0]], tb);   // per-scene bound of a batch
+        }
       }
     }
     const uint32_t m = __ballot_sync(0xffffffffu, adv);
@@ -151,7 +159,7 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
   unsigned long long* abits = reinterpret_cast<unsigned long long*>(sc->counters + 12);
   cudaMemsetAsync(n_cand, 0, sizeof(int64_t), s);
   cudaMemsetAsync(n_adv, 0, sizeof(int64_t), s);
-  launch(k_alpha_init, 1, 32, 0, s, abits);
+  launch(k_alpha_init, blocks_for(sc->n_groups), kBlock, 0, s, abits, sc->group_alpha_bits, sc->n_groups);
   // the hierarchies of the last contact-set build are refitted with swept boxes when they
   // exist (the topology is reused; only the boxes change)
   if (sc->tri_bvh.built)
@@ -164,10 +172,10 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
     EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s));
   EIPC_TIMED(sc, kKQuery, s,
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, sc->dx4, 0.0, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s));
+                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 
-                 sc->topo, sc->x4, sc->dx4, sc->cand, n_cand, sc->cand_cap, p.accd_s, p.accd_max_iter, abits, n_adv,
+                 sc->topo, sc->x4, sc->dx4, sc->cand, n_cand, sc->cand_cap, p.accd_s, p.accd_max_iter, abits, sc->group_alpha_bits, n_adv,
                  sc->status)));
   launch(k_alpha_out, 1, 32, 0, s, abits, alpha, n_adv, n_candidates);
 }

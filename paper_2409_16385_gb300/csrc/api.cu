@@ -19,7 +19,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->x4, s->dx4, s->x4f, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
@@ -114,15 +114,21 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   if (rec_capacity <= 0) rec_capacity = 1ll << 24;
   if (rec_capacity >= (1ll << 31)) rec_capacity = (1ll << 31) - 1;
   s->cand_cap = cand_capacity;
-  // items = contact pairs + lagged friction pairs of one evaluation
-  s->item_cap = cand_capacity < (1ll << 22) ? cand_capacity : (1ll << 22);
+  // items (contact pairs + lagged friction pairs) each emit at least one record, usually
+  // tens: a quarter of the record capacity, at least 4M, bounded by the candidates
+  {
+    const int64_t want = (rec_capacity / 4) > (1ll << 22) ? (rec_capacity / 4) : (1ll << 22);
+    s->item_cap = cand_capacity < want ? cand_capacity : want;
+  }
   s->rec_cap = rec_capacity;
-  s->gcap = rec_capacity;
+  // the gradient records and the per-group energy sort (one key per item) share these
+  s->gcap = rec_capacity > s->item_cap ? rec_capacity : s->item_cap;
   cudaError_t e = cudaSuccess;
   auto ok = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
   ok(dalloc(&s->tris, 3 * F)); ok(dalloc(&s->edges, 2 * E)); ok(dalloc(&s->cage_idx, 4 * Nv));
   ok(dalloc(&s->w, 4 * Nv)); ok(dalloc(&s->x_kin4, 4 * Nv));
   ok(dalloc(&s->vkin, Nv)); ok(dalloc(&s->ekin, E)); ok(dalloc(&s->fkin, F));
+  ok(dalloc(&s->vgroup, Nv)); ok(dalloc(&s->group_alpha_bits, 1)); ok(dalloc(&s->group_count, 4));
   ok(dalloc(&s->x4, 4 * Nv)); ok(dalloc(&s->dx4, 4 * Nv)); ok(dalloc(&s->x4f, 4 * Nv));
   ok(alloc_bvh(s->tri_bvh, F));
   ok(alloc_bvh(s->edge_bvh, E));
@@ -134,6 +140,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->skeys, s->cand_cap)); ok(dalloc(&s->skeys_alt, s->cand_cap));
   ok(dalloc(&s->svals, s->cand_cap)); ok(dalloc(&s->svals_alt, s->cand_cap)); ok(dalloc(&s->sd, s->cand_cap));
   ok(dalloc(&s->item_nodes, 16 * s->item_cap)); ok(dalloc(&s->item_n, s->item_cap));
+  ok(dalloc(&s->item_group, s->item_cap));
   ok(dalloc(&s->rc_h, s->item_cap)); ok(dalloc(&s->ro_h, s->item_cap));
   ok(dalloc(&s->rc_g, s->item_cap)); ok(dalloc(&s->ro_g, s->item_cap)); ok(dalloc(&s->item_E, s->item_cap));
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
@@ -161,6 +168,8 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(cudaMemcpy(s->fkin, fkin.data(), F, cudaMemcpyHostToDevice));
   ok(cudaMemset(s->counters, 0, sizeof(int64_t) * kCntN));
   ok(cudaMemset(s->status, 0, sizeof(DevStatus)));
+  ok(cudaMemset(s->vgroup, 0, sizeof(int32_t) * Nv));
+  s->n_groups = 1;
   ok(cudaMemset(s->x4, 0, sizeof(double) * 4 * Nv));
   ok(cudaMemset(s->dx4, 0, sizeof(double) * 4 * Nv));
   if (e != cudaSuccess) {
@@ -171,11 +180,14 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   Topo& T = s->topo;
   T.nv = Nv; T.ne = E; T.nf = F;
   T.tris = s->tris; T.edges = s->edges; T.vkin = s->vkin; T.ekin = s->ekin; T.fkin = s->fkin;
+  T.vgroup = s->vgroup;
   T.bits_i = bits_for((uint64_t)(Nv > E ? Nv : E));
   T.bits_j = bits_for((uint64_t)(F > E ? F : E));
   s->bits_h = bits_for((uint64_t)Ns * (uint64_t)Ns);
   s->bits_g = bits_for((uint64_t)Ns);
   s->rebuild_interval = 8;
+  s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2;
+  s->tune.query_threads = 128; s->tune.query_bps = 24;
   s->contact_refits = 0;
   *out = s;
   return EIPC_OK;
@@ -262,6 +274,72 @@ eipc_status eipc_timing_read(eipc_scene* sc, double* total_ms, int64_t* launches
     sc->timers->launches[k] = 0;
   }
   return EIPC_OK;
+}
+
+eipc_status eipc_scene_set_groups(eipc_scene* sc, const int32_t* vertex_group, int32_t n_groups) {
+  if (!sc || !vertex_group || n_groups < 1 || n_groups > (1 << 24)) return EIPC_ERR_INVALID;
+  for (int64_t v = 0; v < sc->nv; ++v)
+    if (vertex_group[v] < 0 || vertex_group[v] >= n_groups) return EIPC_ERR_INVALID;
+  // every primitive must lie in one group (a pair never spans two scenes)
+  std::vector<int32_t> tr(3 * sc->nf), ed(2 * sc->ne);
+  if (cudaMemcpy(tr.data(), sc->tris, sizeof(int32_t) * tr.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(ed.data(), sc->edges, sizeof(int32_t) * ed.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return EIPC_ERR_CUDA;
+  for (int64_t f = 0; f < sc->nf; ++f)
+    if (vertex_group[tr[3 * f]] != vertex_group[tr[3 * f + 1]] || vertex_group[tr[3 * f]] != vertex_group[tr[3 * f + 2]])
+      return EIPC_ERR_INVALID;
+  for (int64_t e = 0; e < sc->ne; ++e)
+    if (vertex_group[ed[2 * e]] != vertex_group[ed[2 * e + 1]]) return EIPC_ERR_INVALID;
+  unsigned long long* gb = nullptr;
+  int64_t* gc = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&gb), sizeof(unsigned long long) * n_groups) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&gc), sizeof(int64_t) * (2 * (size_t)n_groups + 2)) != cudaSuccess) {
+    if (gb) cudaFree(gb);
+    cudaGetLastError();
+    return EIPC_ERR_NOMEM;
+  }
+  if (cudaMemcpy(sc->vgroup, vertex_group, sizeof(int32_t) * sc->nv, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(gb); cudaFree(gc);
+    return EIPC_ERR_CUDA;
+  }
+  cudaFree(sc->group_alpha_bits);
+  cudaFree(sc->group_count);
+  sc->group_alpha_bits = gb;
+  sc->group_count = gc;
+  sc->n_groups = n_groups;
+  sc->tri_bvh.built = sc->edge_bvh.built = false;   // leaf records carry the group
+  return EIPC_OK;
+}
+
+eipc_status eipc_group_energy(eipc_scene* sc, double* E_groups, eipc_stream stream) {
+  if (!sc || !E_groups) return EIPC_ERR_INVALID;
+  group_energy_launch(sc, E_groups, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_group_alpha(eipc_scene* sc, double* alpha_groups, eipc_stream stream) {
+  if (!sc || !alpha_groups) return EIPC_ERR_INVALID;
+  group_alpha_launch(sc, alpha_groups, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int32_t blocks_per_sm,
+                            int32_t variant) {
+  if (!sc || blocks_per_sm < 1 || blocks_per_sm > 64) return EIPC_ERR_INVALID;
+  if (kernel == 0) {
+    if ((threads != 64 && threads != 128) || (variant != 2 && variant != 3)) return EIPC_ERR_INVALID;
+    sc->tune.eval_threads = threads;
+    sc->tune.eval_bps = blocks_per_sm;
+    sc->tune.eval_variant = variant;
+    return EIPC_OK;
+  }
+  if (kernel == 1) {
+    if (threads != 64 && threads != 128 && threads != 256) return EIPC_ERR_INVALID;
+    sc->tune.query_threads = threads;
+    sc->tune.query_bps = blocks_per_sm;
+    return EIPC_OK;
+  }
+  return EIPC_ERR_INVALID;
 }
 
 eipc_status eipc_set_rebuild_interval(eipc_scene* sc, int32_t n) {

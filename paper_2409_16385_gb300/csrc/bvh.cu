@@ -181,11 +181,16 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
     int32_t prim = (int32_t)sorted[l];
     leaf_prim[l] = prim;
     int kin = prim_kin(kind, T, prim);
-    // the leaf's vertex ids and kinematic flag, in leaf order for the traversal
-    if (kind == kTri)
-      leaf_info[l] = make_int4(T.tris[3 * (int64_t)prim], T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2], kin);
-    else
-      leaf_info[l] = make_int4(T.edges[2 * (int64_t)prim], T.edges[2 * (int64_t)prim + 1], -1, kin);
+    // the leaf's vertex ids, and (kinematic flag | scene group << 1), in leaf order for the
+    // traversal
+    if (kind == kTri) {
+      const int32_t v0 = T.tris[3 * (int64_t)prim];
+      leaf_info[l] = make_int4(v0, T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2],
+                               kin | (T.vgroup[v0] << 1));
+    } else {
+      const int32_t v0 = T.edges[2 * (int64_t)prim];
+      leaf_info[l] = make_int4(v0, T.edges[2 * (int64_t)prim + 1], -1, kin | (T.vgroup[v0] << 1));
+    }
     if (n == 1) continue;
     float lo[3], hi[3];
     for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
@@ -238,7 +243,7 @@ __device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_ca
 // One launch for both query sets: threads [0, nv) run vertex boxes against the triangle
 // tree (PT), threads [nv, nv + ne) run edge boxes against the edge tree (EE, j > i), the
 // edges in that tree's Morton order so neighbouring threads take similar paths.
-__global__ void __launch_bounds__(128) k_query(Bvh tt, Bvh te, Topo T, const double* __restrict__ x4,
+__global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const double* __restrict__ x4,
                                                const double* __restrict__ dx4, double pad, uint64_t* cand,
                                                int64_t* n_cand, int64_t cap, DevStatus* st) {
   const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);
@@ -255,18 +260,19 @@ __global__ void __launch_bounds__(128) k_query(Bvh tt, Bvh te, Topo T, const dou
     if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
     else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
     const bool qkin = prim_kin(qkind, T, q);
+    const int32_t qgroup = T.vgroup[qa];   // primitives of different scenes never pair
     auto leaf = [&](int32_t lpos) {
       const int4 info = __ldg(t.leaf_info + lpos);
       if (is_pt) {
         if (info.x == qa || info.y == qa || info.z == qa) return;
-        if (qkin && info.w) return;
+        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
         const int32_t p = t.leaf_prim[lpos];
         emit(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
       } else {
         // each EE pair is found once, from the edge earlier in Morton order
         if (lpos <= qpos) return;
         if (info.x == qa || info.x == qb || info.y == qa || info.y == qb) return;
-        if (qkin && info.w) return;
+        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
         const int32_t p = t.leaf_prim[lpos];
         const uint32_t lo = (uint32_t)(p < q ? p : q), hi = (uint32_t)(p < q ? q : p);
         emit(pair_key(1, lo, hi, T.bits_i, T.bits_j), cand, n_cand, cap, st);
@@ -349,10 +355,10 @@ void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
 }
 
 void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
-               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s) {
+               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps) {
   const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
-  launch(k_query, blocks_for(nq, 24, 128), 128, 0, s, tri, edge, topo, x4, dx4, pad, cand, n_cand, cap, st);
+  launch(k_query, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, x4, dx4, pad, cand, n_cand, cap, st);
 }
 
 }  // namespace eipc

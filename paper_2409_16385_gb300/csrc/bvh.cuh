@@ -44,6 +44,7 @@ struct Topo {
   const uint8_t* vkin;   // [nv]
   const uint8_t* ekin;   // [ne] both ends kinematic
   const uint8_t* fkin;   // [nf] all three kinematic
+  const int32_t* vgroup; // [nv] independent-scene id of each vertex (0 when not batched)
   int bits_i, bits_j;    // pair key packing
 };
 
@@ -71,6 +72,7 @@ void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
 // are appended as pair keys to cand[0..cap) with the running count in *n_cand, and an
 // overflow raises CAND_OVERFLOW.
 void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
-               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s);
+               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads = 128,
+               int bps = 24);
 
 }  // namespace eipc

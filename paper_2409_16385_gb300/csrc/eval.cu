@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
                                                        const int64_t* lag_count, int64_t lag_cap,
                                                        const int32_t* __restrict__ cage_idx, int64_t item_cap,
                                                        int32_t* __restrict__ item_nodes, int32_t* __restrict__ item_n,
+                                                       int32_t* __restrict__ item_group, const int32_t* __restrict__ vgroup,
                                                        int64_t* __restrict__ rc_h, int64_t* __restrict__ rc_g,
                                                        int64_t* n_items, DevStatus* st) {
   const int64_t P = clamp_count(pr.count, pr.capacity);
@@ -95,6 +96,7 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
     }
     for (int u = 0; u < cnt; ++u) item_nodes[kMaxNodes * k + u] = nodes[u];
     item_n[k] = cnt;
+    item_group[k] = vgroup[v[0]];
     rc_h[k] = (int64_t)cnt * (cnt + 1) / 2;
     rc_g[k] = cnt;
   }
@@ -341,7 +343,10 @@ __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32
   A.hvals[pos] = (uint32_t)pos;
 }
 
-__global__ void __launch_bounds__(kEvalThreads) k_eval_barrier(EvalArgs A) {
+// MINB = 2: no register cap (248 registers, 2 blocks of 128 per SM); MINB = 3: at most 170
+// registers (3 blocks per SM, a few hundred bytes of spills).  Chosen at run time.
+template <int MINB>
+__global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A) {
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t np = P < nit ? P : nit;
@@ -831,7 +836,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   sc->timers->start(kKItems, s);
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
                                                            fr ? lag->capacity : 0, sc->cage_idx, item_cap,
-                                                           sc->item_nodes, sc->item_n, sc->rc_h, sc->rc_g,
+                                                           sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
+                                                           sc->rc_h, sc->rc_g,
                                                            cnt + kCntItems, sc->status);
   int64_t* tot_h = cnt + 9;
   int64_t* tot_g = cnt + 10;
@@ -846,7 +852,11 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   EIPC_TIMED(sc, kKEvalBarrier, s,
-             (launch(k_eval_barrier, blocks_for(pr.capacity, 16, kEvalThreads), kEvalThreads, 0, s, A)));
+             (sc->tune.eval_variant == 3
+                  ? launch(k_eval_barrier<3>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
+                           sc->tune.eval_threads, 0, s, A)
+                  : launch(k_eval_barrier<2>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
+                           sc->tune.eval_threads, 0, s, A)));
   if (fr)
     EIPC_TIMED(sc, kKEvalFriction, s,
                (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,

@@ -206,7 +206,7 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   }
   EIPC_TIMED(sc, kKQuery, s,
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s));
+                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
   int64_t* n_cand2 = sc->counters + 15;
   cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
   sc->timers->start(kKNarrow, s);

@@ -16,6 +16,11 @@ struct eipc_scene {
   uint8_t* vkin;
   uint8_t* ekin;
   uint8_t* fkin;
+  int32_t* vgroup;       // [nv] independent-scene id per vertex (all 0 unless set)
+  int32_t n_groups;
+  unsigned long long* group_alpha_bits;   // [n_groups] CCD bound per group (IEEE bits)
+  int64_t* group_count;  // [n_groups + 1] items per group, then offsets
+  int32_t* item_group;   // [item_cap] group of each evaluated item
   eipc::Topo topo;
   // positions (padded, 4 doubles per vertex)
   double* x4;
@@ -68,6 +73,10 @@ struct eipc_scene {
   double* sum_partial;   // [kScanBlocks]
   int bits_h, bits_g;    // key widths of the reduction sorts
   int rebuild_interval;  // contact LBVH: full rebuild every this many build_candidates calls
+  struct {
+    int eval_threads = 128, eval_bps = 16, eval_variant = 2;
+    int query_threads = 128, query_bps = 24;
+  } tune;                // launch shapes of the tunable kernels (eipc_set_launch)
   int contact_refits;    // refits since the last full rebuild
   eipc::DevStatus* status;
   eipc::Timers* timers;   // host-side event timers (off unless enabled)
@@ -93,6 +102,8 @@ void lag_launch(eipc_scene* sc, const double* q_n, const eipc_pairs& pr, const e
 void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
                  double* E, double* g_r, const eipc_bsr& H, cudaStream_t s);
 int bits_for(uint64_t maxval);
+void group_energy_launch(eipc_scene* sc, double* E_groups, cudaStream_t s);
+void group_alpha_launch(eipc_scene* sc, double* alpha_groups, cudaStream_t s);
 void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_params& p, double* alpha,
                  int64_t* n_candidates, cudaStream_t s);
 }  // namespace eipc

@@ -25,6 +25,7 @@ plate lowered between rigid tines (dish rack, Sec. IV-B).
 from __future__ import annotations
 
 import dataclasses
+import functools
 import math
 from typing import Callable, Dict, List, Tuple
 
@@ -115,6 +116,12 @@ def icosphere(level: int) -> Tuple[np.ndarray, np.ndarray]:
 def geodesic_sphere(n: int) -> Tuple[np.ndarray, np.ndarray]:
     """Unit geodesic sphere of frequency n: each icosahedron face cut into n^2 triangles,
     points projected to the sphere (10 n^2 + 2 verts, 20 n^2 tris)."""
+    v, f = _geodesic_sphere_cached(int(n))
+    return v.copy(), f.copy()
+
+
+@functools.lru_cache(maxsize=None)
+def _geodesic_sphere_cached(n: int) -> Tuple[np.ndarray, np.ndarray]:
     base_v, base_f = _icosahedron()
     index: Dict[tuple, int] = {}
     pts: List[np.ndarray] = []
@@ -216,7 +223,11 @@ def open_cylinder(radius: float, height: float, n_around: int, n_up: int):
 def edges_of(tris: np.ndarray) -> np.ndarray:
     e = np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]]).astype(np.int64)
     e.sort(axis=1)
-    e = np.unique(e, axis=0)
+    # unique rows in lexicographic order, via one int64 key per row
+    n = int(e.max()) + 1 if len(e) else 1
+    key = np.sort(e[:, 0] * n + e[:, 1])
+    key = key[np.concatenate([[True], key[1:] != key[:-1]])] if len(key) else key
+    e = np.stack([key // n, key % n], 1)
     return np.ascontiguousarray(e.astype(np.int32))
 
 
@@ -264,24 +275,32 @@ def embed_weights(points: np.ndarray, nodes: np.ndarray, tets: np.ndarray, grid)
     nyz = dims[1] * dims[2]
     best_t = np.full(len(points), np.iinfo(np.int64).max, dtype=np.int64)
     best_w = np.zeros((len(points), 4))
-    base = np.floor((points - lo) / h).astype(np.int64)
+    rel = (points - lo) / h
+    base = np.floor(rel).astype(np.int64)
+    # A point more than 1e-8 cells inside its own cube has barycentrics below -1e-9 in every
+    # tet of the other cubes, so only points near a cube face search the 26 neighbours.
+    fr = rel - base
+    near = np.nonzero(np.any((fr < 1e-8) | (fr > 1.0 - 1e-8), axis=1))[0]
+    everyone = np.arange(len(points))
     for di in (-1, 0, 1):
         for dj in (-1, 0, 1):
             for dk in (-1, 0, 1):
-                cell = base + np.array([di, dj, dk])
-                ok = np.all((cell >= 0) & (cell < dims), axis=1)
-                if not ok.any():
+                cand = near if (di or dj or dk) else everyone
+                cell = base[cand] + np.array([di, dj, dk])
+                inside = np.all((cell >= 0) & (cell < dims), axis=1)
+                sel, cell = cand[inside], cell[inside]
+                if len(sel) == 0:
                     continue
                 cid = cell[:, 0] * nyz + cell[:, 1] * dims[2] + cell[:, 2]
                 for s in range(5):
-                    t = np.where(ok, cid * 5 + s, 0)
+                    t = cid * 5 + s
                     v = nodes[tets[t]]
                     D = np.stack([v[:, 1] - v[:, 0], v[:, 2] - v[:, 0], v[:, 3] - v[:, 0]], axis=2)
-                    lam = np.linalg.solve(D, (points - v[:, 0])[:, :, None])[:, :, 0]
+                    lam = np.linalg.solve(D, (points[sel] - v[:, 0])[:, :, None])[:, :, 0]
                     wts = np.concatenate([1.0 - lam.sum(1, keepdims=True), lam], 1)
-                    good = ok & np.all(wts >= -1e-12, axis=1) & (t < best_t)
-                    best_t[good] = t[good]
-                    best_w[good] = wts[good]
+                    good = np.all(wts >= -1e-12, axis=1) & (t < best_t[sel])
+                    best_t[sel[good]] = t[good]
+                    best_w[sel[good]] = wts[good]
     if np.any(best_t == np.iinfo(np.int64).max):
         raise ValueError("point outside the cage")
     return tets[best_t].astype(np.int32), best_w
@@ -598,15 +617,126 @@ def plate_in_rack(seed: int = 0, plate_cells=(150, 100), n_tines: int = 10,
     return sc
 
 
+def _grid_dims(n_nodes: float, ext) -> Tuple[int, int, int]:
+    """Cube counts of a cage grid over a box with extents `ext` holding about n_nodes nodes."""
+    ext = np.asarray(ext, float)
+    h = (np.prod(ext) / max(n_nodes, 8.0)) ** (1.0 / 3.0)
+    return tuple(int(max(1, round(e / h))) for e in ext)
+
+
+def batched_grasp(n_scenes: int = 256, seed: int = 0, min_tris: int = 2000, max_tris: int = 50000,
+                  spacing: float = 0.2) -> Scene:
+    """`n_scenes` independent bubble-grasp scenes concatenated into one (disjoint vertex and
+    cage-node ranges; `body` holds each vertex's scene id).  Scene s has a total surface size
+    log-uniform in [min_tris, max_tris] (half body, a quarter per membrane), cages of about
+    one node per 40 surface vertices, and its own closing phase (a multiple of 3 iterates, so
+    every scene's friction lags on the same iterates); scenes sit on a grid `spacing` apart.
+    iterate(t) / dq(t) concatenate each scene's iterate / direction at its own phase + t."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in range(n_scenes):
+        T = float(np.exp(rng.uniform(np.log(min_tris), np.log(max_tris))))
+        nb = max(4, int(round(np.sqrt(T / 2 / 20))))
+        nm = max(3, int(round(np.sqrt(T / 4 / 20))))
+        body_nodes = 10 * nb * nb / 40.0
+        mem_nodes = 10 * nm * nm / 40.0
+        bc = _grid_dims(body_nodes, (0.11, 0.11, 0.11))
+        mc = _grid_dims(mem_nodes, (0.123, 0.033, 0.083))
+        sc = bubble_grasp(seed=seed * 100003 + s, n_body=nb, n_mem=nm, body_cage=bc, mem_cage=mc)
+        phase = 3 * int(rng.integers(0, sc.n_iterates // 3))
+        parts.append((sc, phase))
+    g = int(np.ceil(n_scenes ** (1.0 / 3.0)))
+    tris, cage_idx, w, xk, body, nodes, tets = [], [], [], [], [], [], []
+    v_off = 0
+    n_off = 0
+    offsets = []
+    for s, (sc, phase) in enumerate(parts):
+        o = spacing * np.array([s % g, (s // g) % g, s // (g * g)], float)
+        offsets.append((n_off, sc.Ns, o))
+        tris.append(sc.tris + v_off)
+        idx = sc.cage_idx.copy()
+        idx[idx >= 0] += n_off
+        cage_idx.append(idx)
+        w.append(sc.w)
+        xk.append(np.where(sc.kinematic[:, None], sc.x_kin + o, 0.0))
+        body.append(np.full(sc.Nv, s, np.int32))
+        nodes.append(sc.q_rest + o)
+        tets.append(sc.cage_tets + n_off)
+        v_off += sc.Nv
+        n_off += sc.Ns
+    tris = np.ascontiguousarray(np.concatenate(tris).astype(np.int32))
+    out = Scene(name="batched_grasp", tris=tris, edges=edges_of(tris),
+                cage_idx=np.ascontiguousarray(np.concatenate(cage_idx)), w=np.ascontiguousarray(np.concatenate(w)),
+                x_kin=np.ascontiguousarray(np.concatenate(xk)), Ns=n_off, cage_tets=np.concatenate(tets),
+                q_rest=np.ascontiguousarray(np.concatenate(nodes)), body=np.concatenate(body),
+                params=dict(parts[0][0].params))
+    n_it = parts[0][0].n_iterates
+
+    def cat(fn, t):
+        q = np.zeros((n_off, 3))
+        for (sc, phase), (no, ns, o) in zip(parts, offsets):
+            q[no:no + ns] = fn(sc, (phase + t) % n_it) + o
+        return q
+
+    def cat_dq(t):
+        q = np.zeros((n_off, 3))
+        for (sc, phase), (no, ns, o) in zip(parts, offsets):
+            q[no:no + ns] = sc.dq((phase + t) % n_it)
+        return q
+
+    out.n_iterates = n_it
+    out.iterate = lambda t: cat(lambda sc, tt: sc.iterate(tt), t)
+    out.lag_of = parts[0][0].lag_of
+    out.dq = cat_dq
+    out.parts = parts
+    out.n_scenes = n_scenes
+    out.node_ranges = [(no, ns) for no, ns, _ in offsets]
+    vr, fr, er = [], [], []
+    v0 = f0 = 0
+    for sc, _ in parts:
+        vr.append((v0, sc.Nv)); fr.append((f0, sc.F))
+        v0 += sc.Nv; f0 += sc.F
+    # edges_of sorts rows lexicographically and the vertex ranges are increasing, so each
+    # scene's edges form one contiguous run, in the scene's own order
+    e0 = 0
+    for sc, _ in parts:
+        er.append((e0, sc.E)); e0 += sc.E
+    out.vertex_ranges, out.tri_ranges, out.edge_ranges = vr, fr, er
+
+    def part_scene(s: int) -> Scene:
+        """Scene s alone, in the batch's coordinates (translated by its grid offset), so
+        that its positions are bitwise those of its vertices in the batch."""
+        sc, phase = parts[s]
+        no, ns, o = offsets[s]
+        one = Scene(name=f"batched_grasp[{s}]", tris=sc.tris.copy(), edges=sc.edges.copy(),
+                    cage_idx=sc.cage_idx.copy(), w=sc.w.copy(),
+                    x_kin=np.ascontiguousarray(np.where(sc.kinematic[:, None], sc.x_kin + o, 0.0)),
+                    Ns=sc.Ns, cage_tets=sc.cage_tets.copy(), q_rest=sc.q_rest + o,
+                    body=sc.body.copy(), params=dict(sc.params))
+        one.n_iterates = n_it
+        one.iterate = lambda t: sc.iterate((phase + t) % n_it) + o
+        one.lag_of = sc.lag_of
+        one.dq = lambda t: sc.dq((phase + t) % n_it)
+        return one
+
+    out.part_scene = part_scene
+    return out
+
+
 def make_config(k: int, seed: int = 0, small: bool = False) -> Scene:
-    """k = 1: sphere on pad; 2: bubble grasp; 3: plate in rack.  small=True gives reduced
-    resolutions of configs 2 and 3 that the brute-force oracle enumerates in seconds."""
+    """k = 1: sphere on pad; 2: bubble grasp; 3: plate in rack; 4: 256 batched bubble grasps.
+    small=True gives reduced versions (configs 2 and 3 that the brute-force oracle enumerates
+    in seconds; 16 small scenes for config 4)."""
     if k == 1:
         return sphere_on_pad(seed)
     if k == 2:
         if small:
             return bubble_grasp(seed, n_body=16, n_mem=10, body_cage=(5, 5, 5), mem_cage=(8, 3, 6))
         return bubble_grasp(seed)
+    if k == 4:
+        if small:
+            return batched_grasp(n_scenes=16, seed=seed, min_tris=2000, max_tris=8000)
+        return batched_grasp(n_scenes=256, seed=seed)
     if k == 3:
         if small:
             return plate_in_rack(seed, plate_cells=(40, 30), n_tines=4, tine_segs=(16, 20),
