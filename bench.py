@@ -56,6 +56,7 @@ def parse():
                     help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step")
     ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain per-scene comparison")
     ap.add_argument("--retune", action="store_true", help="batched: ignore the autotuner cache")
+    ap.add_argument("--no-tune", action="store_true", help="batched: library default launch shapes")
     return ap.parse_args()
 
 
@@ -569,6 +570,31 @@ def _sized_stage(sc, caps, groups, dev, Q, DQ, lag_of, ts):
     raise RuntimeError("capacities did not converge")
 
 
+def batched_oracle_sample(b, t, budget_s=20.0, seed=0, max_tris=8000):
+    """The oracle's whole contact stage at iterate t on whole scenes of the batch, drawn
+    in a seeded random order among those of at most max_tris triangles (the brute-force
+    enumeration is quadratic in the scene size, so a large scene alone would exceed the
+    budget), until about budget_s seconds of host time are spent."""
+    import oracle
+    oracle.build()
+    order = np.random.default_rng(seed).permutation(b.n_scenes)
+    pairs, secs, used = 0, 0.0, []
+    for s in order:
+        if secs >= budget_s:
+            break
+        if b.parts[int(s)][0].F > max_tris:
+            continue
+        one = b.part_scene(int(s))
+        p, dt, _ = oracle_sample(one, t, 1.0)
+        pairs += p; secs += dt; used.append(int(s))
+    tris = sum(b.parts[s][0].F for s in used)
+    return dict(value=pairs / secs if secs > 0 else 0.0, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"iterate {t}: whole contact stage (brute-force contact set, lagged friction, evaluation, CCD) "
+                       f"of {len(used)} of the {b.n_scenes} scenes ({tris} triangles), drawn in seeded random order "
+                       f"among those of at most {max_tris} triangles; "
+                       f"{pairs} pairs in {secs:.1f} s")
+
+
 def run_batched(args, ws, rank, local):
     """256 independent grasp scenes (surface sizes log-uniform in [2k, 50k] triangles, own
     closing phase each) in one scene with one group per scene.  One step is one CUDA graph
@@ -591,17 +617,18 @@ def run_batched(args, ws, rank, local):
     K, W = args.steps, args.warmup
     t0 = W % n_it
     size_ts = sorted({t0, (t0 + 3) % n_it, (t0 + 29) % n_it, (t0 + 47) % n_it})
-    caps = dict(pair=1 << 22, bsr=1 << 21, cand=args.cand_cap, rec=args.rec_cap or (1 << 27))
-    if args.quick:
-        caps = dict(pair=1 << 20, bsr=1 << 20, cand=args.cand_cap, rec=args.rec_cap or (1 << 24))
+    # starting capacities; the sizing pass grows whichever overflows
+    caps = dict(pair=1 << 20, bsr=1 << 20, cand=args.cand_cap or (1 << 24), rec=args.rec_cap or (1 << 24))
     st = _sized_stage(b, caps, (b.body, G), dev, Q, DQ, lag_of, size_ts)
 
     # ---- autotuned launch shapes (cached per device and workload)
     def tune_stage():
         st(False)
     st.q.copy_(Q[t0]); st.dq.copy_(DQ[t0])
-    tuned = autotune.tune(st.cs, tune_stage, f"{BATCH_WORKLOAD if not args.quick else 'batched_grasp_16'}",
-                          force=args.retune)
+    tuned = {}
+    if not args.no_tune:
+        tuned = autotune.tune(st.cs, tune_stage, f"{BATCH_WORKLOAD if not args.quick else 'batched_grasp_16'}",
+                              force=args.retune)
 
     # ---- one graph per (lag step, hierarchy rebuild) combination
     R = 8
@@ -777,15 +804,7 @@ def run_batched(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        _, t_cal, _ = oracle_sample(b, t0, 1e-4, seed=999)
-        frac = min(1.0 / 12, 1e-4 * 20.0 / max(t_cal, 1e-3))
-        p, dt, c = oracle_sample(b, t0, frac)
-        cpu = dict(value=p / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                   sample=f"iterate {t0}: brute-force contact set of a {frac:.5f} fraction of the batch's vertices "
-                          f"and edges (queries), lagged friction, evaluation and CCD of those queries; "
-                          f"{p} pairs in {dt:.1f} s")
+        cpu = batched_oracle_sample(b, t0, budget_s=20.0)
 
     sizes = [sc.F for sc, _ in b.parts]
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=K, warmup=W,
@@ -801,7 +820,8 @@ def run_batched(args, ws, rank, local):
                 clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
                 ccd_queries_per_s=total_cand_all / total_s_all, e2e=e2e, cpu_baseline=cpu,
                 plain_per_scene=plain, speedup_vs_plain=(value / plain["value"]) if plain else None,
-                autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"])
+                autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"],
+                                  candidates=v.get("candidates"))
                           for k, v in tuned.items()},
                 kernels_per_graph={f"lag={a},rebuild={c}": int(n) for (a, c), n in kernels_per_graph.items()},
                 capacities=st.caps, scene_generation_s=gen_s,

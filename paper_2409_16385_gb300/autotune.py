@@ -1,6 +1,7 @@
-"""Launch-shape autotuner for the two kernels whose best shape depends on the workload:
-the per-pair barrier evaluation (threads per block, grid cap in blocks per SM, register
-budget) and the BVH traversal (threads per block, grid cap).
+"""Launch-shape autotuner for the kernels whose best shape depends on the workload: the
+per-pair barrier evaluation (threads per block, grid cap in blocks per SM, register
+budget), the BVH traversal (threads per block, grid cap) and the BVH refit (how its
+bottom-up arrival counters are ordered).
 
 Results never depend on the shape: every kernel is a grid-stride loop over a device-side
 count, and every reduction order is fixed by sort keys, not by the launch.  So the tuner
@@ -21,7 +22,11 @@ EVAL_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
 QUERY_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
     (threads, bps, 2) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32))
 
-SPACES = {"eval_barrier": EVAL_SPACE, "bvh_query": QUERY_SPACE}
+REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1))
+
+SPACES = {"eval_barrier": EVAL_SPACE, "bvh_query": QUERY_SPACE, "bvh_refit": REFIT_SPACE}
+# the library timer that brackets each tunable kernel's launches
+TIMERS = {"eval_barrier": "eval_barrier", "bvh_query": "bvh_query", "bvh_refit": "bvh_build"}
 
 
 def default_cache_path() -> str:
@@ -67,7 +72,8 @@ def time_kernel(cs, stage: Callable[[], None], kernel: str, reps: int = 3) -> fl
     return samples[len(samples) // 2]
 
 
-def tune(cs, stage: Callable[[], None], workload_key: str, kernels: Iterable[str] = ("eval_barrier", "bvh_query"),
+def tune(cs, stage: Callable[[], None], workload_key: str,
+         kernels: Iterable[str] = ("eval_barrier", "bvh_query", "bvh_refit"),
          cache_path: Optional[str] = None, reps: int = 3, force: bool = False) -> Dict[str, dict]:
     """Chooses and applies a launch shape for each kernel on `cs` (a ContactScene).
 
@@ -85,17 +91,19 @@ def tune(cs, stage: Callable[[], None], workload_key: str, kernels: Iterable[str
             cs.set_launch(kernel, *shape)
             out[kernel] = dict(entry[kernel], cached=True)
             continue
+        timer = TIMERS[kernel]
         stage()                                   # warm: hierarchies built, caches primed
-        default_ms = time_kernel(cs, stage, kernel, reps)
-        best, best_ms = None, float("inf")
+        default_ms = time_kernel(cs, stage, timer, reps)
+        best, best_ms, seen = None, float("inf"), {}
         for shape in SPACES[kernel]:
             cs.set_launch(kernel, *shape)
             stage()
-            ms = time_kernel(cs, stage, kernel, reps)
+            ms = time_kernel(cs, stage, timer, reps)
+            seen["x".join(map(str, shape))] = ms
             if ms < best_ms:
                 best, best_ms = shape, ms
         cs.set_launch(kernel, *best)
-        entry[kernel] = dict(shape=list(best), ms=best_ms, default_ms=default_ms)
+        entry[kernel] = dict(shape=list(best), ms=best_ms, default_ms=default_ms, candidates=seen)
         out[kernel] = dict(entry[kernel], cached=False)
     table[key] = entry
     _store(path, table)

@@ -187,7 +187,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   s->bits_g = bits_for((uint64_t)Ns);
   s->rebuild_interval = 8;
   s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2;
-  s->tune.query_threads = 128; s->tune.query_bps = 24;
+  s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.refit_variant = 1;
   s->contact_refits = 0;
   *out = s;
   return EIPC_OK;
@@ -337,6 +337,11 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
     if (threads != 64 && threads != 128 && threads != 256) return EIPC_ERR_INVALID;
     sc->tune.query_threads = threads;
     sc->tune.query_bps = blocks_per_sm;
+    return EIPC_OK;
+  }
+  if (kernel == 2) {
+    if (threads != 256 || (variant != 0 && variant != 1)) return EIPC_ERR_INVALID;
+    sc->tune.refit_variant = variant;
     return EIPC_OK;
   }
   return EIPC_ERR_INVALID;

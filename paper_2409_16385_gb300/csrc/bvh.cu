@@ -112,16 +112,6 @@ __global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Top
   }
 }
 
-// leaf boxes only, for refitting an existing hierarchy
-__global__ void __launch_bounds__(kBlock) k_leaf_boxes(PrimKind kind, int64_t n, Topo T, const double* __restrict__ x4,
-                                                       const double* __restrict__ dx4, float* __restrict__ leaf_box) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride()) {
-    float lo[3], hi[3];
-    prim_box(kind, i, T, x4, dx4, 0.0, lo, hi);
-    for (int k = 0; k < 3; ++k) { leaf_box[6 * i + k] = lo[k]; leaf_box[6 * i + 3 + k] = hi[k]; }
-  }
-}
-
 __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
   if (j < 0 || j >= n) return -1;
   uint64_t a = k[i], b = k[j];
@@ -164,56 +154,97 @@ __device__ __forceinline__ uint8_t prim_kin(PrimKind kind, const Topo& T, int64_
   return kind == kTri ? T.fkin[p] : (kind == kEdge ? T.ekin[p] : T.vkin[p]);
 }
 
+template <bool first>
 __device__ __forceinline__ void write_child(BvhNode* nd, int slot, const float lo[3], const float hi[3], int kin) {
   float* l = slot ? nd->lo1 : nd->lo0;
   float* h = slot ? nd->hi1 : nd->hi0;
   for (int k = 0; k < 3; ++k) { __stcg(&l[k], lo[k]); __stcg(&h[k], hi[k]); }
-  if (kin) atomicOr(&nd->kin, 1 << slot);
+  if (first && kin) atomicOr(&nd->kin, 1 << slot);
+}
+
+// Arrival counter of the bottom-up refit with release-acquire semantics at device scope:
+// the child box a thread stored before its increment is visible to the thread whose
+// increment comes second, which then reads both boxes.
+__device__ __forceinline__ int32_t arrive_acq_rel(int32_t* f) {
+  int32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(f) : "memory");
+  return old;
+}
+
+template <bool fences>
+__device__ __forceinline__ int32_t arrive(int32_t* f) {
+  if (fences) {
+    __threadfence();
+    return atomicAdd(f, 1);
+  }
+  return arrive_acq_rel(f);
+}
+
+// leaf boxes in leaf order, for refitting an existing hierarchy
+__global__ void __launch_bounds__(kBlock) k_leaf_boxes(PrimKind kind, int64_t n, Topo T, const int32_t* __restrict__ leaf_prim,
+                                                       const double* __restrict__ x4, const double* __restrict__ dx4,
+                                                       float* __restrict__ leaf_box) {
+  for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
+    float lo[3], hi[3];
+    prim_box(kind, leaf_prim[l], T, x4, dx4, 0.0, lo, hi);
+    float2* o = reinterpret_cast<float2*>(leaf_box + 6 * l);
+    o[0] = make_float2(lo[0], lo[1]);
+    o[1] = make_float2(lo[2], hi[0]);
+    o[2] = make_float2(hi[1], hi[2]);
+  }
 }
 
 // Bottom-up refit: the second child to finish a node unions both child boxes and
-// carries on upward; the first one stops.  No thread ever waits on another.
+// carries on upward; the first one stops.  No thread ever waits on another.  On a build
+// (`first`) it also writes the per-leaf records and the kinematic bits, which a refit of
+// the same hierarchy leaves as they are.  Leaf boxes are indexed by primitive on a build
+// (written by the Morton pass) and by leaf on a refit (k_leaf_boxes).
+template <bool first, bool fences>
 __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo T, const uint32_t* __restrict__ sorted,
                                                   const float* __restrict__ leaf_box, BvhNode* nodes,
                                                   const int32_t* __restrict__ parent, int32_t* leaf_prim,
                                                   int4* __restrict__ leaf_info, int32_t* flag) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
-    int32_t prim = (int32_t)sorted[l];
-    leaf_prim[l] = prim;
-    int kin = prim_kin(kind, T, prim);
-    // the leaf's vertex ids, and (kinematic flag | scene group << 1), in leaf order for the
-    // traversal
-    if (kind == kTri) {
-      const int32_t v0 = T.tris[3 * (int64_t)prim];
-      leaf_info[l] = make_int4(v0, T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2],
-                               kin | (T.vgroup[v0] << 1));
+    int kin = 0;
+    float lo[3], hi[3];
+    if (first) {
+      const int32_t prim = (int32_t)sorted[l];
+      leaf_prim[l] = prim;
+      kin = prim_kin(kind, T, prim);
+      // the leaf's vertex ids, and (kinematic flag | scene group << 1), in leaf order for
+      // the traversal
+      if (kind == kTri) {
+        const int32_t v0 = T.tris[3 * (int64_t)prim];
+        leaf_info[l] = make_int4(v0, T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2],
+                                 kin | (T.vgroup[v0] << 1));
+      } else {
+        const int32_t v0 = T.edges[2 * (int64_t)prim];
+        leaf_info[l] = make_int4(v0, T.edges[2 * (int64_t)prim + 1], -1, kin | (T.vgroup[v0] << 1));
+      }
+      for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
     } else {
-      const int32_t v0 = T.edges[2 * (int64_t)prim];
-      leaf_info[l] = make_int4(v0, T.edges[2 * (int64_t)prim + 1], -1, kin | (T.vgroup[v0] << 1));
+      const float2* b = reinterpret_cast<const float2*>(leaf_box + 6 * l);
+      const float2 a0 = b[0], a1 = b[1], a2 = b[2];
+      lo[0] = a0.x; lo[1] = a0.y; lo[2] = a1.x; hi[0] = a1.y; hi[1] = a2.x; hi[2] = a2.y;
     }
     if (n == 1) continue;
-    float lo[3], hi[3];
-    for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
     int32_t node = parent[n - 1 + l];
     int slot = (nodes[node].c0 == ~(int32_t)l) ? 0 : 1;
-    write_child(&nodes[node], slot, lo, hi, kin);
-    __threadfence();
-    if (atomicAdd(&flag[node], 1) == 0) continue;
+    write_child<first>(&nodes[node], slot, lo, hi, kin);
+    if (arrive<fences>(&flag[node]) == 0) continue;
     for (int64_t step = 0; step < n; ++step) {   // a root path has at most n-1 nodes
-      __threadfence();
+      if (fences) __threadfence();
       const BvhNode* nd = &nodes[node];
       for (int k = 0; k < 3; ++k) {
         lo[k] = fminf(__ldcg(&nd->lo0[k]), __ldcg(&nd->lo1[k]));
         hi[k] = fmaxf(__ldcg(&nd->hi0[k]), __ldcg(&nd->hi1[k]));
       }
-      int kk = atomicOr(&nodes[node].kin, 0);
-      kin = (kk & 3) == 3;
+      if (first) kin = (__ldcg(&nd->kin) & 3) == 3;
       if (node == 0) break;
       int32_t p = parent[node];
       slot = (nodes[p].c0 == node) ? 0 : 1;
-      write_child(&nodes[p], slot, lo, hi, kin);
-      __threadfence();
-      if (atomicAdd(&flag[p], 1) == 0) break;
+      write_child<first>(&nodes[p], slot, lo, hi, kin);
+      if (arrive<fences>(&flag[p]) == 0) break;
       node = p;
     }
   }
@@ -324,7 +355,7 @@ __global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const dou
 }  // namespace
 
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, int32_t* bounds_ws,
-               uint32_t* sort_hist, cudaStream_t s) {
+               uint32_t* sort_hist, cudaStream_t s, int refit_variant) {
   if (t.n <= 0) return;
   launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
   launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, dx4, topo.nv, bounds_ws);
@@ -336,8 +367,14 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   cudaMemsetAsync(t.nodes, 0, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1), s);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
   if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent);
-  launch(k_refit, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv, t.leaf_box, t.nodes, t.parent, t.leaf_prim,
-         t.leaf_info, t.refit_flag);
+  if (refit_variant == 0)
+    launch(k_refit<true, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
+           static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
+           t.leaf_info, t.refit_flag);
+  else
+    launch(k_refit<true, false>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
+           static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
+           t.leaf_info, t.refit_flag);
   t.built = true;
 }
 
@@ -346,12 +383,20 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
   launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, static_cast<const double*>(nullptr), topo.nv, bounds_ws);
 }
 
-void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s) {
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
+               int refit_variant) {
   if (t.n <= 0) return;
-  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, x4, dx4, t.leaf_box);
+  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, static_cast<const int32_t*>(t.leaf_prim), x4,
+         dx4, t.leaf_box);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
-  launch(k_refit, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted, static_cast<const float*>(t.leaf_box),
-         t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim, t.leaf_info, t.refit_flag);
+  if (refit_variant == 0)
+    launch(k_refit<false, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
+           static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
+           t.leaf_info, t.refit_flag);
+  else
+    launch(k_refit<false, false>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
+           static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
+           t.leaf_info, t.refit_flag);
 }
 
 void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,

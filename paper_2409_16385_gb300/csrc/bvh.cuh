@@ -55,8 +55,10 @@ __host__ __device__ __forceinline__ uint64_t pair_key(int type, uint32_t i, uint
 
 // Build the tree over primitives of `kind` from positions x4 (padded), optionally swept
 // by dx4 (CCD); `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
+// refit_variant: 0 = arrival counters behind full device fences, 1 = release-acquire
+// arrival counters (same result)
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4,
-               int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s);
+               int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant);
 
 // Scene box of the positions x4 into bounds_ws (6 order-preserving ints: lo xyz, hi xyz).
 void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s);
@@ -64,7 +66,8 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
 // Refit the hierarchy of the last bvh_build with new leaf boxes (x4, optionally swept by
 // dx4): any binary tree over the primitives with conservative boxes gives the same exact
 // candidate set, so the Morton sort and hierarchy can be reused while the topology stays.
-void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s);
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
+               int refit_variant);
 
 // Traverse both trees in one launch: every vertex box (grown by `pad`, or swept by dx4)
 // against the triangle tree -> PT candidates, every edge box against the edge tree -> EE

@@ -193,14 +193,16 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   // candidate set is exact for any hierarchy; only traversal cost depends on its quality)
   const bool rebuild = !sc->tri_bvh.built || !sc->edge_bvh.built || sc->contact_refits + 1 >= sc->rebuild_interval;
   if (rebuild) {
-    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
-    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s));
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s,
+                                      sc->tune.refit_variant));
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s,
+                                      sc->tune.refit_variant));
     sc->contact_refits = 0;
   } else {
     sc->timers->start(kKBvh, s);
     scene_bounds(sc->topo, sc->x4, sc->bounds_ws, s);    // the narrow-phase screen reads it
-    bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, s);
-    bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s);
+    bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
+    bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
     sc->timers->stop(kKBvh, s);
     ++sc->contact_refits;
   }
