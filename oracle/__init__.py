@@ -57,6 +57,8 @@ def lib():
         L.orc_eval.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
                                dbl, dbl, dbl, dbl, ctypes.c_int]
         L.orc_eval.restype = P
+        L.orc_hvp.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
+                              dbl, dbl, dbl, dbl, P, P, P]
         L.orc_result_nnzb.argtypes = [P]
         L.orc_result_nnzb.restype = i64
         L.orc_result_copy.argtypes = [P, P, P, P, P, P, P]
@@ -224,6 +226,29 @@ def eval_contact(scene, x: np.ndarray, prs: Dict[str, np.ndarray], lag: Optional
     finally:
         L.orc_result_free(h)
     return dict(E=float(E[0]), g=g, I=I, J=J, V=V, Ek=Ek[:np_])
+
+
+def hvp(scene, x: np.ndarray, prs: Dict[str, np.ndarray], lag: Optional[Dict[str, np.ndarray]], u: np.ndarray,
+        params: Optional[dict] = None):
+    """Unprojected contact Hessian times a full-space direction u [Nv,3] (kinematic
+    vertices included): returns (J^T y [Ns,3], sum of y over kinematic vertices [3])."""
+    p = dict(scene.params) if params is None else params
+    np_ = len(prs["type"])
+    if lag is None or p["mu"] == 0.0:
+        nfr = 0
+        lag = dict(v=np.zeros((0, 4), np.int32), gamma=np.zeros((0, 4)), n=np.zeros((0, 3)),
+                   anchor=np.zeros((0, 3)), lam=np.zeros(0))
+    else:
+        nfr = len(lag["lam"])
+    out_r = np.zeros((scene.Ns, 3))
+    out_k = np.zeros(3)
+    lib().orc_hvp(scene.Nv, _p(_f64(x)), scene.F, _p(_i32(scene.tris)), scene.E, _p(_i32(scene.edges)),
+                  _p(_i32(scene.cage_idx)), _p(_f64(scene.w)), scene.Ns, np_,
+                  _p(_i32(prs["type"])), _p(_i32(prs["i"])), _p(_i32(prs["j"])), nfr,
+                  _p(_i32(lag["v"])), _p(_f64(lag["gamma"])), _p(_f64(lag["n"])), _p(_f64(lag["anchor"])),
+                  _p(_f64(lag["lam"])), float(p["dhat"]), float(p["kappa"]), float(p["mu"]),
+                  float(p["eps_v"] * p["h"]), _p(_f64(u)), _p(out_r), _p(out_k))
+    return out_r, out_k
 
 
 def pair_friction(v4, gamma4, n3, anchor3, lam, x4, mu, eps):

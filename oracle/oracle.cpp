@@ -586,6 +586,65 @@ orc_eval_result* orc_eval(int64_t nv, const double* x, int64_t nf, const int32_t
   return res;
 }
 
+// Hessian-vector product of the contact potential without PSD projection, for a full-space
+// direction u (one 3-vector per vertex, kinematic vertices included):
+//   y = (sum_k kappa hess b_k + sum_f hess D_f) u
+//   out_r = J^T y over the embedded vertices (reduced, [ns*3]);
+//   out_kin = sum of y over the kinematic vertices ([3]).
+// With u = J v this is H_r v for the unprojected H_r of orc_eval; with u nonzero on the
+// kinematic vertices it is the mixed derivative of g_r with respect to their positions.
+void orc_hvp(int64_t nv, const double* x, int64_t nf, const int32_t* tris, int64_t ne, const int32_t* edges,
+             const int32_t* idx, const double* w, int64_t ns, int64_t np, const int32_t* type, const int32_t* pi,
+             const int32_t* pj, int64_t nfr, const int32_t* lv, const double* lgamma, const double* ln,
+             const double* lanchor, const double* llambda, double dhat, double kappa, double mu, double eps,
+             const double* u, double* out_r, double* out_kin) {
+  Mesh m{nv, nf, ne, x, tris, edges, nullptr};
+  std::vector<double> y(3 * nv, 0.0);
+  auto apply = [&](const int32_t v[4], const Local& L) {
+    double u4[12], y4[12];
+    gather4(u, v, u4);
+    for (int i = 0; i < 12; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < 12; ++j) acc += L.H[i * 12 + j] * u4[j];
+      y4[i] = acc;
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int k = 0; k < 3; ++k) y[3 * v[a] + k] += y4[3 * a + k];
+  };
+  for (int64_t k = 0; k < np; ++k) {
+    int32_t v[4];
+    stencil(m, type[k], pi[k], pj[k], v);
+    double x4[12];
+    gather4(x, v, x4);
+    Local L;
+    barrier_local(type[k], x4, dhat, kappa, L);
+    apply(v, L);
+  }
+  if (mu > 0.0) {
+    for (int64_t f = 0; f < nfr; ++f) {
+      Lag L;
+      for (int a = 0; a < 4; ++a) { L.v[a] = lv[4 * f + a]; L.gamma[a] = lgamma[4 * f + a]; }
+      for (int q = 0; q < 3; ++q) { L.n[q] = ln[3 * f + q]; L.anchor[q] = lanchor[3 * f + q]; }
+      L.lambda = llambda[f];
+      double x4[12];
+      gather4(x, L.v, x4);
+      Local F;
+      friction_local(L, x4, mu, eps, F);
+      apply(L.v, F);
+    }
+  }
+  for (int64_t i = 0; i < 3 * ns; ++i) out_r[i] = 0.0;
+  for (int k = 0; k < 3; ++k) out_kin[k] = 0.0;
+  for (int64_t a = 0; a < nv; ++a) {
+    if (idx[4 * a] < 0) {
+      for (int k = 0; k < 3; ++k) out_kin[k] += y[3 * a + k];
+      continue;
+    }
+    for (int i = 0; i < 4; ++i)
+      for (int k = 0; k < 3; ++k) out_r[3 * idx[4 * a + i] + k] += w[4 * a + i] * y[3 * a + k];
+  }
+}
+
 int64_t orc_result_nnzb(const orc_eval_result* r) { return (int64_t)r->R.H.size(); }
 
 void orc_result_copy(const orc_eval_result* r, double* E, double* g, int32_t* I, int32_t* J,

@@ -723,12 +723,45 @@ def batched_grasp(n_scenes: int = 256, seed: int = 0, min_tris: int = 2000, max_
     return out
 
 
+def pad_lift(seed: int = 0, small: bool = False, n_steps: int = 20, theta: float = 1e-4) -> Scene:
+    """The sphere-on-pad scene as a dynamic trajectory: the cage is linear corotational
+    (E = 5e4 Pa, nu = 0.45, rho = 1e3 kg/m^3, the soft body of Sec. IV-A) under gravity,
+    its top layer of nodes held fixed; the kinematic pad moves up by `theta` per time step
+    (h = 1e-2 s) for `n_steps` steps; checkpoints every 5 steps.  Inputs only: the driver
+    and the adjoint read these attributes.
+      q0            starting (and rest) cage positions, zero initial velocity
+      fixed_nodes   bool [Ns], the top cage layer
+      material      dict(E, nu, rho)
+      gravity       [3] m/s^2
+      pad_dir       unit direction of the pad motion; the pad at step n sits at
+                    x_kin + n * theta * pad_dir
+    small=True: level-2 icosphere, 3^3 cage cubes, 12 x 12 pad (for CPU tests)."""
+    if small:
+        sc = sphere_on_pad(seed, level=2, pad_cells=12, cage_cubes=3)
+    else:
+        sc = sphere_on_pad(seed)
+    sc.name = "pad_lift" + ("_small" if small else "")
+    sc.q0 = sc.iterate(0)
+    ztop = sc.q_rest[:, 2].max()
+    sc.fixed_nodes = np.abs(sc.q_rest[:, 2] - ztop) < 1e-12
+    sc.material = dict(E=5e4, nu=0.45, rho=1e3)
+    sc.gravity = np.array([0.0, 0.0, -9.81])
+    sc.pad_dir = np.array([0.0, 0.0, 1.0])
+    sc.theta = float(theta)
+    sc.n_steps = int(n_steps)
+    sc.checkpoint_every = 5
+    return sc
+
+
 def make_config(k: int, seed: int = 0, small: bool = False) -> Scene:
-    """k = 1: sphere on pad; 2: bubble grasp; 3: plate in rack; 4: 256 batched bubble grasps.
+    """k = 1: sphere on pad; 2: bubble grasp; 3: plate in rack; 4: 256 batched bubble grasps;
+    5: the sphere on a rising pad, a 20-step dynamic trajectory (the adjoint's workload).
     small=True gives reduced versions (configs 2 and 3 that the brute-force oracle enumerates
-    in seconds; 16 small scenes for config 4)."""
+    in seconds; 16 small scenes for config 4; a coarse sphere for config 5)."""
     if k == 1:
         return sphere_on_pad(seed)
+    if k == 5:
+        return pad_lift(seed, small=small)
     if k == 2:
         if small:
             return bubble_grasp(seed, n_body=16, n_mem=10, body_cage=(5, 5, 5), mem_cage=(8, 3, 6))
