@@ -66,8 +66,12 @@ enum {
 typedef struct {
   double dhat, kappa, mu, eps_v, h, accd_s;
   int32_t accd_max_iter;
-  int32_t reserved;
+  int32_t flags;            /* EIPC_PARAM_* bits, 0 for the defaults */
 } eipc_params;
+
+/* eipc_params.flags: EIPC_PARAM_NO_PROJECTION makes eipc_eval_contact return the exact
+ * (unprojected) Hessian instead of the projected-Newton one. */
+enum { EIPC_PARAM_NO_PROJECTION = 1 };
 
 /* Contact pair list, all device arrays owned by the caller.  Pair k is a point-triangle
  * pair (type 0: i = vertex, j = triangle) or an edge-edge pair (type 1: i < j edge ids),
@@ -160,6 +164,24 @@ eipc_status eipc_eval_contact(eipc_scene* scene, const double* q, const eipc_pai
 eipc_status eipc_accd_toi(eipc_scene* scene, const double* x, const double* dx,
                           const eipc_params* p, double* alpha, int64_t* n_candidates,
                           eipc_stream stream);
+
+/* Hessian-vector product of the contact potential (Eq. 7-8 barrier and lagged friction,
+ * reduced by Eq. 17) WITHOUT the PSD projection: the exact second derivative that an
+ * adjoint (implicit differentiation of a Newton step) needs.  With y = H u, where H is
+ * the full-space contact Hessian at x = J q over `pairs` (and `lag`, if given and mu > 0)
+ * and u is J v on the embedded vertices and kin_dir on every kinematic vertex:
+ *   out_r[Ns*3]  (device) <- J^T y, i.e. H_r v plus the mixed term of the kinematic motion;
+ *   out_kin[3]   (device, may be NULL) <- the sum of y over the kinematic vertices, i.e.
+ *                 the derivative of the contact force on the kinematic set along v.
+ * v: device [Ns*3]; kin_dir: HOST array of 3 doubles, or NULL for zero.  The reduction
+ * is deterministic (sort by node, fixed-order warp sums), like eipc_eval_contact's. */
+eipc_status eipc_contact_hvp(eipc_scene* scene, const double* q, const eipc_pairs* pairs, const eipc_lag* lag,
+                             const eipc_params* params, const double* v, const double* kin_dir, double* out_r,
+                             double* out_kin, eipc_stream stream);
+
+/* New prescribed positions of the kinematic vertices: x_kin is a DEVICE array [Nv*3]
+ * (rows of embedded vertices are ignored).  Asynchronous on `stream`, capturable. */
+eipc_status eipc_scene_set_kinematic(eipc_scene* scene, const double* x_kin, eipc_stream stream);
 
 /* Synchronises the stream, copies the device status word and clears it.
  * flags <- OR of EIPC_FLAG_*; needed[0..3] <- pairs, candidates, records, BSR blocks

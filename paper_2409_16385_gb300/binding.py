@@ -24,13 +24,14 @@ FLAGS = {1: "PENETRATION", 2: "PAIR_OVERFLOW", 4: "CAND_OVERFLOW", 8: "REC_OVERF
 EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_candidates", "eipc_friction_lag",
            "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
-           "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch"]
+           "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
+           "eipc_contact_hvp", "eipc_scene_set_kinematic"]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("mu", ctypes.c_double),
                 ("eps_v", ctypes.c_double), ("h", ctypes.c_double), ("accd_s", ctypes.c_double),
-                ("accd_max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("accd_max_iter", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class _Pairs(ctypes.Structure):
@@ -98,6 +99,11 @@ def load(build_if_missing: bool = True):
     L.eipc_group_alpha.restype = i32
     L.eipc_set_launch.argtypes = [P, i32, i32, i32, i32]
     L.eipc_set_launch.restype = i32
+    L.eipc_contact_hvp.argtypes = [P, P, ctypes.POINTER(_Pairs), ctypes.POINTER(_Lag), ctypes.POINTER(Params), P, P, P,
+                                   P, P]
+    L.eipc_contact_hvp.restype = i32
+    L.eipc_scene_set_kinematic.argtypes = [P, P, P]
+    L.eipc_scene_set_kinematic.restype = i32
     _lib = L
     return L
 
@@ -260,16 +266,50 @@ class ContactScene:
                                           ctypes.byref(lc), _stream()), "eipc_friction_lag")
         return lag
 
-    def eval_contact(self, q, pairs: PairList, lag: Optional[LagState] = None, E=None, g_r=None, H: Optional[BSR] = None):
+    def eval_contact(self, q, pairs: PairList, lag: Optional[LagState] = None, E=None, g_r=None, H: Optional[BSR] = None,
+                     project: bool = True):
+        """(E, g_r, H_r); project=False returns the exact Hessian instead of the
+        projected-Newton one."""
         import torch
         E = E if E is not None else torch.zeros(1, dtype=torch.float64, device=self.device)
         g_r = g_r if g_r is not None else torch.zeros((self.Ns, 3), dtype=torch.float64, device=self.device)
         H = H if H is not None else self.new_bsr()
         pc, hc = pairs._c(), H._c()
         lp = ctypes.byref(lag._c()) if lag is not None else None
-        _check(self.lib.eipc_eval_contact(self.handle, _ptr(q), ctypes.byref(pc), lp, ctypes.byref(self.params), _ptr(E),
+        prm = self.params
+        if not project:
+            prm = Params(*[getattr(self.params, f) for f, _ in Params._fields_])
+            prm.flags = 1
+        _check(self.lib.eipc_eval_contact(self.handle, _ptr(q), ctypes.byref(pc), lp, ctypes.byref(prm), _ptr(E),
                                           _ptr(g_r), ctypes.byref(hc), _stream()), "eipc_eval_contact")
         return E, g_r, H
+
+    def contact_hvp(self, q, pairs: PairList, v, lag: Optional[LagState] = None, kin_dir=None, out=None,
+                    out_kin=None):
+        """Exact (unprojected) contact Hessian applied to the reduced direction v [Ns,3],
+        with the kinematic vertices moving along kin_dir (3 floats, or None).  Returns
+        (J^T H u [Ns,3], sum of H u over the kinematic vertices [3])."""
+        import torch
+        out = out if out is not None else torch.empty((self.Ns, 3), dtype=torch.float64, device=self.device)
+        out_kin = out_kin if out_kin is not None else torch.empty(3, dtype=torch.float64, device=self.device)
+        kd = None
+        if kin_dir is not None:
+            kd_arr = (ctypes.c_double * 3)(*[float(c) for c in kin_dir])
+            kd = ctypes.cast(kd_arr, ctypes.c_void_p)
+        pc = pairs._c()
+        lp = ctypes.byref(lag._c()) if lag is not None else None
+        _check(self.lib.eipc_contact_hvp(self.handle, _ptr(q), ctypes.byref(pc), lp, ctypes.byref(self.params), _ptr(v),
+                                         kd, _ptr(out), _ptr(out_kin), _stream()), "eipc_contact_hvp")
+        return out, out_kin
+
+    def set_kinematic(self, x_kin):
+        """New positions of the kinematic vertices (device f64 [Nv,3]; other rows ignored)."""
+        _check(self.lib.eipc_scene_set_kinematic(self.handle, _ptr(x_kin), _stream()), "eipc_scene_set_kinematic")
+
+    def set_params(self, **kw):
+        """Change contact parameters (dhat, kappa, mu, eps_v, h, accd_s, accd_max_iter)."""
+        for k, v in kw.items():
+            setattr(self.params, k, type(getattr(self.params, k))(v))
 
     def accd_toi(self, x, dx, alpha=None, n_candidates=None):
         import torch

@@ -1,5 +1,6 @@
 // C ABI entry points (include/embipc.h): argument checks, scene creation and workspace
 // sizing, and the enqueueing of each call's kernels on the caller's stream.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -19,7 +20,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
@@ -60,7 +61,7 @@ cudaError_t alloc_bvh(Bvh& t, int64_t n) {
 
 bool params_ok(const eipc_params* p) {
   return p && p->dhat > 0.0 && p->kappa > 0.0 && p->mu >= 0.0 && p->eps_v > 0.0 && p->h > 0.0 && p->accd_s > 0.0 &&
-         p->accd_s < 1.0 && p->accd_max_iter > 0;
+         p->accd_s < 1.0 && p->accd_max_iter > 0 && (p->flags & ~EIPC_PARAM_NO_PROJECTION) == 0;
 }
 
 bool pairs_ok(const eipc_pairs* p) {
@@ -146,6 +147,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
   ok(dalloc(&s->hvals, s->rec_cap)); ok(dalloc(&s->hvals_alt, s->rec_cap)); ok(dalloc(&s->hrec, 9 * s->rec_cap));
   ok(dalloc(&s->ublk, 9 * s->rec_cap));
+  ok(dalloc(&s->hvp_out, 3 * (Ns + 1)));
   ok(dalloc(&s->seg_flag, s->rec_cap)); ok(dalloc(&s->seg_id, s->rec_cap)); ok(dalloc(&s->seg_start, s->rec_cap));
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, 3 * s->gcap));
@@ -230,6 +232,27 @@ eipc_status eipc_eval_contact(eipc_scene* sc, const double* q, const eipc_pairs*
                                                                           !lag->anchor || !lag->lambda))))
     return EIPC_ERR_INVALID;
   eval_launch(sc, q, *pairs, lag, *p, E, g_r, *H, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_contact_hvp(eipc_scene* sc, const double* q, const eipc_pairs* pairs, const eipc_lag* lag,
+                             const eipc_params* p, const double* v, const double* kin_dir, double* out_r,
+                             double* out_kin, eipc_stream stream) {
+  if (!sc || (!q && sc->ns > 0) || !params_ok(p) || !pairs_ok(pairs) || (!v && sc->ns > 0) ||
+      (!out_r && sc->ns > 0))
+    return EIPC_ERR_INVALID;
+  if (lag && (!lag->count || lag->capacity < 0 || (lag->capacity > 0 && (!lag->v || !lag->gamma || !lag->n ||
+                                                                          !lag->anchor || !lag->lambda))))
+    return EIPC_ERR_INVALID;
+  if (kin_dir && !(std::isfinite(kin_dir[0]) && std::isfinite(kin_dir[1]) && std::isfinite(kin_dir[2])))
+    return EIPC_ERR_INVALID;
+  hvp_launch(sc, q, *pairs, lag, *p, v, kin_dir, out_r, out_kin, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_scene_set_kinematic(eipc_scene* sc, const double* x_kin, eipc_stream stream) {
+  if (!sc || !x_kin) return EIPC_ERR_INVALID;
+  set_kinematic_launch(sc, x_kin, (cudaStream_t)stream);
   return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
 }
 

@@ -252,6 +252,9 @@ struct EvalArgs {
   double* grec;
   double* item_E;
   DevStatus* st;
+  bool project;            // PSD-project the barrier Hessians (projected Newton)
+  const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
+  double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
 };
 
 // Eigen-decomposition of the symmetric 5x5 K: an FP32 Jacobi pre-diagonalisation of K/|K|,
@@ -343,8 +346,104 @@ __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32
   A.hvals[pos] = (uint32_t)pos;
 }
 
+// The barrier Hessian of one active pair in its span (Sec. III-B, Eq. 7; the 12 x 12
+// Hessian of kappa b(d(x)) lies in the span of c^ (x) e_xyz and a^_j (x) r^): the
+// orthonormal 4-vectors basis[0] = c^, basis[1..2] = a^_1, a^_2, the unit direction r^
+// between the closest points, and the 5 x 5 matrix K of the Hessian in that basis,
+// unprojected and symmetric.  Also the energy kappa b(d) and b'(d).
+struct BarrierSpan {
+  double E, b1, cn;
+  V3 rh;
+  double basis[3][4];
+  double K[5][5];
+};
+
+__device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, double d, double dhat, double kappa,
+                                             BarrierSpan& B) {
+  const double lg = log(d / dhat);
+  const double m = d - dhat;
+  const double b = -m * m * lg;
+  const double b1 = -2.0 * m * lg - m * m / d;
+  const double b2 = -2.0 * lg - 4.0 * m / d + (m * m) / (d * d);
+  B.E = kappa * b;
+  B.b1 = b1;
+  // r and r^
+  V3 r = {0.0, 0.0, 0.0};
+  for (int a = 0; a < 4; ++a) r = r + Y[a] * S.c[a];
+  const double rn = sqrt(dot(r, r));
+  B.rh = r * (1.0 / rn);
+  const V3 rh = B.rh;
+  // orthonormal 4-vectors c^, a^_1, a^_2
+  const double cn = sqrt(S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3]);
+  B.cn = cn;
+  for (int a = 0; a < 4; ++a) B.basis[0][a] = S.c[a] / cn;
+  for (int j = 0; j < 2; ++j) {
+    if (j < S.m) {
+      double t[4];
+      for (int a = 0; a < 4; ++a) t[a] = S.a[j][a];
+      for (int i = 0; i <= j; ++i) {
+        double pr = 0.0;
+        for (int a = 0; a < 4; ++a) pr += B.basis[i][a] * t[a];
+        for (int a = 0; a < 4; ++a) t[a] -= pr * B.basis[i][a];
+      }
+      double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+      for (int a = 0; a < 4; ++a) B.basis[1 + j][a] = t[a] / tn;
+    } else {
+      for (int a = 0; a < 4; ++a) B.basis[1 + j][a] = 0.0;
+    }
+  }
+  // v_j, M = 2 [v_j . v_l], g_j = Q^T G_j
+  V3 vj[2];
+  for (int j = 0; j < 2; ++j) {
+    vj[j] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) vj[j] = vj[j] + Y[a] * S.a[j][a];
+  }
+  double (&K)[5][5] = B.K;
+  const double kb = kappa * cn * cn;
+  const double rr = kappa * (b2 - b1 / d);
+  const double rhv[3] = {rh.x, rh.y, rh.z};
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) K[p][q] = cn * cn * (rr * rhv[p] * rhv[q]) + (p == q ? kb * b1 / d : 0.0);
+  for (int p = 0; p < 5; ++p)
+    for (int q = 3; q < 5; ++q) { K[p][q] = 0.0; K[q][p] = 0.0; }
+  if (S.m > 0) {
+    double g[2][5];
+    for (int j = 0; j < S.m; ++j) {
+      double ca = 0.0;
+      for (int a = 0; a < 4; ++a) ca += B.basis[0][a] * S.a[j][a];
+      const double vv[3] = {vj[j].x, vj[j].y, vj[j].z};
+      for (int p = 0; p < 3; ++p) g[j][p] = 2.0 * cn * vv[p] + 2.0 * d * ca * rhv[p];
+      for (int l = 0; l < 2; ++l) {
+        double al = 0.0;
+        for (int a = 0; a < 4; ++a) al += B.basis[1 + l][a] * S.a[j][a];
+        g[j][3 + l] = 2.0 * d * al;
+      }
+    }
+    double Mi[2][2];
+    if (S.m == 1) {
+      Mi[0][0] = 1.0 / (2.0 * dot(vj[0], vj[0]));
+    } else {
+      const double m00 = 2.0 * dot(vj[0], vj[0]), m01 = 2.0 * dot(vj[0], vj[1]), m11 = 2.0 * dot(vj[1], vj[1]);
+      const double det = m00 * m11 - m01 * m01;
+      Mi[0][0] = m11 / det; Mi[1][1] = m00 / det; Mi[0][1] = Mi[1][0] = -m01 / det;
+    }
+    const double beta = -kappa * b1 / (2.0 * d);
+    for (int p = 0; p < 5; ++p)
+      for (int q = 0; q < 5; ++q) {
+        double s2 = 0.0;
+        for (int j = 0; j < S.m; ++j)
+          for (int l = 0; l < S.m; ++l) s2 += g[j][p] * Mi[j][l] * g[l][q];
+        K[p][q] += beta * s2;
+      }
+  }
+  // symmetrise against rounding
+  for (int p = 0; p < 5; ++p)
+    for (int q = p + 1; q < 5; ++q) { const double t = 0.5 * (K[p][q] + K[q][p]); K[p][q] = t; K[q][p] = t; }
+}
+
 // MINB = 2: no register cap (248 registers, 2 blocks of 128 per SM); MINB = 3: at most 170
-// registers (3 blocks per SM, a few hundred bytes of spills).  Chosen at run time.
+// registers (3 blocks per SM, a few hundred bytes of spills).  Chosen at run time.  With
+// A.project false the pair Hessians are kept as they are (no PSD projection).
 template <int MINB>
 __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A) {
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
@@ -378,91 +477,24 @@ __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A)
       const double d = sqrt(S.d2);
       active = d < A.dhat;
       if (active) {
-        const double dh = A.dhat;
-        const double lg = log(d / dh);
-        const double m = d - dh;
-        const double b = -m * m * lg;
-        b1 = -2.0 * m * lg - m * m / d;
-        const double b2 = -2.0 * lg - 4.0 * m / d + (m * m) / (d * d);
-        E = A.kappa * b;
-        // r and r^
-        V3 r = {0.0, 0.0, 0.0};
-        for (int a = 0; a < 4; ++a) r = r + Y[a] * S.c[a];
-        const double rn = sqrt(dot(r, r));
-        rh = r * (1.0 / rn);
-        // orthonormal 4-vectors c^, a^_1, a^_2
-        cn = sqrt(S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3]);
-        for (int a = 0; a < 4; ++a) basis[0][a] = S.c[a] / cn;
-        for (int j = 0; j < 2; ++j) {
-          if (j < S.m) {
-            double t[4];
-            for (int a = 0; a < 4; ++a) t[a] = S.a[j][a];
-            for (int i = 0; i <= j; ++i) {
-              double pr = 0.0;
-              for (int a = 0; a < 4; ++a) pr += basis[i][a] * t[a];
-              for (int a = 0; a < 4; ++a) t[a] -= pr * basis[i][a];
-            }
-            double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
-            for (int a = 0; a < 4; ++a) basis[1 + j][a] = t[a] / tn;
-          } else {
-            for (int a = 0; a < 4; ++a) basis[1 + j][a] = 0.0;
-          }
-        }
-        // v_j, M = 2 [v_j . v_l], g_j = Q^T G_j
-        V3 vj[2];
-        for (int j = 0; j < 2; ++j) {
-          vj[j] = {0.0, 0.0, 0.0};
-          for (int a = 0; a < 4; ++a) vj[j] = vj[j] + Y[a] * S.a[j][a];
-        }
-        double K[5][5];
-        const double kb = A.kappa * cn * cn;
-        const double rr = A.kappa * (b2 - b1 / d);
-        const double rhv[3] = {rh.x, rh.y, rh.z};
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) K[p][q] = cn * cn * (rr * rhv[p] * rhv[q]) + (p == q ? kb * b1 / d : 0.0);
-        for (int p = 0; p < 5; ++p)
-          for (int q = 3; q < 5; ++q) { K[p][q] = 0.0; K[q][p] = 0.0; }
-        if (S.m > 0) {
-          double g[2][5];
-          for (int j = 0; j < S.m; ++j) {
-            double ca = 0.0;
-            for (int a = 0; a < 4; ++a) ca += basis[0][a] * S.a[j][a];
-            const double vv[3] = {vj[j].x, vj[j].y, vj[j].z};
-            for (int p = 0; p < 3; ++p) g[j][p] = 2.0 * cn * vv[p] + 2.0 * d * ca * rhv[p];
-            for (int l = 0; l < 2; ++l) {
-              double al = 0.0;
-              for (int a = 0; a < 4; ++a) al += basis[1 + l][a] * S.a[j][a];
-              g[j][3 + l] = 2.0 * d * al;
-            }
-          }
-          double Mi[2][2];
-          if (S.m == 1) {
-            Mi[0][0] = 1.0 / (2.0 * dot(vj[0], vj[0]));
-          } else {
-            const double m00 = 2.0 * dot(vj[0], vj[0]), m01 = 2.0 * dot(vj[0], vj[1]), m11 = 2.0 * dot(vj[1], vj[1]);
-            const double det = m00 * m11 - m01 * m01;
-            Mi[0][0] = m11 / det; Mi[1][1] = m00 / det; Mi[0][1] = Mi[1][0] = -m01 / det;
-          }
-          const double beta = -A.kappa * b1 / (2.0 * d);
+        BarrierSpan B;
+        barrier_span(Y, S, d, A.dhat, A.kappa, B);
+        E = B.E; b1 = B.b1; cn = B.cn; rh = B.rh;
+        for (int c = 0; c < 3; ++c)
+          for (int a = 0; a < 4; ++a) basis[c][a] = B.basis[c][a];
+        if (A.project) {
+          double V[5][5];
+          eigen5(B.K, V);
           for (int p = 0; p < 5; ++p)
             for (int q = 0; q < 5; ++q) {
               double s = 0.0;
-              for (int j = 0; j < S.m; ++j)
-                for (int l = 0; l < S.m; ++l) s += g[j][p] * Mi[j][l] * g[l][q];
-              K[p][q] += beta * s;
+              for (int e = 0; e < 5; ++e) s += (B.K[e][e] > 0.0 ? V[p][e] * B.K[e][e] * V[q][e] : 0.0);
+              Kp[p][q] = s;
             }
+        } else {
+          for (int p = 0; p < 5; ++p)
+            for (int q = 0; q < 5; ++q) Kp[p][q] = B.K[p][q];
         }
-        // symmetrise against rounding, then project
-        for (int p = 0; p < 5; ++p)
-          for (int q = p + 1; q < 5; ++q) { const double s = 0.5 * (K[p][q] + K[q][p]); K[p][q] = s; K[q][p] = s; }
-        double V[5][5];
-        eigen5(K, V);
-        for (int p = 0; p < 5; ++p)
-          for (int q = 0; q < 5; ++q) {
-            double s = 0.0;
-            for (int e = 0; e < 5; ++e) s += (K[e][e] > 0.0 ? V[p][e] * K[e][e] * V[q][e] : 0.0);
-            Kp[p][q] = s;
-          }
       }
     }
     A.item_E[k] = E;
@@ -578,6 +610,150 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
         emit_upper(A, pos2, nodes[a], nodes[b], B);
       }
     }
+  }
+}
+
+// ------------------------------------------------------------------ Hessian-vector product
+// y = H u for the unprojected contact Hessian H and the full-space direction u = J v on the
+// embedded vertices, u = kin_dir on the kinematic ones.  Each item emits one record per
+// cage node of its stencil (J^T y restricted to the item) and one record under key ns
+// holding the sum of y over its kinematic vertices; the gradient reduction sums them.
+
+__global__ void k_hvp_counts(const int32_t* __restrict__ item_n, const int64_t* n_items, int64_t cap,
+                             int64_t* __restrict__ rc_g) {
+  const int64_t n = clamp_count(n_items, cap);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride())
+    rc_g[k] = (int64_t)item_n[k] + 1;
+}
+
+// coefficient sums over the kinematic vertices of a stencil
+__device__ __forceinline__ void kinematic_sums(const int32_t v[4], const int32_t* __restrict__ cage_idx,
+                                               const double coef[3][4], int ncoef, double out[3]) {
+  for (int c = 0; c < 3; ++c) out[c] = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    if (__ldg(cage_idx + 4 * (int64_t)v[a]) >= 0) continue;
+    for (int c = 0; c < ncoef; ++c) out[c] += coef[c][a];
+  }
+}
+
+__device__ __forceinline__ V3 load_dir(const double* __restrict__ v, int32_t node) {
+  return {v[3 * (int64_t)node], v[3 * (int64_t)node + 1], v[3 * (int64_t)node + 2]};
+}
+
+__device__ __forceinline__ void emit_g(const EvalArgs& A, int64_t pos, uint64_t key, V3 y) {
+  if (pos >= A.gcap) return;
+  A.gkeys[pos] = key;
+  A.gvals[pos] = (uint32_t)pos;
+  A.grec[3 * pos] = y.x; A.grec[3 * pos + 1] = y.y; A.grec[3 * pos + 2] = y.z;
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
+  const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
+  const int64_t nit = *A.n_items;
+  const int64_t np = P < nit ? P : nit;
+  const V3 kd = {A.kin_dir[0], A.kin_dir[1], A.kin_dir[2]};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < np; k += grid_stride()) {
+    int32_t v[4];
+    const int type = A.pr.type[k];
+    stencil_vertices(A.T, type, A.pr.i[k], A.pr.j[k], v);
+    V3 Y[4];
+    const V3 X0 = load_x(A.x4, v[0]);
+    for (int a = 0; a < 4; ++a) Y[a] = load_x(A.x4, v[a]) - X0;
+    Stencil S;
+    if (type == 0) pt_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    const int n = A.item_n[k];
+    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+    const int64_t og = A.ro_g[k];
+    bool active = false;
+    double t[5] = {0, 0, 0, 0, 0};
+    double nw[kMaxNodes][3];
+    double ks[3] = {0, 0, 0};
+    V3 rh = {0.0, 0.0, 0.0};
+    if (!(S.d2 > 0.0)) {
+      raise_flag(A.st, EIPC_FLAG_PENETRATION);
+    } else {
+      const double d = sqrt(S.d2);
+      active = d < A.dhat;
+      if (active) {
+        BarrierSpan B;
+        barrier_span(Y, S, d, A.dhat, A.kappa, B);
+        rh = B.rh;
+        node_weights(v, A.cage_idx, A.w, nodes, n, B.basis, 3, nw);
+        kinematic_sums(v, A.cage_idx, B.basis, 3, ks);
+        // the direction in the span: Q^T u
+        V3 uc = kd * ks[0];
+        double ur[2] = {ks[1] * dot(kd, rh), ks[2] * dot(kd, rh)};
+        for (int u = 0; u < n; ++u) {
+          const V3 vu = load_dir(A.hv_dir, nodes[u]);
+          uc = uc + vu * nw[u][0];
+          const double vr = dot(vu, rh);
+          ur[0] += nw[u][1] * vr;
+          ur[1] += nw[u][2] * vr;
+        }
+        const double in5[5] = {uc.x, uc.y, uc.z, ur[0], ur[1]};
+        for (int p = 0; p < 5; ++p) {
+          double acc = 0.0;
+          for (int q = 0; q < 5; ++q) acc += B.K[p][q] * in5[q];
+          t[p] = acc;
+        }
+      }
+    }
+    const V3 tc = {t[0], t[1], t[2]};
+    for (int u = 0; u < n; ++u) {
+      V3 y = {0.0, 0.0, 0.0};
+      if (active) y = tc * nw[u][0] + rh * (nw[u][1] * t[3] + nw[u][2] * t[4]);
+      emit_g(A, og + u, (uint64_t)nodes[u], y);
+    }
+    V3 yk = {0.0, 0.0, 0.0};
+    if (active) yk = tc * ks[0] + rh * (ks[1] * t[3] + ks[2] * t[4]);
+    emit_g(A, og + n, (uint64_t)A.ns, yk);
+  }
+}
+
+__global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_lag lag, double mu, double eps) {
+  const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
+  const int64_t nit = *A.n_items;
+  const int64_t L = nit - P;
+  const V3 kd = {A.kin_dir[0], A.kin_dir[1], A.kin_dir[2]};
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < L; f += grid_stride()) {
+    const int64_t k = P + f;
+    const int4 q4 = reinterpret_cast<const int4*>(lag.v)[f];
+    const int32_t v[4] = {q4.x, q4.y, q4.z, q4.w};
+    double gam[4];
+    for (int a = 0; a < 4; ++a) gam[a] = lag.gamma[4 * f + a];
+    const V3 nrm = {lag.n[3 * f], lag.n[3 * f + 1], lag.n[3 * f + 2]};
+    const V3 anc = {lag.anchor[3 * f], lag.anchor[3 * f + 1], lag.anchor[3 * f + 2]};
+    const double ml = mu * lag.lambda[f];
+    V3 vs = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 4; ++a) vs = vs + load_x(A.x4, v[a]) * gam[a];
+    vs = vs - anc;
+    const V3 u = vs - nrm * dot(nrm, vs);
+    const double y2 = dot(u, u);
+    double f1y, f1p_minus;   // f1(y)/y, f1'(y) - f1(y)/y
+    if (y2 == 0.0) {
+      f1y = 2.0 / eps; f1p_minus = 0.0;
+    } else {
+      const double y = sqrt(y2);
+      if (y < eps) { f1y = 2.0 / eps - y / (eps * eps); f1p_minus = -y / (eps * eps); }
+      else { f1y = 1.0 / y; f1p_minus = -1.0 / y; }
+    }
+    const int n = A.item_n[k];
+    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+    const double coef[3][4] = {{gam[0], gam[1], gam[2], gam[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    double nw[kMaxNodes][3];
+    node_weights(v, A.cage_idx, A.w, nodes, n, coef, 1, nw);
+    double ks[3];
+    kinematic_sums(v, A.cage_idx, coef, 1, ks);
+    // s = sum_a gamma_a u_a, then F s with F = mu lambda [f1/y (I - n n^T) + (f1' - f1/y) u u^T / y^2]
+    V3 sd = kd * ks[0];
+    for (int a = 0; a < n; ++a) sd = sd + load_dir(A.hv_dir, nodes[a]) * nw[a][0];
+    const V3 sp = sd - nrm * dot(nrm, sd);
+    V3 Fs = sp * (ml * f1y);
+    if (y2 > 0.0) Fs = Fs + u * (ml * f1p_minus * dot(u, sd) / y2);
+    const int64_t og = A.ro_g[k];
+    for (int a = 0; a < n; ++a) emit_g(A, og + a, (uint64_t)nodes[a], Fs * nw[a][0]);
+    emit_g(A, og + n, (uint64_t)A.ns, Fs * ks[0]);
   }
 }
 
@@ -851,6 +1027,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.ro_h = sc->ro_h; A.ro_g = sc->ro_g; A.n_items = cnt + kCntItems; A.rec_cap = sc->rec_cap; A.gcap = sc->gcap;
   A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
+  A.project = (p.flags & EIPC_PARAM_NO_PROJECTION) == 0;
+  A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (sc->tune.eval_variant == 3
                   ? launch(k_eval_barrier<3>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
@@ -914,6 +1092,56 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   launch(k_sum_partial, kScanBlocks, kBlock, 0, s, sc->item_E, cnt + kCntItems, item_cap, sc->sum_partial);
   launch(k_sum_final, 1, 32, 0, s, sc->sum_partial, kScanBlocks, E);
   sc->timers->stop(kKEnergy, s);
+}
+
+void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
+                const double* v, const double* kin_dir, double* out_r, double* out_kin, cudaStream_t s) {
+  EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
+  const bool fr = lag && p.mu > 0.0;
+  int64_t* cnt = sc->counters;
+  cudaMemsetAsync(cnt + kCntItems, 0, 5 * sizeof(int64_t), s);
+  cudaMemsetAsync(cnt + kCntZero, 0, sizeof(int64_t), s);
+  const int64_t item_cap = sc->item_cap;
+  launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
+         fr ? lag->capacity : 0, sc->cage_idx, item_cap, sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
+         sc->rc_h, sc->rc_g, cnt + kCntItems, sc->status);
+  launch(k_hvp_counts, blocks_for(item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(sc->item_n),
+         static_cast<const int64_t*>(cnt + kCntItems), item_cap, sc->rc_g);
+  int64_t* tot_g = cnt + 10;
+  exclusive_scan_i64(sc->rc_g, sc->ro_g, cnt + kCntItems, item_cap, tot_g, sc->scan_partial, s);
+  launch(k_rec_check, 1, 32, 0, s, static_cast<const int64_t*>(cnt + kCntZero), static_cast<const int64_t*>(tot_g),
+         sc->rec_cap, sc->gcap, cnt + kCntRecH, cnt + kCntRecG, sc->status);
+  EvalArgs A;
+  A.T = sc->topo; A.pr = pr; A.cage_idx = sc->cage_idx; A.w = sc->w; A.x4 = sc->x4; A.ns = sc->ns;
+  A.dhat = p.dhat; A.kappa = p.kappa; A.item_nodes = sc->item_nodes; A.item_n = sc->item_n;
+  A.ro_h = sc->ro_h; A.ro_g = sc->ro_g; A.n_items = cnt + kCntItems; A.rec_cap = sc->rec_cap; A.gcap = sc->gcap;
+  A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
+  A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
+  A.project = false;
+  A.hv_dir = v;
+  for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
+  EIPC_TIMED(sc, kKEvalBarrier, s,
+             (launch(k_hvp_barrier, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
+  if (fr)
+    EIPC_TIMED(sc, kKEvalFriction, s,
+               (launch(k_hvp_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
+                       p.eps_v * p.h)));
+  sc->timers->start(kKGReduce, s);
+  int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap, sc->bits_g,
+                          sc->sort_hist, s);
+  const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
+  const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
+  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
+  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
+  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
+         sc->gseg_start);
+  cudaMemsetAsync(sc->hvp_out, 0, sizeof(double) * 3 * (sc->ns + 1), s);
+  launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG,
+         cnt + kCntSegG, sc->gcap, sc->hvp_out);
+  cudaMemcpyAsync(out_r, sc->hvp_out, sizeof(double) * 3 * sc->ns, cudaMemcpyDeviceToDevice, s);
+  if (out_kin)
+    cudaMemcpyAsync(out_kin, sc->hvp_out + 3 * sc->ns, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s);
+  sc->timers->stop(kKGReduce, s);
 }
 
 }  // namespace eipc

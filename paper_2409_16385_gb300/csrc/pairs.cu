@@ -182,6 +182,24 @@ void embed_launch(const eipc_scene* sc, const double* q, double* out, int out_pa
          displacement, outf, sc->status);
 }
 
+namespace {
+// new prescribed positions for the kinematic rows (cage_idx[4v] < 0) only
+__global__ void __launch_bounds__(kBlock) k_set_kinematic(int64_t nv, const int32_t* __restrict__ cage_idx,
+                                                          const double* __restrict__ x_kin, double* __restrict__ x_kin4) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
+    if (cage_idx[4 * v] >= 0) continue;
+    x_kin4[4 * v] = x_kin[3 * v];
+    x_kin4[4 * v + 1] = x_kin[3 * v + 1];
+    x_kin4[4 * v + 2] = x_kin[3 * v + 2];
+  }
+}
+}  // namespace
+
+void set_kinematic_launch(eipc_scene* sc, const double* x_kin, cudaStream_t s) {
+  launch(k_set_kinematic, blocks_for(sc->nv), kBlock, 0, s, sc->nv, static_cast<const int32_t*>(sc->cage_idx), x_kin,
+         sc->x_kin4);
+}
+
 void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const eipc_pairs& out, cudaStream_t s) {
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
   int64_t* n_cand = sc->counters + kCntCand;

@@ -56,6 +56,7 @@ struct eipc_scene {
   uint32_t* hvals_alt;
   double* hrec;          // [rec_cap*9]
   double* ublk;          // [rec_cap*9] reduced upper-triangle blocks
+  double* hvp_out;       // [(ns+1)*3] Hessian-vector product: reduced rows, then the kinematic sum
   int64_t* seg_flag;     // [rec_cap]
   int64_t* seg_id;       // [rec_cap]
   int64_t* seg_start;    // [rec_cap]
@@ -104,6 +105,9 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                  double* E, double* g_r, const eipc_bsr& H, cudaStream_t s);
 int bits_for(uint64_t maxval);
 void group_energy_launch(eipc_scene* sc, double* E_groups, cudaStream_t s);
+void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
+                const double* v, const double* kin_dir, double* out_r, double* out_kin, cudaStream_t s);
+void set_kinematic_launch(eipc_scene* sc, const double* x_kin, cudaStream_t s);
 void group_alpha_launch(eipc_scene* sc, double* alpha_groups, cudaStream_t s);
 void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_params& p, double* alpha,
                  int64_t* n_candidates, cudaStream_t s);

@@ -1,0 +1,142 @@
+"""Cage elasticity of Embedded IPC on the GPU (torch): Phi(q) = sum_T V_T Psi(F_T) with the
+linear corotational density Psi(F) = mu ||F - R||^2 + lambda/2 (tr S - 3)^2, F = R S the
+polar decomposition, F_T = D_T (D_T^0)^{-1}, and V_T the sum of the per-vertex volumes of
+the embedded vertices inside tet T (Sec. III-D; the material of Sec. IV-A).
+
+Derivatives are closed form.  P = dPsi/dF = 2 mu (F - R) + lambda (tr S - 3) R.  For the
+exact Hessian, the rotation's differential is dR = R [w]_x with
+(tr(S) I - S) w = axial(R^T dF - dF^T R), because R^T dF - dF^T R = W S + S W for the
+skew W = R^T dR; and d tr S = R : dF.  Hence
+    dP = 2 mu (dF - dR) + lambda (R : dF) R + lambda (tr S - 3) dR.
+The projected-Newton Hessian clamps the negative eigenvalues of each tet's 9 x 9
+Hessian in F.
+"""
+from __future__ import annotations
+
+import torch
+
+
+def lame(E: float, nu: float):
+    return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+
+
+def _skew(w):
+    z = torch.zeros_like(w[..., 0])
+    return torch.stack([torch.stack([z, -w[..., 2], w[..., 1]], -1),
+                        torch.stack([w[..., 2], z, -w[..., 0]], -1),
+                        torch.stack([-w[..., 1], w[..., 0], z], -1)], -2)
+
+
+def _axial(K):
+    return torch.stack([K[..., 2, 1], K[..., 0, 2], K[..., 1, 0]], -1)
+
+
+class CorotationalCage:
+    """Elasticity of one cage: tets [T,4] (node ids), rest positions q0 [Ns,3], tet
+    volumes V_T [T] (device tensors, float64)."""
+
+    def __init__(self, tets, q0, V_T, mu: float, lam: float):
+        self.tets = tets.long()
+        self.ns = q0.shape[0]
+        self.mu, self.lam = float(mu), float(lam)
+        Dm = self._ds(q0)
+        self.Dm_inv = torch.linalg.inv(Dm)
+        self.V_T = V_T
+        # B maps a tet's 12 node displacements (node-major 3a + c) to dF (row-major 3i + j)
+        T = self.tets.shape[0]
+        B = torch.zeros((T, 9, 12), dtype=q0.dtype, device=q0.device)
+        colsum = self.Dm_inv.sum(1)                     # sum_k Dminv[k, j]
+        for i in range(3):
+            for j in range(3):
+                B[:, 3 * i + j, i] = -colsum[:, j]      # node 0, component i
+                for a in range(1, 4):
+                    B[:, 3 * i + j, 3 * a + i] = self.Dm_inv[:, a - 1, j]
+        self.B = B
+        self.dofs = (3 * self.tets[:, :, None] + torch.arange(3, device=q0.device)[None, None, :]).reshape(T, 12)
+
+    def _ds(self, q):
+        t = self.tets
+        return torch.stack([q[t[:, 1]] - q[t[:, 0]], q[t[:, 2]] - q[t[:, 0]], q[t[:, 3]] - q[t[:, 0]]], dim=2)
+
+    def deformation(self, q):
+        return self._ds(q) @ self.Dm_inv
+
+    @staticmethod
+    def polar(F):
+        U, s, Vh = torch.linalg.svd(F)
+        flip = (torch.linalg.det(U) * torch.linalg.det(Vh)) < 0
+        if bool(flip.any()):
+            U = U.clone(); s = s.clone()
+            U[flip, :, 2] = -U[flip, :, 2]
+            s[flip, 2] = -s[flip, 2]
+        R = U @ Vh
+        S = Vh.transpose(-1, -2) @ torch.diag_embed(s) @ Vh
+        return R, 0.5 * (S + S.transpose(-1, -2))
+
+    def _stress(self, F):
+        R, S = self.polar(F)
+        tr = S.diagonal(dim1=-2, dim2=-1).sum(-1)
+        P = 2.0 * self.mu * (F - R) + self.lam * (tr - 3.0)[:, None, None] * R
+        return P, R, S, tr
+
+    def _scatter(self, G):
+        """dE/dDs per tet [T,3,3] (columns = nodes 1..3) -> nodal vectors [Ns,3]."""
+        out = torch.zeros((self.ns, 3), dtype=G.dtype, device=G.device)
+        t = self.tets
+        for a in range(3):
+            out.index_add_(0, t[:, a + 1], G[:, :, a])
+        out.index_add_(0, t[:, 0], -G.sum(2))
+        return out
+
+    def energy(self, q) -> torch.Tensor:
+        F = self.deformation(q)
+        R, S = self.polar(F)
+        tr = S.diagonal(dim1=-2, dim2=-1).sum(-1)
+        D = F - R
+        psi = self.mu * (D * D).sum((-1, -2)) + 0.5 * self.lam * (tr - 3.0) ** 2
+        return (self.V_T * psi).sum()
+
+    def gradient(self, q):
+        P, _, _, _ = self._stress(self.deformation(q))
+        return self._scatter(self.V_T[:, None, None] * (P @ self.Dm_inv.transpose(1, 2)))
+
+    def _dP(self, dF, R, S, tr):
+        trI = tr[:, None, None] * torch.eye(3, dtype=S.dtype, device=S.device) - S
+        Rt = R.transpose(-1, -2)
+        k = _axial(Rt @ dF - dF.transpose(-1, -2) @ R)
+        w = torch.linalg.solve(trI, k.unsqueeze(-1)).squeeze(-1)
+        dR = R @ _skew(w)
+        RdF = (R * dF).sum((-1, -2))
+        return (2.0 * self.mu * (dF - dR) + self.lam * RdF[:, None, None] * R
+                + self.lam * (tr - 3.0)[:, None, None] * dR)
+
+    def hvp(self, q, v):
+        """Exact Hessian of Phi at q times v [Ns,3]."""
+        F = self.deformation(q)
+        _, R, S, tr = self._stress(F)
+        dF = self._ds(v) @ self.Dm_inv
+        dP = self._dP(dF, R, S, tr)
+        return self._scatter(self.V_T[:, None, None] * (dP @ self.Dm_inv.transpose(1, 2)))
+
+    def tet_hessians(self, q, project: bool):
+        """12 x 12 Hessian of V_T Psi per tet (node-major), exact or PSD-projected in F."""
+        F = self.deformation(q)
+        _, R, S, tr = self._stress(F)
+        T = F.shape[0]
+        E = torch.eye(9, dtype=F.dtype, device=F.device).reshape(9, 3, 3)
+        cols = [self._dP(E[c].expand(T, 3, 3), R, S, tr).reshape(T, 9) for c in range(9)]
+        HF = torch.stack(cols, dim=2)
+        HF = 0.5 * (HF + HF.transpose(1, 2))
+        if project:
+            lam, V = torch.linalg.eigh(HF)
+            HF = V @ torch.diag_embed(lam.clamp_min(0.0)) @ V.transpose(1, 2)
+        return self.V_T[:, None, None] * (self.B.transpose(1, 2) @ HF @ self.B)
+
+    def assemble_dense(self, Ht):
+        n = 3 * self.ns
+        H = torch.zeros((n, n), dtype=Ht.dtype, device=Ht.device)
+        T = Ht.shape[0]
+        rows = self.dofs[:, :, None].expand(T, 12, 12).reshape(-1)
+        cols = self.dofs[:, None, :].expand(T, 12, 12).reshape(-1)
+        H.index_put_((rows, cols), Ht.reshape(-1), accumulate=True)
+        return H
