@@ -52,11 +52,12 @@ def parse():
     ap.add_argument("--json-out", default="")
     ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
     ap.add_argument("--rec-cap", type=int, default=0, help="reduction record capacity (0: library default)")
-    ap.add_argument("--workload", choices=["bubble_grasp", "batched"], default="bubble_grasp",
-                    help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step")
+    ap.add_argument("--workload", choices=["bubble_grasp", "batched", "adjoint"], default="bubble_grasp",
+                    help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step; "
+                         "adjoint: trajectory gradient of the sphere on a rising pad")
     ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain per-scene comparison")
-    ap.add_argument("--retune", action="store_true", help="batched: ignore the autotuner cache")
-    ap.add_argument("--no-tune", action="store_true", help="batched: library default launch shapes")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (no autotuning)")
     return ap.parse_args()
 
 
@@ -133,14 +134,14 @@ def measured_peaks():
 
 # Algorithmic work per unit:
 #   eval_barrier  FP64 flops per contact pair, counted by ncu on the bubble-grasp workload
-#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 460.1e6 / 115,559)
+#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 399.3e6 / 115,583)
 #   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-FP64_FLOPS_PER_PAIR = 3980.0
+FP64_FLOPS_PER_PAIR = 3455.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
-# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
-# (eval_barrier: 203.9 MB per launch of 115,559 pairs)
-NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 1764.0}
+# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code; empty
+# until the current kernels have been captured
+NCU_TRAFFIC_PER_UNIT = {}
 
 
 def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
@@ -292,6 +293,15 @@ def run_ours(args, ws, rank, local):
     cs.build_candidates(Q[first], out=pairs)
     cs.friction_lag(Q[first], pairs, out=lag)
 
+    # launch shapes from the autotuner (cached per device and workload)
+    tuned = {}
+    if not args.no_tune:
+        from paper_2409_16385_gb300 import autotune
+        tuned = autotune.tune(cs, lambda: step(t0, Q[t0], DQ[t0]), WORKLOAD + ("_small" if args.quick else ""),
+                              force=args.retune)
+        cs.build_candidates(Q[first], out=pairs)
+        cs.friction_lag(Q[first], pairs, out=lag)
+
     # warm-up with every kernel timer on: picks the dominant kernel for the roofline
     cs.timing_enable(None)
     start_t = (t0 - args.warmup) % n_it
@@ -416,7 +426,9 @@ def run_ours(args, ws, rank, local):
                             pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K),
                 clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
                 ccd_queries_per_s=total_cand_all / total_s_all, stages=stage,
-                e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()})
+                e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()},
+                autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"])
+                          for k, v in tuned.items()})
     if rank == 0:
         print(json.dumps(line), flush=True)
         if args.json_out:
@@ -834,6 +846,110 @@ def run_batched(args, ws, rank, local):
     st.cs.close()
 
 
+# --------------------------------------------------------------------------- adjoint
+
+def hvp_stage(cs, sc, Q, lag_of, t0, K, flush, dev):
+    """Stage-only device time of the exact-Hessian HVP beside the projected evaluation on
+    the same pairs (bubble-grasp iterates): contact pairs per second of each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    pairs, lag = cs.new_pairs(), cs.new_lag()
+    first = lag_of[t0]
+    cs.build_candidates(Q[first], out=pairs)
+    cs.friction_lag(Q[first], pairs, out=lag)
+    v = torch.randn((sc.Ns, 3), dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+    out = torch.empty_like(v)
+    out_kin = torch.empty(3, dtype=torch.float64, device=dev)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros((sc.Ns, 3), dtype=torch.float64, device=dev)
+    H = cs.new_bsr()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t_h = t_e = 0.0
+    n_p = 0
+    for k in range(K):
+        t = (t0 + k) % sc.n_iterates
+        cs.build_candidates(Q[t], out=pairs)
+        n_p += int(pairs.count.item())
+        flush.zero_()
+        ev[0].record(stream)
+        cs.contact_hvp(Q[t], pairs, v, lag=lag, out=out, out_kin=out_kin)
+        ev[1].record(stream)
+        flush.zero_()
+        ev[2].record(stream)
+        cs.eval_contact(Q[t], pairs, lag, E=E, g_r=g, H=H)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        t_h += ev[0].elapsed_time(ev[1])
+        t_e += ev[2].elapsed_time(ev[3])
+    return dict(hvp_pairs_per_s=n_p / (t_h / 1e3), eval_pairs_per_s=n_p / (t_e / 1e3), hvp_ms=t_h / K,
+                eval_ms=t_e / K, pairs_per_call=n_p / K)
+
+
+def run_adjoint(args, ws, rank, local):
+    """The trajectory gradient of the sphere on a rising pad (20 backward-Euler steps of the
+    reduced Newton driver, checkpoints every 5): dL/dtheta and dL/dkappa for L = ||g_c(q_20)||^2
+    by the HVP kernel and implicit steps, timed forward and backward; plus the HVP kernel's
+    stage throughput on the bubble-grasp pairs beside the projected evaluation."""
+    import torch
+    from paper_2409_16385_gb300 import ContactScene, scenes
+    from paper_2409_16385_gb300.adjoint import trajectory_loss
+    from paper_2409_16385_gb300.sim import Simulator
+
+    dev = torch.device("cuda", local)
+    sc = scenes.make_config(5, small=args.quick)
+    sim = Simulator(sc, device=str(dev))
+    K, W = max(1, args.steps // 10), max(1, args.warmup // 3)
+    stream = torch.cuda.current_stream()
+    th0, ka0 = sc.theta, sc.params["kappa"]
+    fwd, bwd, newton = [], [], []
+    for k in range(W + K):
+        th = torch.tensor(th0, dtype=torch.float64, device=dev, requires_grad=True)
+        ka = torch.tensor(ka0, dtype=torch.float64, device=dev, requires_grad=True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L = trajectory_loss(sim, th, ka, sc.n_steps, sc.checkpoint_every)
+        e1.record(stream)
+        L.backward()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if k >= W:
+            fwd.append(e0.elapsed_time(e1)); bwd.append(e1.elapsed_time(e2))
+    _, _, infos = sim.trajectory(th0, ka0)
+    newton = [i.iterations for i in infos]
+    # central differences of the same trajectory (h = 1e-7 on theta, 1e-3 relative on kappa)
+    def loss(t, k_):
+        with torch.no_grad():
+            return float(trajectory_loss(sim, torch.tensor(t, dtype=torch.float64, device=dev),
+                                         torch.tensor(k_, dtype=torch.float64, device=dev), sc.n_steps, 0))
+    fd_t = (loss(th0 + 1e-7, ka0) - loss(th0 - 1e-7, ka0)) / 2e-7
+    fd_k = (loss(th0, ka0 * (1 + 1e-3)) - loss(th0, ka0 * (1 - 1e-3))) / (2e-3 * ka0)
+    d_t, d_k = float(th.grad), float(ka.grad)
+    # HVP kernel throughput on the bubble-grasp workload
+    sb = scenes.make_config(2, small=args.quick)
+    cs = ContactScene(sb, pair_capacity=1 << 21, bsr_capacity=1 << 21)
+    Q = torch.tensor(np.stack([sb.iterate(t) for t in range(sb.n_iterates)]), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stage = hvp_stage(cs, sb, Q, [sb.lag_of(t) for t in range(sb.n_iterates)], 5, max(5, args.steps), flush, dev)
+    steps_s = sc.n_steps / ((np.mean(fwd) + np.mean(bwd)) / 1e3)
+    line = dict(metric="trajectory gradient: time steps differentiated per second", value=steps_s,
+                unit="steps/s", n_gpus=ws, steps=K, warmup=W, ms_per_step=float(np.mean(fwd) + np.mean(bwd)) / sc.n_steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64", data="synthetic (seeded)",
+                config=dict(workload=sc.name, steps_per_trajectory=sc.n_steps, checkpoint_every=sc.checkpoint_every,
+                            cage_nodes=sc.Ns, vertices=sc.Nv, triangles=sc.F, theta=th0, kappa=ka0,
+                            solver="dense adjoint solves, exact Hessian; HVP kernel for the loss and theta terms"),
+                trajectory_ms=dict(forward=float(np.mean(fwd)), backward=float(np.mean(bwd))),
+                newton_iterations=newton,
+                gradient=dict(dL_dtheta=d_t, dL_dkappa=d_k, fd_dL_dtheta=fd_t, fd_dL_dkappa=fd_k,
+                              rel_err_theta=abs(fd_t - d_t) / abs(d_t), rel_err_kappa=abs(fd_k - d_k) / abs(d_k)),
+                hvp_stage=dict(workload=sb.name, **stage))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+
+
 def main():
     args = parse()
     backend = "gloo" if args.impl == "reference" else "nccl"
@@ -842,6 +958,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batched":
         run_batched(args, ws, rank, local)
+    elif args.workload == "adjoint":
+        run_adjoint(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -200,11 +200,20 @@ __device__ __forceinline__ void jacobi(double A[N][N], double V[N][N], bool seed
       for (int q = p + 1; q < N; ++q) {
         const double apq = A[p][q];
         if (apq != 0.0) {
-          const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-          const double at = fabs(theta);
-          double t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
-          t = theta < 0.0 ? -t : t;
-          const double c = rsqrt(t * t + 1.0);
+          const double gap = A[q][q] - A[p][p];
+          double t, c;
+          if (fabs(apq) < 1e-6 * fabs(gap)) {
+            // small angle (the usual case after the FP32 pre-diagonalisation):
+            // t = apq / gap to O(t^3), c = 1 - t^2 / 2 to O(t^4), both below 1e-17
+            t = apq / gap;
+            c = 1.0 - 0.5 * t * t;
+          } else {
+            const double theta = gap / (2.0 * apq);
+            const double at = fabs(theta);
+            t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
+            t = theta < 0.0 ? -t : t;
+            c = rsqrt(t * t + 1.0);
+          }
           const double s = t * c;
 #pragma unroll
           for (int k = 0; k < N; ++k) {
@@ -253,6 +262,8 @@ struct EvalArgs {
   double* item_E;
   DevStatus* st;
   bool project;            // PSD-project the barrier Hessians (projected Newton)
+  const uint32_t* order;   // processing order of the barrier items (null: index order)
+  int64_t* queue;          // next unclaimed position of `order` (work queue)
   const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
   double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
 };
@@ -362,9 +373,11 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
                                              BarrierSpan& B) {
   const double lg = log(d / dhat);
   const double m = d - dhat;
+  const double inv_d = 1.0 / d;
+  const double md = m * inv_d;
   const double b = -m * m * lg;
-  const double b1 = -2.0 * m * lg - m * m / d;
-  const double b2 = -2.0 * lg - 4.0 * m / d + (m * m) / (d * d);
+  const double b1 = -2.0 * m * lg - m * md;
+  const double b2 = -2.0 * lg - 4.0 * md + md * md;
   B.E = kappa * b;
   B.b1 = b1;
   // r and r^
@@ -376,7 +389,8 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
   // orthonormal 4-vectors c^, a^_1, a^_2
   const double cn = sqrt(S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3]);
   B.cn = cn;
-  for (int a = 0; a < 4; ++a) B.basis[0][a] = S.c[a] / cn;
+  const double inv_cn = 1.0 / cn;
+  for (int a = 0; a < 4; ++a) B.basis[0][a] = S.c[a] * inv_cn;
   for (int j = 0; j < 2; ++j) {
     if (j < S.m) {
       double t[4];
@@ -386,8 +400,8 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
         for (int a = 0; a < 4; ++a) pr += B.basis[i][a] * t[a];
         for (int a = 0; a < 4; ++a) t[a] -= pr * B.basis[i][a];
       }
-      double tn = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
-      for (int a = 0; a < 4; ++a) B.basis[1 + j][a] = t[a] / tn;
+      const double inv_tn = rsqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2] + t[3] * t[3]);
+      for (int a = 0; a < 4; ++a) B.basis[1 + j][a] = t[a] * inv_tn;
     } else {
       for (int a = 0; a < 4; ++a) B.basis[1 + j][a] = 0.0;
     }
@@ -400,10 +414,11 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
   }
   double (&K)[5][5] = B.K;
   const double kb = kappa * cn * cn;
-  const double rr = kappa * (b2 - b1 / d);
+  const double rr = kappa * (b2 - b1 * inv_d);
+  const double kd = kb * b1 * inv_d;
   const double rhv[3] = {rh.x, rh.y, rh.z};
   for (int p = 0; p < 3; ++p)
-    for (int q = 0; q < 3; ++q) K[p][q] = cn * cn * (rr * rhv[p] * rhv[q]) + (p == q ? kb * b1 / d : 0.0);
+    for (int q = 0; q < 3; ++q) K[p][q] = cn * cn * (rr * rhv[p] * rhv[q]) + (p == q ? kd : 0.0);
   for (int p = 0; p < 5; ++p)
     for (int q = 3; q < 5; ++q) { K[p][q] = 0.0; K[q][p] = 0.0; }
   if (S.m > 0) {
@@ -421,13 +436,13 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
     }
     double Mi[2][2];
     if (S.m == 1) {
-      Mi[0][0] = 1.0 / (2.0 * dot(vj[0], vj[0]));
+      Mi[0][0] = 0.5 / dot(vj[0], vj[0]);
     } else {
       const double m00 = 2.0 * dot(vj[0], vj[0]), m01 = 2.0 * dot(vj[0], vj[1]), m11 = 2.0 * dot(vj[1], vj[1]);
-      const double det = m00 * m11 - m01 * m01;
-      Mi[0][0] = m11 / det; Mi[1][1] = m00 / det; Mi[0][1] = Mi[1][0] = -m01 / det;
+      const double inv_det = 1.0 / (m00 * m11 - m01 * m01);
+      Mi[0][0] = m11 * inv_det; Mi[1][1] = m00 * inv_det; Mi[0][1] = Mi[1][0] = -m01 * inv_det;
     }
-    const double beta = -kappa * b1 / (2.0 * d);
+    const double beta = -0.5 * kappa * b1 * inv_d;
     for (int p = 0; p < 5; ++p)
       for (int q = 0; q < 5; ++q) {
         double s2 = 0.0;
@@ -441,6 +456,110 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
     for (int q = p + 1; q < 5; ++q) { const double t = 0.5 * (K[p][q] + K[q][p]); K[p][q] = t; K[q][p] = t; }
 }
 
+// One barrier item: distance, span Hessian (projected unless A.project is false), energy,
+// gradient records and upper-triangle Hessian records at the item's own offsets.
+__device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) {
+  int32_t v[4];
+  const int type = A.pr.type[k];
+  stencil_vertices(A.T, type, A.pr.i[k], A.pr.j[k], v);
+  V3 X[4];
+  for (int a = 0; a < 4; ++a) X[a] = load_x(A.x4, v[a]);
+  // positions relative to the first vertex (distance and derivatives are translation
+  // invariant; this keeps the differences exact-ish)
+  V3 Y[4];
+  for (int a = 0; a < 4; ++a) Y[a] = X[a] - X[0];
+  Stencil S;
+  if (type == 0) pt_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+  else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+  const int n = A.item_n[k];
+  const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+  const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+  double E = 0.0;
+  double Kp[5][5];
+  double cn = 0.0, b1 = 0.0;
+  V3 rh = {0.0, 0.0, 0.0};
+  double basis[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // c^, a^_1, a^_2
+  bool active = false;
+  if (!(S.d2 > 0.0)) {
+    raise_flag(A.st, EIPC_FLAG_PENETRATION);
+  } else {
+    const double d = sqrt(S.d2);
+    active = d < A.dhat;
+    if (active) {
+      BarrierSpan B;
+      barrier_span(Y, S, d, A.dhat, A.kappa, B);
+      E = B.E; b1 = B.b1; cn = B.cn; rh = B.rh;
+      for (int c = 0; c < 3; ++c)
+        for (int a = 0; a < 4; ++a) basis[c][a] = B.basis[c][a];
+      if (A.project) {
+        double V[5][5];
+        eigen5(B.K, V);
+        // K+ = (V max(Lambda, 0)) V^T, upper triangle mirrored
+        double W[5][5];
+        for (int e = 0; e < 5; ++e) {
+          const double le = B.K[e][e] > 0.0 ? B.K[e][e] : 0.0;
+          for (int p = 0; p < 5; ++p) W[p][e] = V[p][e] * le;
+        }
+        for (int p = 0; p < 5; ++p)
+          for (int q = p; q < 5; ++q) {
+            double s = 0.0;
+            for (int e = 0; e < 5; ++e) s += W[p][e] * V[q][e];
+            Kp[p][q] = s;
+            Kp[q][p] = s;
+          }
+      } else {
+        for (int p = 0; p < 5; ++p)
+          for (int q = 0; q < 5; ++q) Kp[p][q] = B.K[p][q];
+      }
+    }
+  }
+  A.item_E[k] = E;
+  // per-node scalars omega, alpha_1, alpha_2
+  double nw[kMaxNodes][3];
+  if (active) {
+    node_weights(v, A.cage_idx, A.w, nodes, n, basis, 3, nw);
+  } else {
+    for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
+  }
+  // gradient records: kappa b' |c| omega_I r^
+  for (int u = 0; u < n; ++u) {
+    const int64_t pos = og + u;
+    if (pos < A.gcap) {
+      const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
+      A.gkeys[pos] = (uint64_t)nodes[u];
+      A.gvals[pos] = (uint32_t)pos;
+      A.grec[3 * pos] = s * rh.x; A.grec[3 * pos + 1] = s * rh.y; A.grec[3 * pos + 2] = s * rh.z;
+    }
+  }
+  // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
+  // (min(I_u, I_v), max(I_u, I_v)) and transposed when I_u > I_v
+  const double rhv[3] = {rh.x, rh.y, rh.z};
+  int64_t pos = oh;
+  for (int u = 0; u < n; ++u) {
+    double Bu[3][5];
+    if (active) {
+      double t[5];
+      for (int q = 0; q < 5; ++q) t[q] = nw[u][1] * Kp[3][q] + nw[u][2] * Kp[4][q];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 5; ++q) Bu[p][q] = nw[u][0] * Kp[p][q] + rhv[p] * t[q];
+    }
+    for (int w2 = u; w2 < n; ++w2, ++pos) {
+      if (pos >= A.rec_cap) continue;
+      double B[3][3];
+      if (active) {
+        for (int p = 0; p < 3; ++p) {
+          const double s = nw[w2][1] * Bu[p][3] + nw[w2][2] * Bu[p][4];
+          for (int q = 0; q < 3; ++q) B[p][q] = nw[w2][0] * Bu[p][q] + s * rhv[q];
+        }
+      } else {
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
+      }
+      emit_upper(A, pos, nodes[u], nodes[w2], B);
+    }
+  }
+}
+
 // MINB = 2: no register cap (248 registers, 2 blocks of 128 per SM); MINB = 3: at most 170
 // registers (3 blocks per SM, a few hundred bytes of spills).  Chosen at run time.  With
 // A.project false the pair Hessians are kept as they are (no PSD projection).
@@ -449,99 +568,21 @@ __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A)
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t np = P < nit ? P : nit;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < np; k += grid_stride()) {
-    int32_t v[4];
-    const int type = A.pr.type[k];
-    stencil_vertices(A.T, type, A.pr.i[k], A.pr.j[k], v);
-    V3 X[4];
-    for (int a = 0; a < 4; ++a) X[a] = load_x(A.x4, v[a]);
-    // positions relative to the first vertex (distance and derivatives are translation
-    // invariant; this keeps the differences exact-ish)
-    V3 Y[4];
-    for (int a = 0; a < 4; ++a) Y[a] = X[a] - X[0];
-    Stencil S;
-    if (type == 0) pt_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
-    else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
-    const int n = A.item_n[k];
-    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
-    const int64_t oh = A.ro_h[k], og = A.ro_g[k];
-    double E = 0.0;
-    double Kp[5][5];
-    double cn = 0.0, b1 = 0.0;
-    V3 rh = {0.0, 0.0, 0.0};
-    double basis[3][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};  // c^, a^_1, a^_2
-    bool active = false;
-    if (!(S.d2 > 0.0)) {
-      raise_flag(A.st, EIPC_FLAG_PENETRATION);
-    } else {
-      const double d = sqrt(S.d2);
-      active = d < A.dhat;
-      if (active) {
-        BarrierSpan B;
-        barrier_span(Y, S, d, A.dhat, A.kappa, B);
-        E = B.E; b1 = B.b1; cn = B.cn; rh = B.rh;
-        for (int c = 0; c < 3; ++c)
-          for (int a = 0; a < 4; ++a) basis[c][a] = B.basis[c][a];
-        if (A.project) {
-          double V[5][5];
-          eigen5(B.K, V);
-          for (int p = 0; p < 5; ++p)
-            for (int q = 0; q < 5; ++q) {
-              double s = 0.0;
-              for (int e = 0; e < 5; ++e) s += (B.K[e][e] > 0.0 ? V[p][e] * B.K[e][e] * V[q][e] : 0.0);
-              Kp[p][q] = s;
-            }
-        } else {
-          for (int p = 0; p < 5; ++p)
-            for (int q = 0; q < 5; ++q) Kp[p][q] = B.K[p][q];
-        }
-      }
-    }
-    A.item_E[k] = E;
-    // per-node scalars omega, alpha_1, alpha_2
-    double nw[kMaxNodes][3];
-    if (active) {
-      node_weights(v, A.cage_idx, A.w, nodes, n, basis, 3, nw);
-    } else {
-      for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
-    }
-    // gradient records: kappa b' |c| omega_I r^
-    for (int u = 0; u < n; ++u) {
-      const int64_t pos = og + u;
-      if (pos < A.gcap) {
-        const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
-        A.gkeys[pos] = (uint64_t)nodes[u];
-        A.gvals[pos] = (uint32_t)pos;
-        A.grec[3 * pos] = s * rh.x; A.grec[3 * pos + 1] = s * rh.y; A.grec[3 * pos + 2] = s * rh.z;
-      }
-    }
-    // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
-    // (min(I_u, I_v), max(I_u, I_v)) and transposed when I_u > I_v
-    const double rhv[3] = {rh.x, rh.y, rh.z};
-    int64_t pos = oh;
-    for (int u = 0; u < n; ++u) {
-      double Bu[3][5];
-      if (active) {
-        double t[5];
-        for (int q = 0; q < 5; ++q) t[q] = nw[u][1] * Kp[3][q] + nw[u][2] * Kp[4][q];
-        for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 5; ++q) Bu[p][q] = nw[u][0] * Kp[p][q] + rhv[p] * t[q];
-      }
-      for (int w2 = u; w2 < n; ++w2, ++pos) {
-        if (pos >= A.rec_cap) continue;
-        double B[3][3];
-        if (active) {
-          for (int p = 0; p < 3; ++p) {
-            const double s = nw[w2][1] * Bu[p][3] + nw[w2][2] * Bu[p][4];
-            for (int q = 0; q < 3; ++q) B[p][q] = nw[w2][0] * Bu[p][q] + s * rhv[q];
-          }
-        } else {
-          for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
-        }
-        emit_upper(A, pos, nodes[u], nodes[w2], B);
-      }
-    }
+  if (!A.order) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < np; k += grid_stride())
+      eval_barrier_item(A, k);
+    return;
+  }
+  // scheduled: each warp takes the next 32 items of the order from a queue, so warps
+  // that drew light items come back for more (dynamic balance)
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < (1 << 30); ++round) {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(A.queue), 32ull);
+    const int64_t base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+    if (base >= np) break;
+    const int64_t idx = base + lane;
+    if (idx < np) eval_barrier_item(A, (int64_t)A.order[idx]);
   }
 }
 
@@ -754,6 +795,22 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_
     const int64_t og = A.ro_g[k];
     for (int a = 0; a < n; ++a) emit_g(A, og + a, (uint64_t)nodes[a], Fs * nw[a][0]);
     emit_g(A, og + n, (uint64_t)A.ns, Fs * ks[0]);
+  }
+}
+
+// Schedule of the barrier evaluation: items keyed by (number of cage nodes, descending;
+// pair type), friction items last.  A warp's lanes then take the same branch and emit
+// the same number of blocks, and the heaviest items go first so the tail is light.  Only
+// the processing order changes: every item writes its records at offsets fixed by its
+// own index.
+__global__ void __launch_bounds__(kBlock) k_eval_order_keys(const int32_t* __restrict__ type, const int32_t* __restrict__ item_n,
+                                                            const int64_t* n_pairs, int64_t pair_cap, const int64_t* n_items,
+                                                            uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int64_t P = clamp_count(n_pairs, pair_cap);
+  const int64_t n = *n_items;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
+    keys[k] = k < P ? (uint64_t)((31 - (item_n[k] & 31)) << 1 | (type[k] & 1)) : (uint64_t)(1u << 7);
+    vals[k] = (uint32_t)k;
   }
 }
 
@@ -1029,6 +1086,17 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   A.project = (p.flags & EIPC_PARAM_NO_PROJECTION) == 0;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
+  {
+    // (node count, type) schedule; the pair-sort buffers are free once the pairs are built
+    launch(k_eval_order_keys, blocks_for(item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(pr.type),
+           static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(pr.count), pr.capacity,
+           static_cast<const int64_t*>(cnt + kCntItems), sc->skeys, sc->svals);
+    const int wo = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, cnt + kCntItems, item_cap, 8,
+                                  sc->sort_hist, s);
+    A.order = wo ? sc->svals_alt : sc->svals;
+    A.queue = cnt + kCntEvalQueue;
+    cudaMemsetAsync(A.queue, 0, sizeof(int64_t), s);
+  }
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (sc->tune.eval_variant == 3
                   ? launch(k_eval_barrier<3>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
@@ -1118,6 +1186,8 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   A.project = false;
+  A.order = nullptr;
+  A.queue = nullptr;
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
   EIPC_TIMED(sc, kKEvalBarrier, s,

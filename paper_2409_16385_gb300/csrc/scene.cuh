@@ -33,7 +33,7 @@ struct eipc_scene {
   int64_t cand_cap;
   uint64_t* cand;
   uint64_t* cand2;       // candidates the FP32 screen passed on to the FP64 test
-  int64_t* counters;     // [16] device counters (see kCnt*)
+  int64_t* counters;     // [kCntN] device counters (see kCnt*)
   // narrow phase survivors
   uint64_t* skeys;
   uint64_t* skeys_alt;
@@ -87,7 +87,7 @@ struct eipc_scene {
 namespace eipc {
 // device counters
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
-       kCntAccd = 7, kCntZero = 8, kCntN = 16 };
+       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \
   do {                                    \
