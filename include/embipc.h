@@ -69,9 +69,15 @@ typedef struct {
   int32_t flags;            /* EIPC_PARAM_* bits, 0 for the defaults */
 } eipc_params;
 
-/* eipc_params.flags: EIPC_PARAM_NO_PROJECTION makes eipc_eval_contact return the exact
- * (unprojected) Hessian instead of the projected-Newton one. */
-enum { EIPC_PARAM_NO_PROJECTION = 1 };
+/* eipc_params.flags:
+ *   EIPC_PARAM_NO_PROJECTION makes eipc_eval_contact return the exact (unprojected) Hessian
+ *     instead of the projected-Newton one;
+ *   EIPC_PARAM_DEDUP makes eipc_build_candidates return the deduplicated contact set: each
+ *     pair stands for the feature pair realising its distance (face-vertex, vertex-edge,
+ *     vertex-vertex, edge-edge interior), and pairs realising the same feature pair count
+ *     once, as the first of them in (type, i, j) order.  The paper's set B (Sec. III-B)
+ *     counts every pair; this is the IPC-style alternative. */
+enum { EIPC_PARAM_NO_PROJECTION = 1, EIPC_PARAM_DEDUP = 2 };
 
 /* Contact pair list, all device arrays owned by the caller.  Pair k is a point-triangle
  * pair (type 0: i = vertex, j = triangle) or an edge-edge pair (type 1: i < j edge ids),

@@ -59,6 +59,7 @@ def lib():
         L.orc_eval.restype = P
         L.orc_hvp.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
                               dbl, dbl, dbl, dbl, P, P, P]
+        L.orc_dedup.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, P]
         L.orc_result_nnzb.argtypes = [P]
         L.orc_result_nnzb.restype = i64
         L.orc_result_copy.argtypes = [P, P, P, P, P, P, P]
@@ -187,6 +188,22 @@ def pairs_of(scene, x: np.ndarray, ptype: int, queries: np.ndarray, dhat: Option
         if n <= cap:
             return dict(i=i[:n], j=j[:n], d=d[:n])
         cap = int(n)
+
+
+def dedup(scene, x: np.ndarray, prs: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:
+    """The deduplicated contact set: pairs realising the same feature pair (face-vertex,
+    vertex-edge, vertex-vertex, edge-edge interior) count once, the first in (type, i, j)
+    order standing for them."""
+    order = np.lexsort((prs["j"], prs["i"], prs["type"]))
+    t, i, j = (np.ascontiguousarray(prs[k][order], np.int32) for k in ("type", "i", "j"))
+    keep = np.zeros(len(t), np.int32)
+    lib().orc_dedup(scene.Nv, _p(_f64(x)), scene.F, _p(_i32(scene.tris)), scene.E, _p(_i32(scene.edges)), len(t),
+                    _p(t), _p(i), _p(j), _p(keep))
+    sel = keep.astype(bool)
+    out = dict(type=t[sel], i=i[sel], j=j[sel])
+    if "d" in prs:
+        out["d"] = np.asarray(prs["d"])[order][sel]
+    return out
 
 
 def friction_lag(scene, xn: np.ndarray, prs: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:

@@ -645,6 +645,56 @@ void orc_hvp(int64_t nv, const double* x, int64_t nf, const int32_t* tris, int64
   }
 }
 
+// Deduplicated contact set, the IPC-style alternative to the paper's literal set B (which
+// counts every pair): each pair stands for the pair of mesh features that realises its
+// distance -- face and vertex, vertex and edge, two vertices, or two edges in their
+// interiors -- and pairs realising the same feature pair count once.  Pairs are visited
+// in the given order (callers pass (type, i, j) order); keep[k] = 1 for the first pair of
+// each feature pair, 0 for the rest.
+void orc_dedup(int64_t nv, const double* x, int64_t nf, const int32_t* tris, int64_t ne, const int32_t* edges,
+               int64_t np, const int32_t* type, const int32_t* pi, const int32_t* pj, int32_t* keep) {
+  Mesh m{nv, nf, ne, x, tris, edges, nullptr};
+  std::map<std::pair<int32_t, int32_t>, int32_t> edge_of;
+  for (int64_t e = 0; e < ne; ++e)
+    edge_of[{std::min(edges[2 * e], edges[2 * e + 1]), std::max(edges[2 * e], edges[2 * e + 1])}] = (int32_t)e;
+  auto edge_id = [&](int32_t a, int32_t b) {
+    auto it = edge_of.find({std::min(a, b), std::max(a, b)});
+    return it == edge_of.end() ? -1 : it->second;
+  };
+  std::map<std::array<int64_t, 3>, int64_t> seen;
+  for (int64_t k = 0; k < np; ++k) {
+    int32_t v[4];
+    stencil(m, type[k], pi[k], pj[k], v);
+    V3<double> p[4];
+    for (int a = 0; a < 4; ++a) p[a] = P(x, v[a]);
+    int reg; double c[4];
+    pair_d2(type[k], p, &reg, c);
+    std::array<int64_t, 3> key;
+    if (type[k] == 0) {
+      if (reg == PT_FACE) {
+        key = {0, pj[k], pi[k]};                                  // face, vertex
+      } else if (reg <= 3) {
+        const int e = reg - 1;                                    // edge (t_e, t_e+1)
+        key = {1, pi[k], edge_id(v[1 + e], v[1 + (e + 1) % 3])};
+      } else {
+        const int32_t t = v[1 + (reg - 4)];                       // vertex t_(reg-4)
+        key = {2, std::min(v[0], t), std::max(v[0], t)};
+      }
+    } else {
+      if (reg == 0) {
+        key = {3, pi[k], pj[k]};                                  // two edge interiors
+      } else if (reg <= 4) {
+        const int e = reg - 1;                                    // endpoint e against the other edge
+        key = e < 2 ? std::array<int64_t, 3>{1, v[e], pj[k]} : std::array<int64_t, 3>{1, v[e], pi[k]};
+      } else {
+        const int ia = (reg - 5) / 2, ib = (reg - 5) % 2;          // endpoint against endpoint
+        key = {2, std::min(v[ia], v[2 + ib]), std::max(v[ia], v[2 + ib])};
+      }
+    }
+    keep[k] = seen.emplace(key, k).second ? 1 : 0;
+  }
+}
+
 int64_t orc_result_nnzb(const orc_eval_result* r) { return (int64_t)r->R.H.size(); }
 
 void orc_result_copy(const orc_eval_result* r, double* E, double* g, int32_t* I, int32_t* J,

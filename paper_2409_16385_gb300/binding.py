@@ -279,7 +279,7 @@ class ContactScene:
         prm = self.params
         if not project:
             prm = Params(*[getattr(self.params, f) for f, _ in Params._fields_])
-            prm.flags = 1
+            prm.flags = self.params.flags | 1
         _check(self.lib.eipc_eval_contact(self.handle, _ptr(q), ctypes.byref(pc), lp, ctypes.byref(prm), _ptr(E),
                                           _ptr(g_r), ctypes.byref(hc), _stream()), "eipc_eval_contact")
         return E, g_r, H
@@ -305,6 +305,10 @@ class ContactScene:
     def set_kinematic(self, x_kin):
         """New positions of the kinematic vertices (device f64 [Nv,3]; other rows ignored)."""
         _check(self.lib.eipc_scene_set_kinematic(self.handle, _ptr(x_kin), _stream()), "eipc_scene_set_kinematic")
+
+    def set_dedup(self, on: bool = True):
+        """Deduplicated contact sets from build_candidates (EIPC_PARAM_DEDUP)."""
+        self.params.flags = (self.params.flags | 2) if on else (self.params.flags & ~2)
 
     def set_params(self, **kw):
         """Change contact parameters (dhat, kappa, mu, eps_v, h, accd_s, accd_max_iter)."""

@@ -1,8 +1,10 @@
 // C ABI entry points (include/embipc.h): argument checks, scene creation and workspace
 // sizing, and the enqueueing of each call's kernels on the caller's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "scene.cuh"
@@ -20,7 +22,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
@@ -61,7 +63,7 @@ cudaError_t alloc_bvh(Bvh& t, int64_t n) {
 
 bool params_ok(const eipc_params* p) {
   return p && p->dhat > 0.0 && p->kappa > 0.0 && p->mu >= 0.0 && p->eps_v > 0.0 && p->h > 0.0 && p->accd_s > 0.0 &&
-         p->accd_s < 1.0 && p->accd_max_iter > 0 && (p->flags & ~EIPC_PARAM_NO_PROJECTION) == 0;
+         p->accd_s < 1.0 && p->accd_max_iter > 0 && (p->flags & ~(EIPC_PARAM_NO_PROJECTION | EIPC_PARAM_DEDUP)) == 0;
 }
 
 bool pairs_ok(const eipc_pairs* p) {
@@ -147,12 +149,13 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
   ok(dalloc(&s->hvals, s->rec_cap)); ok(dalloc(&s->hvals_alt, s->rec_cap)); ok(dalloc(&s->hrec, 9 * s->rec_cap));
   ok(dalloc(&s->ublk, 9 * s->rec_cap));
-  ok(dalloc(&s->hvp_out, 3 * (Ns + 1)));
+  ok(dalloc(&s->hvp_out, 3 * (Ns + 64)));
   ok(dalloc(&s->seg_flag, s->rec_cap)); ok(dalloc(&s->seg_id, s->rec_cap)); ok(dalloc(&s->seg_start, s->rec_cap));
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, 3 * s->gcap));
   ok(dalloc(&s->gseg_flag, s->gcap)); ok(dalloc(&s->gseg_id, s->gcap)); ok(dalloc(&s->gseg_start, s->gcap));
   ok(dalloc(&s->row_count, Ns + 1));
+  ok(dalloc(&s->edge_key, E > 0 ? E : 1)); ok(dalloc(&s->edge_id, E > 0 ? E : 1));
   ok(dalloc(&s->scan_partial, kScanBlocks + 1)); ok(dalloc(&s->sum_partial, kScanBlocks));
   ok(dalloc(&s->status, 1));
   if (e != cudaSuccess) {
@@ -168,6 +171,23 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(cudaMemcpy(s->vkin, vkin.data(), Nv, cudaMemcpyHostToDevice));
   ok(cudaMemcpy(s->ekin, ekin.data(), E, cudaMemcpyHostToDevice));
   ok(cudaMemcpy(s->fkin, fkin.data(), F, cudaMemcpyHostToDevice));
+  {
+    // edge lookup table for the deduplicated pair set: keys a * Nv + b (a < b) sorted
+    std::vector<std::pair<uint64_t, int32_t>> ek((size_t)E);
+    for (int64_t e2 = 0; e2 < E; ++e2) {
+      int64_t a = edges[2 * e2], b = edges[2 * e2 + 1];
+      if (a > b) std::swap(a, b);
+      ek[(size_t)e2] = {(uint64_t)a * (uint64_t)Nv + (uint64_t)b, (int32_t)e2};
+    }
+    std::sort(ek.begin(), ek.end());
+    std::vector<uint64_t> keys((size_t)E);
+    std::vector<int32_t> ids((size_t)E);
+    for (size_t q = 0; q < ek.size(); ++q) { keys[q] = ek[q].first; ids[q] = ek[q].second; }
+    if (E > 0) {
+      ok(cudaMemcpy(s->edge_key, keys.data(), sizeof(uint64_t) * E, cudaMemcpyHostToDevice));
+      ok(cudaMemcpy(s->edge_id, ids.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice));
+    }
+  }
   ok(cudaMemset(s->counters, 0, sizeof(int64_t) * kCntN));
   ok(cudaMemset(s->status, 0, sizeof(DevStatus)));
   ok(cudaMemset(s->vgroup, 0, sizeof(int32_t) * Nv));
@@ -187,6 +207,11 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   T.bits_j = bits_for((uint64_t)(F > E ? F : E));
   s->bits_h = bits_for((uint64_t)Ns * (uint64_t)Ns);
   s->bits_g = bits_for((uint64_t)Ns);
+  {
+    int64_t mx = Nv > E ? Nv : E;
+    mx = mx > F ? mx : F;
+    s->feat_bits = bits_for((uint64_t)mx);
+  }
   s->rebuild_interval = 8;
   s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2;
   s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.refit_variant = 1;

@@ -657,14 +657,37 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
 // ------------------------------------------------------------------ Hessian-vector product
 // y = H u for the unprojected contact Hessian H and the full-space direction u = J v on the
 // embedded vertices, u = kin_dir on the kinematic ones.  Each item emits one record per
-// cage node of its stencil (J^T y restricted to the item) and one record under key ns
-// holding the sum of y over its kinematic vertices; the gradient reduction sums them.
+// cage node of its stencil (J^T y restricted to the item) and, if it touches kinematic
+// vertices, one record holding the sum of y over them under key ns + (item mod 64); the
+// gradient reduction sums the records, and the 64 kinematic partials are added in order.
+constexpr int kKinSlots = 64;
 
-__global__ void k_hvp_counts(const int32_t* __restrict__ item_n, const int64_t* n_items, int64_t cap,
-                             int64_t* __restrict__ rc_g) {
+__device__ __forceinline__ bool item_has_kinematic(const Topo& T, const eipc_pairs& pr, int64_t P, const int32_t* lag_v,
+                                                   int64_t L, int64_t k, const int32_t* __restrict__ cage_idx) {
+  int32_t v[4];
+  item_vertices(T, pr, P, lag_v, L, k, v);
+  bool any = false;
+  for (int a = 0; a < 4; ++a) any |= __ldg(cage_idx + 4 * (int64_t)v[a]) < 0;
+  return any;
+}
+
+__global__ void k_hvp_counts(Topo T, eipc_pairs pr, const int32_t* lag_v, const int64_t* lag_count, int64_t lag_cap,
+                             const int32_t* __restrict__ cage_idx, const int32_t* __restrict__ item_n,
+                             const int64_t* n_items, int64_t cap, int64_t* __restrict__ rc_g) {
   const int64_t n = clamp_count(n_items, cap);
+  const int64_t P = clamp_count(pr.count, pr.capacity);
+  const int64_t L = lag_v ? clamp_count(lag_count, lag_cap) : 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride())
-    rc_g[k] = (int64_t)item_n[k] + 1;
+    rc_g[k] = (int64_t)item_n[k] + (item_has_kinematic(T, pr, P, lag_v, L, k, cage_idx) ? 1 : 0);
+}
+
+__global__ void k_hvp_kin_sum(const double* __restrict__ rows, double* __restrict__ out_kin) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a[3] = {0.0, 0.0, 0.0};
+    for (int s = 0; s < kKinSlots; ++s)
+      for (int c = 0; c < 3; ++c) a[c] += rows[3 * s + c];
+    for (int c = 0; c < 3; ++c) out_kin[c] = a[c];
+  }
 }
 
 // coefficient sums over the kinematic vertices of a stencil
@@ -746,9 +769,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
       if (active) y = tc * nw[u][0] + rh * (nw[u][1] * t[3] + nw[u][2] * t[4]);
       emit_g(A, og + u, (uint64_t)nodes[u], y);
     }
-    V3 yk = {0.0, 0.0, 0.0};
-    if (active) yk = tc * ks[0] + rh * (ks[1] * t[3] + ks[2] * t[4]);
-    emit_g(A, og + n, (uint64_t)A.ns, yk);
+    bool kin = false;
+    for (int a = 0; a < 4; ++a) kin |= __ldg(A.cage_idx + 4 * (int64_t)v[a]) < 0;
+    if (kin) {
+      V3 yk = {0.0, 0.0, 0.0};
+      if (active) yk = tc * ks[0] + rh * (ks[1] * t[3] + ks[2] * t[4]);
+      emit_g(A, og + n, (uint64_t)(A.ns + (k & (kKinSlots - 1))), yk);
+    }
   }
 }
 
@@ -794,7 +821,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_
     if (y2 > 0.0) Fs = Fs + u * (ml * f1p_minus * dot(u, sd) / y2);
     const int64_t og = A.ro_g[k];
     for (int a = 0; a < n; ++a) emit_g(A, og + a, (uint64_t)nodes[a], Fs * nw[a][0]);
-    emit_g(A, og + n, (uint64_t)A.ns, Fs * ks[0]);
+    bool kin = false;
+    for (int a = 0; a < 4; ++a) kin |= __ldg(A.cage_idx + 4 * (int64_t)v[a]) < 0;
+    if (kin) emit_g(A, og + n, (uint64_t)(A.ns + (k & (kKinSlots - 1))), Fs * ks[0]);
   }
 }
 
@@ -1173,7 +1202,9 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
          fr ? lag->capacity : 0, sc->cage_idx, item_cap, sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
          sc->rc_h, sc->rc_g, cnt + kCntItems, sc->status);
-  launch(k_hvp_counts, blocks_for(item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(sc->item_n),
+  launch(k_hvp_counts, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr,
+         fr ? static_cast<const int64_t*>(lag->count) : nullptr, fr ? lag->capacity : 0,
+         static_cast<const int32_t*>(sc->cage_idx), static_cast<const int32_t*>(sc->item_n),
          static_cast<const int64_t*>(cnt + kCntItems), item_cap, sc->rc_g);
   int64_t* tot_g = cnt + 10;
   exclusive_scan_i64(sc->rc_g, sc->ro_g, cnt + kCntItems, item_cap, tot_g, sc->scan_partial, s);
@@ -1197,20 +1228,20 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
                (launch(k_hvp_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
                        p.eps_v * p.h)));
   sc->timers->start(kKGReduce, s);
-  int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap, sc->bits_g,
-                          sc->sort_hist, s);
+  int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap,
+                          bits_for((uint64_t)(sc->ns + kKinSlots)), sc->sort_hist, s);
   const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
   const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
   launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
   exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
   launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
          sc->gseg_start);
-  cudaMemsetAsync(sc->hvp_out, 0, sizeof(double) * 3 * (sc->ns + 1), s);
+  cudaMemsetAsync(sc->hvp_out, 0, sizeof(double) * 3 * (sc->ns + kKinSlots), s);
   launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG,
          cnt + kCntSegG, sc->gcap, sc->hvp_out);
   cudaMemcpyAsync(out_r, sc->hvp_out, sizeof(double) * 3 * sc->ns, cudaMemcpyDeviceToDevice, s);
   if (out_kin)
-    cudaMemcpyAsync(out_kin, sc->hvp_out + 3 * sc->ns, sizeof(double) * 3, cudaMemcpyDeviceToDevice, s);
+    launch(k_hvp_kin_sum, 1, 32, 0, s, static_cast<const double*>(sc->hvp_out + 3 * sc->ns), out_kin);
   sc->timers->stop(kKGReduce, s);
 }
 

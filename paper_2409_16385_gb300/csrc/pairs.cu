@@ -149,6 +149,103 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
   }
 }
 
+// ---------------------------------------------------------------- constraint deduplication
+// IPC-style reading of the pair set: a pair stands for the feature pair that realises its
+// distance (face-vertex, vertex-edge, vertex-vertex, or edge-edge interior), and pairs that
+// realise the same feature pair count once, represented by the first in (type, i, j) order.
+// Feature keys: kind << 2B | id1 << B | id2, B bits per id.
+enum { kFeatFV = 0, kFeatVE = 1, kFeatVV = 2, kFeatEE = 3 };
+
+__device__ __forceinline__ int32_t edge_id_of(int32_t a, int32_t b, int64_t nv, const uint64_t* __restrict__ ekey,
+                                              const int32_t* __restrict__ eid, int64_t ne) {
+  if (a > b) { const int32_t t = a; a = b; b = t; }
+  const uint64_t key = (uint64_t)a * (uint64_t)nv + (uint64_t)b;
+  int64_t lo = 0, hi = ne;                 // first position with ekey >= key
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ekey[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < ne && ekey[lo] == key) ? eid[lo] : -1;
+}
+
+__device__ __forceinline__ uint64_t feature_key(int kind, uint32_t a, uint32_t b, int B) {
+  return ((uint64_t)kind << (2 * B)) | ((uint64_t)a << B) | (uint64_t)b;
+}
+
+__global__ void __launch_bounds__(kBlock) k_feature_keys(Topo T, const double* __restrict__ x4,
+                                                         const uint64_t* __restrict__ keys, const int64_t* n_surv,
+                                                         int64_t cap, const uint64_t* __restrict__ ekey,
+                                                         const int32_t* __restrict__ eid, int B,
+                                                         uint64_t* __restrict__ fkeys, uint32_t* __restrict__ fvals,
+                                                         DevStatus* st) {
+  const int64_t n = clamp_count(n_surv, cap);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
+    int type; int32_t i, j;
+    unpack(keys[k], T.bits_i, T.bits_j, &type, &i, &j);
+    int32_t v[4];
+    if (type == 0) {
+      v[0] = i; v[1] = T.tris[3 * (int64_t)j]; v[2] = T.tris[3 * (int64_t)j + 1]; v[3] = T.tris[3 * (int64_t)j + 2];
+    } else {
+      v[0] = T.edges[2 * (int64_t)i]; v[1] = T.edges[2 * (int64_t)i + 1];
+      v[2] = T.edges[2 * (int64_t)j]; v[3] = T.edges[2 * (int64_t)j + 1];
+    }
+    V3 X[4];
+    for (int a = 0; a < 4; ++a) X[a] = load_x(x4, v[a]);
+    Stencil S;
+    if (type == 0) pt_distance<true>(X[0] - X[0], X[1] - X[0], X[2] - X[0], X[3] - X[0], &S);
+    else ee_distance<true>(X[0] - X[0], X[1] - X[0], X[2] - X[0], X[3] - X[0], &S);
+    // the stencil's nonzero weights name the realising features
+    int nz[4], m = 0;
+    for (int a = 0; a < 4; ++a)
+      if (S.c[a] != 0.0) nz[m++] = a;
+    uint64_t f;
+    if (S.m == 2) {
+      f = type == 0 ? feature_key(kFeatFV, (uint32_t)j, (uint32_t)i, B) : feature_key(kFeatEE, (uint32_t)i, (uint32_t)j, B);
+    } else if (S.m == 1) {
+      // one point (the weight +-1 alone on its side) against the interior of a segment
+      int pnt, s0, s1;
+      if (type == 0) { pnt = 0; s0 = nz[1]; s1 = nz[2]; }
+      else if ((S.c[0] != 0.0) != (S.c[1] != 0.0)) { pnt = S.c[0] != 0.0 ? 0 : 1; s0 = 2; s1 = 3; }
+      else { pnt = S.c[2] != 0.0 ? 2 : 3; s0 = 0; s1 = 1; }
+      int32_t e;
+      if (type == 1) e = (s0 == 2) ? j : i;
+      else e = edge_id_of(v[s0], v[s1], T.nv, ekey, eid, T.ne);
+      if (e < 0) { raise_flag(st, EIPC_FLAG_BAD_INDEX); e = 0; }
+      f = feature_key(kFeatVE, (uint32_t)v[pnt], (uint32_t)e, B);
+    } else {
+      int32_t a = v[nz[0]], b = v[m > 1 ? nz[1] : nz[0]];
+      if (a > b) { const int32_t t = a; a = b; b = t; }
+      f = feature_key(kFeatVV, (uint32_t)a, (uint32_t)b, B);
+    }
+    fkeys[k] = f;
+    fvals[k] = (uint32_t)k;
+  }
+}
+
+// sorted by feature: the first pair of each feature (lowest pair position, the sort being
+// stable) is kept
+__global__ void __launch_bounds__(kBlock) k_feature_firsts(const uint64_t* __restrict__ fkeys,
+                                                           const uint32_t* __restrict__ fvals, const int64_t* n_surv,
+                                                           int64_t cap, int64_t* __restrict__ keep) {
+  const int64_t n = clamp_count(n_surv, cap);
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += grid_stride())
+    keep[fvals[s]] = (s == 0 || fkeys[s] != fkeys[s - 1]) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock) k_feature_compact(const uint64_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ vals,
+                                                            const int64_t* __restrict__ keep,
+                                                            const int64_t* __restrict__ pos, const int64_t* n_surv,
+                                                            int64_t cap, uint64_t* __restrict__ keys2,
+                                                            uint32_t* __restrict__ vals2) {
+  const int64_t n = clamp_count(n_surv, cap);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride())
+    if (keep[k]) {
+      keys2[pos[k]] = keys[k];
+      vals2[pos[k]] = vals[k];
+    }
+}
+
 // Sorted survivors -> caller's pair arrays.
 __global__ void __launch_bounds__(kBlock) k_emit_pairs(Topo T, const uint64_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ vals, const double* __restrict__ sd,
@@ -242,7 +339,28 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
                              sc->sort_hist, s);
   const uint64_t* k = which ? sc->skeys_alt : sc->skeys;
   const uint32_t* v = which ? sc->svals_alt : sc->svals;
-  launch(k_emit_pairs, blocks_for(out.capacity, 8), kBlock, 0, s, sc->topo, k, v, sc->sd, n_surv, sc->cand_cap, out,
+  const int64_t* n_out = n_surv;
+  if (p.flags & EIPC_PARAM_DEDUP) {
+    // feature keys in the record buffers (free until the evaluation), stable sort, firsts,
+    // compaction back into (type, i, j) order in the other half of the pair-sort buffers
+    const int64_t cap = sc->rec_cap < sc->cand_cap ? sc->rec_cap : sc->cand_cap;
+    launch(k_feature_keys, blocks_for(cap, 8), kBlock, 0, s, sc->topo, static_cast<const double*>(sc->x4), k,
+           static_cast<const int64_t*>(n_surv), cap, static_cast<const uint64_t*>(sc->edge_key),
+           static_cast<const int32_t*>(sc->edge_id), sc->feat_bits, sc->hkeys, sc->hvals, sc->status);
+    const int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_surv, cap, 2 + 2 * sc->feat_bits,
+                                  sc->sort_hist, s);
+    launch(k_feature_firsts, blocks_for(cap, 8), kBlock, 0, s, static_cast<const uint64_t*>(wf ? sc->hkeys_alt : sc->hkeys),
+           static_cast<const uint32_t*>(wf ? sc->hvals_alt : sc->hvals), static_cast<const int64_t*>(n_surv), cap,
+           sc->seg_flag);
+    int64_t* n_kept = sc->counters + kCntDedup;
+    exclusive_scan_i64(sc->seg_flag, sc->seg_id, n_surv, cap, n_kept, sc->scan_partial, s);
+    uint64_t* k2 = which ? sc->skeys : sc->skeys_alt;
+    uint32_t* v2 = which ? sc->svals : sc->svals_alt;
+    launch(k_feature_compact, blocks_for(cap, 8), kBlock, 0, s, k, v, static_cast<const int64_t*>(sc->seg_flag),
+           static_cast<const int64_t*>(sc->seg_id), static_cast<const int64_t*>(n_surv), cap, k2, v2);
+    k = k2; v = v2; n_out = n_kept;
+  }
+  launch(k_emit_pairs, blocks_for(out.capacity, 8), kBlock, 0, s, sc->topo, k, v, sc->sd, n_out, sc->cand_cap, out,
                                                                sc->status);
   sc->timers->stop(kKPairSort, s);
 }

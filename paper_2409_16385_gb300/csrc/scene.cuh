@@ -56,7 +56,10 @@ struct eipc_scene {
   uint32_t* hvals_alt;
   double* hrec;          // [rec_cap*9]
   double* ublk;          // [rec_cap*9] reduced upper-triangle blocks
-  double* hvp_out;       // [(ns+1)*3] Hessian-vector product: reduced rows, then the kinematic sum
+  double* hvp_out;       // [(ns+64)*3] Hessian-vector product: reduced rows, then 64 kinematic partials
+  uint64_t* edge_key;    // [ne] sorted a * nv + b of every edge (a < b), for edge-id lookup
+  int32_t* edge_id;      // [ne] edge id of each sorted key
+  int feat_bits;         // bits per id in the feature keys of the deduplicated pair set
   int64_t* seg_flag;     // [rec_cap]
   int64_t* seg_id;       // [rec_cap]
   int64_t* seg_start;    // [rec_cap]
@@ -87,7 +90,7 @@ struct eipc_scene {
 namespace eipc {
 // device counters
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
-       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntN = 24 };
+       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntDedup = 17, kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \
   do {                                    \
