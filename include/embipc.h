@@ -185,6 +185,15 @@ eipc_status eipc_contact_hvp(eipc_scene* scene, const double* q, const eipc_pair
                              const eipc_params* params, const double* v, const double* kin_dir, double* out_r,
                              double* out_kin, eipc_stream stream);
 
+/* EE mollifier, the IPC-style variant for nearly parallel edges (the paper applies none):
+ * with factor > 0, an edge-edge pair (i, j) with c = |e_i x e_j|^2 below
+ * eps_x = factor * rest_len2[i] * rest_len2[j] carries kappa m(c) b(d), m(c) = c (2/eps_x
+ * - c/eps_x^2), in every later eval_contact, contact_hvp and friction_lag (whose lambda is
+ * scaled by m at x^n); such pairs take a full 12 x 12 Hessian (PSD-projected by Jacobi for
+ * eval_contact).  IPC's factor is 1e-3.  rest_len2: HOST [E], squared rest lengths of the
+ * edges, all > 0.  factor = 0 turns it off.  Synchronous (copies rest_len2). */
+eipc_status eipc_scene_set_mollifier(eipc_scene* scene, const double* rest_len2, double factor);
+
 /* New prescribed positions of the kinematic vertices: x_kin is a DEVICE array [Nv*3]
  * (rows of embedded vertices are ignored).  Asynchronous on `stream`, capturable. */
 eipc_status eipc_scene_set_kinematic(eipc_scene* scene, const double* x_kin, eipc_stream stream);

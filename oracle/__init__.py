@@ -60,6 +60,8 @@ def lib():
         L.orc_hvp.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
                               dbl, dbl, dbl, dbl, P, P, P]
         L.orc_dedup.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, P]
+        L.orc_set_mollifier.argtypes = [i64, P, dbl]
+        L.orc_pair_barrier_mollified.argtypes = [P, dbl, dbl, dbl, P, P, P]
         L.orc_result_nnzb.argtypes = [P]
         L.orc_result_nnzb.restype = i64
         L.orc_result_copy.argtypes = [P, P, P, P, P, P, P]
@@ -188,6 +190,27 @@ def pairs_of(scene, x: np.ndarray, ptype: int, queries: np.ndarray, dhat: Option
         if n <= cap:
             return dict(i=i[:n], j=j[:n], d=d[:n])
         cap = int(n)
+
+
+MOLLIFIER_FACTOR = 1e-3
+
+
+def set_mollifier(scene, x_rest: Optional[np.ndarray], factor: float = MOLLIFIER_FACTOR) -> None:
+    """Turn the EE mollifier on (eps_x = factor |e_i|^2 |e_j|^2 at the rest positions
+    x_rest) or off (x_rest None).  Applies to every later oracle call."""
+    if x_rest is None:
+        lib().orc_set_mollifier(0, None, 0.0)
+        return
+    e = scene.edges
+    r2 = np.ascontiguousarray(np.sum((x_rest[e[:, 1]] - x_rest[e[:, 0]]) ** 2, axis=1), np.float64)
+    lib().orc_set_mollifier(len(r2), _p(r2), float(factor))
+
+
+def pair_barrier_mollified(x4: np.ndarray, eps: float, dhat: float, kappa: float):
+    E = np.zeros(1); g = np.zeros(12); H = np.zeros(144)
+    lib().orc_pair_barrier_mollified(_p(_f64(x4).reshape(12)), float(eps), float(dhat), float(kappa), _p(E), _p(g),
+                                     _p(H))
+    return float(E[0]), g, H.reshape(12, 12)
 
 
 def dedup(scene, x: np.ndarray, prs: Dict[str, np.ndarray]) -> Dict[str, np.ndarray]:

@@ -237,12 +237,38 @@ struct Local {
   double H[144];
 };
 
-// kappa b(d(x)) with exact derivatives; H is the raw (unprojected) Hessian
-void barrier_local(int type, const double* x4, double dhat, double kappa, Local& out) {
+// EE mollifier (the IPC-style variant; the paper applies none): per-edge rest squared
+// lengths and the factor of eps_x = factor |e_i^rest|^2 |e_j^rest|^2; factor <= 0 = off.
+std::vector<double> g_rest_len2;
+double g_moll_factor = 0.0;
+
+// m(c) = -c^2 / eps^2 + 2 c / eps for c = |e_i x e_j|^2 < eps, else 1
+template <class T>
+T mollifier(const T& c, double eps) {
+  if (val(c) >= eps) return T(1.0);
+  return c * (T(2.0 / eps) - c * T(1.0 / (eps * eps)));
+}
+
+double moll_eps(int type, int64_t i, int64_t j) {
+  if (type != 1 || g_moll_factor <= 0.0 || g_rest_len2.empty() || i < 0 || j < 0) return 0.0;
+  return g_moll_factor * g_rest_len2[i] * g_rest_len2[j];
+}
+
+// kappa m(x) b(d(x)) with exact derivatives (m = 1 unless an EE pair is mollified); H is
+// the raw (unprojected) Hessian
+void barrier_local(int type, int64_t pi, int64_t pj, const double* x4, double dhat, double kappa, Local& out) {
   int reg; double c[4];
   AD s = pair_d2_ad(type, x4, &reg, c);
   AD d = sqrt(s);
   AD b = barrier(d, dhat);
+  const double eps = moll_eps(type, pi, pj);
+  if (eps > 0.0) {
+    V3<AD> p[4];
+    for (int a = 0; a < 4; ++a)
+      p[a] = {AD::var(x4[3 * a], 3 * a), AD::var(x4[3 * a + 1], 3 * a + 1), AD::var(x4[3 * a + 2], 3 * a + 2)};
+    V3<AD> n = cross(p[1] - p[0], p[3] - p[2]);
+    b = mollifier(dot(n, n), eps) * b;
+  }
   out.E = kappa * b.v;
   for (int i = 0; i < 12; ++i) out.g[i] = kappa * b.g[i];
   for (int i = 0; i < 12; ++i)
@@ -442,7 +468,7 @@ void orc_f0(double y, double eps, double* out3) {
 void orc_pair_barrier(int type, const double* x4, double dhat, double kappa, double* E,
                       double* g12, double* H144, double* Hp144) {
   Local L;
-  barrier_local(type, x4, dhat, kappa, L);
+  barrier_local(type, -1, -1, x4, dhat, kappa, L);
   *E = L.E;
   std::memcpy(g12, L.g, sizeof(L.g));
   std::memcpy(H144, L.H, sizeof(L.H));
@@ -526,7 +552,14 @@ void orc_friction_lag(int64_t nv, const double* xn, int64_t nf, const int32_t* t
     orc_barrier(d, dhat, bb);
     for (int a = 0; a < 4; ++a) { lv[4 * k + a] = s[a]; lgamma[4 * k + a] = c[a]; }
     for (int q = 0; q < 3; ++q) { ln[3 * k + q] = r[q] / rn; lanchor[3 * k + q] = r[q]; }
-    llambda[k] = kappa * std::fabs(bb[1]);
+    // lagged normal force magnitude; a mollified EE pair scales it by m(x^n)
+    double mk = 1.0;
+    const double eps = moll_eps(type[k], pi[k], pj[k]);
+    if (eps > 0.0) {
+      V3<double> n = cross(p[1] - p[0], p[3] - p[2]);
+      mk = mollifier(dot(n, n), eps);
+    }
+    llambda[k] = kappa * mk * std::fabs(bb[1]);
   }
 }
 
@@ -556,7 +589,7 @@ orc_eval_result* orc_eval(int64_t nv, const double* x, int64_t nf, const int32_t
     double x4[12];
     gather4(x, st[k].data(), x4);
     Local L;
-    barrier_local(type[k], x4, dhat, kappa, L);
+    barrier_local(type[k], pi[k], pj[k], x4, dhat, kappa, L);
     if (project) {
       double Hp[144];
       psd_project(12, L.H, Hp);
@@ -617,7 +650,7 @@ void orc_hvp(int64_t nv, const double* x, int64_t nf, const int32_t* tris, int64
     double x4[12];
     gather4(x, v, x4);
     Local L;
-    barrier_local(type[k], x4, dhat, kappa, L);
+    barrier_local(type[k], pi[k], pj[k], x4, dhat, kappa, L);
     apply(v, L);
   }
   if (mu > 0.0) {
@@ -693,6 +726,28 @@ void orc_dedup(int64_t nv, const double* x, int64_t nf, const int32_t* tris, int
     }
     keep[k] = seen.emplace(key, k).second ? 1 : 0;
   }
+}
+
+// EE mollifier: rest squared lengths of the ne edges and the factor of eps_x (<= 0: off)
+void orc_set_mollifier(int64_t ne, const double* rest_len2, double factor) {
+  g_rest_len2.assign(rest_len2, rest_len2 + (factor > 0.0 ? ne : 0));
+  g_moll_factor = factor;
+}
+
+// one mollified EE stencil with eps_x given: energy, gradient, raw Hessian (for pins)
+void orc_pair_barrier_mollified(const double* x4, double eps, double dhat, double kappa, double* E, double* g12,
+                                double* H144) {
+  const std::vector<double> keep = g_rest_len2;
+  const double keep_f = g_moll_factor;
+  g_rest_len2.assign(2, 1.0);
+  g_moll_factor = eps;
+  Local L;
+  barrier_local(1, 0, 1, x4, dhat, kappa, L);
+  g_rest_len2 = keep;
+  g_moll_factor = keep_f;
+  *E = L.E;
+  std::memcpy(g12, L.g, sizeof(L.g));
+  std::memcpy(H144, L.H, sizeof(L.H));
 }
 
 int64_t orc_result_nnzb(const orc_eval_result* r) { return (int64_t)r->R.H.size(); }

@@ -25,7 +25,7 @@ EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_
            "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
            "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
-           "eipc_contact_hvp", "eipc_scene_set_kinematic"]
+           "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier"]
 
 
 class Params(ctypes.Structure):
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = True):
     L.eipc_contact_hvp.restype = i32
     L.eipc_scene_set_kinematic.argtypes = [P, P, P]
     L.eipc_scene_set_kinematic.restype = i32
+    L.eipc_scene_set_mollifier.argtypes = [P, P, ctypes.c_double]
+    L.eipc_scene_set_mollifier.restype = i32
     _lib = L
     return L
 
@@ -305,6 +307,17 @@ class ContactScene:
     def set_kinematic(self, x_kin):
         """New positions of the kinematic vertices (device f64 [Nv,3]; other rows ignored)."""
         _check(self.lib.eipc_scene_set_kinematic(self.handle, _ptr(x_kin), _stream()), "eipc_scene_set_kinematic")
+
+    def set_mollifier(self, x_rest=None, factor: float = 1e-3):
+        """EE mollifier with eps_x = factor |e_i|^2 |e_j|^2 at the rest positions x_rest
+        (host [Nv,3]); x_rest None turns it off."""
+        if x_rest is None:
+            _check(self.lib.eipc_scene_set_mollifier(self.handle, None, 0.0), "eipc_scene_set_mollifier")
+            return
+        e = np.asarray(self.scene.edges)
+        xr = np.asarray(x_rest, np.float64)
+        r2 = np.ascontiguousarray(np.sum((xr[e[:, 1]] - xr[e[:, 0]]) ** 2, axis=1), np.float64)
+        _check(self.lib.eipc_scene_set_mollifier(self.handle, r2.ctypes.data, float(factor)), "eipc_scene_set_mollifier")
 
     def set_dedup(self, on: bool = True):
         """Deduplicated contact sets from build_candidates (EIPC_PARAM_DEDUP)."""

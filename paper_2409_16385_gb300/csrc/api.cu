@@ -22,7 +22,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
@@ -156,6 +156,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->gseg_flag, s->gcap)); ok(dalloc(&s->gseg_id, s->gcap)); ok(dalloc(&s->gseg_start, s->gcap));
   ok(dalloc(&s->row_count, Ns + 1));
   ok(dalloc(&s->edge_key, E > 0 ? E : 1)); ok(dalloc(&s->edge_id, E > 0 ? E : 1));
+  ok(dalloc(&s->moll_r2, E > 0 ? E : 1));
   ok(dalloc(&s->scan_partial, kScanBlocks + 1)); ok(dalloc(&s->sum_partial, kScanBlocks));
   ok(dalloc(&s->status, 1));
   if (e != cudaSuccess) {
@@ -273,6 +274,18 @@ eipc_status eipc_contact_hvp(eipc_scene* sc, const double* q, const eipc_pairs* 
     return EIPC_ERR_INVALID;
   hvp_launch(sc, q, *pairs, lag, *p, v, kin_dir, out_r, out_kin, (cudaStream_t)stream);
   return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
+eipc_status eipc_scene_set_mollifier(eipc_scene* sc, const double* rest_len2, double factor) {
+  if (!sc || !(factor >= 0.0) || !std::isfinite(factor) || (factor > 0.0 && !rest_len2)) return EIPC_ERR_INVALID;
+  if (factor > 0.0) {
+    for (int64_t e = 0; e < sc->ne; ++e)
+      if (!(rest_len2[e] > 0.0) || !std::isfinite(rest_len2[e])) return EIPC_ERR_INVALID;
+    if (sc->ne > 0 && cudaMemcpy(sc->moll_r2, rest_len2, sizeof(double) * sc->ne, cudaMemcpyHostToDevice) != cudaSuccess)
+      return EIPC_ERR_CUDA;
+  }
+  sc->moll_factor = factor;
+  return EIPC_OK;
 }
 
 eipc_status eipc_scene_set_kinematic(eipc_scene* sc, const double* x_kin, eipc_stream stream) {

@@ -263,6 +263,8 @@ struct EvalArgs {
   DevStatus* st;
   bool project;            // PSD-project the barrier Hessians (projected Newton)
   const uint32_t* order;   // processing order of the barrier items (null: index order)
+  const double* moll_r2;   // EE mollifier: rest squared edge lengths (null: off)
+  double moll_factor;      // eps_x = moll_factor |e_i|^2 |e_j|^2
   int64_t* queue;          // next unclaimed position of `order` (work queue)
   const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
   double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
@@ -456,6 +458,160 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
     for (int q = p + 1; q < 5; ++q) { const double t = 0.5 * (K[p][q] + K[q][p]); K[p][q] = t; K[q][p] = t; }
 }
 
+// ------------------------------------------------------------------ EE mollifier
+// IPC-style variant (the paper applies none): an edge-edge pair whose edges are nearly
+// parallel, c = |e_i x e_j|^2 < eps_x = factor |e_i^rest|^2 |e_j^rest|^2, carries
+// kappa m(c) b(d) with m(c) = c (2 / eps - c / eps^2), which is C1 at c = eps and vanishes
+// as the edges become parallel.  Its Hessian leaves the 5-dimensional span, so these rare
+// pairs take a full 12 x 12 path (exact Hessian; Jacobi projection for projected Newton).
+
+__device__ __forceinline__ bool ee_mollified(const EvalArgs& A, int type, int32_t i, int32_t j, const V3 Y[4],
+                                             double* eps, double* c) {
+  if (type != 1 || !A.moll_r2) return false;
+  const V3 nn = cross(Y[1] - Y[0], Y[3] - Y[2]);
+  *c = dot(nn, nn);
+  *eps = A.moll_factor * A.moll_r2[i] * A.moll_r2[j];
+  return *c < *eps;
+}
+
+// energy, gradient and exact Hessian (node-major 3a + k) of kappa m(c(x)) b(d(x))
+__device__ __noinline__ void mollified_local(const V3* Y, const Stencil& S, double d, double dhat, double kappa,
+                                             double eps, double c, double* E, double* g, double* H) {
+  BarrierSpan B;
+  barrier_span(Y, S, d, dhat, kappa, B);
+  const double rhv[3] = {B.rh.x, B.rh.y, B.rh.z};
+  double Q[12][5];
+#pragma unroll 1
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) {
+      for (int p = 0; p < 3; ++p) Q[3 * a + k][p] = (k == p) ? B.basis[0][a] : 0.0;
+      Q[3 * a + k][3] = B.basis[1][a] * rhv[k];
+      Q[3 * a + k][4] = B.basis[2][a] * rhv[k];
+    }
+  double QK[12][5];
+#pragma unroll 1
+  for (int r = 0; r < 12; ++r)
+    for (int p = 0; p < 5; ++p) {
+      double acc = 0.0;
+      for (int q = 0; q < 5; ++q) acc += Q[r][q] * B.K[q][p];
+      QK[r][p] = acc;
+    }
+  // kappa grad b = kappa b' c_a r^ (c_a = |c| basis0_a)
+  double gb[12];
+  for (int a = 0; a < 4; ++a)
+    for (int k = 0; k < 3; ++k) gb[3 * a + k] = kappa * B.b1 * B.cn * B.basis[0][a] * rhv[k];
+  // c = |e0 x e1|^2: gradient and Hessian blocks in (e0, e1)
+  const V3 e0 = Y[1] - Y[0], e1 = Y[3] - Y[2];
+  const double s00 = dot(e0, e0), s11 = dot(e1, e1), s01 = dot(e0, e1);
+  const double E0[3] = {e0.x, e0.y, e0.z}, E1[3] = {e1.x, e1.y, e1.z};
+  double ge[2][3];
+  for (int k = 0; k < 3; ++k) {
+    ge[0][k] = 2.0 * (s11 * E0[k] - s01 * E1[k]);
+    ge[1][k] = 2.0 * (s00 * E1[k] - s01 * E0[k]);
+  }
+  double gc[12];
+  for (int k = 0; k < 3; ++k) {
+    gc[k] = -ge[0][k]; gc[3 + k] = ge[0][k]; gc[6 + k] = -ge[1][k]; gc[9 + k] = ge[1][k];
+  }
+  const double m = c * (2.0 / eps - c / (eps * eps));
+  const double m1 = 2.0 / eps - 2.0 * c / (eps * eps);
+  const double m2 = -2.0 / (eps * eps);
+  const double kb = B.E;                 // kappa b
+  *E = m * kb;
+  for (int r = 0; r < 12; ++r) g[r] = m * gb[r] + kb * m1 * gc[r];
+  // the e-blocks of the Hessian of c
+  auto hc = [&](int ea, int eb, int k, int l) -> double {
+    const double dl = (k == l) ? 1.0 : 0.0;
+    if (ea == 0 && eb == 0) return 2.0 * (s11 * dl - E1[k] * E1[l]);
+    if (ea == 1 && eb == 1) return 2.0 * (s00 * dl - E0[k] * E0[l]);
+    if (ea == 0) return 4.0 * E0[k] * E1[l] - 2.0 * E1[k] * E0[l] - 2.0 * s01 * dl;
+    return 4.0 * E1[k] * E0[l] - 2.0 * E0[k] * E1[l] - 2.0 * s01 * dl;
+  };
+  const int edge_of[4] = {0, 0, 1, 1};
+  const double sgn[4] = {-1.0, 1.0, -1.0, 1.0};
+#pragma unroll 1
+  for (int r = 0; r < 12; ++r) {
+    const int a = r / 3, k = r % 3;
+    for (int q = 0; q < 12; ++q) {
+      const int b2 = q / 3, l = q % 3;
+      double hb = 0.0;
+      for (int p = 0; p < 5; ++p) hb += QK[r][p] * Q[q][p];
+      const double hcv = sgn[a] * sgn[b2] * hc(edge_of[a], edge_of[b2], k, l);
+      H[12 * r + q] = m * hb + kb * (m2 * gc[r] * gc[q] + m1 * hcv) + m1 * (gb[r] * gc[q] + gc[r] * gb[q]);
+    }
+  }
+  for (int r = 0; r < 12; ++r)
+    for (int q = r + 1; q < 12; ++q) {
+      const double t = 0.5 * (H[12 * r + q] + H[12 * q + r]);
+      H[12 * r + q] = t; H[12 * q + r] = t;
+    }
+}
+
+// cyclic Jacobi on an N x N symmetric matrix in memory, then A <- V max(Lambda, 0) V^T
+__device__ __noinline__ void psd_project_mem(double* A, int N) {
+  double V[144];
+  for (int i = 0; i < N * N; ++i) V[i] = (i / N == i % N) ? 1.0 : 0.0;
+  double fro = 0.0;
+  for (int i = 0; i < N * N; ++i) fro += A[i] * A[i];
+  const double tol = 1e-28 * fro;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) off += A[p * N + q] * A[p * N + q];
+    if (off <= tol) break;
+    for (int p = 0; p < N; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        const double apq = A[p * N + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q * N + q] - A[p * N + p]) / (2.0 * apq);
+        const double at = fabs(theta);
+        double t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
+        t = theta < 0.0 ? -t : t;
+        const double cs = rsqrt(t * t + 1.0), sn = t * cs;
+        for (int k = 0; k < N; ++k) {
+          const double akp = A[k * N + p], akq = A[k * N + q];
+          A[k * N + p] = cs * akp - sn * akq;
+          A[k * N + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < N; ++k) {
+          const double apk = A[p * N + k], aqk = A[q * N + k];
+          A[p * N + k] = cs * apk - sn * aqk;
+          A[q * N + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < N; ++k) {
+          const double vkp = V[k * N + p], vkq = V[k * N + q];
+          V[k * N + p] = cs * vkp - sn * vkq;
+          V[k * N + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  double lam[12];
+  for (int e = 0; e < N; ++e) lam[e] = A[e * N + e] > 0.0 ? A[e * N + e] : 0.0;
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) {
+      double acc = 0.0;
+      for (int e = 0; e < N; ++e) acc += V[p * N + e] * lam[e] * V[q * N + e];
+      A[p * N + q] = acc;
+    }
+}
+
+// weight of each stencil vertex on each of the item's cage nodes (0 for kinematic)
+__device__ __forceinline__ void vertex_node_weights(const int32_t v[4], const int32_t* __restrict__ cage_idx,
+                                                    const double* __restrict__ w, const int32_t* nodes, int n,
+                                                    double W[4][kMaxNodes]) {
+  for (int a = 0; a < 4; ++a) {
+    for (int u = 0; u < n; ++u) W[a][u] = 0.0;
+    const int4 id = __ldg(reinterpret_cast<const int4*>(cage_idx) + v[a]);
+    if (id.x < 0) continue;
+    const int ids[4] = {id.x, id.y, id.z, id.w};
+    for (int s2 = 0; s2 < 4; ++s2) {
+      int u = 0;
+      while (u < n - 1 && nodes[u] != ids[s2]) ++u;
+      W[a][u] += __ldg(w + 4 * (int64_t)v[a] + s2);
+    }
+  }
+}
+
 // One barrier item: distance, span Hessian (projected unless A.project is false), energy,
 // gradient records and upper-triangle Hessian records at the item's own offsets.
 __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) {
@@ -485,6 +641,8 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   } else {
     const double d = sqrt(S.d2);
     active = d < A.dhat;
+    double eps_m, c_m;
+    if (active && ee_mollified(A, type, A.pr.i[k], A.pr.j[k], Y, &eps_m, &c_m)) return;   // k_eval_mollified
     if (active) {
       BarrierSpan B;
       barrier_span(Y, S, d, A.dhat, A.kappa, B);
@@ -739,6 +897,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
     } else {
       const double d = sqrt(S.d2);
       active = d < A.dhat;
+      double eps_m, c_m;
+      if (active && ee_mollified(A, type, A.pr.i[k], A.pr.j[k], Y, &eps_m, &c_m)) continue;   // k_hvp_mollified
       if (active) {
         BarrierSpan B;
         barrier_span(Y, S, d, A.dhat, A.kappa, B);
@@ -824,6 +984,90 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_
     bool kin = false;
     for (int a = 0; a < 4; ++a) kin |= __ldg(A.cage_idx + 4 * (int64_t)v[a]) < 0;
     if (kin) emit_g(A, og + n, (uint64_t)(A.ns + (k & (kKinSlots - 1))), Fs * ks[0]);
+  }
+}
+
+// Mollified EE pairs (the main kernels skip them): the full 12 x 12 path, one thread per
+// item, launched only when the mollifier is on.  The records go to the item's own offsets,
+// as for every other item.
+template <bool hvp>
+__global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
+  const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
+  const int64_t nit = *A.n_items;
+  const int64_t np = P < nit ? P : nit;
+  const V3 kd = {A.kin_dir[0], A.kin_dir[1], A.kin_dir[2]};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < np; k += grid_stride()) {
+    const int type = A.pr.type[k];
+    if (type != 1) continue;
+    int32_t v[4];
+    stencil_vertices(A.T, type, A.pr.i[k], A.pr.j[k], v);
+    V3 Y[4];
+    const V3 X0 = load_x(A.x4, v[0]);
+    for (int a = 0; a < 4; ++a) Y[a] = load_x(A.x4, v[a]) - X0;
+    double eps_m, c_m;
+    if (!ee_mollified(A, type, A.pr.i[k], A.pr.j[k], Y, &eps_m, &c_m)) continue;
+    Stencil S;
+    ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
+    if (!(S.d2 > 0.0)) continue;             // flagged by the main kernel
+    const double d = sqrt(S.d2);
+    if (!(d < A.dhat)) continue;
+    const int n = A.item_n[k];
+    const int32_t* nodes = A.item_nodes + kMaxNodes * k;
+    const int64_t og = A.ro_g[k];
+    double g12[12], H12[144], Em;
+    mollified_local(Y, S, d, A.dhat, A.kappa, eps_m, c_m, &Em, g12, H12);
+    double W[4][kMaxNodes];
+    vertex_node_weights(v, A.cage_idx, A.w, nodes, n, W);
+    if (hvp) {
+      double u12[12], y12[12];
+      bool kin = false;
+      for (int a = 0; a < 4; ++a) {
+        const bool ka = __ldg(A.cage_idx + 4 * (int64_t)v[a]) < 0;
+        kin |= ka;
+        V3 ua = ka ? kd : V3{0.0, 0.0, 0.0};
+        for (int u = 0; u < n; ++u) ua = ua + load_dir(A.hv_dir, nodes[u]) * W[a][u];
+        u12[3 * a] = ua.x; u12[3 * a + 1] = ua.y; u12[3 * a + 2] = ua.z;
+      }
+      for (int r = 0; r < 12; ++r) {
+        double acc = 0.0;
+        for (int q = 0; q < 12; ++q) acc += H12[12 * r + q] * u12[q];
+        y12[r] = acc;
+      }
+      for (int u = 0; u < n; ++u) {
+        V3 y = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 4; ++a) y = y + V3{y12[3 * a], y12[3 * a + 1], y12[3 * a + 2]} * W[a][u];
+        emit_g(A, og + u, (uint64_t)nodes[u], y);
+      }
+      if (kin) {
+        V3 yk = {0.0, 0.0, 0.0};
+        for (int a = 0; a < 4; ++a)
+          if (__ldg(A.cage_idx + 4 * (int64_t)v[a]) < 0) yk = yk + V3{y12[3 * a], y12[3 * a + 1], y12[3 * a + 2]};
+        emit_g(A, og + n, (uint64_t)(A.ns + (k & (kKinSlots - 1))), yk);
+      }
+      continue;
+    }
+    if (A.project) psd_project_mem(H12, 12);
+    A.item_E[k] = Em;
+    for (int u = 0; u < n; ++u) {
+      double y[3] = {0.0, 0.0, 0.0};
+      for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 3; ++c) y[c] += W[a][u] * g12[3 * a + c];
+      emit_g(A, og + u, (uint64_t)nodes[u], V3{y[0], y[1], y[2]});
+    }
+    int64_t pos = A.ro_h[k];
+    for (int u = 0; u < n; ++u)
+      for (int w2 = u; w2 < n; ++w2, ++pos) {
+        if (pos >= A.rec_cap) continue;
+        double Bk[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) {
+            const double ww = W[a][u] * W[b][w2];
+            if (ww == 0.0) continue;
+            for (int p = 0; p < 3; ++p)
+              for (int q = 0; q < 3; ++q) Bk[p][q] += ww * H12[12 * (3 * a + p) + 3 * b + q];
+          }
+        emit_upper(A, pos, nodes[u], nodes[w2], Bk);
+      }
   }
 }
 
@@ -1031,7 +1275,8 @@ __global__ void k_sum_final(const double* __restrict__ partial, int nb, double* 
 
 // ------------------------------------------------------------------ friction lag
 __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __restrict__ x4, eipc_pairs pr,
-                                                      double dhat, double kappa, eipc_lag out, DevStatus* st) {
+                                                      double dhat, double kappa, eipc_lag out, DevStatus* st,
+                                                      const double* __restrict__ moll_r2, double moll_factor) {
   const int64_t P = clamp_count(pr.count, pr.capacity);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *out.count = P < out.capacity ? P : out.capacity;
@@ -1064,7 +1309,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __re
     for (int a = 0; a < 4; ++a) out.gamma[4 * k + a] = S.c[a];
     out.n[3 * k] = rrel.x / rn; out.n[3 * k + 1] = rrel.y / rn; out.n[3 * k + 2] = rrel.z / rn;
     out.anchor[3 * k] = anc.x; out.anchor[3 * k + 1] = anc.y; out.anchor[3 * k + 2] = anc.z;
-    out.lambda[k] = kappa * fabs(b1);
+    // a mollified EE pair's lagged normal force is scaled by m(x^n)
+    double mk = 1.0;
+    if (type == 1 && moll_r2) {
+      const V3 nn = cross(Y[1] - Y[0], Y[3] - Y[2]);
+      const double c = dot(nn, nn);
+      const double eps = moll_factor * moll_r2[pr.i[k]] * moll_r2[pr.j[k]];
+      if (c < eps) mk = c * (2.0 / eps - c / (eps * eps));
+    }
+    out.lambda[k] = kappa * mk * fabs(b1);
   }
 }
 
@@ -1085,7 +1338,8 @@ void lag_launch(eipc_scene* sc, const double* q_n, const eipc_pairs& pr, const e
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q_n, sc->x4, 1, 0, s));
   EIPC_TIMED(sc, kKLag, s,
              (launch(k_lag, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, sc->topo, sc->x4, pr, p.dhat,
-                                                                                      p.kappa, out, sc->status)));
+                     p.kappa, out, sc->status, static_cast<const double*>(sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr),
+                     sc->moll_factor)));
 }
 
 void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
@@ -1114,6 +1368,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   A.project = (p.flags & EIPC_PARAM_NO_PROJECTION) == 0;
+  A.moll_r2 = sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr;
+  A.moll_factor = sc->moll_factor;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
   {
     // (node count, type) schedule; the pair-sort buffers are free once the pairs are built
@@ -1132,6 +1388,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                            sc->tune.eval_threads, 0, s, A)
                   : launch(k_eval_barrier<2>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
                            sc->tune.eval_threads, 0, s, A)));
+  if (A.moll_r2)
+    EIPC_TIMED(sc, kKEvalBarrier, s, (launch(k_mollified<false>, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
   if (fr)
     EIPC_TIMED(sc, kKEvalFriction, s,
                (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
@@ -1217,12 +1475,16 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   A.project = false;
+  A.moll_r2 = sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr;
+  A.moll_factor = sc->moll_factor;
   A.order = nullptr;
   A.queue = nullptr;
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (launch(k_hvp_barrier, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
+  if (A.moll_r2)
+    EIPC_TIMED(sc, kKEvalBarrier, s, (launch(k_mollified<true>, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
   if (fr)
     EIPC_TIMED(sc, kKEvalFriction, s,
                (launch(k_hvp_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,

@@ -60,6 +60,8 @@ struct eipc_scene {
   uint64_t* edge_key;    // [ne] sorted a * nv + b of every edge (a < b), for edge-id lookup
   int32_t* edge_id;      // [ne] edge id of each sorted key
   int feat_bits;         // bits per id in the feature keys of the deduplicated pair set
+  double* moll_r2;       // [ne] rest squared edge lengths of the EE mollifier
+  double moll_factor;    // eps_x = moll_factor |e_i|^2 |e_j|^2; 0 = mollifier off
   int64_t* seg_flag;     // [rec_cap]
   int64_t* seg_id;       // [rec_cap]
   int64_t* seg_start;    // [rec_cap]

@@ -723,6 +723,39 @@ def batched_grasp(n_scenes: int = 256, seed: int = 0, min_tris: int = 2000, max_
     return out
 
 
+def parallel_sheets(seed: int = 0, cells: int = 12, angle_deg: float = 0.5, gap_frac: float = 0.5) -> Scene:
+    """Two triangulated 2 x 2 cm sheets, a kinematic one at z = 0 and an embedded one
+    (in a one-cube-thick cage) gap_frac dhat above it, turned by angle_deg in its plane, so
+    that many edge-edge pairs within dhat are nearly parallel (the case the EE mollifier
+    treats).  Cage nodes get N(0, 1 um) jitter; a second iterate slides the upper sheet by
+    a seeded 0.2 dhat in-plane step.  dhat = 1e-3, mu = 0.5."""
+    params = dict(DEFAULT_PARAMS)
+    dhat = params["dhat"]
+    rng = np.random.default_rng(seed)
+    h = 0.01
+    lv, lt = grid_plane(cells, cells, -h, h, -h, h)
+    uv, ut = grid_plane(cells, cells, -0.9 * h, 0.9 * h, -0.9 * h, 0.9 * h)
+    a = np.deg2rad(angle_deg)
+    R = np.array([[np.cos(a), -np.sin(a), 0.0], [np.sin(a), np.cos(a), 0.0], [0.0, 0.0, 1.0]])
+    uv = uv @ R.T
+    uv[:, 2] = gap_frac * dhat
+    nodes, tets, grid = grid_cage(uv.min(0) - np.array([1e-3, 1e-3, 5e-4]), uv.max(0) + np.array([1e-3, 1e-3, 5e-4]),
+                                  (6, 6, 1))
+    b = _Builder()
+    b.add_embedded(uv, ut[:, [0, 2, 1]], nodes, tets, grid)
+    b.add_kinematic(lv, lt)
+    sc = b.scene("parallel_sheets", params)
+    q0 = sc.q_rest + rng.normal(0.0, 1e-6, size=sc.q_rest.shape)
+    step = np.zeros_like(q0)
+    step[:, :2] = rng.normal(size=2) / np.sqrt(2.0) * 0.2 * dhat
+    its = [q0, q0 + step]
+    sc.n_iterates = 2
+    sc.iterate = lambda t: its[t].copy()
+    sc.lag_of = lambda t: 0
+    sc.dq = lambda t: np.tile(np.array([0.0, 0.0, -2.0 * dhat]), (sc.Ns, 1))
+    return sc
+
+
 def pad_lift(seed: int = 0, small: bool = False, n_steps: int = 20, theta: float = 1e-4) -> Scene:
     """The sphere-on-pad scene as a dynamic trajectory: the cage is linear corotational
     (E = 5e4 Pa, nu = 0.45, rho = 1e3 kg/m^3, the soft body of Sec. IV-A) under gravity,
