@@ -52,12 +52,13 @@ def parse():
     ap.add_argument("--json-out", default="")
     ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
     ap.add_argument("--rec-cap", type=int, default=0, help="reduction record capacity (0: library default)")
-    ap.add_argument("--workload", choices=["bubble_grasp", "batched", "adjoint"], default="bubble_grasp",
+    ap.add_argument("--workload", choices=["bubble_grasp", "batched", "adjoint", "physical"], default="bubble_grasp",
                     help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step; "
                          "adjoint: trajectory gradient of the sphere on a rising pad")
     ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain per-scene comparison")
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (no autotuning)")
+    ap.add_argument("--solver", choices=["auto", "dense", "pcg"], default="auto", help="physical: linear solver")
     return ap.parse_args()
 
 
@@ -950,6 +951,61 @@ def run_adjoint(args, ws, rank, local):
                 json.dump(line, f, indent=1)
 
 
+# --------------------------------------------------------------------------- physical
+
+def run_physical(args, ws, rank, local):
+    """The bubble grasp simulated by the reduced Newton driver (membranes' outer cage layers
+    position-controlled, body and membranes elastic under gravity, friction lagged every
+    step): time per backward-Euler step, Newton and Krylov iterations, and the contact-stage
+    share.  --solver auto picks the dense solve up to 12k free DoFs (this scene has 7.6k)."""
+    import torch
+    from paper_2409_16385_gb300 import scenes
+    from paper_2409_16385_gb300.sim import Simulator
+
+    dev = torch.device("cuda", local)
+    sc = scenes.bubble_grasp_physical(small=args.quick)
+    sim = Simulator(sc, device=str(dev), solver=args.solver, pair_capacity=1 << 21, bsr_capacity=1 << 21,
+                    rec_capacity=1 << 24)
+    sim.pcg_rtol = 1e-8
+    K = max(2, args.steps // 5)
+    kappa = sc.params["kappa"]
+    lag = sim.initial_lag(kappa)
+    qs = [sim.q0.clone(), sim.q0.clone()]
+    stream = torch.cuda.current_stream()
+    sim.cs.timing_enable(None)
+    ms, infos, pairs = [], [], []
+    zero = torch.zeros(3, dtype=torch.float64, device=dev)
+    for n in range(1, K + 1):
+        if n > 1:
+            lag = sim.cs.friction_lag(qs[-1], sim.cs.build_candidates(qs[-1], out=sim.cs.new_pairs()))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        q, info = sim.step(qs[-1], qs[-2], zero, kappa, lag, rtol=1e-8, q_fixed=sim.prescribed(n))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1)); infos.append(info)
+        pairs.append(int(sim.cs.build_candidates(q).count.item()))
+        qs.append(q)
+    kt = sim.cs.timing_read()
+    contact_ms = sum(v[0] for v in kt.values())
+    line = dict(metric="physical simulation: backward-Euler steps per second", value=1e3 / float(np.mean(ms)),
+                unit="steps/s", n_gpus=ws, steps=K, warmup=0, ms_per_step=float(np.mean(ms)), higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic (seeded)",
+                config=dict(workload=sc.name, cage_nodes=sc.Ns, free_dofs=int(sim.free.sum()) * 3, vertices=sc.Nv,
+                            triangles=sc.F, closing_per_step=1e-4, newton_rtol=1e-8, solver=sim.solver,
+                            pcg_rtol=sim.pcg_rtol),
+                newton_iterations=[i.iterations for i in infos], pcg_iterations=[i.krylov_iterations for i in infos],
+                residuals=[i.residual for i in infos], contact_pairs=pairs,
+                contact_stage_ms_total=contact_ms, step_ms=ms,
+                kernel_ms_total={k: round(v[0], 3) for k, v in kt.items()})
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+
+
 def main():
     args = parse()
     backend = "gloo" if args.impl == "reference" else "nccl"
@@ -960,6 +1016,8 @@ def main():
         run_batched(args, ws, rank, local)
     elif args.workload == "adjoint":
         run_adjoint(args, ws, rank, local)
+    elif args.workload == "physical":
+        run_physical(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -194,6 +194,13 @@ eipc_status eipc_contact_hvp(eipc_scene* scene, const double* q, const eipc_pair
  * edges, all > 0.  factor = 0 turns it off.  Synchronous (copies rest_len2). */
 eipc_status eipc_scene_set_mollifier(eipc_scene* scene, const double* rest_len2, double factor);
 
+/* y <- alpha A x + beta y for a 3x3-block CSR matrix A with nrows block rows (the eipc_bsr
+ * layout: row_ptr[nrows+1], col[nnzb], val[nnzb*9] row-major blocks), for the Krylov
+ * solves of a Newton step.  x, y: device [nrows*3] (x must not alias y); beta = 0 ignores
+ * y's old contents.  One warp per block row with a fixed summation order (deterministic). */
+eipc_status eipc_bsr_spmv(int64_t nrows, const int32_t* row_ptr, const int32_t* col, const double* val,
+                          const double* x, double alpha, double beta, double* y, eipc_stream stream);
+
 /* New prescribed positions of the kinematic vertices: x_kin is a DEVICE array [Nv*3]
  * (rows of embedded vertices are ignored).  Asynchronous on `stream`, capturable. */
 eipc_status eipc_scene_set_kinematic(eipc_scene* scene, const double* x_kin, eipc_stream stream);

@@ -66,17 +66,19 @@ def polar_rotation(F: np.ndarray, max_iters: int = 80) -> np.ndarray:
     return R
 
 
-def psi(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
+def psi(F: np.ndarray, mu, lam) -> np.ndarray:
+    """mu, lam: numbers or one value per matrix of the batch."""
     R = polar_rotation(F)
     D = F - R
     tr = np.einsum("...ij,...ij->...", R, F)        # tr(R^T F)
     return mu * np.einsum("...ij,...ij->...", D, D) + 0.5 * lam * (tr - 3.0) ** 2
 
 
-def first_pk(F: np.ndarray, mu: float, lam: float) -> np.ndarray:
+def first_pk(F: np.ndarray, mu, lam) -> np.ndarray:
     R = polar_rotation(F)
     tr = np.einsum("...ij,...ij->...", R, F)
-    return 2.0 * mu * (F - R) + lam * (tr - 3.0)[..., None, None] * R
+    mu3 = np.asarray(mu)[..., None, None]
+    return 2.0 * mu3 * (F - R) + (np.asarray(lam) * (tr - 3.0))[..., None, None] * R
 
 
 def first_pk_differential(F: np.ndarray, dF: np.ndarray, mu: float, lam: float, step: float = 1e-30) -> np.ndarray:
@@ -110,9 +112,8 @@ def vertex_volumes(sc) -> np.ndarray:
 class Model:
     """Everything the driver needs that does not change along a trajectory."""
     sc: object
-    mu: float
-    lam: float
-    rho: float
+    mu: np.ndarray           # [T] Lame parameters per tet
+    lam: np.ndarray
     h: float
     Dm_inv: np.ndarray       # [T,3,3]
     V_T: np.ndarray          # [T]
@@ -122,8 +123,8 @@ class Model:
 
 
 def build_model(sc) -> Model:
-    mu, lam = lame(sc.material["E"], sc.material["nu"])
-    rho = sc.material["rho"]
+    """Materials: sc.materials (body id -> E, nu, rho; a tet takes the body of the vertices
+    inside it) or one sc.material.  Dirichlet nodes: sc.prescribed_nodes or sc.fixed_nodes."""
     tets = sc.cage_tets
     q0 = sc.q0
     Dm = np.stack([q0[tets[:, 1]] - q0[tets[:, 0]], q0[tets[:, 2]] - q0[tets[:, 0]],
@@ -134,19 +135,33 @@ def build_model(sc) -> Model:
     where = {tuple(t): i for i, t in enumerate(tets.tolist())}
     V_T = np.zeros(len(tets))
     emb = ~sc.kinematic
+    mats = getattr(sc, "materials", None)
+    tet_body = np.zeros(len(tets), np.int64)
     for k in np.nonzero(emb)[0]:
-        V_T[where[tuple(sc.cage_idx[k].tolist())]] += Vk[k]
+        t = where[tuple(sc.cage_idx[k].tolist())]
+        V_T[t] += Vk[k]
+        tet_body[t] = sc.body[k]
+
+    def mat(b):
+        return mats[int(b)] if mats else sc.material
+
+    E = np.array([mat(b)["E"] for b in tet_body])
+    nu = np.array([mat(b)["nu"] for b in tet_body])
+    mu, lam = lame(E, nu)
     M = np.zeros((sc.Ns, sc.Ns))
     f = np.zeros((sc.Ns, 3))
     for k in np.nonzero(emb)[0]:
         idx, w = sc.cage_idx[k], sc.w[k]
-        m = rho * Vk[k]
+        m = mat(sc.body[k])["rho"] * Vk[k]
         M[np.ix_(idx, idx)] += m * np.outer(w, w)
         f[idx] += m * w[:, None] * sc.gravity[None, :]
     active = np.zeros(sc.Ns, bool)
     active[tets[V_T > 0].ravel()] = True
-    return Model(sc=sc, mu=mu, lam=lam, rho=rho, h=sc.params["h"], Dm_inv=Dm_inv, V_T=V_T, M=M, f_ext=f,
-                 free=active & ~sc.fixed_nodes)
+    fixed = getattr(sc, "prescribed_nodes", None)
+    if fixed is None:
+        fixed = sc.fixed_nodes
+    return Model(sc=sc, mu=mu, lam=lam, h=sc.params["h"], Dm_inv=Dm_inv, V_T=V_T, M=M, f_ext=f,
+                 free=active & ~fixed)
 
 
 def _deformation(m: Model, q: np.ndarray) -> np.ndarray:
@@ -262,7 +277,8 @@ def _evaluate(m: Model, sc_n, q, q_tilde, lag, hessian: bool):
     return phi, g, scale, x, H
 
 
-def newton_step(m: Model, q_prev, q_prev2, shift, kappa, lag, rtol: float = 1e-12, max_iter: int = 100):
+def newton_step(m: Model, q_prev, q_prev2, shift, kappa, lag, rtol: float = 1e-12, max_iter: int = 100,
+                q_fixed=None):
     """q^{n+1} = argmin E_IPC by projected Newton with the CCD step bound and backtracking,
     until the free residual is below rtol times the largest force term (its rounding floor
     is a few 1e-13) or the step is below four ulps of the positions.  Returns
@@ -270,6 +286,8 @@ def newton_step(m: Model, q_prev, q_prev2, shift, kappa, lag, rtol: float = 1e-1
     sc_n = shifted_scene(m, shift, kappa)
     q_tilde = 2.0 * q_prev - q_prev2
     q = q_prev.copy()
+    if q_fixed is not None:
+        q[~m.free] = q_fixed[~m.free]
     free3 = np.repeat(m.free, 3)
     for it in range(max_iter):
         phi, g, scale, x, H = _evaluate(m, sc_n, q, q_tilde, lag, True)
@@ -310,11 +328,19 @@ def trajectory(m: Model, theta: float, kappa: float, n_steps: Optional[int] = No
     """States q_0 .. q_N for pad displacement theta per step and contact stiffness kappa."""
     N = m.sc.n_steps if n_steps is None else n_steps
     lag = initial_lag(m, kappa)
+    every = getattr(m.sc, "lag_every_step", False) and m.sc.params["mu"] > 0
+    pad_dir = np.asarray(getattr(m.sc, "pad_dir", (0.0, 0.0, 1.0)), float)
+    presc = getattr(m.sc, "prescribed_q", None)
     qs = [m.sc.q0.copy()]
     prev2 = m.sc.q0.copy()
     iters = []
     for n in range(1, N + 1):
-        q, it = newton_step(m, qs[-1], prev2, n * theta * m.sc.pad_dir, kappa, lag)
+        if every and n > 1:
+            scp = shifted_scene(m, (n - 1) * theta * pad_dir, kappa)
+            xp = embed(scp, qs[-1])
+            lag = friction_lag(scp, xp, pairs(scp, xp))
+        q, it = newton_step(m, qs[-1], prev2, n * theta * pad_dir, kappa, lag,
+                            q_fixed=None if presc is None else presc(n))
         prev2 = qs[-1]
         qs.append(q)
         iters.append(it)

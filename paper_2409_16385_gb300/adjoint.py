@@ -110,7 +110,7 @@ def solve_adjoint(sim, q, theta, kappa, lag, n, rhs, method: str = "dense"):
     def apply(v):
         V = v.reshape(-1, 3) * mask
         Hc, _ = sim.cs.contact_hvp(q, pairs, V.contiguous(), lag=lag)
-        out = sim.M @ V + h2 * (sim.elastic.hvp(q, V) + Hc)
+        out = sim.mass_apply(V) + h2 * (sim.elastic.hvp(q, V) + Hc)
         return (out * mask).reshape(-1)
 
     return _minres(apply, (rhs * mask).reshape(-1)).reshape(-1, 3)
@@ -133,7 +133,7 @@ class ImplicitStep(torch.autograd.Function):
         sim, lag, n = ctx.sim, ctx.lag, ctx.n
         h2 = sim.h ** 2
         Z = solve_adjoint(sim, q, theta, kappa, lag, n, qbar, ImplicitStep.solver)
-        MZ = sim.M @ Z
+        MZ = sim.mass_apply(Z)
         pairs = _system(sim, q, theta, kappa, lag, n)
         _, kin = sim.cs.contact_hvp(q, pairs, Z.contiguous(), lag=lag)
         _, g, _ = sim.cs.eval_contact(q, pairs, lag)

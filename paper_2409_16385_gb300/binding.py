@@ -25,7 +25,7 @@ EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_
            "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
            "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
-           "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier"]
+           "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier", "eipc_bsr_spmv"]
 
 
 class Params(ctypes.Structure):
@@ -106,6 +106,8 @@ def load(build_if_missing: bool = True):
     L.eipc_scene_set_kinematic.restype = i32
     L.eipc_scene_set_mollifier.argtypes = [P, P, ctypes.c_double]
     L.eipc_scene_set_mollifier.restype = i32
+    L.eipc_bsr_spmv.argtypes = [i64, P, P, P, P, ctypes.c_double, ctypes.c_double, P, P]
+    L.eipc_bsr_spmv.restype = i32
     _lib = L
     return L
 
@@ -398,6 +400,17 @@ class ContactScene:
                "eipc_status_read")
         names = [n for b, n in FLAGS.items() if flags.value & b]
         return dict(flags=int(flags.value), names=names, needed=need.tolist(), accd_iters=int(it[0]))
+
+
+def bsr_spmv(row_ptr, col, val, x, out=None, alpha: float = 1.0, beta: float = 0.0):
+    """y = alpha A x + beta y for a 3x3-block CSR matrix (device tensors; x, y [n,3])."""
+    import torch
+    L = load()
+    n = row_ptr.shape[0] - 1
+    y = out if out is not None else torch.zeros_like(x)
+    _check(L.eipc_bsr_spmv(n, _ptr(row_ptr), _ptr(col), _ptr(val), _ptr(x), float(alpha), float(beta), _ptr(y), _stream()),
+           "eipc_bsr_spmv")
+    return y
 
 
 # -------------------------------------------------------------- functional front end

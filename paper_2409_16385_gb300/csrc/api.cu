@@ -276,6 +276,14 @@ eipc_status eipc_contact_hvp(eipc_scene* sc, const double* q, const eipc_pairs* 
   return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
 }
 
+eipc_status eipc_bsr_spmv(int64_t nrows, const int32_t* row_ptr, const int32_t* col, const double* val,
+                          const double* x, double alpha, double beta, double* y, eipc_stream stream) {
+  if (nrows < 0 || (nrows > 0 && (!row_ptr || !x || !y)) || !std::isfinite(alpha) || !std::isfinite(beta))
+    return EIPC_ERR_INVALID;
+  bsr_spmv_launch(nrows, row_ptr, col, val, x, alpha, beta, y, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
+}
+
 eipc_status eipc_scene_set_mollifier(eipc_scene* sc, const double* rest_len2, double factor) {
   if (!sc || !(factor >= 0.0) || !std::isfinite(factor) || (factor > 0.0 && !rest_len2)) return EIPC_ERR_INVALID;
   if (factor > 0.0) {

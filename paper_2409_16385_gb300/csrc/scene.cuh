@@ -113,6 +113,8 @@ void group_energy_launch(eipc_scene* sc, double* E_groups, cudaStream_t s);
 void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
                 const double* v, const double* kin_dir, double* out_r, double* out_kin, cudaStream_t s);
 void set_kinematic_launch(eipc_scene* sc, const double* x_kin, cudaStream_t s);
+void bsr_spmv_launch(int64_t nrows, const int32_t* row_ptr, const int32_t* col, const double* val, const double* x,
+                     double alpha, double beta, double* y, cudaStream_t s);
 void group_alpha_launch(eipc_scene* sc, double* alpha_groups, cudaStream_t s);
 void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_params& p, double* alpha,
                  int64_t* n_candidates, cudaStream_t s);

@@ -33,12 +33,16 @@ def _axial(K):
 
 class CorotationalCage:
     """Elasticity of one cage: tets [T,4] (node ids), rest positions q0 [Ns,3], tet
-    volumes V_T [T] (device tensors, float64)."""
+    volumes V_T [T] (device tensors, float64); Lame parameters mu, lam as numbers or as
+    per-tet tensors [T] (several bodies with their own materials)."""
 
-    def __init__(self, tets, q0, V_T, mu: float, lam: float):
+    def __init__(self, tets, q0, V_T, mu, lam):
         self.tets = tets.long()
         self.ns = q0.shape[0]
-        self.mu, self.lam = float(mu), float(lam)
+        T = self.tets.shape[0]
+        as_t = lambda a: (a.to(q0) if torch.is_tensor(a) else torch.full((T,), float(a), dtype=q0.dtype,
+                                                                          device=q0.device))
+        self.mu, self.lam = as_t(mu), as_t(lam)
         Dm = self._ds(q0)
         self.Dm_inv = torch.linalg.inv(Dm)
         self.V_T = V_T
@@ -76,7 +80,7 @@ class CorotationalCage:
     def _stress(self, F):
         R, S = self.polar(F)
         tr = S.diagonal(dim1=-2, dim2=-1).sum(-1)
-        P = 2.0 * self.mu * (F - R) + self.lam * (tr - 3.0)[:, None, None] * R
+        P = 2.0 * self.mu[:, None, None] * (F - R) + (self.lam * (tr - 3.0))[:, None, None] * R
         return P, R, S, tr
 
     def _scatter(self, G):
@@ -107,8 +111,8 @@ class CorotationalCage:
         w = torch.linalg.solve(trI, k.unsqueeze(-1)).squeeze(-1)
         dR = R @ _skew(w)
         RdF = (R * dF).sum((-1, -2))
-        return (2.0 * self.mu * (dF - dR) + self.lam * RdF[:, None, None] * R
-                + self.lam * (tr - 3.0)[:, None, None] * dR)
+        mu, lam = self.mu[:, None, None], self.lam[:, None, None]
+        return 2.0 * mu * (dF - dR) + lam * RdF[:, None, None] * R + lam * (tr - 3.0)[:, None, None] * dR
 
     def hvp(self, q, v):
         """Exact Hessian of Phi at q times v [Ns,3]."""
@@ -131,6 +135,30 @@ class CorotationalCage:
             lam, V = torch.linalg.eigh(HF)
             HF = V @ torch.diag_embed(lam.clamp_min(0.0)) @ V.transpose(1, 2)
         return self.V_T[:, None, None] * (self.B.transpose(1, 2) @ HF @ self.B)
+
+    def block_pattern(self):
+        """3x3-block CSR pattern of the cage Hessian (node pairs sharing a tet) and, per tet,
+        the block index of each (a, b) node pair: (row_ptr [Ns+1] int32, col int32,
+        slot [T,4,4] int64)."""
+        t = self.tets
+        T = t.shape[0]
+        I = t[:, :, None].expand(T, 4, 4).reshape(-1)
+        J = t[:, None, :].expand(T, 4, 4).reshape(-1)
+        key = I * self.ns + J
+        uniq, inv = torch.unique(key, sorted=True, return_inverse=True)
+        rows = uniq // self.ns
+        counts = torch.bincount(rows, minlength=self.ns)
+        row_ptr = torch.zeros(self.ns + 1, dtype=torch.int64, device=t.device)
+        row_ptr[1:] = torch.cumsum(counts, 0)
+        return row_ptr.to(torch.int32), (uniq % self.ns).to(torch.int32), inv.reshape(T, 4, 4)
+
+    def assemble_blocks(self, Ht, slot, nnzb):
+        """Per-tet 12 x 12 Hessians -> values [nnzb,3,3] on the block pattern."""
+        T = Ht.shape[0]
+        blocks = Ht.reshape(T, 4, 3, 4, 3).permute(0, 1, 3, 2, 4).reshape(T * 16, 3, 3)
+        out = torch.zeros((nnzb, 3, 3), dtype=Ht.dtype, device=Ht.device)
+        out.index_add_(0, slot.reshape(-1), blocks)
+        return out
 
     def assemble_dense(self, Ht):
         n = 3 * self.ns

@@ -552,6 +552,41 @@ def bubble_grasp(seed: int = 0, n_body: int = 71, n_mem: int = 45,
     sc.iterate = lambda t: q_at(float(t))
     sc.lag_of = lambda t: (t // iters_per_step) * iters_per_step
     sc.dq = dq_at
+    sc.node_slices = dict(body=sl_body, top=sl_top, bottom=sl_bot)
+    return sc
+
+
+def bubble_grasp_physical(seed: int = 0, small: bool = False, n_steps: int = 10, closing: float = 1e-4) -> Scene:
+    """The bubble-grasp geometry simulated instead of replayed (Sec. IV-A set-up): the body
+    (E = 5e4 Pa, nu = 0.45, rho = 1e3 kg/m^3) and both membranes (E = 1e4 Pa, nu = 0.45,
+    rho = 10 kg/m^3) are elastic cages under gravity; each membrane's outermost cage layer
+    (away from the body) is position-controlled, moving toward the body by `closing` per
+    time step (h = 1e-2 s); everything else is free.  Friction lags once per time step.
+    Inputs for the driver: q0, prescribed_nodes, prescribed_q(n), materials, gravity."""
+    if small:
+        sc = bubble_grasp(seed, n_body=16, n_mem=10, body_cage=(5, 5, 5), mem_cage=(8, 3, 6))
+    else:
+        sc = bubble_grasp(seed)
+    sc.name = "bubble_grasp_physical" + ("_small" if small else "")
+    q0 = sc.iterate(0)
+    sc.q0 = q0
+    presc = np.zeros(sc.Ns, bool)
+    sign = np.zeros(sc.Ns)
+    for name, sgn in (("top", -1.0), ("bottom", 1.0)):
+        sl = sc.node_slices[name]
+        y = q0[sl, 1]
+        layer = np.abs(y - (y.max() if sgn < 0 else y.min())) < 1e-9
+        idx = np.arange(sc.Ns)[sl][layer]
+        presc[idx] = True
+        sign[idx] = sgn
+    sc.prescribed_nodes = presc
+    sc.fixed_nodes = presc
+    sc.prescribed_q = lambda n: q0 + (n * closing * sign)[:, None] * np.array([0.0, 1.0, 0.0])
+    sc.materials = {0: dict(E=5e4, nu=0.45, rho=1e3), 1: dict(E=1e4, nu=0.45, rho=10.0),
+                    2: dict(E=1e4, nu=0.45, rho=10.0)}
+    sc.gravity = np.array([0.0, 0.0, -9.81])
+    sc.n_steps = int(n_steps)
+    sc.lag_every_step = True
     return sc
 
 
