@@ -100,9 +100,8 @@ def solve_adjoint(sim, q, theta, kappa, lag, n, rhs, method: str = "dense"):
     z = torch.zeros_like(rhs).reshape(-1)
     if method == "dense":
         sim.set_state(n * theta * sim.pad_dir, float(kappa))
-        _, _, _, Hc = sim.contact(q, lag, project=False)
-        A = sim.M3 + h2 * (sim.elastic.assemble_dense(sim.elastic.tet_hessians(q, False)) + Hc)
-        z[free3] = torch.linalg.solve(A[free3][:, free3], rhs.reshape(-1)[free3])
+        A = sim._system_dense(q, lag, project=False)
+        z[free3] = torch.linalg.solve(A, rhs.reshape(-1)[free3])
         return z.reshape(-1, 3)
     pairs = _system(sim, q, theta, kappa, lag, n)
     mask = sim.free[:, None].to(rhs.dtype)

@@ -140,7 +140,11 @@ class Simulator:
             r_i = rows
             M.index_put_((r_i, self.col.long()), Mb, accumulate=True)
             self.M = M
-            self.M3 = torch.kron(M, eye)
+            # free-DoF numbering for the dense systems (-1 on Dirichlet DoFs)
+            fi = torch.full((3 * self.Ns,), -1, dtype=torch.int64, device=self.dev)
+            fi[self.free3] = torch.arange(int(self.free3.sum()), device=self.dev)
+            self.free_index = fi
+            self.M3f = torch.kron(M[self.free][:, self.free], eye).contiguous()
         self.pcg_rtol = 1e-10
         self.pcg_max = 5000
 
@@ -199,19 +203,45 @@ class Simulator:
         return float(phi), g, float(scale)
 
     # ---------------------------------------------------------------- Newton directions
-    def _direction_dense(self, q, lag, g):
+    def _free_block(self, rows, cols, vals, out):
+        """Accumulate dense entries (DoF rows, cols, values) into the free-DoF block."""
+        fr, fc = self.free_index[rows], self.free_index[cols]
+        keep = (fr >= 0) & (fc >= 0)
+        out.index_put_((fr[keep], fc[keep]), vals[keep], accumulate=True)
+
+    def _system_dense(self, q, lag, project: bool):
+        """M + h^2 (hess Phi + H_c) on the free DoFs (exact, or projected)."""
         h2 = self.h ** 2
-        _, _, _, Hc = self.contact(q, lag, project=False)
-        H = self.M3 + h2 * (self.elastic.assemble_dense(self.elastic.tet_hessians(q, False)) + Hc)
-        Hf = H[self.free3][:, self.free3]
-        _, info = torch.linalg.cholesky_ex(Hf)
+        A = self.M3f.clone()
+        Ht = h2 * self.elastic.tet_hessians(q, project)
+        T = Ht.shape[0]
+        d = self.elastic.dofs
+        self._free_block(d[:, :, None].expand(T, 12, 12).reshape(-1), d[:, None, :].expand(T, 12, 12).reshape(-1),
+                         Ht.reshape(-1), A)
+        _, _, _, Hc = self.contact(q, lag, project=project, dense=False)
+        nnzb = int(Hc.nnzb.item())
+        rp = Hc.row_ptr.long()
+        rows = torch.repeat_interleave(torch.arange(self.Ns, device=self.dev), rp[1:] - rp[:-1])
+        cols = Hc.col[:nnzb].long()
+        ar = torch.arange(3, device=self.dev)
+        r3 = (3 * rows[:, None, None] + ar[None, :, None]).expand(nnzb, 3, 3).reshape(-1)
+        c3 = (3 * cols[:, None, None] + ar[None, None, :]).expand(nnzb, 3, 3).reshape(-1)
+        self._free_block(r3, c3, h2 * Hc.val[:nnzb].reshape(-1), A)
+        return A
+
+    def _direction_dense(self, q, lag, g):
+        A = self._system_dense(q, lag, project=False)
+        L, info = torch.linalg.cholesky_ex(A)
         exact = int(info.item()) == 0
         if not exact:
-            _, _, _, Hcp = self.contact(q, lag, project=True)
-            H = self.M3 + h2 * (self.elastic.assemble_dense(self.elastic.tet_hessians(q, True)) + Hcp)
-            Hf = H[self.free3][:, self.free3]
+            A = self._system_dense(q, lag, project=True)
+            L, info = torch.linalg.cholesky_ex(A)
+            if int(info.item()) != 0:          # semidefinite at rounding: a dense LU instead
+                L = None
+        b = -g.reshape(-1)[self.free3]
+        x = torch.cholesky_solve(b[:, None], L).squeeze(1) if L is not None else torch.linalg.solve(A, b)
         p = torch.zeros(3 * self.Ns, dtype=torch.float64, device=self.dev)
-        p[self.free3] = -torch.linalg.solve(Hf, g.reshape(-1)[self.free3])
+        p[self.free3] = x
         return p.reshape(-1, 3), exact, 0
 
     def _direction_pcg(self, q, lag, g):
