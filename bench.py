@@ -140,9 +140,9 @@ def measured_peaks():
 #   others        DRAM bytes per unit of their minimum input + output traffic
 FP64_FLOPS_PER_PAIR = 3455.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
-# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code; empty
-# until the current kernels have been captured
-NCU_TRAFFIC_PER_UNIT = {}
+# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
+# (eval_barrier at the autotuned launch shape: 49.1 MB + 241.8 MB for 115,583 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 2517.0}
 
 
 def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
