@@ -250,8 +250,9 @@ eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_strea
  * (eval), 64, 128, 256 (traversal) or 256 (refit); blocks_per_sm: cap on the grid as a
  * multiple of the 152 SMs (1..64; ignored by the refit); variant: eval 2 = no register
  * cap, 3 = at most 170 registers (3 blocks of 128 per SM); refit 0 = arrival counters
- * behind full device fences, 1 = release-acquire arrival counters.  Results never depend
- * on the shape. */
+ * behind full device fences, 1 = release-acquire arrival counters, 2 = treelets of up to
+ * 32 leaves refitted per warp in shared memory below release-acquire counters (default).
+ * Results never depend on the shape. */
 eipc_status eipc_set_launch(eipc_scene* scene, int32_t kernel, int32_t threads, int32_t blocks_per_sm,
                             int32_t variant);
 

@@ -22,7 +22,7 @@ EVAL_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
 QUERY_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
     (threads, bps, 2) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32))
 
-REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1))
+REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1), (256, 8, 2))
 
 SPACES = {"eval_barrier": EVAL_SPACE, "bvh_query": QUERY_SPACE, "bvh_refit": REFIT_SPACE}
 # the library timer that brackets each tunable kernel's launches

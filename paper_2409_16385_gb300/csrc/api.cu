@@ -25,9 +25,11 @@ void free_scene(eipc_scene* s) {
   void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
-                  s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
+                  s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->tri_bvh.range, s->tri_bvh.tl_root, s->tri_bvh.up_start,
+                  s->tri_bvh.tl_count, s->edge_bvh.n_dev, s->edge_bvh.nodes, s->edge_bvh.leaf_info,
                   s->edge_bvh.parent, s->edge_bvh.leaf_prim, s->edge_bvh.leaf_box, s->edge_bvh.refit_flag,
-                  s->edge_bvh.keys, s->edge_bvh.vals, s->edge_bvh.keys_alt, s->edge_bvh.vals_alt, s->bounds_ws,
+                  s->edge_bvh.keys, s->edge_bvh.vals, s->edge_bvh.keys_alt, s->edge_bvh.vals_alt, s->edge_bvh.range,
+                  s->edge_bvh.tl_root, s->edge_bvh.up_start, s->edge_bvh.tl_count, s->bounds_ws,
                   s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
                   s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
                   s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->ublk, s->seg_flag, s->seg_id, s->seg_start,
@@ -57,6 +59,10 @@ cudaError_t alloc_bvh(Bvh& t, int64_t n) {
   ok(dalloc(&t.vals, n));
   ok(dalloc(&t.keys_alt, n));
   ok(dalloc(&t.vals_alt, n));
+  ok(dalloc(&t.range, n > 1 ? n - 1 : 1));
+  ok(dalloc(&t.tl_root, n));
+  ok(dalloc(&t.up_start, n));
+  ok(dalloc(&t.tl_count, 2));
   if (e == cudaSuccess) e = cudaMemcpy(t.n_dev, &n, sizeof(int64_t), cudaMemcpyHostToDevice);
   return e;
 }
@@ -215,7 +221,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   }
   s->rebuild_interval = 8;
   s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2;
-  s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.refit_variant = 1;
+  s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.refit_variant = 2;
   s->contact_refits = 0;
   *out = s;
   return EIPC_OK;
@@ -409,7 +415,7 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
     return EIPC_OK;
   }
   if (kernel == 2) {
-    if (threads != 256 || (variant != 0 && variant != 1)) return EIPC_ERR_INVALID;
+    if (threads != 256 || variant < 0 || variant > 2) return EIPC_ERR_INVALID;
     sc->tune.refit_variant = variant;
     return EIPC_OK;
   }

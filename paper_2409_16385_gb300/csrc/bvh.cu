@@ -121,7 +121,8 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, 
 
 // Karras 2012: internal node i covers a key range; its split is the highest differing bit.
 __global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict__ keys, int64_t n,
-                                                     BvhNode* __restrict__ nodes, int32_t* __restrict__ parent) {
+                                                     BvhNode* __restrict__ nodes, int32_t* __restrict__ parent,
+                                                     int2* __restrict__ range) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1; i += grid_stride()) {
     int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = delta(keys, n, i, i - dir);
@@ -145,6 +146,7 @@ __global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict_
     nodes[i].c0 = c0;
     nodes[i].c1 = c1;
     nodes[i].split = (int32_t)gamma;   // last leaf position under child 0
+    range[i] = make_int2((int32_t)lo, (int32_t)hi);
     parent[c0 >= 0 ? c0 : (n - 1 + ~c0)] = (int32_t)i;
     parent[c1 >= 0 ? c1 : (n - 1 + ~c1)] = (int32_t)i;
   }
@@ -180,13 +182,31 @@ __device__ __forceinline__ int32_t arrive(int32_t* f) {
   return arrive_acq_rel(f);
 }
 
-// leaf boxes in leaf order, for refitting an existing hierarchy
-__global__ void __launch_bounds__(kBlock) k_leaf_boxes(PrimKind kind, int64_t n, Topo T, const int32_t* __restrict__ leaf_prim,
+// leaf boxes in leaf order, for refitting an existing hierarchy; the leaf's vertex ids
+// come from its leaf record (coalesced) rather than the primitive tables
+__global__ void __launch_bounds__(kBlock) k_leaf_boxes(int64_t n, const int4* __restrict__ leaf_info,
                                                        const double* __restrict__ x4, const double* __restrict__ dx4,
                                                        float* __restrict__ leaf_box) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
+    const int4 li = leaf_info[l];
+    const int32_t v[3] = {li.x, li.y, li.z};
+    double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int a = 0; a < 3; ++a) {
+      if (v[a] < 0) continue;
+      const V3 p = load_x(x4, v[a]);
+      const double c[3] = {p.x, p.y, p.z};
+      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
+      if (dx4) {
+        const V3 d = load_x(dx4, v[a]);
+        const double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
+        for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
+      }
+    }
     float lo[3], hi[3];
-    prim_box(kind, leaf_prim[l], T, x4, dx4, 0.0, lo, hi);
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = __double2float_rd(dlo[k]);
+      hi[k] = __double2float_ru(dhi[k]);
+    }
     float2* o = reinterpret_cast<float2*>(leaf_box + 6 * l);
     o[0] = make_float2(lo[0], lo[1]);
     o[1] = make_float2(lo[2], hi[0]);
@@ -246,6 +266,131 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
       write_child<first>(&nodes[p], slot, lo, hi, kin);
       if (arrive<fences>(&flag[p]) == 0) break;
       node = p;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- two-phase refit
+// Every subtree covers a contiguous leaf range and its internal nodes carry indices inside
+// that range.  At build time the tree is cut into treelets: subtrees of at most kTreelet
+// leaves whose parent covers more.  A refit then (A) refits each treelet with one warp:
+// its leaf boxes, leaf parents and node links are loaded coalesced into shared memory and
+// the bottom-up union runs on shared-memory arrival counters, with no dependent global
+// loads; and (B) climbs from the treelet roots (and the few leaves hanging directly off
+// larger nodes) with the release-acquire counters.  Box unions are exact, so the boxes
+// are those of any other refit order.
+
+__global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2* __restrict__ range,
+                                                          const int32_t* __restrict__ parent, int32_t* __restrict__ tl_root,
+                                                          int32_t* __restrict__ up_start, int32_t* __restrict__ count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n - 1; i += grid_stride()) {
+    if (i < n - 1) {                              // internal node i
+      const int2 r = range[i];
+      const int64_t size = (int64_t)r.y - r.x + 1;
+      const int64_t psize = (i == 0) ? INT64_MAX : (int64_t)range[parent[i]].y - range[parent[i]].x + 1;
+      if (size <= kTreelet && psize > kTreelet) {
+        tl_root[atomicAdd(&count[0], 1)] = (int32_t)i;
+        up_start[atomicAdd(&count[1], 1)] = (int32_t)i;
+      }
+    } else {                                      // leaf l = i - (n - 1)
+      const int64_t l = i - (n - 1);
+      const int32_t p = parent[i];
+      if ((int64_t)range[p].y - range[p].x + 1 > kTreelet) up_start[atomicAdd(&count[1], 1)] = ~(int32_t)l;
+    }
+  }
+}
+
+constexpr int kTreeletWarps = kBlock / 32;
+
+__global__ void __launch_bounds__(kBlock) k_treelet_refit(int64_t n, const int32_t* __restrict__ tl_root,
+                                                          const int32_t* __restrict__ count, const int2* __restrict__ range,
+                                                          const int32_t* __restrict__ parent, const float* __restrict__ leaf_box,
+                                                          BvhNode* __restrict__ nodes) {
+  __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
+  __shared__ int scnt[kTreeletWarps][kTreelet];
+  __shared__ int spar[kTreeletWarps][kTreelet];
+  __shared__ int sc0[kTreeletWarps][kTreelet];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntl = count[0];
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntl; w += nw) {
+    const int32_t root = tl_root[w];
+    const int2 rg = range[root];
+    const int lo = rg.x, m = rg.y - rg.x + 1;           // m <= kTreelet leaves, m - 1 internal nodes
+    // node links of the indices lo .. hi (the treelet's internal nodes are among them)
+    if (lane < m && lo + lane < n - 1) {
+      spar[wib][lane] = parent[lo + lane];
+      sc0[wib][lane] = nodes[lo + lane].c0;
+    }
+    scnt[wib][lane] = 0;
+    __syncwarp();
+    if (lane < m) {
+      const int32_t l = lo + lane;
+      float b[6];
+      for (int k = 0; k < 6; ++k) b[k] = leaf_box[6 * (int64_t)l + k];
+      int32_t child = ~l;
+      int32_t node = parent[n - 1 + l];
+      for (int step = 0; step < kTreelet; ++step) {  // a treelet is at most kTreelet - 1 deep
+        const int off = node - lo;
+        if (off < 0 || off >= m) break;              // (a subtree's nodes lie in its leaf range)
+        const int slot = (sc0[wib][off] == child) ? 0 : 1;
+        float* dl = slot ? nodes[node].lo1 : nodes[node].lo0;
+        float* dh = slot ? nodes[node].hi1 : nodes[node].hi0;
+        for (int k = 0; k < 3; ++k) { __stcg(&dl[k], b[k]); __stcg(&dh[k], b[3 + k]); }
+        for (int k = 0; k < 6; ++k) sbox[wib][off][slot][k] = b[k];
+        __threadfence_block();
+        if (atomicAdd(&scnt[wib][off], 1) == 0) break;   // the sibling finishes this node
+        __threadfence_block();
+        for (int k = 0; k < 3; ++k) {
+          b[k] = fminf(sbox[wib][off][0][k], sbox[wib][off][1][k]);
+          b[3 + k] = fmaxf(sbox[wib][off][0][3 + k], sbox[wib][off][1][3 + k]);
+        }
+        if (node == root) break;                     // its box goes up in phase B
+        child = node;
+        node = spar[wib][off];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_upper_refit(int64_t n, const int32_t* __restrict__ up_start,
+                                                        const int32_t* __restrict__ count, const int32_t* __restrict__ parent,
+                                                        const float* __restrict__ leaf_box, BvhNode* nodes, int32_t* flag) {
+  const int64_t nu = count[1];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nu; k += grid_stride()) {
+    const int32_t st = up_start[k];
+    float lo[3], hi[3];
+    int32_t child, node;
+    if (st >= 0) {                                   // a treelet root: its box from its children
+      const BvhNode* nd = &nodes[st];
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
+        hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
+      }
+      if (st == 0) continue;                         // the whole tree was one treelet
+      child = st;
+      node = parent[st];
+    } else {                                         // a leaf under a larger node
+      const int32_t l = ~st;
+      for (int q = 0; q < 3; ++q) { lo[q] = leaf_box[6 * (int64_t)l + q]; hi[q] = leaf_box[6 * (int64_t)l + 3 + q]; }
+      child = st;
+      node = parent[n - 1 + l];
+    }
+    for (int64_t step = 0; step < n; ++step) {       // a root path has at most n-1 nodes
+      const int slot = (nodes[node].c0 == child) ? 0 : 1;
+      float* dl = slot ? nodes[node].lo1 : nodes[node].lo0;
+      float* dh = slot ? nodes[node].hi1 : nodes[node].hi0;
+      for (int q = 0; q < 3; ++q) { __stcg(&dl[q], lo[q]); __stcg(&dh[q], hi[q]); }
+      if (arrive<false>(&flag[node]) == 0) break;
+      const BvhNode* nd = &nodes[node];
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
+        hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
+      }
+      if (node == 0) break;
+      child = node;
+      node = parent[node];
     }
   }
 }
@@ -366,7 +511,7 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   t.sorted = sv;
   cudaMemsetAsync(t.nodes, 0, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1), s);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
-  if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent);
+  if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent, t.range);
   if (refit_variant == 0)
     launch(k_refit<true, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
@@ -375,6 +520,11 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
     launch(k_refit<true, false>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
            t.leaf_info, t.refit_flag);
+  if (t.n > 1) {
+    cudaMemsetAsync(t.tl_count, 0, 2 * sizeof(int32_t), s);
+    launch(k_treelet_lists, blocks_for(2 * t.n), kBlock, 0, s, t.n, static_cast<const int2*>(t.range),
+           static_cast<const int32_t*>(t.parent), t.tl_root, t.up_start, t.tl_count);
+  }
   t.built = true;
 }
 
@@ -386,10 +536,16 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
 void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
                int refit_variant) {
   if (t.n <= 0) return;
-  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, static_cast<const int32_t*>(t.leaf_prim), x4,
-         dx4, t.leaf_box);
+  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int4*>(t.leaf_info), x4, dx4, t.leaf_box);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
-  if (refit_variant == 0)
+  if (refit_variant == 2 && t.n > 1) {
+    launch(k_treelet_refit, blocks_for(t.n, 8), kBlock, 0, s, t.n, static_cast<const int32_t*>(t.tl_root),
+           static_cast<const int32_t*>(t.tl_count), static_cast<const int2*>(t.range),
+           static_cast<const int32_t*>(t.parent), static_cast<const float*>(t.leaf_box), t.nodes);
+    launch(k_upper_refit, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int32_t*>(t.up_start),
+           static_cast<const int32_t*>(t.tl_count), static_cast<const int32_t*>(t.parent),
+           static_cast<const float*>(t.leaf_box), t.nodes, t.refit_flag);
+  } else if (refit_variant == 0)
     launch(k_refit<false, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
            t.leaf_info, t.refit_flag);

@@ -32,7 +32,14 @@ struct Bvh {
   bool built;            // a hierarchy exists and can be refitted
   uint64_t* keys_alt;    // [n]
   uint32_t* vals_alt;    // [n]
+  int2* range;           // [n-1] leaf range [lo, hi] of each internal node
+  int32_t* tl_root;      // [n] roots of the treelets (subtrees of <= kTreelet leaves under a larger parent)
+  int32_t* up_start;     // [n] starts of the refit's upper climb: a treelet root (>= 0) or a leaf ~l
+  int32_t* tl_count;     // [2] number of treelet roots, number of upper starts
 };
+
+// leaves per treelet of the two-phase refit (one warp per treelet)
+constexpr int kTreelet = 32;
 
 enum PrimKind { kVertex = 0, kEdge = 1, kTri = 2 };
 
@@ -56,7 +63,8 @@ __host__ __device__ __forceinline__ uint64_t pair_key(int type, uint32_t i, uint
 // Build the tree over primitives of `kind` from positions x4 (padded), optionally swept
 // by dx4 (CCD); `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
 // refit_variant: 0 = arrival counters behind full device fences, 1 = release-acquire
-// arrival counters (same result)
+// arrival counters, 2 = treelets of <= 32 leaves refitted by one warp each in shared memory,
+// then release-acquire counters above them (all give the same boxes)
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant);
 

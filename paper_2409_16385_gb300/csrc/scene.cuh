@@ -82,7 +82,7 @@ struct eipc_scene {
   struct {
     int eval_threads = 128, eval_bps = 16, eval_variant = 2;
     int query_threads = 128, query_bps = 24;
-    int refit_variant = 1;
+    int refit_variant = 2;
   } tune;                // launch shapes of the tunable kernels (eipc_set_launch)
   int contact_refits;    // refits since the last full rebuild
   eipc::DevStatus* status;

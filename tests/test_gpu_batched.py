@@ -201,7 +201,7 @@ def test_launch_shape_does_not_change_results():
     b = _batch()
     outs = []
     for shape in [None, ("eval_barrier", 64, 8, 3), ("eval_barrier", 128, 2, 2), ("bvh_query", 256, 4, 2),
-                  ("bvh_query", 64, 32, 2), ("bvh_refit", 256, 8, 0)]:
+                  ("bvh_query", 64, 32, 2), ("bvh_refit", 256, 8, 0), ("bvh_refit", 256, 8, 1)]:
         cs = _contact_scene(b, (b.body, b.n_scenes))
         if shape is not None:
             cs.set_launch(*shape)
