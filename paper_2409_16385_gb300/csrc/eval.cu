@@ -268,6 +268,11 @@ struct EvalArgs {
   int64_t* queue;          // next unclaimed position of `order` (work queue)
   const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
   double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
+  // Presorted records (energy/gradient/Hessian evaluation): the keys were written and
+  // sorted before the evaluation, and record r goes to its sorted position hinv[r] (ginv[r])
+  // without a key.  Null: record r is written at r with its key (Hessian-vector products).
+  const uint32_t* hinv;
+  const uint32_t* ginv;
 };
 
 // Eigen-decomposition of the symmetric 5x5 K: an FP32 Jacobi pre-diagonalisation of K/|K|,
@@ -342,21 +347,36 @@ __device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
 // the first node is the larger one
 __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32_t Iu, int32_t Iv,
                                            const double B[3][3]) {
-  double* p = A.hrec + 9 * pos;
-  if (Iu <= Iv) {
-    A.hkeys[pos] = (uint64_t)Iu * (uint64_t)A.ns + (uint64_t)Iv;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) p[3 * a + b] = B[a][b];
+  const bool swap = Iu > Iv;
+  int64_t dst = pos;
+  if (A.hinv) {
+    dst = A.hinv[pos];
   } else {
-    A.hkeys[pos] = (uint64_t)Iv * (uint64_t)A.ns + (uint64_t)Iu;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) p[3 * a + b] = B[b][a];
+    A.hkeys[pos] = swap ? (uint64_t)Iv * (uint64_t)A.ns + (uint64_t)Iu : (uint64_t)Iu * (uint64_t)A.ns + (uint64_t)Iv;
+    A.hvals[pos] = (uint32_t)pos;
   }
-  A.hvals[pos] = (uint32_t)pos;
+  double v[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) v[3 * a + b] = swap ? B[b][a] : B[a][b];
+  double2* p = reinterpret_cast<double2*>(A.hrec + kHRecStride * dst);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) p[c] = make_double2(v[2 * c], v[2 * c + 1]);
+  A.hrec[kHRecStride * dst + 8] = v[8];
+}
+
+// one gradient record (presorted or keyed, as emit_upper)
+__device__ __forceinline__ void emit_grad(const EvalArgs& A, int64_t pos, uint64_t key, double y0, double y1, double y2) {
+  int64_t dst = pos;
+  if (A.ginv) {
+    dst = A.ginv[pos];
+  } else {
+    A.gkeys[pos] = key;
+    A.gvals[pos] = (uint32_t)pos;
+  }
+  *reinterpret_cast<double2*>(A.grec + kGRecStride * dst) = make_double2(y0, y1);
+  A.grec[kGRecStride * dst + 2] = y2;
 }
 
 // The barrier Hessian of one active pair in its span (Sec. III-B, Eq. 7; the 12 x 12
@@ -684,9 +704,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
     const int64_t pos = og + u;
     if (pos < A.gcap) {
       const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
-      A.gkeys[pos] = (uint64_t)nodes[u];
-      A.gvals[pos] = (uint32_t)pos;
-      A.grec[3 * pos] = s * rh.x; A.grec[3 * pos + 1] = s * rh.y; A.grec[3 * pos + 2] = s * rh.z;
+      emit_grad(A, pos, (uint64_t)nodes[u], s * rh.x, s * rh.y, s * rh.z);
     }
   }
   // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
@@ -796,9 +814,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
       const int64_t pos = og + a;
       if (pos < A.gcap) {
         const double s = ml * f1y * nw[a][0];
-        A.gkeys[pos] = (uint64_t)nodes[a];
-        A.gvals[pos] = (uint32_t)pos;
-        A.grec[3 * pos] = s * u.x; A.grec[3 * pos + 1] = s * u.y; A.grec[3 * pos + 2] = s * u.z;
+        emit_grad(A, pos, (uint64_t)nodes[a], s * u.x, s * u.y, s * u.z);
       }
       for (int b = a; b < n; ++b, ++pos2) {
         if (pos2 >= A.rec_cap) continue;
@@ -864,9 +880,7 @@ __device__ __forceinline__ V3 load_dir(const double* __restrict__ v, int32_t nod
 
 __device__ __forceinline__ void emit_g(const EvalArgs& A, int64_t pos, uint64_t key, V3 y) {
   if (pos >= A.gcap) return;
-  A.gkeys[pos] = key;
-  A.gvals[pos] = (uint32_t)pos;
-  A.grec[3 * pos] = y.x; A.grec[3 * pos + 1] = y.y; A.grec[3 * pos + 2] = y.z;
+  emit_grad(A, pos, key, y.x, y.y, y.z);
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
@@ -1126,40 +1140,13 @@ __device__ __forceinline__ void warp_tree_sum(double acc[W]) {
     for (int c = 0; c < W; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], o);
 }
 
-// upper-triangle blocks: segment s -> (ukey[s], ublk[s])
-__global__ void __launch_bounds__(kBlock) k_seg_sum_h(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                                      const double* __restrict__ rec, const int64_t* __restrict__ start,
-                                                      const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
-                                                      uint64_t* __restrict__ ukey, double* __restrict__ ublk) {
-  const int64_t R = clamp_count(n_rec, cap);
-  const int64_t S = *n_seg;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
-    const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
-    double acc[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) acc[c] = 0.0;
-    for (int64_t r = b + lane; r < e; r += 32) {
-      const double* p = rec + 9 * (int64_t)vals[r];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) acc[c] += p[c];
-    }
-    warp_tree_sum<9>(acc);
-    if (lane == 0) {
-      ukey[s] = keys[b];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) ublk[9 * s + c] = acc[c];
-    }
-  }
-}
-
 // every upper block (I, J) becomes the full-pattern entry (I, J) and, off the diagonal,
 // the transposed entry (J, I); diagonal blocks get a sentinel twin that sorts last
 __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restrict__ ukey, const int64_t* n_seg,
                                                          int64_t ns, uint64_t sentinel, int64_t cap,
                                                          uint64_t* __restrict__ fkey, uint32_t* __restrict__ fval,
-                                                         int64_t* n_full_sort, int64_t* n_diag, DevStatus* st) {
+                                                         int64_t* n_full_sort, int64_t* n_diag, DevStatus* st,
+                                                         int32_t* __restrict__ dst) {
   const int64_t S0 = *n_seg;
   const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1177,41 +1164,8 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restr
     } else {
       fkey[2 * s + 1] = sentinel;
       fval[2 * s + 1] = 0;
+      dst[2 * s + 1] = -1;
       atomicAdd(reinterpret_cast<unsigned long long*>(n_diag), 1ull);
-    }
-  }
-}
-
-// sorted full entries -> BSR columns and values, row counts
-__global__ void __launch_bounds__(kBlock) k_emit_bsr(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
-                                                     const double* __restrict__ ublk, const int64_t* n_full_sort,
-                                                     const int64_t* n_diag, int64_t ns, eipc_bsr H,
-                                                     int64_t* __restrict__ row_count, DevStatus* st) {
-  const int64_t nnzb = *n_full_sort - *n_diag;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *H.nnzb = nnzb;
-    if (nnzb > H.capacity) {
-      raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
-      raise_need(st, &st->need_bsr, nnzb);
-    }
-  }
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzb; e += grid_stride()) {
-    const uint64_t key = fkey[e];
-    const int64_t row = (int64_t)(key / (uint64_t)ns), col = (int64_t)(key % (uint64_t)ns);
-    atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
-    if (e < H.capacity) {
-      const uint32_t v = fval[e];
-      const double* b = ublk + 9 * (int64_t)(v >> 1);
-      H.col[e] = (int32_t)col;
-      if (v & 1u) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) H.val[9 * e + 3 * a + c] = b[3 * c + a];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) H.val[9 * e + c] = b[c];
-      }
     }
   }
 }
@@ -1228,7 +1182,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict
     const int64_t b = start[s], e = (s + 1 < S) ? start[s + 1] : R;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t r = b + lane; r < e; r += 32) {
-      const double* p = rec + 3 * (int64_t)vals[r];
+      const double* p = rec + kGRecStride * (int64_t)vals[r];
 #pragma unroll
       for (int c = 0; c < 3; ++c) acc[c] += p[c];
     }
@@ -1238,6 +1192,255 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict
 #pragma unroll
       for (int c = 0; c < 3; ++c) g[3 * node + c] = acc[c];
     }
+  }
+}
+
+// ---- presorted reduction: the record keys of the energy/gradient/Hessian evaluation
+// depend only on each item's cage nodes, so they are written, sorted and turned into the
+// BSR pattern before the evaluation; the evaluation then writes every record straight to
+// its sorted position and the sums read contiguous records.
+
+// keys of item k's records in the order the evaluation emits them: gradient record u
+// (node I_u), Hessian record (u, v), u <= v (nodes (min, max)).  One warp per item, lanes
+// on consecutive records.
+__global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__ item_nodes,
+                                                     const int32_t* __restrict__ item_n, const int64_t* __restrict__ ro_h,
+                                                     const int64_t* __restrict__ ro_g, const int64_t* n_items,
+                                                     int64_t rec_cap, int64_t gcap, int64_t ns,
+                                                     uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hvals,
+                                                     uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gvals) {
+  const int64_t nit = *n_items;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nit; k += nw) {
+    const int n = item_n[k];
+    const int32_t* nodes = item_nodes + kMaxNodes * k;
+    const int64_t og = ro_g[k], oh = ro_h[k];
+    if (lane < n && og + lane < gcap) {
+      gkeys[og + lane] = (uint64_t)nodes[lane];
+      gvals[og + lane] = (uint32_t)(og + lane);
+    }
+    const int nrec = n * (n + 1) / 2;
+    for (int l = lane; l < nrec; l += 32) {
+      // row u of the upper triangle holds n - u records
+      int u = 0, before = 0;
+      while (before + (n - u) <= l) { before += n - u; ++u; }
+      const int w2 = u + (l - before);
+      const int64_t pos = oh + l;
+      if (pos >= rec_cap) continue;
+      const uint64_t Iu = (uint64_t)nodes[u], Iv = (uint64_t)nodes[w2];
+      hkeys[pos] = Iu <= Iv ? Iu * (uint64_t)ns + Iv : Iv * (uint64_t)ns + Iu;
+      hvals[pos] = (uint32_t)pos;
+    }
+  }
+}
+
+// inverse of the sort permutation: record perm[p] sits at sorted position p
+__global__ void __launch_bounds__(kBlock) k_inverse(const uint32_t* __restrict__ perm, const int64_t* n_dev, int64_t cap,
+                                                    uint32_t* __restrict__ inv) {
+  const int64_t n = clamp_count(n_dev, cap);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += grid_stride()) inv[perm[p]] = (uint32_t)p;
+}
+
+// key of each segment
+__global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict__ keys, const int64_t* __restrict__ start,
+                                                     const int64_t* n_seg, uint64_t* __restrict__ ukey) {
+  const int64_t S = *n_seg;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) ukey[s] = keys[start[s]];
+}
+
+// sorted full entries -> BSR columns, row counts, and for each upper segment s the BSR
+// entry of its block (dst[2s]) and of its transpose (dst[2s+1]; -1 on the diagonal or
+// beyond the capacity)
+__global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
+                                                        const int64_t* n_full_sort, const int64_t* n_diag, int64_t ns,
+                                                        eipc_bsr H, int64_t* __restrict__ row_count,
+                                                        int32_t* __restrict__ dst, DevStatus* st) {
+  const int64_t nnzb = *n_full_sort - *n_diag;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *H.nnzb = nnzb;
+    if (nnzb > H.capacity) {
+      raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
+      raise_need(st, &st->need_bsr, nnzb);
+    }
+  }
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzb; e += grid_stride()) {
+    const uint64_t key = fkey[e];
+    const int64_t row = (int64_t)(key / (uint64_t)ns);
+    atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
+    const uint32_t v = fval[e];
+    dst[2 * (int64_t)(v >> 1) + (v & 1u)] = e < H.capacity ? (int32_t)e : -1;
+    if (e < H.capacity) H.col[e] = (int32_t)(key % (uint64_t)ns);
+  }
+}
+
+// Segment sums over contiguous presorted records in two passes.  Each segment is cut into
+// units of kSegChunk consecutive records counted from its own first record; pass 1 adds
+// each unit's records in order (one thread per unit, every lane doing useful FP64 adds,
+// no shuffle tree), pass 2 adds a segment's unit sums in order (one thread per segment).
+// The grouping depends only on the segment's own records, so a scene's sums are the same
+// bits whether it is evaluated alone or inside a batch, and a long segment is spread over
+// many threads.
+constexpr int kSegChunk = 32;
+
+// units per segment: unit[s] = ceil(len_s / kSegChunk) (exclusive-scanned afterwards)
+__global__ void __launch_bounds__(kBlock) k_seg_units(const int64_t* __restrict__ start, const int64_t* n_rec,
+                                                      const int64_t* n_seg, int64_t cap, int64_t* __restrict__ unit) {
+  const int64_t R = clamp_count(n_rec, cap);
+  const int64_t S = *n_seg;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
+    const int64_t len = ((s + 1 < S) ? start[s + 1] : R) - start[s];
+    unit[s] = (len + kSegChunk - 1) / kSegChunk;
+  }
+}
+
+// the segment owning unit u: largest s with unit[s] <= u (unit exclusive-scanned, S >= 1)
+__device__ __forceinline__ int64_t segment_of_unit(const int64_t* __restrict__ unit, int64_t S, int64_t u) {
+  int64_t lo = 0, hi = S - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (unit[mid] <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// row r of a record array with rows of W values at a 16-byte aligned stride P, loaded
+// two values at a time
+template <int W, int P>
+__device__ __forceinline__ void load_row(const double* __restrict__ x, int64_t r, double v[W]) {
+  const double2* p = reinterpret_cast<const double2*>(x + P * r);
+#pragma unroll
+  for (int c = 0; c + 1 < W; c += 2) {
+    const double2 t = __ldg(p + c / 2);
+    v[c] = t.x;
+    v[c + 1] = t.y;
+  }
+  if (W & 1) v[W - 1] = __ldg(x + P * r + W - 1);
+}
+
+// acc += x[r] for r = b, b+1, ..., e-1 in that order; the loads of four consecutive rows
+// are issued before their adds so that a thread has several loads in flight
+template <int W, int P>
+__device__ __forceinline__ void add_in_order(const double* __restrict__ x, int64_t b, int64_t e, double acc[W]) {
+  int64_t r = b;
+  for (; r + 4 <= e; r += 4) {
+    double v[4][W];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) load_row<W, P>(x, r + q, v[q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < W; ++c) acc[c] += v[q][c];
+  }
+  for (; r < e; ++r) {
+    double v[W];
+    load_row<W, P>(x, r, v);
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] += v[c];
+  }
+}
+
+template <int W, int P>
+__global__ void __launch_bounds__(kBlock) k_seg_pieces(const double* __restrict__ rec, const int64_t* __restrict__ start,
+                                                       const int64_t* __restrict__ unit, const int64_t* n_units,
+                                                       const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
+                                                       double* __restrict__ piece) {
+  const int64_t R = clamp_count(n_rec, cap);
+  const int64_t S = *n_seg;
+  const int64_t U = *n_units;
+  if (S <= 0) return;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < U; u += grid_stride()) {
+    const int64_t s = segment_of_unit(unit, S, u);
+    const int64_t end = (s + 1 < S) ? start[s + 1] : R;
+    const int64_t b = start[s] + (u - unit[s]) * kSegChunk;
+    const int64_t e = (b + kSegChunk < end) ? b + kSegChunk : end;
+    double acc[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) acc[c] = 0.0;
+    add_in_order<W, P>(rec, b, e, acc);
+    double* p = piece + W * u;
+#pragma unroll
+    for (int c = 0; c < W; ++c) p[c] = acc[c];
+  }
+}
+
+// Sum over the 32 lanes of a warp of the L-vectors a (L a power of two <= 16) by
+// reduce-scatter: at each step the lanes pair up across one lane bit, each keeps half of
+// the vector and adds its partner's copy of that half; when one entry is left, plain
+// butterfly adds finish.  8 + 4 + 2 + 1 + 1 adds for L = 16 instead of 5 L.  Returns
+// the full sum of component (lane >> (5 - log2 L)); the order of the adds is fixed.
+template <int L>
+__device__ __forceinline__ double warp_reduce_scatter(double (&a)[L], int lane) {
+  int o = 16;
+#pragma unroll
+  for (int len = L; len > 1; len >>= 1, o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < len / 2; ++i) {
+      const double send = hi ? a[i] : a[i + len / 2];
+      const double keep = hi ? a[i + len / 2] : a[i];
+      a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double v = a[0];
+#pragma unroll
+  for (; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Hessian pass 2, one warp per segment: lane l adds unit sums l, l+32, ... of its segment
+// in order, then warp_reduce_scatter; the block goes into the BSR values at dst[2s] and,
+// transposed, at dst[2s+1]
+__global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __restrict__ piece,
+                                                             const int64_t* __restrict__ unit, const int64_t* n_units,
+                                                             const int64_t* n_seg, int64_t cap,
+                                                             const int32_t* __restrict__ dst, eipc_bsr H) {
+  const int64_t S0 = *n_seg;
+  const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;      // the segments k_full_entries kept
+  const int64_t U = *n_units;
+  const int64_t nnzb = *H.nnzb;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+    const int64_t u1 = (s + 1 < S0) ? unit[s + 1] : U;
+    double acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = 0.0;
+    for (int64_t k = unit[s] + lane; k < u1; k += 32) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc[c] += __ldg(piece + 9 * k + c);
+    }
+    const double v = warp_reduce_scatter<16>(acc, lane);
+    const int c = lane >> 1;
+    if ((lane & 1) == 0 && c < 9) {
+      const int32_t du = dst[2 * s], dl = dst[2 * s + 1];
+      if (du >= 0 && du < nnzb) H.val[9 * (int64_t)du + c] = v;
+      if (dl >= 0 && dl < nnzb) H.val[9 * (int64_t)dl + 3 * (c % 3) + c / 3] = v;
+    }
+  }
+}
+
+// gradient pass 2, one warp per segment (node), as the Hessian's
+__global__ void __launch_bounds__(kBlock) k_seg_sum_g_pieces(const uint64_t* __restrict__ keys,
+                                                             const double* __restrict__ piece,
+                                                             const int64_t* __restrict__ start,
+                                                             const int64_t* __restrict__ unit, const int64_t* n_units,
+                                                             const int64_t* n_seg, double* __restrict__ g) {
+  const int64_t S = *n_seg;
+  const int64_t U = *n_units;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
+    const int64_t u1 = (s + 1 < S) ? unit[s + 1] : U;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t k = unit[s] + lane; k < u1; k += 32) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[c] += __ldg(piece + 3 * k + c);
+    }
+    const double v = warp_reduce_scatter<4>(acc, lane);
+    const int c = lane >> 3;
+    if ((lane & 7) == 0 && c < 3) g[3 * (int64_t)keys[start[s]] + c] = v;
   }
 }
 
@@ -1361,16 +1564,82 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   exclusive_scan_i64(sc->rc_g, sc->ro_g, cnt + kCntItems, item_cap, tot_g, sc->scan_partial, s);
   launch(k_rec_check, 1, 32, 0, s, tot_h, tot_g, sc->rec_cap, sc->gcap, cnt + kCntRecH, cnt + kCntRecG, sc->status);
   sc->timers->stop(kKItems, s);
+
+  // Hessian pattern before the evaluation: record keys (I, J) from the items' cage nodes,
+  // stable sort, segments (one per BSR upper block), the inverse permutation that sends
+  // each record to its sorted position, then the full symmetric pattern (every
+  // off-diagonal upper block also at (J, I)), columns and row pointers
+  sc->timers->start(kKHReduce, s);
+  launch(k_rec_keys, blocks_for(32 * item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(sc->item_nodes),
+         static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(sc->ro_h),
+         static_cast<const int64_t*>(sc->ro_g), static_cast<const int64_t*>(cnt + kCntItems), sc->rec_cap, sc->gcap,
+         sc->ns, sc->hkeys, sc->hvals, sc->gkeys, sc->gvals);
+  const int wh = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, cnt + kCntRecH, sc->rec_cap,
+                                sc->bits_h, sc->sort_hist, s);
+  const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
+  const uint32_t* hv = wh ? sc->hvals_alt : sc->hvals;
+  launch(k_seg_flags, blocks_for(sc->rec_cap), kBlock, 0, s, hk, cnt + kCntRecH, sc->rec_cap, sc->seg_flag);
+  exclusive_scan_i64(sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap, cnt + kCntSegH, sc->scan_partial, s);
+  launch(k_seg_starts, blocks_for(sc->rec_cap), kBlock, 0, s, sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap,
+                                                           sc->seg_start);
+  launch(k_inverse, blocks_for(sc->rec_cap), kBlock, 0, s, hv, static_cast<const int64_t*>(cnt + kCntRecH), sc->rec_cap,
+         sc->hinv);
+  launch(k_seg_units, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const int64_t*>(sc->seg_start),
+         static_cast<const int64_t*>(cnt + kCntRecH), static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->hunit);
+  exclusive_scan_i64(sc->hunit, sc->hunit, cnt + kCntSegH, sc->rec_cap, cnt + kCntUnitsH, sc->scan_partial, s);
+  // seg_flag and seg_id are free after k_seg_starts: they hold the segment keys and the
+  // segments' BSR entries
+  uint64_t* ukey = reinterpret_cast<uint64_t*>(sc->seg_flag);
+  int32_t* dst = reinterpret_cast<int32_t*>(sc->seg_id);
+  launch(k_seg_keys, blocks_for(sc->rec_cap), kBlock, 0, s, hk, static_cast<const int64_t*>(sc->seg_start),
+         static_cast<const int64_t*>(cnt + kCntSegH), ukey);
+  int64_t* n_full = cnt + 13;
+  int64_t* n_diag = cnt + 14;
+  cudaMemsetAsync(n_diag, 0, sizeof(int64_t), s);
+  const uint64_t sentinel = (1ull << sc->bits_h) - 1;
+  launch(k_full_entries, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const uint64_t*>(ukey),
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->ns, sentinel, sc->rec_cap, sc->hkeys, sc->hvals, n_full, n_diag,
+         sc->status, dst);
+  const int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_full, sc->rec_cap, sc->bits_h,
+                                sc->sort_hist, s);
+  const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
+  const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
+  cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
+  launch(k_bsr_pattern, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const int64_t*>(n_full),
+         static_cast<const int64_t*>(n_diag), sc->ns, H, sc->row_count, dst, sc->status);
+  int64_t* nrow = cnt + 11;
+  launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
+  exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);
+  launch(k_rowptr, blocks_for(sc->ns + 1), kBlock, 0, s, sc->row_count, sc->ns, H.row_ptr);
+  sc->timers->stop(kKHReduce, s);
+  // gradient segments (one per node)
+  sc->timers->start(kKGReduce, s);
+  const int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap,
+                                sc->bits_g, sc->sort_hist, s);
+  const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
+  const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
+  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
+  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
+  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
+                                                        sc->gseg_start);
+  launch(k_inverse, blocks_for(sc->gcap), kBlock, 0, s, gv, static_cast<const int64_t*>(cnt + kCntRecG), sc->gcap,
+         sc->ginv);
+  launch(k_seg_units, blocks_for(sc->gcap), kBlock, 0, s, static_cast<const int64_t*>(sc->gseg_start),
+         static_cast<const int64_t*>(cnt + kCntRecG), static_cast<const int64_t*>(cnt + kCntSegG), sc->gcap, sc->gunit);
+  exclusive_scan_i64(sc->gunit, sc->gunit, cnt + kCntSegG, sc->gcap, cnt + kCntUnitsG, sc->scan_partial, s);
+  sc->timers->stop(kKGReduce, s);
+
   EvalArgs A;
   A.T = sc->topo; A.pr = pr; A.cage_idx = sc->cage_idx; A.w = sc->w; A.x4 = sc->x4; A.ns = sc->ns;
   A.dhat = p.dhat; A.kappa = p.kappa; A.item_nodes = sc->item_nodes; A.item_n = sc->item_n;
   A.ro_h = sc->ro_h; A.ro_g = sc->ro_g; A.n_items = cnt + kCntItems; A.rec_cap = sc->rec_cap; A.gcap = sc->gcap;
-  A.hkeys = sc->hkeys; A.hvals = sc->hvals; A.hrec = sc->hrec; A.gkeys = sc->gkeys; A.gvals = sc->gvals;
+  A.hkeys = nullptr; A.hvals = nullptr; A.hrec = sc->hrec; A.gkeys = nullptr; A.gvals = nullptr;
   A.grec = sc->grec; A.item_E = sc->item_E; A.st = sc->status;
   A.project = (p.flags & EIPC_PARAM_NO_PROJECTION) == 0;
   A.moll_r2 = sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr;
   A.moll_factor = sc->moll_factor;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
+  A.hinv = sc->hinv; A.ginv = sc->ginv;
   {
     // (node count, type) schedule; the pair-sort buffers are free once the pairs are built
     launch(k_eval_order_keys, blocks_for(item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(pr.type),
@@ -1394,53 +1663,25 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
     EIPC_TIMED(sc, kKEvalFriction, s,
                (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
                                                                                                     p.eps_v * p.h)));
-  // Hessian: stable sort by (I, J), segmented sum, row pointers
+  // sums over the contiguous presorted records, in sorted order
   sc->timers->start(kKHReduce, s);
-  int wh = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, cnt + kCntRecH, sc->rec_cap, sc->bits_h,
-                          sc->sort_hist, s);
-  const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
-  const uint32_t* hv = wh ? sc->hvals_alt : sc->hvals;
-  launch(k_seg_flags, blocks_for(sc->rec_cap), kBlock, 0, s, hk, cnt + kCntRecH, sc->rec_cap, sc->seg_flag);
-  exclusive_scan_i64(sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap, cnt + kCntSegH, sc->scan_partial, s);
-  launch(k_seg_starts, blocks_for(sc->rec_cap), kBlock, 0, s, sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap,
-                                                           sc->seg_start);
-  // upper blocks; seg_flag is free again after k_seg_starts and holds their keys
-  uint64_t* ukey = reinterpret_cast<uint64_t*>(sc->seg_flag);
-  launch(k_seg_sum_h, blocks_for(sc->rec_cap, 16), kBlock, 0, s, hk, hv, sc->hrec, sc->seg_start, cnt + kCntRecH,
-         cnt + kCntSegH, sc->rec_cap, ukey, sc->ublk);
-  // full symmetric pattern: each off-diagonal upper block also lands transposed at (J, I)
-  int64_t* n_full = cnt + 13;
-  int64_t* n_diag = cnt + 14;
-  cudaMemsetAsync(n_diag, 0, sizeof(int64_t), s);
-  const uint64_t sentinel = (1ull << sc->bits_h) - 1;
-  launch(k_full_entries, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const uint64_t*>(ukey),
-         static_cast<const int64_t*>(cnt + kCntSegH), sc->ns, sentinel, sc->rec_cap, sc->hkeys, sc->hvals, n_full, n_diag,
-         sc->status);
-  int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_full, sc->rec_cap, sc->bits_h,
-                          sc->sort_hist, s);
-  const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
-  const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
-  cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
-  launch(k_emit_bsr, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const double*>(sc->ublk),
-         static_cast<const int64_t*>(n_full), static_cast<const int64_t*>(n_diag), sc->ns, H, sc->row_count, sc->status);
-  int64_t* nrow = cnt + 11;
-  launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
-  exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);
-  launch(k_rowptr, blocks_for(sc->ns + 1), kBlock, 0, s, sc->row_count, sc->ns, H.row_ptr);
+  launch(k_seg_pieces<9, kHRecStride>, blocks_for(sc->rec_cap / kSegChunk + 1, 8), kBlock, 0, s, static_cast<const double*>(sc->hrec),
+         static_cast<const int64_t*>(sc->seg_start), static_cast<const int64_t*>(sc->hunit),
+         static_cast<const int64_t*>(cnt + kCntUnitsH), static_cast<const int64_t*>(cnt + kCntRecH),
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->piece);
+  launch(k_seg_sum_h_pieces, blocks_for(32 * sc->rec_cap, 8), kBlock, 0, s, static_cast<const double*>(sc->piece),
+         static_cast<const int64_t*>(sc->hunit), static_cast<const int64_t*>(cnt + kCntUnitsH),
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, static_cast<const int32_t*>(dst), H);
   sc->timers->stop(kKHReduce, s);
-  // gradient
   sc->timers->start(kKGReduce, s);
-  int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap, sc->bits_g,
-                          sc->sort_hist, s);
-  const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
-  const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
-  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
-  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
-  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
-                                                        sc->gseg_start);
   cudaMemsetAsync(g_r, 0, sizeof(double) * 3 * sc->ns, s);
-  launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG, cnt + kCntSegG,
-                                                       sc->gcap, g_r);
+  launch(k_seg_pieces<3, kGRecStride>, blocks_for(sc->gcap / kSegChunk + 1, 8), kBlock, 0, s, static_cast<const double*>(sc->grec),
+         static_cast<const int64_t*>(sc->gseg_start), static_cast<const int64_t*>(sc->gunit),
+         static_cast<const int64_t*>(cnt + kCntUnitsG), static_cast<const int64_t*>(cnt + kCntRecG),
+         static_cast<const int64_t*>(cnt + kCntSegG), sc->gcap, sc->piece);
+  launch(k_seg_sum_g_pieces, blocks_for(32 * sc->gcap, 8), kBlock, 0, s, gk, static_cast<const double*>(sc->piece),
+         static_cast<const int64_t*>(sc->gseg_start), static_cast<const int64_t*>(sc->gunit),
+         static_cast<const int64_t*>(cnt + kCntUnitsG), static_cast<const int64_t*>(cnt + kCntSegG), g_r);
   sc->timers->stop(kKGReduce, s);
   // energy
   sc->timers->start(kKEnergy, s);
@@ -1481,6 +1722,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.queue = nullptr;
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
+  A.hinv = nullptr; A.ginv = nullptr;
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (launch(k_hvp_barrier, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
   if (A.moll_r2)

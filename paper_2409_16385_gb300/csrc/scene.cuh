@@ -54,8 +54,7 @@ struct eipc_scene {
   uint64_t* hkeys_alt;
   uint32_t* hvals;
   uint32_t* hvals_alt;
-  double* hrec;          // [rec_cap*9]
-  double* ublk;          // [rec_cap*9] reduced upper-triangle blocks
+  double* hrec;          // [rec_cap*kHRecStride] 3x3 blocks, 16-byte aligned rows
   double* hvp_out;       // [(ns+64)*3] Hessian-vector product: reduced rows, then 64 kinematic partials
   uint64_t* edge_key;    // [ne] sorted a * nv + b of every edge (a < b), for edge-id lookup
   int32_t* edge_id;      // [ne] edge id of each sorted key
@@ -65,12 +64,17 @@ struct eipc_scene {
   int64_t* seg_flag;     // [rec_cap]
   int64_t* seg_id;       // [rec_cap]
   int64_t* seg_start;    // [rec_cap]
+  uint32_t* hinv;        // [rec_cap] sorted position of each Hessian record
+  uint32_t* ginv;        // [gcap] sorted position of each gradient record
+  double* piece;         // [9 * (rec_cap + rec_cap / 32 + 2)] partial segment sums (Hessian, then gradient)
+  int64_t* hunit;        // [rec_cap + 1] first summation unit of each Hessian segment
+  int64_t* gunit;        // [gcap + 1] ... of each gradient segment
   int64_t gcap;          // gradient records
   uint64_t* gkeys;
   uint64_t* gkeys_alt;
   uint32_t* gvals;
   uint32_t* gvals_alt;
-  double* grec;          // [gcap*3]
+  double* grec;          // [gcap*kGRecStride] 3-vectors, 16-byte aligned rows
   int64_t* gseg_flag;
   int64_t* gseg_id;
   int64_t* gseg_start;
@@ -91,8 +95,12 @@ struct eipc_scene {
 
 namespace eipc {
 // device counters
+// record row strides (doubles): 9 (3) values padded so that each row starts on 16 bytes
+constexpr int kHRecStride = 10, kGRecStride = 4;
+
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
-       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntDedup = 17, kCntN = 24 };
+       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntDedup = 17, kCntUnitsH = 18, kCntUnitsG = 19,
+       kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \
   do {                                    \

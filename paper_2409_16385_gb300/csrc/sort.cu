@@ -38,27 +38,45 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restric
   for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * kSortBlocks + blockIdx.x] = h[d];
 }
 
-// One warp per digit: exclusive prefix of that digit's counts over the blocks (in place)
-// and the digit's total, stored after the 256 * kSortBlocks counters.
+// One block per digit: exclusive prefix of that digit's counts over the blocks (in place)
+// and the digit's total, stored after the 256 * kSortBlocks counters.  Thread t owns the
+// consecutive counters [t * per, (t + 1) * per); a block scan of the threads' sums gives
+// each its starting offset.
 __global__ void __launch_bounds__(256) k_hist_digits(uint32_t* hist) {
-  const int lane = threadIdx.x & 31;
-  const int d = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (d >= 256) return;
-  uint32_t* row = hist + (size_t)d * kSortBlocks;
-  uint32_t run = 0;
-  for (int b0 = 0; b0 < kSortBlocks; b0 += 32) {
-    const int b = b0 + lane;
-    const uint32_t c = b < kSortBlocks ? row[b] : 0u;
-    uint32_t x = c;
+  constexpr int per = (kSortBlocks + 255) / 256;
+  __shared__ uint32_t wsum[8];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  uint32_t* row = hist + (size_t)blockIdx.x * kSortBlocks;
+  uint32_t c[per];
+  uint32_t mine = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (b < kSortBlocks) row[b] = run + x - c;
-    run += __shfl_sync(0xffffffffu, x, 31);
+  for (int k = 0; k < per; ++k) {
+    const int b = t * per + k;
+    c[k] = b < kSortBlocks ? row[b] : 0u;
+    mine += c[k];
   }
-  if (lane == 0) hist[256 * kSortBlocks + d] = run;
+  uint32_t x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) {
+    before += w < warp ? wsum[w] : 0u;
+    all += wsum[w];
+  }
+  uint32_t run = before + x - mine;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const int b = t * per + k;
+    if (b < kSortBlocks) row[b] = run;
+    run += c[k];
+  }
+  if (t == 0) hist[256 * kSortBlocks + blockIdx.x] = all;
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __restrict__ kin,
@@ -225,7 +243,7 @@ int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t*
     uint64_t* ko = which ? keys : keys_alt;
     uint32_t* vo = which ? vals : vals_alt;
     launch(k_hist, kSortBlocks, kSortThreads, 0, s, ki, n, cap, shift, hist);
-    launch(k_hist_digits, 32, 256, 0, s, hist);
+    launch(k_hist_digits, 256, 256, 0, s, hist);
     launch(k_scatter, kSortBlocks, kSortThreads, 0, s, ki, vi, ko, vo, n, cap, shift, hist);
     which ^= 1;
   }

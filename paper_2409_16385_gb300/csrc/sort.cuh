@@ -6,7 +6,7 @@
 
 namespace eipc {
 
-constexpr int kSortBlocks = 304;   // 2 per SM; each block owns one contiguous chunk
+constexpr int kSortBlocks = 1216;  // 8 per SM; each block owns one contiguous chunk
 constexpr int kSortThreads = 256;  // 8 warps, one element per thread per tile
 
 // Scratch: 256 * kSortBlocks digit counters followed by 256 digit totals.
