@@ -384,6 +384,7 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         ev_ms += ev0.elapsed_time(ev1)
     stage["eval_pairs_per_s"] = n_p / (ev_ms / 1e3)
+    work = cs.work_counts()          # the last iterate's contact build and evaluation
     ac_ms = 0.0; n_c = 0
     for k in range(K):
         t = (t0 + k) % n_it
@@ -398,6 +399,8 @@ def run_ours(args, ws, rank, local):
         n_c += int(ncand.item())
     stage["ccd_queries_per_s"] = n_c / (ac_ms / 1e3)
     stage["ccd_queries_per_s_in_step"] = total_cand / total_s
+    wc = cs.work_counts()
+    work["ccd_candidates"], work["ccd_advanced"] = wc["candidates"], wc["ccd_advanced"]
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -424,7 +427,8 @@ def run_ours(args, ws, rank, local):
                             triangles=sc.F, vertices=sc.Nv, edges=sc.E, cage_nodes=sc.Ns,
                             dhat=sc.params["dhat"], mu=sc.params["mu"], parallelism=f"replicas x{ws}",
                             l2="flushed between steps (256 MiB rewrite)",
-                            pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K),
+                            pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K,
+                            work_last_iterate=work),
                 clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
                 ccd_queries_per_s=total_cand_all / total_s_all, stages=stage,
                 e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()},

@@ -212,6 +212,21 @@ eipc_status eipc_scene_set_kinematic(eipc_scene* scene, const double* x_kin, eip
 eipc_status eipc_status_read(eipc_scene* scene, eipc_stream stream, int32_t* flags, int64_t* needed,
                              int64_t* accd_iters);
 
+/* Work counts of the scene's last calls, for sizing capacities and reading where the time
+ * goes.  Synchronises the stream and copies n (<= EIPC_WORK_COUNTS) int64 entries to the
+ * HOST array out:
+ *   out[0] broad-phase candidates of the last eipc_build_candidates or eipc_accd_toi call;
+ *   out[1] candidates the FP32 screen of the last eipc_build_candidates passed on to the
+ *          exact FP64 test;
+ *   out[2] contact pairs it kept (before deduplication);
+ *   out[3] items of the last evaluation (contact pairs + friction pairs);
+ *   out[4] its Hessian block records, out[5] its gradient records;
+ *   out[6] distinct upper-triangle Hessian blocks, out[7] distinct gradient nodes;
+ *   out[8] CCD candidates the last eipc_accd_toi advanced.
+ * Values beyond a buffer's capacity are clamped as the kernels clamp them. */
+enum { EIPC_WORK_COUNTS = 9 };
+eipc_status eipc_work_counts(eipc_scene* scene, eipc_stream stream, int64_t* out, int32_t n);
+
 /* Tracing: per-kernel CUDA-event timers.  Bit k of mask enables timer k (0 embed,
  * 1 bvh_build, 2 bvh_query, 3 narrow_phase, 4 pair_sort, 5 friction_lag, 6 stencil_nodes,
  * 7 eval_barrier, 8 eval_friction, 9 hessian_reduce, 10 gradient_reduce, 11 energy_sum,

@@ -25,7 +25,8 @@ EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_
            "eipc_eval_contact", "eipc_accd_toi", "eipc_status_read", "eipc_version", "eipc_timing_enable",
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
            "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
-           "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier", "eipc_bsr_spmv"]
+           "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier", "eipc_bsr_spmv",
+           "eipc_work_counts"]
 
 
 class Params(ctypes.Structure):
@@ -81,6 +82,8 @@ def load(build_if_missing: bool = True):
     L.eipc_accd_toi.restype = i32
     L.eipc_status_read.argtypes = [P, P, ctypes.POINTER(i32), P, P]
     L.eipc_status_read.restype = i32
+    L.eipc_work_counts.argtypes = [P, P, P, i32]
+    L.eipc_work_counts.restype = i32
     L.eipc_version.restype = ctypes.c_char_p
     L.eipc_timing_enable.argtypes = [P, ctypes.c_uint32]
     L.eipc_timing_enable.restype = i32
@@ -400,6 +403,16 @@ class ContactScene:
                "eipc_status_read")
         names = [n for b, n in FLAGS.items() if flags.value & b]
         return dict(flags=int(flags.value), names=names, needed=need.tolist(), accd_iters=int(it[0]))
+
+    def work_counts(self) -> dict:
+        """Work counts of the last calls (eipc_work_counts), by name."""
+        out = np.zeros(len(WORK_COUNTS), np.int64)
+        _check(self.lib.eipc_work_counts(self.handle, _stream(), out.ctypes.data, len(WORK_COUNTS)), "eipc_work_counts")
+        return dict(zip(WORK_COUNTS, out.tolist()))
+
+
+WORK_COUNTS = ("candidates", "screened", "pairs", "items", "hessian_records", "gradient_records", "hessian_blocks",
+               "gradient_nodes", "ccd_advanced")
 
 
 def bsr_spmv(row_ptr, col, val, x, out=None, alpha: float = 1.0, beta: float = 0.0):

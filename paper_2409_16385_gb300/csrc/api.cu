@@ -337,6 +337,18 @@ eipc_status eipc_status_read(eipc_scene* sc, eipc_stream stream, int32_t* flags,
   return EIPC_OK;
 }
 
+eipc_status eipc_work_counts(eipc_scene* sc, eipc_stream stream, int64_t* out, int32_t n) {
+  if (!sc || n < 0 || n > EIPC_WORK_COUNTS || (n > 0 && !out)) return EIPC_ERR_INVALID;
+  int64_t c[kCntN];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(c, sc->counters, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess) return EIPC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return EIPC_ERR_CUDA;
+  const int64_t v[EIPC_WORK_COUNTS] = {c[kCntCand], c[kCntScreened], c[kCntSurv], c[kCntItems], c[kCntRecH],
+                                       c[kCntRecG],  c[kCntSegH],     c[kCntSegG], c[kCntAccd]};
+  for (int32_t k = 0; k < n; ++k) out[k] = v[k];
+  return EIPC_OK;
+}
+
 eipc_status eipc_timing_enable(eipc_scene* sc, uint32_t mask) {
   if (!sc) return EIPC_ERR_INVALID;
   if (mask) sc->timers->create();

@@ -147,9 +147,10 @@ __device__ __forceinline__ double ee_distance(V3 a0, V3 a1, V3 b0, V3 b1, Stenci
 // region can only (a) report a lower bound (plane / line distance when the projection is
 // wrongly found inside), or (b) report a boundary value whose excess is bounded by the
 // curvature times the squared parameter error.  Stencils whose parameter solve is not
-// well conditioned (|n|^2 <= 0.1 |e1|^2 |e2|^2: skinny triangles, edges within 18 degrees
-// of parallel) are never screened.  Every pair not screened goes through the exact FP64
-// test, so the kept set is unchanged.
+// well conditioned (|n|^2 <= 0.1 |e1|^2 |e2|^2) are screened by a bound that needs no
+// parameter solve: edges within 18 degrees of parallel by their segment-to-line distances
+// (seg_line_far_f32); skinny triangles not at all.  Every pair not screened goes through
+// the exact FP64 test, so the kept set is unchanged.
 struct F3 {
   float x, y, z;
 };
@@ -188,12 +189,42 @@ __device__ __forceinline__ bool pt_far_f32(F3 p, F3 t0, F3 t1, F3 t2, float r2m)
   return d2 > r2m;
 }
 
+// Segment-to-line lower bound for near-parallel edges: with U = (segment start - line
+// point) x e_line and V = e_seg x e_line, the squared distance from the point at parameter
+// s of the segment to the line is |U + s V|^2 / L (L = |e_line|^2).  Its minimum over
+// s in [0, 1] is |U|^2 (U.V >= 0), |U + V|^2 (U.V <= -|V|^2), else |U x V|^2 / |V|^2
+// (Lagrange's identity, free of the cancellation in |U|^2 - (U.V)^2 / |V|^2).  A case
+// chosen wrongly through rounding of U.V overestimates by at most (err U.V)^2 / |V|^2,
+// of order eps^2 |U|^2: negligible against the margin.  The segments' distance is at least
+// this (the other segment lies on the line), so "far" here proves the pair far.  The
+// interior case needs |V|^2 > 1e-12 |e_seg|^2 L (edges not parallel to within 1e-6 rad),
+// else nothing is proven.
+__device__ __forceinline__ bool seg_line_far_f32(F3 U, F3 V, float Lseg, float L, float r2m) {
+  const float uv = fdot(U, V), vv = fdot(V, V);
+  float g;
+  if (uv >= 0.f) {
+    g = fdot(U, U);
+  } else if (uv <= -vv) {
+    const F3 W = {U.x + V.x, U.y + V.y, U.z + V.z};
+    g = fdot(W, W);
+  } else {
+    if (!(vv > 1e-12f * Lseg * L)) return false;
+    const F3 X = fcross(U, V);
+    g = fdot(X, X) / vv;
+  }
+  return g > r2m * L;
+}
+
 __device__ __forceinline__ bool ee_far_f32(F3 a0, F3 a1, F3 b0, F3 b1, float r2m) {
   const F3 ea = a1 - a0, eb = b1 - b0, w = a0 - b0;
   const float A = fdot(ea, ea), C = fdot(eb, eb);
   const F3 n = fcross(ea, eb);
   const float nn = fdot(n, n);
-  if (!(nn > 0.1f * A * C)) return false;
+  if (!(nn > 0.1f * A * C)) {
+    // near-parallel: segment a against line b, segment b against line a
+    const F3 wb = b0 - a0;
+    return seg_line_far_f32(fcross(w, eb), n, A, C, r2m) || seg_line_far_f32(fcross(wb, ea), n * -1.f, C, A, r2m);
+  }
   const float B = fdot(ea, eb), D = fdot(ea, w), E = fdot(eb, w);
   const float s = (B * E - C * D) / nn, t = (A * E - B * D) / nn;
   float d2;

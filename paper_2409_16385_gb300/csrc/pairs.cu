@@ -116,6 +116,9 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
                                                    int64_t* n_surv, DevStatus* st) {
   const int64_t n = clamp_count(n_cand, cand_cap);
   const int lane = threadIdx.x & 31;
+  // d2 at or above this has sqrt(d2) > dhat: rejected without the square root, the rest
+  // take the test 0 < sqrt(d2) < dhat as it stands
+  const double d2_reject = dhat * dhat * (1.0 + 1e-12);
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
     const int64_t k = base + threadIdx.x;
     bool keep = false;
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
       const double d2 = stencil_d2(T, x4, type, i, j);
       if (!(d2 > 0.0)) {
         raise_flag(st, EIPC_FLAG_PENETRATION);
-      } else {
+      } else if (d2 < d2_reject) {
         d = sqrt(d2);
         keep = d < dhat;
       }
@@ -324,7 +327,7 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   EIPC_TIMED(sc, kKQuery, s,
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
-  int64_t* n_cand2 = sc->counters + 15;
+  int64_t* n_cand2 = sc->counters + kCntScreened;
   cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
   sc->timers->start(kKNarrow, s);
   launch(k_screen, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, static_cast<const float*>(sc->x4f),

@@ -99,7 +99,8 @@ namespace eipc {
 constexpr int kHRecStride = 10, kGRecStride = 4;
 
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
-       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntDedup = 17, kCntUnitsH = 18, kCntUnitsG = 19,
+       kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntScreened = 15, kCntDedup = 17, kCntUnitsH = 18,
+       kCntUnitsG = 19,
        kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \

@@ -197,3 +197,39 @@ def test_refitted_and_rebuilt_hierarchies_agree_bitwise():
                      E.cpu().numpy().tobytes(), g.cpu().numpy().tobytes(), h["val"].tobytes()))
         assert cs.status()["flags"] == 0
     assert outs[0] == outs[1]
+
+
+def test_work_counts_match_the_outputs():
+    """eipc_work_counts: pairs and items as returned, records recomputed from the stencils'
+    cage nodes, and block counts as the BSR pattern shows them."""
+    sc = _scene(2, True)
+    cs = _cs(sc)
+    t = 9
+    q, qn = _t(sc.iterate(t)), _t(sc.iterate(sc.lag_of(t)))
+    lag = cs.friction_lag(qn, cs.build_candidates(qn, out=cs.new_pairs()))
+    pr = cs.build_candidates(q)
+    wc_pairs = cs.work_counts()
+    E, g, H = cs.eval_contact(q, pr, lag)
+    wc = cs.work_counts()
+    ph, lh, hh = pr.host(), lag.host(), H.host()
+    P, L = len(ph["type"]), len(lh["lam"])
+    assert wc_pairs["pairs"] == P and wc["pairs"] == P
+    assert wc_pairs["candidates"] >= wc_pairs["screened"] >= P > 0
+    assert wc["items"] == P + L
+    ci = sc.cage_idx
+
+    def nodes(vs):
+        out = []
+        for v in vs:
+            if ci[v, 0] >= 0:
+                out += [n for n in ci[v] if n not in out]
+        return len(out)
+
+    ns = [nodes([i, *sc.tris[j]] if ty == 0 else [*sc.edges[i], *sc.edges[j]])
+          for ty, i, j in zip(ph["type"], ph["i"], ph["j"])] + [nodes(v) for v in lh["v"]]
+    assert wc["hessian_records"] == sum(n * (n + 1) // 2 for n in ns)
+    assert wc["gradient_records"] == sum(ns)
+    rows = np.repeat(np.arange(sc.Ns), np.diff(hh["row_ptr"]))
+    n_diag = int(np.sum(rows == hh["col"]))
+    assert len(hh["col"]) == 2 * wc["hessian_blocks"] - n_diag
+    assert wc["gradient_nodes"] == n_diag
