@@ -184,29 +184,35 @@ __device__ __forceinline__ int32_t arrive(int32_t* f) {
 
 // leaf boxes in leaf order, for refitting an existing hierarchy; the leaf's vertex ids
 // come from its leaf record (coalesced) rather than the primitive tables
+// FP32 box (rounded outward) of one leaf from its leaf record's vertex ids, over [x, x + dx]
+// when dx4 is given
+__device__ __forceinline__ void leaf_box_of(int4 li, const double* __restrict__ x4, const double* __restrict__ dx4,
+                                            float lo[3], float hi[3]) {
+  const int32_t v[3] = {li.x, li.y, li.z};
+  double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int a = 0; a < 3; ++a) {
+    if (v[a] < 0) continue;
+    const V3 p = load_x(x4, v[a]);
+    const double c[3] = {p.x, p.y, p.z};
+    for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
+    if (dx4) {
+      const V3 d = load_x(dx4, v[a]);
+      const double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
+      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = __double2float_rd(dlo[k]);
+    hi[k] = __double2float_ru(dhi[k]);
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_leaf_boxes(int64_t n, const int4* __restrict__ leaf_info,
                                                        const double* __restrict__ x4, const double* __restrict__ dx4,
                                                        float* __restrict__ leaf_box) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
-    const int4 li = leaf_info[l];
-    const int32_t v[3] = {li.x, li.y, li.z};
-    double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int a = 0; a < 3; ++a) {
-      if (v[a] < 0) continue;
-      const V3 p = load_x(x4, v[a]);
-      const double c[3] = {p.x, p.y, p.z};
-      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
-      if (dx4) {
-        const V3 d = load_x(dx4, v[a]);
-        const double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
-        for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
-      }
-    }
     float lo[3], hi[3];
-    for (int k = 0; k < 3; ++k) {
-      lo[k] = __double2float_rd(dlo[k]);
-      hi[k] = __double2float_ru(dhi[k]);
-    }
+    leaf_box_of(leaf_info[l], x4, dx4, lo, hi);
     float2* o = reinterpret_cast<float2*>(leaf_box + 6 * l);
     o[0] = make_float2(lo[0], lo[1]);
     o[1] = make_float2(lo[2], hi[0]);
@@ -302,40 +308,66 @@ __global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2*
 
 constexpr int kTreeletWarps = kBlock / 32;
 
-__global__ void __launch_bounds__(kBlock) k_treelet_refit(int64_t n, const int32_t* __restrict__ tl_root,
-                                                          const int32_t* __restrict__ count, const int2* __restrict__ range,
-                                                          const int32_t* __restrict__ parent, const float* __restrict__ leaf_box,
-                                                          BvhNode* __restrict__ nodes) {
+// What the two-phase refit needs of one tree; n <= 1 marks an absent tree.
+struct RefitView {
+  int64_t n;
+  const int32_t* tl_root;
+  const int32_t* up_start;
+  const int32_t* count;      // [2]: treelet roots, upper starts
+  const int2* range;
+  const int32_t* parent;
+  const int4* leaf_info;
+  BvhNode* nodes;
+  int32_t* flag;
+};
+
+__host__ __device__ __forceinline__ RefitView refit_view(const Bvh& t) {
+  return RefitView{t.n, t.tl_root, t.up_start, t.tl_count, t.range, t.parent, t.leaf_info, t.nodes, t.refit_flag};
+}
+
+// Phase A of the refit of up to two trees in one launch: one warp per treelet, lane l
+// computing leaf l's box from the positions and climbing in shared memory.  The grid also
+// clears both trees' arrival counters for phase B.
+__global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView B, const double* __restrict__ x4,
+                                                          const double* __restrict__ dx4) {
   __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
   __shared__ int scnt[kTreeletWarps][kTreelet];
   __shared__ int spar[kTreeletWarps][kTreelet];
   __shared__ int sc0[kTreeletWarps][kTreelet];
+  const int nA = A.n > 1 ? (int)A.n : 0, nB = B.n > 1 ? (int)B.n : 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nA + nB; i += grid_stride()) {
+    if (i < nA) A.flag[i] = 0;
+    else B.flag[i - nA] = 0;
+  }
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ntl = count[0];
-  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntl; w += nw) {
-    const int32_t root = tl_root[w];
-    const int2 rg = range[root];
+  const int64_t ntA = nA ? A.count[0] : 0, ntB = nB ? B.count[0] : 0;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < ntA + ntB; w += nw) {
+    const bool inA = w < ntA;
+    const RefitView T = inA ? A : B;
+    const int64_t n = T.n;
+    const int32_t root = T.tl_root[inA ? w : w - ntA];
+    const int2 rg = T.range[root];
     const int lo = rg.x, m = rg.y - rg.x + 1;           // m <= kTreelet leaves, m - 1 internal nodes
     // node links of the indices lo .. hi (the treelet's internal nodes are among them)
     if (lane < m && lo + lane < n - 1) {
-      spar[wib][lane] = parent[lo + lane];
-      sc0[wib][lane] = nodes[lo + lane].c0;
+      spar[wib][lane] = T.parent[lo + lane];
+      sc0[wib][lane] = T.nodes[lo + lane].c0;
     }
     scnt[wib][lane] = 0;
     __syncwarp();
     if (lane < m) {
       const int32_t l = lo + lane;
       float b[6];
-      for (int k = 0; k < 6; ++k) b[k] = leaf_box[6 * (int64_t)l + k];
+      leaf_box_of(T.leaf_info[l], x4, dx4, b, b + 3);
       int32_t child = ~l;
-      int32_t node = parent[n - 1 + l];
+      int32_t node = T.parent[n - 1 + l];
       for (int step = 0; step < kTreelet; ++step) {  // a treelet is at most kTreelet - 1 deep
         const int off = node - lo;
         if (off < 0 || off >= m) break;              // (a subtree's nodes lie in its leaf range)
         const int slot = (sc0[wib][off] == child) ? 0 : 1;
-        float* dl = slot ? nodes[node].lo1 : nodes[node].lo0;
-        float* dh = slot ? nodes[node].hi1 : nodes[node].hi0;
+        float* dl = slot ? T.nodes[node].lo1 : T.nodes[node].lo0;
+        float* dh = slot ? T.nodes[node].hi1 : T.nodes[node].hi0;
         for (int k = 0; k < 3; ++k) { __stcg(&dl[k], b[k]); __stcg(&dh[k], b[3 + k]); }
         for (int k = 0; k < 6; ++k) sbox[wib][off][slot][k] = b[k];
         __threadfence_block();
@@ -354,43 +386,48 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(int64_t n, const int32
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_upper_refit(int64_t n, const int32_t* __restrict__ up_start,
-                                                        const int32_t* __restrict__ count, const int32_t* __restrict__ parent,
-                                                        const float* __restrict__ leaf_box, BvhNode* nodes, int32_t* flag) {
-  const int64_t nu = count[1];
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nu; k += grid_stride()) {
-    const int32_t st = up_start[k];
+// Phase B for up to two trees: one thread per upper start (a treelet root, or a leaf
+// directly under a larger node, its box from the positions) climbs with release-acquire
+// arrival counters; the two trees' climbs run side by side.
+__global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B, const double* __restrict__ x4,
+                                                        const double* __restrict__ dx4) {
+  const int64_t nuA = A.n > 1 ? A.count[1] : 0, nuB = B.n > 1 ? B.count[1] : 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nuA + nuB; k += grid_stride()) {
+    const bool inA = k < nuA;
+    const RefitView T = inA ? A : B;
+    const int64_t n = T.n;
+    const int32_t st = T.up_start[inA ? k : k - nuA];
     float lo[3], hi[3];
     int32_t child, node;
     if (st >= 0) {                                   // a treelet root: its box from its children
-      const BvhNode* nd = &nodes[st];
+      const BvhNode* nd = &T.nodes[st];
       for (int q = 0; q < 3; ++q) {
         lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
         hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
       }
       if (st == 0) continue;                         // the whole tree was one treelet
       child = st;
-      node = parent[st];
+      node = T.parent[st];
     } else {                                         // a leaf under a larger node
       const int32_t l = ~st;
-      for (int q = 0; q < 3; ++q) { lo[q] = leaf_box[6 * (int64_t)l + q]; hi[q] = leaf_box[6 * (int64_t)l + 3 + q]; }
+      leaf_box_of(T.leaf_info[l], x4, dx4, lo, hi);
       child = st;
-      node = parent[n - 1 + l];
+      node = T.parent[n - 1 + l];
     }
     for (int64_t step = 0; step < n; ++step) {       // a root path has at most n-1 nodes
-      const int slot = (nodes[node].c0 == child) ? 0 : 1;
-      float* dl = slot ? nodes[node].lo1 : nodes[node].lo0;
-      float* dh = slot ? nodes[node].hi1 : nodes[node].hi0;
+      const int slot = (T.nodes[node].c0 == child) ? 0 : 1;
+      float* dl = slot ? T.nodes[node].lo1 : T.nodes[node].lo0;
+      float* dh = slot ? T.nodes[node].hi1 : T.nodes[node].hi0;
       for (int q = 0; q < 3; ++q) { __stcg(&dl[q], lo[q]); __stcg(&dh[q], hi[q]); }
-      if (arrive<false>(&flag[node]) == 0) break;
-      const BvhNode* nd = &nodes[node];
+      if (arrive<false>(&T.flag[node]) == 0) break;
+      const BvhNode* nd = &T.nodes[node];
       for (int q = 0; q < 3; ++q) {
         lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
         hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
       }
       if (node == 0) break;
       child = node;
-      node = parent[node];
+      node = T.parent[node];
     }
   }
 }
@@ -533,19 +570,35 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
   launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, static_cast<const double*>(nullptr), topo.nv, bounds_ws);
 }
 
+// both phases of the treelet refit for one or two trees (b may be null)
+static void treelet_refit(Bvh& a, Bvh* b, const double* x4, const double* dx4, cudaStream_t s) {
+  RefitView A = refit_view(a);
+  RefitView Bv = b ? refit_view(*b) : RefitView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const int64_t n = a.n + (b ? b->n : 0);
+  launch(k_treelet_refit, blocks_for(n, 8), kBlock, 0, s, A, Bv, x4, dx4);
+  launch(k_upper_refit, blocks_for(n), kBlock, 0, s, A, Bv, x4, dx4);
+}
+
+void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const double* x4, const double* dx4,
+                    cudaStream_t s, int refit_variant) {
+  if (refit_variant == 2 && a.n > 1 && b.n > 1) {
+    treelet_refit(a, &b, x4, dx4, s);
+    return;
+  }
+  bvh_refit(a, ka, topo, x4, dx4, s, refit_variant);
+  bvh_refit(b, kb, topo, x4, dx4, s, refit_variant);
+}
+
 void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
                int refit_variant) {
   if (t.n <= 0) return;
+  if (refit_variant == 2 && t.n > 1) {
+    treelet_refit(t, nullptr, x4, dx4, s);
+    return;
+  }
   launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int4*>(t.leaf_info), x4, dx4, t.leaf_box);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
-  if (refit_variant == 2 && t.n > 1) {
-    launch(k_treelet_refit, blocks_for(t.n, 8), kBlock, 0, s, t.n, static_cast<const int32_t*>(t.tl_root),
-           static_cast<const int32_t*>(t.tl_count), static_cast<const int2*>(t.range),
-           static_cast<const int32_t*>(t.parent), static_cast<const float*>(t.leaf_box), t.nodes);
-    launch(k_upper_refit, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int32_t*>(t.up_start),
-           static_cast<const int32_t*>(t.tl_count), static_cast<const int32_t*>(t.parent),
-           static_cast<const float*>(t.leaf_box), t.nodes, t.refit_flag);
-  } else if (refit_variant == 0)
+  if (refit_variant == 0)
     launch(k_refit<false, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
            t.leaf_info, t.refit_flag);

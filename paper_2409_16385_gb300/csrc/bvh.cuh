@@ -77,6 +77,14 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
 void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
                int refit_variant);
 
+// Refit of two hierarchies (the triangle and edge trees) at once: with the treelet refit
+// both trees share two launches, so their latency-bound climbs overlap.  The boxes are
+// those of two bvh_refit calls.  With the treelet refit, the leaf boxes are computed inside
+// the refit and leaf_box is not updated (only single-leaf trees and the other refits read
+// it).
+void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const double* x4, const double* dx4,
+                    cudaStream_t s, int refit_variant);
+
 // Traverse both trees in one launch: every vertex box (grown by `pad`, or swept by dx4)
 // against the triangle tree -> PT candidates, every edge box against the edge tree -> EE
 // candidates with j > i.  Incident pairs and all-kinematic pairs are skipped; candidates

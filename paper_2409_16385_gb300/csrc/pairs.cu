@@ -319,8 +319,7 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   } else {
     sc->timers->start(kKBvh, s);
     scene_bounds(sc->topo, sc->x4, sc->bounds_ws, s);    // the narrow-phase screen reads it
-    bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
-    bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
+    bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
     sc->timers->stop(kKBvh, s);
     ++sc->contact_refits;
   }
