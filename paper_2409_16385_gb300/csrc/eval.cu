@@ -124,6 +124,32 @@ __device__ __forceinline__ void node_weights(const int32_t v[4], const int32_t* 
   }
 }
 
+// One Jacobi rotation J (c, s = t c in rows/columns p, q) of the symmetric A held in full,
+// A <- J^T A J, and V <- V J.  The entries outside rows and columns p, q are unchanged; the
+// (p, q) block takes the closed form of the rotation that zeroes a_pq (a_pp - t a_pq,
+// a_qq + t a_pq, 0), so each pair of mirrored entries is computed once.
+template <class T, int N>
+__device__ __forceinline__ void rotate_sym(T A[N][N], T V[N][N], int p, int q, T c, T s, T t, T apq) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k == p || k == q) continue;
+    const T akp = A[k][p], akq = A[k][q];
+    const T np = c * akp - s * akq, nq = s * akp + c * akq;
+    A[k][p] = np; A[p][k] = np;
+    A[k][q] = nq; A[q][k] = nq;
+  }
+  A[p][p] -= t * apq;
+  A[q][q] += t * apq;
+  A[p][q] = T(0);
+  A[q][p] = T(0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const T vkp = V[k][p], vkq = V[k][q];
+    V[k][p] = c * vkp - s * vkq;
+    V[k][q] = s * vkp + c * vkq;
+  }
+}
+
 // Fixed number of cyclic Jacobi sweeps in FP32 (62x the FP64 rate on this part): a cheap
 // approximate eigenbasis V of the symmetric matrix A (scaled to unit norm beforehand).
 template <int N>
@@ -145,24 +171,7 @@ __device__ __forceinline__ void jacobi_f32(float A[N][N], float V[N][N], int swe
           t = theta < 0.f ? -t : t;
           const float c = 1.f / sqrtf(t * t + 1.f);
           const float s = t * c;
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const float akp = A[k][p], akq = A[k][q];
-            A[k][p] = c * akp - s * akq;
-            A[k][q] = s * akp + c * akq;
-          }
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const float apk = A[p][k], aqk = A[q][k];
-            A[p][k] = c * apk - s * aqk;
-            A[q][k] = s * apk + c * aqk;
-          }
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const float vkp = V[k][p], vkq = V[k][q];
-            V[k][p] = c * vkp - s * vkq;
-            V[k][q] = s * vkp + c * vkq;
-          }
+          rotate_sym<float, N>(A, V, p, q, c, s, t, apq);
         }
       }
     }
@@ -215,24 +224,7 @@ __device__ __forceinline__ void jacobi(double A[N][N], double V[N][N], bool seed
             c = rsqrt(t * t + 1.0);
           }
           const double s = t * c;
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const double akp = A[k][p], akq = A[k][q];
-            A[k][p] = c * akp - s * akq;
-            A[k][q] = s * akp + c * akq;
-          }
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const double apk = A[p][k], aqk = A[q][k];
-            A[p][k] = c * apk - s * aqk;
-            A[q][k] = s * apk + c * aqk;
-          }
-#pragma unroll
-          for (int k = 0; k < N; ++k) {
-            const double vkp = V[k][p], vkq = V[k][q];
-            V[k][p] = c * vkp - s * vkq;
-            V[k][q] = s * vkp + c * vkq;
-          }
+          rotate_sym<double, N>(A, V, p, q, c, s, t, apq);
         }
       }
     }
