@@ -135,14 +135,14 @@ def measured_peaks():
 
 # Algorithmic work per unit:
 #   eval_barrier  FP64 flops per contact pair, counted by ncu on the bubble-grasp workload
-#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 399.3e6 / 115,583)
+#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 373.2e6 / 115,583)
 #   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-FP64_FLOPS_PER_PAIR = 3455.0
+FP64_FLOPS_PER_PAIR = 3229.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
-# (eval_barrier at the autotuned launch shape: 49.1 MB + 241.8 MB for 115,583 pairs)
-NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 2517.0}
+# (eval_barrier at the autotuned launch shape: 117.4 MB + 224.5 MB for 115,583 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 2958.0}
 
 
 def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
