@@ -315,7 +315,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     warm = cs.timing_read()
     dominant = max(warm.items(), key=lambda kv: kv[1][0])[0] if warm else "eval_barrier"
-    cs.timing_enable([dominant])
+    # the dominant kernel's launches, and the FP64 evaluation's when it is not the dominant one
+    timed = [dominant] + (["eval_barrier"] if dominant != "eval_barrier" else [])
+    cs.timing_enable(timed)
     st = cs.status()
     if st["flags"] & ~64:
         raise RuntimeError(f"device status after warm-up: {st}")
@@ -367,6 +369,7 @@ def run_ours(args, ws, rank, local):
     # ---- roofline of the dominant kernel, from its live event timer
     dom_ms, dom_n = kt.get(dominant, (0.0, 0))
     roof = roofline_figure(dominant, dom_ms, dom_n, K, total_pairs / K, total_cand / K, sc)
+    roofs = {k: roofline_figure(k, *kt.get(k, (0.0, 0)), K, total_pairs / K, total_cand / K, sc) for k in timed}
 
     # ---- stage-only throughputs (same iterates, pairs precomputed)
     stage = {}
@@ -429,7 +432,7 @@ def run_ours(args, ws, rank, local):
                             l2="flushed between steps (256 MiB rewrite)",
                             pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K,
                             work_last_iterate=work),
-                clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof,
+                clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof, rooflines=roofs,
                 ccd_queries_per_s=total_cand_all / total_s_all, stages=stage,
                 e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()},
                 autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"])

@@ -124,6 +124,27 @@ __device__ __forceinline__ void node_weights(const int32_t v[4], const int32_t* 
   }
 }
 
+// node_weights for one coefficient set: out[u] = sum over (a, slot) with idx == node_u of
+// coef[a] * w[a][slot]
+__device__ __forceinline__ void node_weights1(const int32_t v[4], const int32_t* __restrict__ cage_idx,
+                                              const double* __restrict__ w, const int32_t* nodes, int n,
+                                              const double coef[4], double out[kMaxNodes]) {
+  for (int u = 0; u < n; ++u) out[u] = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    const int4 id = __ldg(reinterpret_cast<const int4*>(cage_idx) + v[a]);
+    if (id.x < 0) continue;
+    const int ids[4] = {id.x, id.y, id.z, id.w};
+    const double2 w01 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a]);
+    const double2 w23 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a] + 1);
+    const double ws[4] = {w01.x, w01.y, w23.x, w23.y};
+    for (int s = 0; s < 4; ++s) {
+      int u = 0;
+      while (u < n - 1 && nodes[u] != ids[s]) ++u;
+      out[u] += coef[a] * ws[s];
+    }
+  }
+}
+
 // One Jacobi rotation J (c, s = t c in rows/columns p, q) of the symmetric A held in full,
 // A <- J^T A J, and V <- V J.  The entries outside rows and columns p, q are unchanged; the
 // (p, q) block takes the closed form of the rotation that zeroes a_pq (a_pp - t a_pq,
@@ -772,48 +793,57 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
     vs = vs - anc;
     const V3 u = vs - nrm * dot(nrm, vs);
     const double y2 = dot(u, u);
-    double f0, f1y, f1p_minus;   // f0(y), f1(y)/y, f1'(y) - f1(y)/y
+    // f0(y), f1(y)/y and (f1'(y) - f1(y)/y) / y^2, with one division for 1/eps (or 1/y)
+    // and one for 1/y^2
+    double f0, f1y, c2;
     if (y2 == 0.0) {
-      f0 = eps / 3.0; f1y = 2.0 / eps; f1p_minus = 0.0;
+      f0 = eps / 3.0; f1y = 2.0 / eps; c2 = 0.0;
     } else {
       const double y = sqrt(y2);
+      double f1p_minus;
       if (y < eps) {
-        f0 = -y2 * y / (3.0 * eps * eps) + y2 / eps + eps / 3.0;
-        f1y = 2.0 / eps - y / (eps * eps);
-        f1p_minus = -y / (eps * eps);   // (2/eps - 2y/eps^2) - (2/eps - y/eps^2)
+        const double ie = 1.0 / eps, yie2 = y * ie * ie;
+        f0 = y2 * (ie - yie2 / 3.0) + eps / 3.0;    // -y^3 / (3 eps^2) + y^2 / eps + eps / 3
+        f1y = 2.0 * ie - yie2;
+        f1p_minus = -yie2;                          // (2/eps - 2y/eps^2) - (2/eps - y/eps^2)
       } else {
-        f0 = y; f1y = 1.0 / y; f1p_minus = -1.0 / y;
+        const double iy = 1.0 / y;
+        f0 = y; f1y = iy; f1p_minus = -iy;
       }
+      c2 = f1p_minus / y2;
     }
     A.item_E[k] = ml * f0;
     const double uu[3] = {u.x, u.y, u.z};
     const double nn[3] = {nrm.x, nrm.y, nrm.z};
+    // F = ml (f1(y)/y (I - n n^T) + (f1'(y) - f1(y)/y) u u^T / y^2), symmetric
     double F[3][3];
     for (int p = 0; p < 3; ++p)
-      for (int q = 0; q < 3; ++q) {
-        double s = f1y * ((p == q ? 1.0 : 0.0) - nn[p] * nn[q]);
-        if (y2 > 0.0) s += f1p_minus * uu[p] * uu[q] / y2;
-        F[p][q] = ml * s;
+      for (int q = p; q < 3; ++q) {
+        const double s = ml * (f1y * ((p == q ? 1.0 : 0.0) - nn[p] * nn[q]) + c2 * uu[p] * uu[q]);
+        F[p][q] = s;
+        F[q][p] = s;
       }
     const int n = A.item_n[k];
     const int32_t* nodes = A.item_nodes + kMaxNodes * k;
-    const double coef[3][4] = {{gam[0], gam[1], gam[2], gam[3]}, {0, 0, 0, 0}, {0, 0, 0, 0}};
-    double nw[kMaxNodes][3];
-    node_weights(v, A.cage_idx, A.w, nodes, n, coef, 1, nw);
+    double nw[kMaxNodes];
+    node_weights1(v, A.cage_idx, A.w, nodes, n, gam, nw);
     const int64_t oh = A.ro_h[k], og = A.ro_g[k];
     int64_t pos2 = oh;
     for (int a = 0; a < n; ++a) {
       const int64_t pos = og + a;
       if (pos < A.gcap) {
-        const double s = ml * f1y * nw[a][0];
+        const double s = ml * f1y * nw[a];
         emit_grad(A, pos, (uint64_t)nodes[a], s * u.x, s * u.y, s * u.z);
       }
       for (int b = a; b < n; ++b, ++pos2) {
         if (pos2 >= A.rec_cap) continue;
         double B[3][3];
-        const double ww = nw[a][0] * nw[b][0];
+        const double ww = nw[a] * nw[b];
         for (int p = 0; p < 3; ++p)
-          for (int q = 0; q < 3; ++q) B[p][q] = ww * F[p][q];
+          for (int q = p; q < 3; ++q) {
+            B[p][q] = ww * F[p][q];
+            B[q][p] = B[p][q];
+          }
         emit_upper(A, pos2, nodes[a], nodes[b], B);
       }
     }
