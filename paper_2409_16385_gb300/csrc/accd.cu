@@ -96,13 +96,36 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
         adv = true;
         V3 mean = (D[0] + D[1] + D[2] + D[3]) * 0.25;
         V3 R[4];
-        double la = 0.0, lb = 0.0;
-        for (int a = 0; a < 4; ++a) {
-          R[a] = D[a] - mean;
-          const double sp = sqrt(dot(R[a], R[a]));
-          if (a < na) la = fmax(la, sp); else lb = fmax(lb, sp);
+        for (int a = 0; a < 4; ++a) R[a] = D[a] - mean;
+        // FP32 shortcut: the first advancement reaches t = 1 exactly when d0 >= L / (1 - s).
+        // An upward-rounded bound L_hi >= L and a conservative FP32 far test proving
+        // d0 > L_hi / (1 - s) give that result without the FP64 distance.  The far radius
+        // carries twice the FP32 tests' distance error budget, 40 M 2^-24 (M: the candidate's
+        // largest coordinate), as an absolute margin, so it holds for any motion size.
+        bool far = false;
+        {
+          float la_f = 0.f, lb_f = 0.f, Mf = 0.f;
+          F3 Xf[4];
+          for (int a = 0; a < 4; ++a) {
+            const float sp = __fsqrt_ru(__double2float_ru(dot(R[a], R[a])));
+            if (a < na) la_f = fmaxf(la_f, sp); else lb_f = fmaxf(lb_f, sp);
+            Xf[a] = F3{(float)X[a].x, (float)X[a].y, (float)X[a].z};
+            Mf = fmaxf(Mf, fmaxf(fabsf(Xf[a].x), fmaxf(fabsf(Xf[a].y), fabsf(Xf[a].z))));
+          }
+          const float err = 80.f * Mf * 5.9604645e-8f;
+          const float r = __fadd_ru(__fmul_ru(__fdiv_ru(__fadd_ru(la_f, lb_f), __double2float_rd(1.0 - s)), 1.000001f),
+                                    err);
+          const float r2m = r * r * 1.004f;
+          far = type == 0 ? pt_far_f32(Xf[0], Xf[1], Xf[2], Xf[3], r2m) : ee_far_f32(Xf[0], Xf[1], Xf[2], Xf[3], r2m);
         }
-        const double L = la + lb;
+        double la = 0.0, lb = 0.0;
+        if (!far) {
+          for (int a = 0; a < 4; ++a) {
+            const double sp = sqrt(dot(R[a], R[a]));
+            if (a < na) la = fmax(la, sp); else lb = fmax(lb, sp);
+          }
+        }
+        const double L = la + lb;              // 0 when proven far: t stays 1
         double t = 1.0;
         if (L > 0.0) {
           const double d0 = pair_distance(type, X);
