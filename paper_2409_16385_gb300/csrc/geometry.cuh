@@ -26,11 +26,16 @@ struct Stencil {
   double d2;
 };
 
-// |p - (e0 + t (e1 - e0))|^2 over t in [0,1]
+// |p - (e0 + t (e1 - e0))|^2 over t in [0,1].  t = clamp((w.e) / (e.e), 0, 1), with the
+// division taken only inside (0, 1): w.e <= 0 gives 0 and w.e >= e.e gives 1, the values the
+// correctly rounded quotient clamps to (also for e = 0 and NaN).
 __device__ __forceinline__ double seg_point_d2(V3 p, V3 e0, V3 e1, double* t_out) {
   V3 e = e1 - e0, w = p - e0;
-  double t = dot(w, e) / dot(e, e);
-  t = fmin(fmax(t, 0.0), 1.0);
+  const double we = dot(w, e), ee = dot(e, e);
+  double t;
+  if (!(we > 0.0)) t = 0.0;
+  else if (we >= ee) t = 1.0;
+  else t = we / ee;
   V3 r = w - e * t;
   *t_out = t;
   return dot(r, r);
