@@ -33,7 +33,7 @@ void free_scene(eipc_scene* s) {
                   s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
                   s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
                   s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start, s->hinv, s->ginv, s->piece, s->hunit, s->gunit,
-                  s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec, s->gseg_flag, s->gseg_id,
+                  s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec,
                   s->gseg_start, s->row_count, s->scan_partial, s->sum_partial, s->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -164,7 +164,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->hunit, s->rec_cap + 1)); ok(dalloc(&s->gunit, s->gcap + 1));
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, kGRecStride * s->gcap));
-  ok(dalloc(&s->gseg_flag, s->gcap)); ok(dalloc(&s->gseg_id, s->gcap)); ok(dalloc(&s->gseg_start, s->gcap));
+  ok(dalloc(&s->gseg_start, s->gcap));
   ok(dalloc(&s->row_count, Ns + 1));
   ok(dalloc(&s->edge_key, E > 0 ? E : 1)); ok(dalloc(&s->edge_id, E > 0 ? E : 1));
   ok(dalloc(&s->moll_r2, E > 0 ? E : 1));

@@ -1137,21 +1137,6 @@ __global__ void k_rec_check(const int64_t* rh_total, const int64_t* rg_total, in
   }
 }
 
-// segment heads of a sorted key array
-__global__ void __launch_bounds__(kBlock) k_seg_flags(const uint64_t* __restrict__ keys, const int64_t* n_dev,
-                                                      int64_t cap, int64_t* __restrict__ flag) {
-  const int64_t n = clamp_count(n_dev, cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride())
-    flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
-}
-
-__global__ void __launch_bounds__(kBlock) k_seg_starts(const int64_t* __restrict__ flag, const int64_t* __restrict__ id,
-                                                       const int64_t* n_dev, int64_t cap, int64_t* __restrict__ start) {
-  const int64_t n = clamp_count(n_dev, cap);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride())
-    if (flag[i]) start[id[i]] = i;
-}
-
 // Segment sums, one warp per segment: lane l adds records b+l, b+l+32, ... in order and a
 // fixed shuffle tree combines the lanes, so the result depends only on the sorted order.
 template <int W>
@@ -1600,17 +1585,13 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                 sc->bits_h, sc->sort_hist, s);
   const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* hv = wh ? sc->hvals_alt : sc->hvals;
-  launch(k_seg_flags, blocks_for(sc->rec_cap), kBlock, 0, s, hk, cnt + kCntRecH, sc->rec_cap, sc->seg_flag);
-  exclusive_scan_i64(sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap, cnt + kCntSegH, sc->scan_partial, s);
-  launch(k_seg_starts, blocks_for(sc->rec_cap), kBlock, 0, s, sc->seg_flag, sc->seg_id, cnt + kCntRecH, sc->rec_cap,
-                                                           sc->seg_start);
+  segment_starts(hk, cnt + kCntRecH, sc->rec_cap, sc->seg_start, cnt + kCntSegH, sc->scan_partial, s);
   launch(k_inverse, blocks_for(sc->rec_cap), kBlock, 0, s, hv, static_cast<const int64_t*>(cnt + kCntRecH), sc->rec_cap,
          sc->hinv);
   launch(k_seg_units, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const int64_t*>(sc->seg_start),
          static_cast<const int64_t*>(cnt + kCntRecH), static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->hunit);
   exclusive_scan_i64(sc->hunit, sc->hunit, cnt + kCntSegH, sc->rec_cap, cnt + kCntUnitsH, sc->scan_partial, s);
-  // seg_flag and seg_id are free after k_seg_starts: they hold the segment keys and the
-  // segments' BSR entries
+  // seg_flag and seg_id hold the segment keys and the segments' BSR entries
   uint64_t* ukey = reinterpret_cast<uint64_t*>(sc->seg_flag);
   int32_t* dst = reinterpret_cast<int32_t*>(sc->seg_id);
   launch(k_seg_keys, blocks_for(sc->rec_cap), kBlock, 0, s, hk, static_cast<const int64_t*>(sc->seg_start),
@@ -1640,10 +1621,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                 sc->bits_g, sc->sort_hist, s);
   const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
   const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
-  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
-  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
-  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
-                                                        sc->gseg_start);
+  segment_starts(gk, cnt + kCntRecG, sc->gcap, sc->gseg_start, cnt + kCntSegG, sc->scan_partial, s);
   launch(k_inverse, blocks_for(sc->gcap), kBlock, 0, s, gv, static_cast<const int64_t*>(cnt + kCntRecG), sc->gcap,
          sc->ginv);
   launch(k_seg_units, blocks_for(sc->gcap), kBlock, 0, s, static_cast<const int64_t*>(sc->gseg_start),
@@ -1758,10 +1736,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
                           bits_for((uint64_t)(sc->ns + kKinSlots)), sc->sort_hist, s);
   const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
   const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
-  launch(k_seg_flags, blocks_for(sc->gcap), kBlock, 0, s, gk, cnt + kCntRecG, sc->gcap, sc->gseg_flag);
-  exclusive_scan_i64(sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap, cnt + kCntSegG, sc->scan_partial, s);
-  launch(k_seg_starts, blocks_for(sc->gcap), kBlock, 0, s, sc->gseg_flag, sc->gseg_id, cnt + kCntRecG, sc->gcap,
-         sc->gseg_start);
+  segment_starts(gk, cnt + kCntRecG, sc->gcap, sc->gseg_start, cnt + kCntSegG, sc->scan_partial, s);
   cudaMemsetAsync(sc->hvp_out, 0, sizeof(double) * 3 * (sc->ns + kKinSlots), s);
   launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG,
          cnt + kCntSegG, sc->gcap, sc->hvp_out);

@@ -61,8 +61,8 @@ struct eipc_scene {
   int feat_bits;         // bits per id in the feature keys of the deduplicated pair set
   double* moll_r2;       // [ne] rest squared edge lengths of the EE mollifier
   double moll_factor;    // eps_x = moll_factor |e_i|^2 |e_j|^2; 0 = mollifier off
-  int64_t* seg_flag;     // [rec_cap]
-  int64_t* seg_id;       // [rec_cap]
+  int64_t* seg_flag;     // [rec_cap] key of each Hessian segment (upper block), as uint64
+  int64_t* seg_id;       // [rec_cap] BSR entries of each segment's block and transpose, as int32 pairs
   int64_t* seg_start;    // [rec_cap]
   uint32_t* hinv;        // [rec_cap] sorted position of each Hessian record
   uint32_t* ginv;        // [gcap] sorted position of each gradient record
@@ -75,8 +75,6 @@ struct eipc_scene {
   uint32_t* gvals;
   uint32_t* gvals_alt;
   double* grec;          // [gcap*kGRecStride] 3-vectors, 16-byte aligned rows
-  int64_t* gseg_flag;
-  int64_t* gseg_id;
   int64_t* gseg_start;
   int64_t* row_count;    // [ns+1]
   int64_t* scan_partial; // [kScanBlocks+1]

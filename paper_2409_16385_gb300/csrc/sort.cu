@@ -232,6 +232,55 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int64_t* __restrict__ 
   }
 }
 
+// ---- segment starts of a sorted key array (a segment = a run of equal keys)
+
+__device__ __forceinline__ int64_t seg_head(const uint64_t* __restrict__ keys, int64_t i) {
+  return (i == 0 || keys[i] != keys[i - 1]) ? 1 : 0;
+}
+
+// per-chunk number of segment heads (chunks of scan_range)
+__global__ void __launch_bounds__(256) k_seg_heads_partial(const uint64_t* __restrict__ keys, const int64_t* n_dev,
+                                                           int64_t cap, int64_t* __restrict__ partial) {
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t c = 0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) c += seg_head(keys, i);
+  c = block_sum_i64(c);
+  if (threadIdx.x == 0) partial[blockIdx.x] = c;
+}
+
+// start[s] = position of the s-th head: each chunk ranks its heads tile by tile from its
+// exclusive partial
+__global__ void __launch_bounds__(256) k_seg_heads_write(const uint64_t* __restrict__ keys, const int64_t* n_dev,
+                                                         int64_t cap, const int64_t* __restrict__ partial,
+                                                         int64_t* __restrict__ start) {
+  __shared__ int32_t wsum[8];
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t run = partial[blockIdx.x];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  for (int64_t tile = beg; tile < end; tile += 256) {
+    const int64_t i = tile + t;
+    const bool h = i < end && seg_head(keys, i);
+    const unsigned m = __ballot_sync(0xffffffffu, h);
+    if (lane == 0) wsum[warp] = __popc(m);
+    __syncthreads();
+    int before = 0, all = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+      before += w < warp ? wsum[w] : 0;
+      all += wsum[w];
+    }
+    if (h) start[run + before + __popc(m & ((1u << lane) - 1u))] = i;
+    __syncthreads();
+    run += all;
+  }
+}
+
 }  // namespace
 
 int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
@@ -255,6 +304,13 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64
   launch(k_scan_partial, kScanBlocks, 256, 0, s, in, n, cap, partial);
   launch(k_scan_partials, 1, 32, 0, s, partial, total);
   launch(k_scan_apply, kScanBlocks, 256, 0, s, in, out, n, cap, partial);
+}
+
+void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,
+                    int64_t* partial, cudaStream_t s) {
+  launch(k_seg_heads_partial, kScanBlocks, 256, 0, s, keys, n, cap, partial);
+  launch(k_scan_partials, 1, 32, 0, s, partial, n_seg);
+  launch(k_seg_heads_write, kScanBlocks, 256, 0, s, keys, n, cap, static_cast<const int64_t*>(partial), start);
 }
 
 }  // namespace eipc

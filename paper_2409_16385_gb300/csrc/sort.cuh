@@ -24,4 +24,10 @@ constexpr int kScanBlocks = 304;
 void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64_t cap,
                         int64_t* total, int64_t* partial, cudaStream_t s);
 
+// Segments of a sorted key array keys[0 .. min(*n, cap)), a segment being a run of equal
+// keys: start[s] = position of segment s's first element, *n_seg = the number of segments.
+// partial needs kScanBlocks + 1 entries.
+void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,
+                    int64_t* partial, cudaStream_t s);
+
 }  // namespace eipc
