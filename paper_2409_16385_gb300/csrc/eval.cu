@@ -1148,9 +1148,13 @@ __device__ __forceinline__ void warp_tree_sum(double acc[W]) {
 }
 
 // every upper block (I, J) becomes the full-pattern entry (I, J) and, off the diagonal,
-// the transposed entry (J, I); diagonal blocks get a sentinel twin that sorts last
+// the transposed entry (J, I); diagonal blocks get a sentinel twin that sorts last.  Entry
+// keys are row | col << br (br a whole number of radix digits): the upper blocks arrive in
+// (I, J) order, so every transposed
+// entry (r, I) of a row r (I < r) precedes the row's own upper entries, in increasing I;
+// a stable sort on the row bits alone then leaves each row's columns increasing.
 __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restrict__ ukey, const int64_t* n_seg,
-                                                         int64_t ns, uint64_t sentinel, int64_t cap,
+                                                         int64_t ns, int br, int64_t cap,
                                                          uint64_t* __restrict__ fkey, uint32_t* __restrict__ fval,
                                                          int64_t* n_full_sort, int64_t* n_diag, DevStatus* st,
                                                          int32_t* __restrict__ dst) {
@@ -1163,13 +1167,13 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restr
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
     const uint64_t key = ukey[s];
     const uint64_t I = key / (uint64_t)ns, J = key % (uint64_t)ns;
-    fkey[2 * s] = key;
+    fkey[2 * s] = I | (J << br);
     fval[2 * s] = (uint32_t)(s << 1);
     if (I != J) {
-      fkey[2 * s + 1] = J * (uint64_t)ns + I;
+      fkey[2 * s + 1] = J | (I << br);
       fval[2 * s + 1] = (uint32_t)((s << 1) | 1);
     } else {
-      fkey[2 * s + 1] = sentinel;
+      fkey[2 * s + 1] = (1ull << br) - 1;           // row bits above every row: sorts last
       fval[2 * s + 1] = 0;
       dst[2 * s + 1] = -1;
       atomicAdd(reinterpret_cast<unsigned long long*>(n_diag), 1ull);
@@ -1260,7 +1264,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict_
 // entry of its block (dst[2s]) and of its transpose (dst[2s+1]; -1 on the diagonal or
 // beyond the capacity)
 __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
-                                                        const int64_t* n_full_sort, const int64_t* n_diag, int64_t ns,
+                                                        const int64_t* n_full_sort, const int64_t* n_diag, int br,
                                                         eipc_bsr H, int64_t* __restrict__ row_count,
                                                         int32_t* __restrict__ dst, DevStatus* st) {
   const int64_t nnzb = *n_full_sort - *n_diag;
@@ -1273,11 +1277,11 @@ __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restri
   }
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzb; e += grid_stride()) {
     const uint64_t key = fkey[e];
-    const int64_t row = (int64_t)(key / (uint64_t)ns);
+    const int64_t row = (int64_t)(key & ((1ull << br) - 1));
     atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
     const uint32_t v = fval[e];
     dst[2 * (int64_t)(v >> 1) + (v & 1u)] = e < H.capacity ? (int32_t)e : -1;
-    if (e < H.capacity) H.col[e] = (int32_t)(key % (uint64_t)ns);
+    if (e < H.capacity) H.col[e] = (int32_t)(key >> br);
   }
 }
 
@@ -1599,17 +1603,20 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   int64_t* n_full = cnt + 13;
   int64_t* n_diag = cnt + 14;
   cudaMemsetAsync(n_diag, 0, sizeof(int64_t), s);
-  const uint64_t sentinel = (1ull << sc->bits_h) - 1;
+  // row field: bits_g rounded up to whole radix digits (the sort passes cover whole bytes,
+  // so the column must start on a byte); 2^bits_g > ns, so the all-ones row of the
+  // diagonal twins is above every row
+  const int rb = ((sc->bits_g + 7) / 8) * 8;
   launch(k_full_entries, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const uint64_t*>(ukey),
-         static_cast<const int64_t*>(cnt + kCntSegH), sc->ns, sentinel, sc->rec_cap, sc->hkeys, sc->hvals, n_full, n_diag,
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->ns, rb, sc->rec_cap, sc->hkeys, sc->hvals, n_full, n_diag,
          sc->status, dst);
-  const int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_full, sc->rec_cap, sc->bits_h,
+  const int wf = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, n_full, sc->rec_cap, rb,
                                 sc->sort_hist, s);
   const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
   cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
   launch(k_bsr_pattern, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const int64_t*>(n_full),
-         static_cast<const int64_t*>(n_diag), sc->ns, H, sc->row_count, dst, sc->status);
+         static_cast<const int64_t*>(n_diag), rb, H, sc->row_count, dst, sc->status);
   int64_t* nrow = cnt + 11;
   launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
   exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);

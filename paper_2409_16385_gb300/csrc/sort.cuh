@@ -12,7 +12,9 @@ constexpr int kSortThreads = 256;  // 8 warps, one element per thread per tile
 // Scratch: 256 * kSortBlocks digit counters followed by 256 digit totals.
 inline size_t sort_hist_entries() { return 256u * kSortBlocks + 256u; }
 
-// Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), on key bits [0, bits).
+// Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), by key: 8-bit digits over
+// bits [0, 8 ceil(bits / 8)), so every key must be below 2^bits (bits above the last whole
+// digit are ignored, bits inside it are not).
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns 0 if the sorted
 // result ends in (keys, vals), 1 if it ends in the alternate buffers.
 int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
