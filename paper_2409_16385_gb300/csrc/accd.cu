@@ -183,25 +183,26 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
   cudaMemsetAsync(n_cand, 0, sizeof(int64_t), s);
   cudaMemsetAsync(n_adv, 0, sizeof(int64_t), s);
   launch(k_alpha_init, blocks_for(sc->n_groups), kBlock, 0, s, abits, sc->group_alpha_bits, sc->n_groups);
-  // the hierarchies of the last contact-set build are refitted with swept boxes when they
-  // exist (the topology is reused; only the boxes change)
+  // swept per-vertex boxes over [x, x + dx]; the hierarchies of the last contact-set build
+  // are refitted with them when they exist (the topology is reused; only the boxes change)
+  EIPC_TIMED(sc, kKBvh, s, vertex_boxes(sc->topo, sc->x4, sc->dx4, 0.0, sc->vbox, nullptr, s));
   if (sc->tri_bvh.built && sc->edge_bvh.built) {
-    EIPC_TIMED(sc, kKBvh, s, bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, s,
+    EIPC_TIMED(sc, kKBvh, s, bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->vbox, s,
                                            sc->tune.refit_variant));
   } else {
     if (sc->tri_bvh.built)
-      EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, s, sc->tune.refit_variant));
+      EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->tri_bvh, kTri, sc->topo, sc->vbox, s, sc->tune.refit_variant));
     else
-      EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s,
+      EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, sc->dx4, sc->vbox, sc->bounds_ws, sc->sort_hist, s,
                                         sc->tune.refit_variant));
     if (sc->edge_bvh.built)
-      EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, s, sc->tune.refit_variant));
+      EIPC_TIMED(sc, kKBvh, s, bvh_refit(sc->edge_bvh, kEdge, sc->topo, sc->vbox, s, sc->tune.refit_variant));
     else
-      EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, sc->bounds_ws, sc->sort_hist, s,
+      EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, sc->dx4, sc->vbox, sc->bounds_ws, sc->sort_hist, s,
                                         sc->tune.refit_variant));
   }
   EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, sc->dx4, 0.0, sc->cand, n_cand, sc->cand_cap,
+             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 

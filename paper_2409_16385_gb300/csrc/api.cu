@@ -22,7 +22,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->vbox, s->vbox_pad, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->tri_bvh.range, s->tri_bvh.tl_root, s->tri_bvh.up_start,
@@ -139,6 +139,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->vkin, Nv)); ok(dalloc(&s->ekin, E)); ok(dalloc(&s->fkin, F));
   ok(dalloc(&s->vgroup, Nv)); ok(dalloc(&s->group_alpha_bits, 1)); ok(dalloc(&s->group_count, 4));
   ok(dalloc(&s->x4, 4 * Nv)); ok(dalloc(&s->dx4, 4 * Nv)); ok(dalloc(&s->x4f, 4 * Nv));
+  ok(dalloc(&s->vbox, 8 * Nv)); ok(dalloc(&s->vbox_pad, 8 * Nv));
   ok(alloc_bvh(s->tri_bvh, F));
   ok(alloc_bvh(s->edge_bvh, E));
   ok(dalloc(&s->bounds_ws, 8));

@@ -60,34 +60,60 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   return v;
 }
 
-// FP32 box of one primitive from FP64 positions, rounded outward; swept over x + dx if
-// dx4 != null; grown by pad (FP64, before rounding).
-__device__ __forceinline__ void prim_box(PrimKind kind, int64_t i, const Topo& T, const double* x4,
-                                         const double* dx4, double pad, float lo[3], float hi[3]) {
-  int32_t v[3];
-  int nvx;
-  if (kind == kVertex) { v[0] = (int32_t)i; nvx = 1; }
-  else if (kind == kEdge) { v[0] = T.edges[2 * i]; v[1] = T.edges[2 * i + 1]; nvx = 2; }
-  else { v[0] = T.tris[3 * i]; v[1] = T.tris[3 * i + 1]; v[2] = T.tris[3 * i + 2]; nvx = 3; }
-  double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int a = 0; a < nvx; ++a) {
-    V3 p = load_x(x4, v[a]);
-    double c[3] = {p.x, p.y, p.z};
-    for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
+// Per-vertex FP32 boxes, rounded outward from the FP64 positions (swept over x + dx when
+// dx4 is given): vbox[8v..8v+5] = lo xyz, hi xyz (rows of 8 floats), and vbox_pad the same
+// grown by pad in FP64 before rounding.  Outward rounding and the pad subtraction are
+// monotone, so the min / max over a primitive's vertices of these boxes is bit for bit the
+// box prim_box computes from the positions: the hierarchy and traversal read these instead
+// of recomputing FP64 minima per primitive.
+__global__ void __launch_bounds__(kBlock) k_vertex_boxes(int64_t nv, const double* __restrict__ x4,
+                                                         const double* __restrict__ dx4, double pad,
+                                                         float* __restrict__ vbox, float* __restrict__ vbox_pad) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
+    const V3 p = load_x(x4, (int32_t)v);
+    double lo[3] = {p.x, p.y, p.z}, hi[3] = {p.x, p.y, p.z};
     if (dx4) {
-      V3 d = load_x(dx4, v[a]);
-      double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
-      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
+      const V3 d = load_x(dx4, (int32_t)v);
+      const double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
+      for (int k = 0; k < 3; ++k) { lo[k] = fmin(lo[k], e[k]); hi[k] = fmax(hi[k], e[k]); }
     }
-  }
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = __double2float_rd(__dsub_rd(dlo[k], pad));
-    hi[k] = __double2float_ru(__dadd_ru(dhi[k], pad));
+    float4* o = reinterpret_cast<float4*>(vbox + 8 * v);
+    o[0] = make_float4(__double2float_rd(lo[0]), __double2float_rd(lo[1]), __double2float_rd(lo[2]),
+                       __double2float_ru(hi[0]));
+    o[1] = make_float4(__double2float_ru(hi[1]), __double2float_ru(hi[2]), 0.f, 0.f);
+    if (vbox_pad) {
+      float4* op = reinterpret_cast<float4*>(vbox_pad + 8 * v);
+      op[0] = make_float4(__double2float_rd(__dsub_rd(lo[0], pad)), __double2float_rd(__dsub_rd(lo[1], pad)),
+                          __double2float_rd(__dsub_rd(lo[2], pad)), __double2float_ru(__dadd_ru(hi[0], pad)));
+      op[1] = make_float4(__double2float_ru(__dadd_ru(hi[1], pad)), __double2float_ru(__dadd_ru(hi[2], pad)), 0.f, 0.f);
+    }
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Topo T, const double* __restrict__ x4,
-                                                   const double* __restrict__ dx4, const int32_t* __restrict__ b,
+// box of up to three vertices from the per-vertex boxes (ids < 0 are skipped)
+__device__ __forceinline__ void verts_box(const float* __restrict__ vbox, int32_t a, int32_t b, int32_t c,
+                                          float lo[3], float hi[3]) {
+  for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+  const int32_t v[3] = {a, b, c};
+  for (int s = 0; s < 3; ++s) {
+    if (v[s] < 0) continue;
+    const float4 p = __ldg(reinterpret_cast<const float4*>(vbox + 8 * (int64_t)v[s]));
+    const float4 q = __ldg(reinterpret_cast<const float4*>(vbox + 8 * (int64_t)v[s]) + 1);
+    lo[0] = fminf(lo[0], p.x); lo[1] = fminf(lo[1], p.y); lo[2] = fminf(lo[2], p.z);
+    hi[0] = fmaxf(hi[0], p.w); hi[1] = fmaxf(hi[1], q.x); hi[2] = fmaxf(hi[2], q.y);
+  }
+}
+
+// box of one primitive from the per-vertex boxes
+__device__ __forceinline__ void prim_box_v(PrimKind kind, int64_t i, const Topo& T, const float* __restrict__ vbox,
+                                           float lo[3], float hi[3]) {
+  if (kind == kVertex) verts_box(vbox, (int32_t)i, -1, -1, lo, hi);
+  else if (kind == kEdge) verts_box(vbox, T.edges[2 * i], T.edges[2 * i + 1], -1, lo, hi);
+  else verts_box(vbox, T.tris[3 * i], T.tris[3 * i + 1], T.tris[3 * i + 2], lo, hi);
+}
+
+__global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Topo T, const float* __restrict__ vbox,
+                                                   const int32_t* __restrict__ b,
                                                    float* __restrict__ leaf_box, uint64_t* __restrict__ keys,
                                                    uint32_t* __restrict__ vals) {
   float blo[3], bext[3];
@@ -98,7 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Top
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += grid_stride()) {
     float lo[3], hi[3];
-    prim_box(kind, i, T, x4, dx4, 0.0, lo, hi);
+    prim_box_v(kind, i, T, vbox, lo, hi);
     uint32_t code = 0;
     for (int k = 0; k < 3; ++k) {
       float c = (0.5f * (lo[k] + hi[k]) - blo[k]) / bext[k];
@@ -184,35 +210,16 @@ __device__ __forceinline__ int32_t arrive(int32_t* f) {
 
 // leaf boxes in leaf order, for refitting an existing hierarchy; the leaf's vertex ids
 // come from its leaf record (coalesced) rather than the primitive tables
-// FP32 box (rounded outward) of one leaf from its leaf record's vertex ids, over [x, x + dx]
-// when dx4 is given
-__device__ __forceinline__ void leaf_box_of(int4 li, const double* __restrict__ x4, const double* __restrict__ dx4,
-                                            float lo[3], float hi[3]) {
-  const int32_t v[3] = {li.x, li.y, li.z};
-  double dlo[3] = {INFINITY, INFINITY, INFINITY}, dhi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  for (int a = 0; a < 3; ++a) {
-    if (v[a] < 0) continue;
-    const V3 p = load_x(x4, v[a]);
-    const double c[3] = {p.x, p.y, p.z};
-    for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], c[k]); dhi[k] = fmax(dhi[k], c[k]); }
-    if (dx4) {
-      const V3 d = load_x(dx4, v[a]);
-      const double e[3] = {p.x + d.x, p.y + d.y, p.z + d.z};
-      for (int k = 0; k < 3; ++k) { dlo[k] = fmin(dlo[k], e[k]); dhi[k] = fmax(dhi[k], e[k]); }
-    }
-  }
-  for (int k = 0; k < 3; ++k) {
-    lo[k] = __double2float_rd(dlo[k]);
-    hi[k] = __double2float_ru(dhi[k]);
-  }
+// FP32 box of one leaf from the per-vertex boxes of its leaf record's vertex ids
+__device__ __forceinline__ void leaf_box_of(int4 li, const float* __restrict__ vbox, float lo[3], float hi[3]) {
+  verts_box(vbox, li.x, li.y, li.z, lo, hi);
 }
 
 __global__ void __launch_bounds__(kBlock) k_leaf_boxes(int64_t n, const int4* __restrict__ leaf_info,
-                                                       const double* __restrict__ x4, const double* __restrict__ dx4,
-                                                       float* __restrict__ leaf_box) {
+                                                       const float* __restrict__ vbox, float* __restrict__ leaf_box) {
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
     float lo[3], hi[3];
-    leaf_box_of(leaf_info[l], x4, dx4, lo, hi);
+    leaf_box_of(leaf_info[l], vbox, lo, hi);
     float2* o = reinterpret_cast<float2*>(leaf_box + 6 * l);
     o[0] = make_float2(lo[0], lo[1]);
     o[1] = make_float2(lo[2], hi[0]);
@@ -328,8 +335,7 @@ __host__ __device__ __forceinline__ RefitView refit_view(const Bvh& t) {
 // Phase A of the refit of up to two trees in one launch: one warp per treelet, lane l
 // computing leaf l's box from the positions and climbing in shared memory.  The grid also
 // clears both trees' arrival counters for phase B.
-__global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView B, const double* __restrict__ x4,
-                                                          const double* __restrict__ dx4) {
+__global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
   __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
   __shared__ int scnt[kTreeletWarps][kTreelet];
   __shared__ int spar[kTreeletWarps][kTreelet];
@@ -359,7 +365,7 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
     if (lane < m) {
       const int32_t l = lo + lane;
       float b[6];
-      leaf_box_of(T.leaf_info[l], x4, dx4, b, b + 3);
+      leaf_box_of(T.leaf_info[l], vbox, b, b + 3);
       int32_t child = ~l;
       int32_t node = T.parent[n - 1 + l];
       for (int step = 0; step < kTreelet; ++step) {  // a treelet is at most kTreelet - 1 deep
@@ -389,8 +395,7 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
 // Phase B for up to two trees: one thread per upper start (a treelet root, or a leaf
 // directly under a larger node, its box from the positions) climbs with release-acquire
 // arrival counters; the two trees' climbs run side by side.
-__global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B, const double* __restrict__ x4,
-                                                        const double* __restrict__ dx4) {
+__global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
   const int64_t nuA = A.n > 1 ? A.count[1] : 0, nuB = B.n > 1 ? B.count[1] : 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nuA + nuB; k += grid_stride()) {
     const bool inA = k < nuA;
@@ -410,7 +415,7 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
       node = T.parent[st];
     } else {                                         // a leaf under a larger node
       const int32_t l = ~st;
-      leaf_box_of(T.leaf_info[l], x4, dx4, lo, hi);
+      leaf_box_of(T.leaf_info[l], vbox, lo, hi);
       child = st;
       node = T.parent[n - 1 + l];
     }
@@ -456,9 +461,8 @@ __device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_ca
 // One launch for both query sets: threads [0, nv) run vertex boxes against the triangle
 // tree (PT), threads [nv, nv + ne) run edge boxes against the edge tree (EE, j > i), the
 // edges in that tree's Morton order so neighbouring threads take similar paths.
-__global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const double* __restrict__ x4,
-                                               const double* __restrict__ dx4, double pad, uint64_t* cand,
-                                               int64_t* n_cand, int64_t cap, DevStatus* st) {
+__global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
+                                               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
   const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);
   const int64_t nv_q = tt.n > 0 ? T.nv : 0;
   for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += grid_stride()) {
@@ -468,7 +472,7 @@ __global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const dou
     const int64_t qpos = is_pt ? -1 : qi - nv_q;     // EE: the query's own leaf position
     const int64_t q = is_pt ? qi : (int64_t)te.leaf_prim[qpos];
     float qlo[3], qhi[3];
-    prim_box(qkind, q, T, x4, dx4, pad, qlo, qhi);
+    prim_box_v(qkind, q, T, vbox_q, qlo, qhi);
     int32_t qa, qb;
     if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
     else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
@@ -536,12 +540,19 @@ __global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const dou
 
 }  // namespace
 
-void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, int32_t* bounds_ws,
-               uint32_t* sort_hist, cudaStream_t s, int refit_variant) {
+void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double pad, float* vbox, float* vbox_pad,
+                  cudaStream_t s) {
+  if (topo.nv <= 0) return;
+  launch(k_vertex_boxes, blocks_for(topo.nv), kBlock, 0, s, topo.nv, x4, dx4, pad, vbox, vbox_pad);
+}
+
+void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, const float* vbox,
+               int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant) {
   if (t.n <= 0) return;
   launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
   launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, dx4, topo.nv, bounds_ws);
-  launch(k_leaves, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, x4, dx4, bounds_ws, t.leaf_box, t.keys, t.vals);
+  launch(k_leaves, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, vbox, static_cast<const int32_t*>(bounds_ws),
+         t.leaf_box, t.keys, t.vals);
   int which = radix_sort_u64(t.keys, t.vals, t.keys_alt, t.vals_alt, t.n_dev, t.n, 30, sort_hist, s);
   const uint64_t* sk = which ? t.keys_alt : t.keys;
   const uint32_t* sv = which ? t.vals_alt : t.vals;
@@ -571,32 +582,31 @@ void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaSt
 }
 
 // both phases of the treelet refit for one or two trees (b may be null)
-static void treelet_refit(Bvh& a, Bvh* b, const double* x4, const double* dx4, cudaStream_t s) {
+static void treelet_refit(Bvh& a, Bvh* b, const float* vbox, cudaStream_t s) {
   RefitView A = refit_view(a);
   RefitView Bv = b ? refit_view(*b) : RefitView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int64_t n = a.n + (b ? b->n : 0);
-  launch(k_treelet_refit, blocks_for(n, 8), kBlock, 0, s, A, Bv, x4, dx4);
-  launch(k_upper_refit, blocks_for(n), kBlock, 0, s, A, Bv, x4, dx4);
+  launch(k_treelet_refit, blocks_for(n, 8), kBlock, 0, s, A, Bv, vbox);
+  launch(k_upper_refit, blocks_for(n), kBlock, 0, s, A, Bv, vbox);
 }
 
-void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const double* x4, const double* dx4,
-                    cudaStream_t s, int refit_variant) {
+void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const float* vbox, cudaStream_t s,
+                    int refit_variant) {
   if (refit_variant == 2 && a.n > 1 && b.n > 1) {
-    treelet_refit(a, &b, x4, dx4, s);
+    treelet_refit(a, &b, vbox, s);
     return;
   }
-  bvh_refit(a, ka, topo, x4, dx4, s, refit_variant);
-  bvh_refit(b, kb, topo, x4, dx4, s, refit_variant);
+  bvh_refit(a, ka, topo, vbox, s, refit_variant);
+  bvh_refit(b, kb, topo, vbox, s, refit_variant);
 }
 
-void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
-               int refit_variant) {
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const float* vbox, cudaStream_t s, int refit_variant) {
   if (t.n <= 0) return;
   if (refit_variant == 2 && t.n > 1) {
-    treelet_refit(t, nullptr, x4, dx4, s);
+    treelet_refit(t, nullptr, vbox, s);
     return;
   }
-  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int4*>(t.leaf_info), x4, dx4, t.leaf_box);
+  launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int4*>(t.leaf_info), vbox, t.leaf_box);
   cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
   if (refit_variant == 0)
     launch(k_refit<false, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
@@ -608,11 +618,11 @@ void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
            t.leaf_info, t.refit_flag);
 }
 
-void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
-               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps) {
+void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* vbox_q, uint64_t* cand,
+               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps) {
   const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
-  launch(k_query, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, x4, dx4, pad, cand, n_cand, cap, st);
+  launch(k_query, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
 }
 
 }  // namespace eipc

@@ -60,38 +60,45 @@ __host__ __device__ __forceinline__ uint64_t pair_key(int type, uint32_t i, uint
   return ((uint64_t)type << (bi + bj)) | ((uint64_t)i << bj) | (uint64_t)j;
 }
 
-// Build the tree over primitives of `kind` from positions x4 (padded), optionally swept
-// by dx4 (CCD); `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
+// Per-vertex FP32 boxes of the positions x4 (padded), swept over x + dx when dx4 is given,
+// rounded outward: vbox[8 nv] unpadded and, when vbox_pad is not null, vbox_pad[8 nv] grown
+// by pad.  The leaf and query boxes below are taken from these; they are bit for bit the
+// boxes computed from the positions primitive by primitive.
+void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double pad, float* vbox, float* vbox_pad,
+                  cudaStream_t s);
+
+// Build the tree over primitives of `kind`: scene bounds from positions x4 (padded),
+// optionally swept by dx4 (CCD), leaf boxes from the matching per-vertex boxes vbox;
+// `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
 // refit_variant: 0 = arrival counters behind full device fences, 1 = release-acquire
 // arrival counters, 2 = treelets of <= 32 leaves refitted by one warp each in shared memory,
 // then release-acquire counters above them (all give the same boxes)
-void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4,
+void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, const float* vbox,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant);
 
 // Scene box of the positions x4 into bounds_ws (6 order-preserving ints: lo xyz, hi xyz).
 void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s);
 
-// Refit the hierarchy of the last bvh_build with new leaf boxes (x4, optionally swept by
-// dx4): any binary tree over the primitives with conservative boxes gives the same exact
+// Refit the hierarchy of the last bvh_build with new leaf boxes (from the per-vertex boxes
+// vbox): any binary tree over the primitives with conservative boxes gives the same exact
 // candidate set, so the Morton sort and hierarchy can be reused while the topology stays.
-void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, cudaStream_t s,
-               int refit_variant);
+void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const float* vbox, cudaStream_t s, int refit_variant);
 
 // Refit of two hierarchies (the triangle and edge trees) at once: with the treelet refit
 // both trees share two launches, so their latency-bound climbs overlap.  The boxes are
 // those of two bvh_refit calls.  With the treelet refit, the leaf boxes are computed inside
 // the refit and leaf_box is not updated (only single-leaf trees and the other refits read
 // it).
-void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const double* x4, const double* dx4,
-                    cudaStream_t s, int refit_variant);
+void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const float* vbox, cudaStream_t s,
+                    int refit_variant);
 
-// Traverse both trees in one launch: every vertex box (grown by `pad`, or swept by dx4)
-// against the triangle tree -> PT candidates, every edge box against the edge tree -> EE
+// Traverse both trees in one launch: every vertex box (from vbox_q: the per-vertex boxes
+// grown by the contact distance, or swept for CCD) against the triangle tree -> PT
+// candidates, every edge box against the edge tree -> EE
 // candidates with j > i.  Incident pairs and all-kinematic pairs are skipped; candidates
 // are appended as pair keys to cand[0..cap) with the running count in *n_cand, and an
 // overflow raises CAND_OVERFLOW.
-void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const double* x4, const double* dx4, double pad,
-               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads = 128,
-               int bps = 24);
+void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* vbox_q, uint64_t* cand,
+               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads = 128, int bps = 24);
 
 }  // namespace eipc

@@ -310,21 +310,23 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   // full rebuild every `rebuild_interval` calls, refit of the same hierarchy in between (the
   // candidate set is exact for any hierarchy; only traversal cost depends on its quality)
   const bool rebuild = !sc->tri_bvh.built || !sc->edge_bvh.built || sc->contact_refits + 1 >= sc->rebuild_interval;
+  // per-vertex boxes: unpadded for the leaves, grown by dhat for the queries
+  EIPC_TIMED(sc, kKBvh, s, vertex_boxes(sc->topo, sc->x4, nullptr, p.dhat, sc->vbox, sc->vbox_pad, s));
   if (rebuild) {
-    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s,
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->tri_bvh, kTri, sc->topo, sc->x4, nullptr, sc->vbox, sc->bounds_ws, sc->sort_hist, s,
                                       sc->tune.refit_variant));
-    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->bounds_ws, sc->sort_hist, s,
+    EIPC_TIMED(sc, kKBvh, s, bvh_build(sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, sc->vbox, sc->bounds_ws, sc->sort_hist, s,
                                       sc->tune.refit_variant));
     sc->contact_refits = 0;
   } else {
     sc->timers->start(kKBvh, s);
     scene_bounds(sc->topo, sc->x4, sc->bounds_ws, s);    // the narrow-phase screen reads it
-    bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->x4, nullptr, s, sc->tune.refit_variant);
+    bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->vbox, s, sc->tune.refit_variant);
     sc->timers->stop(kKBvh, s);
     ++sc->contact_refits;
   }
   EIPC_TIMED(sc, kKQuery, s,
-             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->x4, nullptr, p.dhat, sc->cand, n_cand, sc->cand_cap,
+             bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox_pad, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
   int64_t* n_cand2 = sc->counters + kCntScreened;
   cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);

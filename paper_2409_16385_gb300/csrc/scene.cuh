@@ -26,6 +26,8 @@ struct eipc_scene {
   double* x4;
   double* dx4;
   float* x4f;            // [nv*4] FP32 copy of x4 for the narrow-phase screen
+  float* vbox;           // [nv*8] per-vertex FP32 boxes of the last call (contact or swept)
+  float* vbox_pad;       // [nv*8] the contact ones grown by dhat (the query boxes)
   // broad phase
   eipc::Bvh tri_bvh, edge_bvh;
   int32_t* bounds_ws;
