@@ -576,11 +576,6 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   t.built = true;
 }
 
-void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s) {
-  launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
-  launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, static_cast<const double*>(nullptr), topo.nv, bounds_ws);
-}
-
 // both phases of the treelet refit for one or two trees (b may be null)
 static void treelet_refit(Bvh& a, Bvh* b, const float* vbox, cudaStream_t s) {
   RefitView A = refit_view(a);

@@ -76,9 +76,6 @@ void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double 
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, const float* vbox,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant);
 
-// Scene box of the positions x4 into bounds_ws (6 order-preserving ints: lo xyz, hi xyz).
-void scene_bounds(const Topo& topo, const double* x4, int32_t* bounds_ws, cudaStream_t s);
-
 // Refit the hierarchy of the last bvh_build with new leaf boxes (from the per-vertex boxes
 // vbox): any binary tree over the primitives with conservative boxes gives the same exact
 // candidate set, so the Morton sort and hierarchy can be reused while the topology stays.

@@ -61,21 +61,18 @@ __device__ __forceinline__ double stencil_d2(const Topo& T, const double* __rest
   return ee_distance<false>(load_x(x4, ea[0]), load_x(x4, ea[1]), load_x(x4, eb[0]), load_x(x4, eb[1]), nullptr);
 }
 
-__device__ __forceinline__ float ord_to_float(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
 // FP32 screen (geometry.cuh) over all candidates; the ones it cannot prove farther than
-// dhat are compacted into `out` for the exact FP64 test.  The screen is used only when the
-// scene's largest coordinate M keeps FP32 rounding (M 2^-24 per coordinate) 40 times below
-// the 2e-3 dhat margin; otherwise every candidate is passed on.
+// dhat are compacted into `out` for the exact FP64 test.  The radius carries, besides the
+// relative margin of the far tests, an absolute margin of twice their distance error
+// budget, 80 M 2^-24 with M the candidate's largest coordinate, so the screen holds at any
+// scene size.
 __global__ void __launch_bounds__(kBlock) k_screen(Topo T, const float* __restrict__ x4f,
-                                                   const int32_t* __restrict__ bounds, const uint64_t* __restrict__ cand,
+                                                   const uint64_t* __restrict__ cand,
                                                    const int64_t* n_cand, int64_t cap, double dhat,
                                                    uint64_t* __restrict__ out, int64_t* n_out) {
   const int64_t n = clamp_count(n_cand, cap);
-  float M = 0.f;
-  for (int k = 0; k < 6; ++k) M = fmaxf(M, fabsf(ord_to_float(bounds[k])));
-  const bool use = 40.0 * (double)M * 5.9604644775390625e-8 < 2e-3 * dhat;
-  const float r2m = (float)(dhat * dhat * (1.0 + 4e-3));
+  const float dhat_up = __double2float_ru(dhat);
   const int lane = threadIdx.x & 31;
   for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
     const int64_t k = base + threadIdx.x;
@@ -83,20 +80,23 @@ __global__ void __launch_bounds__(kBlock) k_screen(Topo T, const float* __restri
     uint64_t key = 0;
     if (k < n) {
       key = cand[k];
-      pass = true;
-      if (use) {
-        const int32_t j = (int32_t)(key & ((1ull << T.bits_j) - 1));
-        const int32_t i = (int32_t)((key >> T.bits_j) & ((1ull << T.bits_i) - 1));
-        const int type = (int)(key >> (T.bits_i + T.bits_j));
-        if (type == 0) {
-          const int32_t* f = T.tris + 3 * (int64_t)j;
-          pass = !pt_far_f32(load_xf(x4f, i), load_xf(x4f, f[0]), load_xf(x4f, f[1]), load_xf(x4f, f[2]), r2m);
-        } else {
-          const int32_t* ea = T.edges + 2 * (int64_t)i;
-          const int32_t* eb = T.edges + 2 * (int64_t)j;
-          pass = !ee_far_f32(load_xf(x4f, ea[0]), load_xf(x4f, ea[1]), load_xf(x4f, eb[0]), load_xf(x4f, eb[1]), r2m);
-        }
+      const int32_t j = (int32_t)(key & ((1ull << T.bits_j) - 1));
+      const int32_t i = (int32_t)((key >> T.bits_j) & ((1ull << T.bits_i) - 1));
+      const int type = (int)(key >> (T.bits_i + T.bits_j));
+      F3 P[4];
+      if (type == 0) {
+        const int32_t* f = T.tris + 3 * (int64_t)j;
+        P[0] = load_xf(x4f, i); P[1] = load_xf(x4f, f[0]); P[2] = load_xf(x4f, f[1]); P[3] = load_xf(x4f, f[2]);
+      } else {
+        const int32_t* ea = T.edges + 2 * (int64_t)i;
+        const int32_t* eb = T.edges + 2 * (int64_t)j;
+        P[0] = load_xf(x4f, ea[0]); P[1] = load_xf(x4f, ea[1]); P[2] = load_xf(x4f, eb[0]); P[3] = load_xf(x4f, eb[1]);
       }
+      float M = 0.f;
+      for (int a = 0; a < 4; ++a) M = fmaxf(M, fmaxf(fabsf(P[a].x), fmaxf(fabsf(P[a].y), fabsf(P[a].z))));
+      const float r = __fadd_ru(dhat_up, 80.f * M * 5.9604645e-8f);
+      const float r2m = r * r * 1.004f;
+      pass = type == 0 ? !pt_far_f32(P[0], P[1], P[2], P[3], r2m) : !ee_far_f32(P[0], P[1], P[2], P[3], r2m);
     }
     const uint32_t mask = __ballot_sync(0xffffffffu, pass);
     if (mask) {
@@ -319,10 +319,8 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
                                       sc->tune.refit_variant));
     sc->contact_refits = 0;
   } else {
-    sc->timers->start(kKBvh, s);
-    scene_bounds(sc->topo, sc->x4, sc->bounds_ws, s);    // the narrow-phase screen reads it
-    bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->vbox, s, sc->tune.refit_variant);
-    sc->timers->stop(kKBvh, s);
+    EIPC_TIMED(sc, kKBvh, s,
+               bvh_refit_pair(sc->tri_bvh, kTri, sc->edge_bvh, kEdge, sc->topo, sc->vbox, s, sc->tune.refit_variant));
     ++sc->contact_refits;
   }
   EIPC_TIMED(sc, kKQuery, s,
@@ -332,7 +330,7 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
   sc->timers->start(kKNarrow, s);
   launch(k_screen, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, static_cast<const float*>(sc->x4f),
-         static_cast<const int32_t*>(sc->bounds_ws), static_cast<const uint64_t*>(sc->cand),
+         static_cast<const uint64_t*>(sc->cand),
          static_cast<const int64_t*>(n_cand), sc->cand_cap, p.dhat, sc->cand2, n_cand2);
   launch(k_narrow, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, sc->x4, sc->cand2, n_cand2, sc->cand_cap,
          p.dhat, sc->skeys, sc->svals, sc->sd, n_surv, sc->status);
