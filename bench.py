@@ -19,6 +19,7 @@ rewritten between steps (outside the events) so every step starts with a cold L2
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -43,7 +44,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: 300 for the bubble grasp, so that the clock sampler sees "
+                         "the timed region, 20 for the other workloads)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -59,7 +62,10 @@ def parse():
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (no autotuning)")
     ap.add_argument("--solver", choices=["auto", "dense", "pcg"], default="auto", help="physical: linear solver")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 300 if args.workload == "bubble_grasp" and args.impl == "ours" else 20
+    return args
 
 
 def dist_setup(backend):
@@ -79,7 +85,7 @@ def dist_setup(backend):
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -87,6 +93,11 @@ class ClockSampler:
         self.idx = gpu_index
         self.proc = None
         self.lines = []
+        self.window = None          # (t0, t1) wall-clock seconds of the timed region
+
+    def mark(self, t0, t1):
+        """Keep only the samples taken between t0 and t1 (time.time() seconds)."""
+        self.window = (t0, t1)
 
     def start(self):
         try:
@@ -109,13 +120,20 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in out.strip().splitlines():
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
+            if self.window is not None:
+                try:
+                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                if not (self.window[0] - 0.05 <= ts <= self.window[1] + 0.05):
+                    continue
             try:
-                sm.append(float(f[1])); mx.append(float(f[2]))
+                sm.append(float(f[2])); mx.append(float(f[3]))
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
+            for n, v in zip(names, f[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
         if not sm:
@@ -327,10 +345,12 @@ def run_ours(args, ws, rank, local):
     counts = torch.zeros((K, 2), dtype=torch.int64, device=dev)
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
     launches0 = lib.eipc_launch_count()
+    clocks.start()
+    time.sleep(0.3)                  # the sampler is running before the timed region starts
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    tw0 = time.time()
     wall0 = time.perf_counter()
     for k in range(K):
         t = (t0 + k) % n_it
@@ -341,9 +361,11 @@ def run_ours(args, ws, rank, local):
         counts[k, 0].copy_(pairs.count[0])
         counts[k, 1].copy_(ncand[0])
     torch.cuda.synchronize()
+    tw1 = time.time()
     wall = time.perf_counter() - wall0
     if ws > 1:
         dist.barrier()
+    clocks.mark(tw0, tw1)
     clk = clocks.stop()
     launches = lib.eipc_launch_count() - launches0
     step_ms = np.array([a.elapsed_time(b) for a, b in evs])
@@ -692,10 +714,12 @@ def run_batched(args, ws, rank, local):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     counts = torch.zeros((K, 2), dtype=torch.int64, device=dev)
     clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    time.sleep(0.3)                  # the sampler is running before the timed region starts
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    tw0 = time.time()
     wall0 = time.perf_counter()
     launches = 0
     for k in range(K):
@@ -707,9 +731,11 @@ def run_batched(args, ws, rank, local):
         counts[k, 0].copy_(st.pairs.count[0])
         counts[k, 1].copy_(st.ncand[0])
     torch.cuda.synchronize()
+    tw1 = time.time()
     wall = time.perf_counter() - wall0
     if ws > 1:
         dist.barrier()
+    clocks.mark(tw0, tw1)
     clk = clocks.stop()
     s1 = st.cs.status()
     if s1["flags"] & ~64:
