@@ -1479,12 +1479,14 @@ __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict
   }
 }
 
+// one warp: lane l adds partials l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sum_final(const double* __restrict__ partial, int nb, double* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < nb; ++b) t += partial[b];
-    *out = t;
-  }
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double t = 0.0;
+  for (int b = lane; b < nb; b += 32) t += partial[b];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if (lane == 0) *out = t;
 }
 
 // ------------------------------------------------------------------ friction lag
