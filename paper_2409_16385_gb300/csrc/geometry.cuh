@@ -144,11 +144,12 @@ __device__ __forceinline__ double ee_distance(V3 a0, V3 a1, V3 b0, V3 b1, Stenci
 }
 
 // ---------------------------------------------------------------- FP32 screen
-// "Certainly farther than r" tests in FP32 only (62x the FP64 rate on GB300), on an FP32
-// copy of the positions (absolute coordinates within a 0.25 m scene: each coordinate is off
-// by <= 1.5e-8 m, each difference by <= 3e-8 m).  A pair is declared far only if its FP32
-// squared distance exceeds r^2 (1 + 4e-3), i.e. d > r (1 + 2e-3), a margin of >= 4e-7 m
-// for r >= 2e-4 m against distance errors of order 1e-7 m.  Misclassifying the closest
+// "Certainly farther than r" tests in FP32 only (62x the FP64 rate on GB300), on FP32 copies
+// of the positions.  With M the largest coordinate of the candidate's points, each FP32
+// coordinate is off by <= M 2^-24 and the FP32 distance by a small multiple of that (taken
+// as 40 M 2^-24).  The callers prove far with a radius grown by twice that, 80 M 2^-24, and
+// declare a pair far only if its FP32 squared distance also exceeds r^2 (1 + 4e-3), i.e.
+// d > r (1 + 2e-3): the margin holds at any scene size.  Misclassifying the closest
 // region can only (a) report a lower bound (plane / line distance when the projection is
 // wrongly found inside), or (b) report a boundary value whose excess is bounded by the
 // curvature times the squared parameter error.  Stencils whose parameter solve is not
