@@ -116,29 +116,36 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in out.strip().splitlines():
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 10:
-                continue
-            if self.window is not None:
-                try:
-                    ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                except ValueError:
-                    continue
-                if not (self.window[0] - 0.05 <= ts <= self.window[1] + 0.05):
-                    continue
+        return parse_clock_samples(out, self.window)
+
+
+def parse_clock_samples(text, window=None):
+    """Median SM clock, maximum SM clock, active slowdown reasons and sample count from the
+    CSV lines of ClockSampler.FIELDS; with window = (t0, t1), only the samples whose
+    timestamp lies within 50 ms of [t0, t1] (time.time() seconds) count."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in text.strip().splitlines():
+        f = [x.strip() for x in ln.split(",")]
+        if len(f) < 10:
+            continue
+        if window is not None:
             try:
-                sm.append(float(f[2])); mx.append(float(f[3]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
                 continue
-            for n, v in zip(names, f[6:10]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
-        return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons), samples=len(sm))
+            if not (window[0] - 0.05 <= ts <= window[1] + 0.05):
+                continue
+        try:
+            sm.append(float(f[2])); mx.append(float(f[3]))
+        except ValueError:
+            continue
+        for n, v in zip(names, f[6:10]):
+            if v.lower().startswith("active"):
+                reasons.add(n)
+    if not sm:
+        return dict(sm_mhz=None, sm_max_mhz=None, reasons=["no samples"], samples=0)
+    return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons), samples=len(sm))
 
 
 def measured_peaks():
