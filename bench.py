@@ -148,6 +148,21 @@ def parse_clock_samples(text, window=None):
     return dict(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), reasons=sorted(reasons), samples=len(sm))
 
 
+def across_ranks(total_s, total_pairs, total_cand, ws, device):
+    """Whole-job totals of the timed steps: the slowest rank's seconds (the job ends with its
+    last rank) and the pairs and candidates of all ranks.  One rank: the values as given."""
+    if ws <= 1:
+        return total_s, total_pairs, total_cand
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([total_s, total_pairs, total_cand], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -384,15 +399,7 @@ def run_ours(args, ws, rank, local):
     total_s = step_ms.sum() / 1e3
     total_pairs = float(cnt[:, 0].sum())
     total_cand = float(cnt[:, 1].sum())
-    if ws > 1:
-        tt = torch.tensor([total_s, total_pairs, total_cand], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_s_all, total_pairs_all, total_cand_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        total_s_all, total_pairs_all, total_cand_all = total_s, total_pairs, total_cand
+    total_s_all, total_pairs_all, total_cand_all = across_ranks(total_s, total_pairs, total_cand, ws, dev)
     value = total_pairs_all / total_s_all
 
     # ---- roofline of the dominant kernel, from its live event timer
@@ -750,13 +757,7 @@ def run_batched(args, ws, rank, local):
     step_ms = np.array([a.elapsed_time(c) for a, c in evs])
     cnt = counts.cpu().numpy()
     total_s, total_pairs, total_cand = step_ms.sum() / 1e3, float(cnt[:, 0].sum()), float(cnt[:, 1].sum())
-    if ws > 1:
-        tt = torch.tensor([total_s, total_pairs, total_cand], dtype=torch.float64, device=dev)
-        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        total_s_all, total_pairs_all, total_cand_all = float(mx[0]), float(sm[1]), float(sm[2])
-    else:
-        total_s_all, total_pairs_all, total_cand_all = total_s, total_pairs, total_cand
+    total_s_all, total_pairs_all, total_cand_all = across_ranks(total_s, total_pairs, total_cand, ws, dev)
     value = total_pairs_all / total_s_all
     Eg_last = st.Eg.cpu().numpy()
     ag_last = st.ag.cpu().numpy()
