@@ -64,3 +64,27 @@ def test_binding_refuses_to_run_without_cuda():
     from paper_2409_16385_gb300 import ContactScene, scenes
     with pytest.raises(RuntimeError):
         ContactScene(scenes.make_config(1))
+
+
+def test_entry_points_reject_misuse_without_gpu_work():
+    """Host-detectable misuse returns EIPC_ERR_INVALID before any device call: a null scene,
+    a count out of range, a launch shape outside the documented set, non-finite scalars."""
+    import numpy as np
+    lib = binding.load()
+    INVALID = -1
+    out = np.zeros(16, np.int64)
+    assert lib.eipc_work_counts(None, None, out.ctypes.data, 9) == INVALID
+    flags = ctypes.c_int32(0)
+    need = np.zeros(4, np.int64)
+    it = np.zeros(1, np.int64)
+    assert lib.eipc_status_read(None, None, ctypes.byref(flags), need.ctypes.data, it.ctypes.data) == INVALID
+    assert lib.eipc_set_launch(None, 0, 128, 8, 2) == INVALID
+    assert lib.eipc_set_rebuild_interval(None, 4) == INVALID
+    ms = np.zeros(16); n = np.zeros(16, np.int64)
+    assert lib.eipc_timing_read(None, ms.ctypes.data, n.ctypes.data, 4) == INVALID
+    x = np.zeros(3); y = np.zeros(3)
+    rp = np.zeros(2, np.int32)
+    assert lib.eipc_bsr_spmv(-1, rp.ctypes.data, None, None, x.ctypes.data, 1.0, 0.0, y.ctypes.data, None) == INVALID
+    assert lib.eipc_bsr_spmv(1, rp.ctypes.data, None, None, x.ctypes.data, float("nan"), 0.0, y.ctypes.data,
+                             None) == INVALID
+    assert lib.eipc_bsr_spmv(1, None, None, None, x.ctypes.data, 1.0, 0.0, y.ctypes.data, None) == INVALID
