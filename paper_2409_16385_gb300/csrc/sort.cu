@@ -1,7 +1,8 @@
-// Stable LSD radix sort and exclusive scan with device-resident element counts.
+// Stable LSD radix sort, exclusive scan and segment starts with device-resident element
+// counts.
 //
 // Radix pass (8-bit digit): each of kSortBlocks blocks owns one contiguous chunk of the
-// input.  (1) per-block digit histograms, (2) one warp per digit turns its counts into
+// input.  (1) per-block digit histograms, (2) one block per digit turns its counts into
 // exclusive per-block prefixes and a digit total, (3) each block scans the 256 digit totals
 // for its digit bases and scatters its chunk tile by tile: warp peers
 // with equal digits are found with __match_any_sync, per-warp digit counts are prefix-
