@@ -22,8 +22,11 @@
 // Friction (Sec. III-B, lagged): D = mu lambda f0(|u|), u = (I - n n^T)(sum gamma_a x_a - anchor),
 //   grad = mu lambda f1(y)/y gamma (x) u,   hess = (gamma gamma^T) (x) F,
 //   F = mu lambda [(f1/y)(I - n n^T) + (f1' - f1/y) u^ u^T]   (PSD as written).
-// Records (key = I * Ns + J, 3x3 block) are written at per-pair offsets, sorted stably by
-// key and summed per key in pair order: the result is bitwise repeatable.
+// Records (key = I * Ns + J, 3x3 block): the keys depend only on each item's cage nodes, so
+// they are written and stably sorted before the evaluation, which then writes every block to
+// its sorted position; each key's records are summed in a fixed order that depends only on
+// that key's own records (32-record units, then a fixed warp tree), so the result is bitwise
+// repeatable and the same for a scene alone or inside a batch.
 #include "geometry.cuh"
 #include "scene.cuh"
 #include "sort.cuh"
