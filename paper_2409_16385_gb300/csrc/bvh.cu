@@ -64,8 +64,8 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
 // dx4 is given): vbox[8v..8v+5] = lo xyz, hi xyz (rows of 8 floats), and vbox_pad the same
 // grown by pad in FP64 before rounding.  Outward rounding and the pad subtraction are
 // monotone, so the min / max over a primitive's vertices of these boxes is bit for bit the
-// box prim_box computes from the positions: the hierarchy and traversal read these instead
-// of recomputing FP64 minima per primitive.
+// box made from the primitive's FP64 positions (FP64 min / max, padded, rounded outward):
+// the hierarchy and traversal read these instead of recomputing FP64 minima per primitive.
 __global__ void __launch_bounds__(kBlock) k_vertex_boxes(int64_t nv, const double* __restrict__ x4,
                                                          const double* __restrict__ dx4, double pad,
                                                          float* __restrict__ vbox, float* __restrict__ vbox_pad) {
