@@ -67,6 +67,12 @@ def test_point_above_a_face_interior_is_kept():
     lit = oracle.pairs(sc, x)
     dd = oracle.dedup(sc, x, lit)
     assert len(lit["type"]) == 1 and len(dd["type"]) == 1
+    # two vertices over the same face are two feature pairs: both kept
+    pts = np.array([[0.3, 0.3, 0.5 * DHAT], [0.2, 0.5, 0.7 * DHAT]])
+    sc, x = _scene(pts, surf, [[0, 1, 2]])
+    lit = oracle.pairs(sc, x)
+    dd = oracle.dedup(sc, x, lit)
+    assert len(lit["type"]) == 2 and len(dd["type"]) == 2
 
 
 def _feature(sc, x, t, i, j, edge_of):

@@ -75,6 +75,23 @@ def test_hvp_of_a_kinematic_shift_matches_central_differences():
         assert np.abs(fd - hv).max() <= 1e-7 * scale, axis
 
 
+def test_kinematic_sum_balances_the_reduced_rows():
+    """The contact potential is invariant under a common translation of every vertex (on
+    each side of a pair the closest-point weights sum to 1, resp. -1), so its Hessian
+    times any u sums to zero over all vertices.  The embedding weights of a vertex sum to 1,
+    so the reduced rows sum to the embedded vertices' part: the kinematic sum is minus the
+    sum of the reduced rows."""
+    sc, q, prs, lag = _setup()
+    x = oracle.embed(sc, q)
+    r = np.random.default_rng(3)
+    for _ in range(3):
+        u = r.normal(size=(sc.Nv, 3))
+        hv, kin_sum = oracle.hvp(sc, x, prs, lag, u)
+        scale = np.abs(hv).sum(0).max()
+        assert np.abs(kin_sum).max() > 1e-3 * scale
+        assert np.abs(kin_sum + hv.sum(0)).max() <= 1e-10 * scale
+
+
 def test_mixed_blocks_are_symmetric():
     sc, q, prs, lag = _setup()
     kin = sc.kinematic

@@ -70,7 +70,11 @@ def test_no_change_above_the_threshold_and_continuity_at_it():
     E, g, H = oracle.pair_barrier_mollified(x4, eps, DHAT, KAPPA)
     E0, g0, H0, _ = oracle.pair_barrier(1, x4, DHAT, KAPPA)
     assert E == E0 and np.array_equal(g, g0) and np.array_equal(H, H0)
+    # also where c is only a little above eps_x: m = 1 for every c >= eps_x
     x4 = _edges(4e-3)
+    E, g, H = oracle.pair_barrier_mollified(x4, _c(x4) / 1.5, DHAT, KAPPA)
+    E0, g0, H0, _ = oracle.pair_barrier(1, x4, DHAT, KAPPA)
+    assert E == E0 and np.array_equal(g, g0) and np.array_equal(H, H0)
     c = _c(x4)
     lo = oracle.pair_barrier_mollified(x4, c * (1 - 1e-9), DHAT, KAPPA)
     hi = oracle.pair_barrier_mollified(x4, c * (1 + 1e-9), DHAT, KAPPA)

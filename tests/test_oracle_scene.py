@@ -215,6 +215,38 @@ def test_pair_set_known_configuration():
     assert (prs["type"] == 1).sum() == 0
 
 
+def test_friction_lag_is_the_lagged_contact_force():
+    """The lagged state of Sec. III-B, pinned to the per-pair barrier gradient: lambda is the
+    magnitude of the contact force at x^n, i.e. of the barrier gradient summed over one side
+    of the pair (moving a side rigidly by delta changes d by n . delta); n is the direction in
+    which that side's distance grows; the anchor joins the closest points, so its length is
+    the pair distance; gamma holds barycentric weights of the closest points, nonnegative
+    and summing to 1 on side A, to -1 on side B."""
+    sc = _scene(1)
+    p = sc.params
+    x = oracle.embed(sc, sc.iterate(0))
+    prs = oracle.pairs(sc, x)
+    lag = oracle.friction_lag(sc, x, prs)
+    n_pairs = len(prs["type"])
+    assert n_pairs > 20
+    for k in range(0, n_pairs, max(1, n_pairs // 200)):
+        t, i, j = prs["type"][k], prs["i"][k], prs["j"][k]
+        s = _stencil(sc, t, i, j)
+        assert np.array_equal(lag["v"][k], s)
+        _, g, _, _ = oracle.pair_barrier(t, x[s].ravel(), p["dhat"], p["kappa"])
+        side_a = 1 if t == 0 else 2
+        force = g.reshape(4, 3)[:side_a].sum(0)
+        fn = np.linalg.norm(force)
+        assert abs(lag["lam"][k] - fn) <= 1e-10 * fn
+        n = lag["n"][k]
+        assert abs(np.linalg.norm(n) - 1.0) <= 1e-14
+        assert n @ force <= -(1.0 - 1e-9) * fn          # b' < 0: the force pushes along n
+        assert abs(np.linalg.norm(lag["anchor"][k]) - prs["d"][k]) <= 1e-12 * prs["d"][k]
+        gam = lag["gamma"][k]
+        assert np.all(gam[:side_a] >= -1e-15) and np.all(gam[side_a:] <= 1e-15)
+        assert abs(gam[:side_a].sum() - 1.0) <= 1e-14 and abs(gam[side_a:].sum() + 1.0) <= 1e-14
+
+
 # ----------------------------------------------------------------------- CCD step bound
 
 def test_ca_point_plane_constant_velocity():
@@ -250,6 +282,31 @@ def test_ca_separating_and_edges():
     # tangential sliding at constant gap never stops the step
     dx4 = np.array([0.5, 0, 0, 0.5, 0, 0, 0, 0, 0, 0, 0, 0], float)
     assert oracle.ca_pair(1, x4, dx4)[0] == 1.0
+
+
+def test_ca_bound_depends_only_on_relative_motion():
+    """Advancement removes the stencil's mean displacement (Sec. III-C, the accumulated CCD
+    reading), so a common translation added to all four displacements leaves the bound
+    unchanged up to rounding, however large it is."""
+    r = np.random.default_rng(5)
+    T = np.array([[-1.0, -1.0, 0.0], [2.0, -1.0, 0.0], [-1.0, 2.0, 0.0]]) * 1e-2
+    stopped = 0
+    for trial in range(30):
+        ptype = trial % 2
+        if ptype == 0:
+            x4 = np.concatenate([[1e-3, 2e-3, 1e-3], T.ravel()])
+        else:
+            gap = 1e-3
+            x4 = np.array([-1e-2, 0, 0, 1e-2, 0, 0, 0, -1e-2, gap, 0, 1e-2, gap], float)
+        dx4 = r.normal(size=12) * 1e-3
+        # side A closes on side B along z at 2e-3 per unit step, plus random relative motion
+        dx4[2::3] += (np.array([1.0, 1.0, -1.0, -1.0]) if ptype else np.array([-1.0, 0.0, 0.0, 0.0])) * 2e-3
+        t0 = oracle.ca_pair(ptype, x4, dx4, s=0.1)[0]
+        u = r.normal(size=3) * 5e-2
+        t1 = oracle.ca_pair(ptype, x4, dx4 + np.tile(u, 4), s=0.1)[0]
+        assert abs(t1 - t0) <= 1e-9 * t0, (trial, t0, t1)
+        stopped += t0 < 1.0
+    assert stopped >= 20
 
 
 def test_ca_iteration_cap_returns_safe_time():

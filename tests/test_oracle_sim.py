@@ -8,6 +8,7 @@ stress.  Mass: total mass and weight against the enclosed volume.  Driver: the c
 step satisfies its optimality condition, lowers the incremental potential and leaves the
 surfaces apart.  Adjoint: against central differences of the whole trajectory.
 """
+import dataclasses
 import functools
 
 import numpy as np
@@ -103,6 +104,40 @@ def test_volumes_mass_and_weight():
     assert abs(m.M.sum() - rho * vol) <= 1e-12 * rho * vol          # sum of weights is 1
     assert np.allclose(m.f_ext.sum(0), rho * vol * sc.gravity, rtol=1e-12)
     assert np.allclose(m.M, m.M.T) and np.linalg.eigvalsh(m.M).min() > -1e-15
+
+
+def test_reduced_mass_is_the_kinetic_energy_through_the_embedding():
+    """M^q = J^T M J (Sec. III-D): for any reduced velocity v, v^T M^q v equals the lumped
+    full-space kinetic form sum_k rho V_k |(J v)_k|^2, with J v taken by the embedding."""
+    sc, m = _model()
+    Vk = sim.vertex_volumes(sc)
+    rho = sc.material["rho"]
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        v = rng.normal(size=(sc.Ns, 3))
+        xv = oracle.embed(sc, v, displacement=True)
+        full = float(np.sum(rho * Vk[:, None] * xv * xv))
+        assert abs(float(np.sum(v * (m.M @ v))) - full) <= 1e-12 * full
+
+
+def test_free_flight_of_a_rigid_translation_is_exact():
+    """Far from any contact and with every cage node free, a body translated rigidly and
+    moving at constant velocity takes one backward-Euler step exactly
+    (Sec. III-A): q^{n+1} = 2 q^n - q^{n-1} + h^2 g.  The elastic forces of a translation
+    vanish, and J^T M J applied to a uniform field is J^T f_ext / g, since the weights sum
+    to 1."""
+    sc, m = _model()
+    active = np.zeros(sc.Ns, bool)
+    active[sc.cage_tets[m.V_T > 0].ravel()] = True
+    m_free = dataclasses.replace(m, free=active)
+    up = np.array([0.0, 0.0, 1.0])                   # a metre from the pad and its motion
+    qp = sc.q0 + up
+    vel = np.array([1e-3, -2e-3, 5e-4])
+    q, it = sim.newton_step(m_free, qp, qp - vel, np.zeros(3), sc.params["kappa"], None)
+    h = sc.params["h"]
+    expect = qp + vel + h * h * sc.gravity
+    assert it <= 3
+    assert np.abs(q[active] - expect[active]).max() <= 1e-12
 
 
 def test_elastic_gradient_and_hessian_match_central_differences():
