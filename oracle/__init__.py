@@ -22,15 +22,21 @@ _SRCS = ["oracle.cpp", "ad.hpp", "geometry.hpp", "predicates.hpp"]
 _lib = None
 
 
+def compile_so(src_dir: str, out: str) -> None:
+    """Compiles oracle.cpp (and the headers beside it) from src_dir into the shared library
+    `out`, written under a temporary name first."""
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           os.path.join(src_dir, "oracle.cpp"), "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, out)
+
+
 def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     src_time = max(os.path.getmtime(os.path.join(_HERE, s)) for s in _SRCS)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < src_time:
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-               os.path.join(_HERE, "oracle.cpp"), "-o", tmp]
-        subprocess.check_call(cmd)
-        os.replace(tmp, _SO)
+        compile_so(_HERE, _SO)
     return _SO
 
 
@@ -38,49 +44,53 @@ def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_SO)
-        P = ctypes.c_void_p
-        i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-        L.orc_embed.argtypes = [i64, P, P, P, P, P]
-        L.orc_pair_d2.argtypes = [ctypes.c_int, P, P, P]
-        L.orc_pair_d2.restype = dbl
-        L.orc_barrier.argtypes = [dbl, dbl, P]
-        L.orc_f0.argtypes = [dbl, dbl, P]
-        L.orc_pair_barrier.argtypes = [ctypes.c_int, P, dbl, dbl, P, P, P, P]
-        L.orc_psd_project.argtypes = [ctypes.c_int, P, P]
-        L.orc_eigen.argtypes = [ctypes.c_int, P, P, P]
-        L.orc_pairs.argtypes = [i64, P, P, i64, P, i64, P, dbl, i64, P, P, P, P]
-        L.orc_pairs.restype = i64
-        L.orc_pairs_of.argtypes = [i64, P, P, i64, P, i64, P, dbl, ctypes.c_int, i64, P, i64, P, P, P]
-        L.orc_pairs_of.restype = i64
-        L.orc_friction_lag.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, dbl, dbl, P, P, P, P, P]
-        L.orc_eval.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
-                               dbl, dbl, dbl, dbl, ctypes.c_int]
-        L.orc_eval.restype = P
-        L.orc_hvp.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
-                              dbl, dbl, dbl, dbl, P, P, P]
-        L.orc_dedup.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, P]
-        L.orc_set_mollifier.argtypes = [i64, P, dbl]
-        L.orc_pair_barrier_mollified.argtypes = [P, dbl, dbl, dbl, P, P, P]
-        L.orc_result_nnzb.argtypes = [P]
-        L.orc_result_nnzb.restype = i64
-        L.orc_result_copy.argtypes = [P, P, P, P, P, P, P]
-        L.orc_result_free.argtypes = [P]
-        L.orc_pair_friction.argtypes = [P, P, P, P, dbl, P, dbl, dbl, P, P, P]
-        L.orc_ca_pair.argtypes = [ctypes.c_int, P, P, dbl, ctypes.c_int, P, P]
-        L.orc_ca_pair.restype = dbl
-        L.orc_accd.argtypes = [i64, P, P, P, i64, P, i64, P, dbl, ctypes.c_int, P, P, P]
-        L.orc_accd.restype = dbl
-        L.orc_accd_list.argtypes = [i64, P, P, P, i64, P, P, i64, P, i64, P, dbl, ctypes.c_int, P]
-        L.orc_accd_list.restype = dbl
-        L.orc_accd_of.argtypes = [i64, P, P, P, i64, P, i64, P, dbl, ctypes.c_int, ctypes.c_int, i64, P, P, P]
-        L.orc_accd_of.restype = dbl
-        L.orc_intersection_free.argtypes = [i64, P, i64, P, i64, P]
-        L.orc_intersection_free.restype = ctypes.c_int
-        L.orc_num_threads.restype = ctypes.c_int
-        L.orc_set_threads.argtypes = [ctypes.c_int]
-        _lib = L
+        _lib = bind(ctypes.CDLL(_SO))
     return _lib
+
+
+def bind(L):
+    """Declares the argument and result types of every entry point of a loaded oracle."""
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    L.orc_embed.argtypes = [i64, P, P, P, P, P]
+    L.orc_pair_d2.argtypes = [ctypes.c_int, P, P, P]
+    L.orc_pair_d2.restype = dbl
+    L.orc_barrier.argtypes = [dbl, dbl, P]
+    L.orc_f0.argtypes = [dbl, dbl, P]
+    L.orc_pair_barrier.argtypes = [ctypes.c_int, P, dbl, dbl, P, P, P, P]
+    L.orc_psd_project.argtypes = [ctypes.c_int, P, P]
+    L.orc_eigen.argtypes = [ctypes.c_int, P, P, P]
+    L.orc_pairs.argtypes = [i64, P, P, i64, P, i64, P, dbl, i64, P, P, P, P]
+    L.orc_pairs.restype = i64
+    L.orc_pairs_of.argtypes = [i64, P, P, i64, P, i64, P, dbl, ctypes.c_int, i64, P, i64, P, P, P]
+    L.orc_pairs_of.restype = i64
+    L.orc_friction_lag.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, dbl, dbl, P, P, P, P, P]
+    L.orc_eval.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
+                           dbl, dbl, dbl, dbl, ctypes.c_int]
+    L.orc_eval.restype = P
+    L.orc_hvp.argtypes = [i64, P, i64, P, i64, P, P, P, i64, i64, P, P, P, i64, P, P, P, P, P,
+                          dbl, dbl, dbl, dbl, P, P, P]
+    L.orc_dedup.argtypes = [i64, P, i64, P, i64, P, i64, P, P, P, P]
+    L.orc_set_mollifier.argtypes = [i64, P, dbl]
+    L.orc_pair_barrier_mollified.argtypes = [P, dbl, dbl, dbl, P, P, P]
+    L.orc_result_nnzb.argtypes = [P]
+    L.orc_result_nnzb.restype = i64
+    L.orc_result_copy.argtypes = [P, P, P, P, P, P, P]
+    L.orc_result_free.argtypes = [P]
+    L.orc_pair_friction.argtypes = [P, P, P, P, dbl, P, dbl, dbl, P, P, P]
+    L.orc_ca_pair.argtypes = [ctypes.c_int, P, P, dbl, ctypes.c_int, P, P]
+    L.orc_ca_pair.restype = dbl
+    L.orc_accd.argtypes = [i64, P, P, P, i64, P, i64, P, dbl, ctypes.c_int, P, P, P]
+    L.orc_accd.restype = dbl
+    L.orc_accd_list.argtypes = [i64, P, P, P, i64, P, P, i64, P, i64, P, dbl, ctypes.c_int, P]
+    L.orc_accd_list.restype = dbl
+    L.orc_accd_of.argtypes = [i64, P, P, P, i64, P, i64, P, dbl, ctypes.c_int, ctypes.c_int, i64, P, P, P]
+    L.orc_accd_of.restype = dbl
+    L.orc_intersection_free.argtypes = [i64, P, i64, P, i64, P]
+    L.orc_intersection_free.restype = ctypes.c_int
+    L.orc_num_threads.restype = ctypes.c_int
+    L.orc_set_threads.argtypes = [ctypes.c_int]
+    return L
 
 
 def _p(a: np.ndarray):
