@@ -55,6 +55,9 @@ CA_EDGES = ("test_oracle_scene", "test_ca_separating_and_edges", [()])
 CA_CAP = ("test_oracle_scene", "test_ca_iteration_cap_returns_safe_time", [()])
 ACCD = ("test_oracle_scene", "test_accd_no_penetration_after_accepted_step_config1", [()])
 CA_REL = ("test_oracle_scene", "test_ca_bound_depends_only_on_relative_motion", [()])
+ACCD_SAMPLED = ("test_oracle_scene", "test_restricted_step_bounds_match_the_full_one", [()])
+PAIRS_EE_SAMPLED = ("test_oracle_scene", "test_restricted_edge_pairs_match_the_full_set", [()])
+NO_PENETRATION = ("test_oracle_scene", "test_trajectories_are_intersection_free_small", [()])
 LAG = ("test_oracle_scene", "test_friction_lag_is_the_lagged_contact_force", [()])
 HVP_FD = ("test_oracle_hvp", "test_hvp_matches_central_differences_of_the_gradient", [()])
 HVP_KIN = ("test_oracle_hvp", "test_hvp_of_a_kinematic_shift_matches_central_differences", [()])
@@ -143,6 +146,16 @@ MUTANTS = [
     ("accd_unswept_boxes", "oracle.cpp",
      "Box a = prim_box(m0, type, i, side_a, x), b = prim_box(m1, type, i, side_a, x1.data());",
      "Box a = prim_box(m0, type, i, side_a, x), b = a;", [ACCD]),
+    ("accd_sampled_update", "oracle.cpp", "++ncand; iters += n;\n      if (t < alpha) alpha = t;",
+     "++ncand; iters += n;\n      if (t < 0.0) alpha = t;", [ACCD_SAMPLED]),
+    ("accd_list_update", "oracle.cpp", "iters += n;\n    if (t < alpha) alpha = t;",
+     "iters += n;\n    if (t < 0.0) alpha = t;", [ACCD_SAMPLED]),
+    ("pairs_sampled_order", "oracle.cpp", "if (type == 1 && j < i) std::swap(i, j);\n      int32_t s[4];",
+     "int32_t s[4];", [PAIRS_EE_SAMPLED]),
+    ("pairs_sampled_range", "oracle.cpp", "if (d > 0.0 && d < dhat) out.push_back",
+     "if (d > 0.0 && d < 1.5 * dhat) out.push_back", [PAIRS_EE_SAMPLED, PAIRS]),
+    ("intersection_decision", "predicates.hpp", "return !(has_pos && has_neg);", "return has_pos && has_neg;",
+     [ACCD, NO_PENETRATION]),
     # the exact Hessian-vector product
     ("hvp_operand", "oracle.cpp", "acc += L.H[i * 12 + j] * u4[j];", "acc += L.H[i * 12 + j] * u4[i];",
      [HVP_FD, HVP_H]),

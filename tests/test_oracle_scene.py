@@ -309,6 +309,96 @@ def test_ca_bound_depends_only_on_relative_motion():
     assert stopped >= 20
 
 
+def _sheets(n=4, gap=1e-3, seed=0):
+    """Two n x n vertex grids of triangles, the lower one kinematic, the upper one closing
+    on it by twice the gap with a random jitter per vertex."""
+    r = np.random.default_rng(seed)
+    g = np.stack(np.meshgrid(np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 2) * 2e-3
+    lo = np.concatenate([g, np.zeros((n * n, 1))], 1)
+    hi = np.concatenate([g + 7e-4, np.full((n * n, 1), gap)], 1)
+    quads = [(i * n + j, (i + 1) * n + j, i * n + j + 1, (i + 1) * n + j + 1)
+             for i in range(n - 1) for j in range(n - 1)]
+    tri = np.array([t for a, b, c, d in quads for t in ((a, b, c), (b, d, c))], np.int32)
+    tris = np.concatenate([tri, tri + n * n]).astype(np.int32)
+    V = np.concatenate([lo, hi])
+    nv = len(V)
+    cage_idx = np.full((nv, 4), -1, np.int32)
+    cage_idx[n * n:] = 0
+    sc = scenes.Scene(name="sheets", tris=tris, edges=scenes.edges_of(tris), cage_idx=cage_idx,
+                      w=np.zeros((nv, 4)), x_kin=V, Ns=1, cage_tets=np.zeros((0, 4), np.int32),
+                      q_rest=np.zeros((1, 3)), body=np.zeros(nv, np.int32), params=dict(scenes.DEFAULT_PARAMS))
+    dx = np.zeros_like(V)
+    dx[n * n:] = r.normal(size=(n * n, 3)) * 3e-4 + np.array([0.0, 0.0, -2.0 * gap])
+    return sc, V, dx
+
+
+def _swept_candidates(sc, x, dx):
+    """Every non-incident, not all-kinematic PT and EE pair whose swept boxes (over the
+    start and end positions of its vertices) overlap, by brute force."""
+    x1 = x + dx
+    kin = sc.kinematic
+
+    def boxes(ids):
+        pts = np.concatenate([x[ids], x1[ids]], axis=1)
+        return pts.min(1), pts.max(1)
+
+    vlo, vhi = boxes(np.arange(sc.Nv)[:, None])
+    flo, fhi = boxes(sc.tris)
+    elo, ehi = boxes(sc.edges)
+    out = {"type": [], "i": [], "j": []}
+    for v in range(sc.Nv):
+        for f in range(sc.F):
+            st = np.array([v, *sc.tris[f]])
+            if v in sc.tris[f] or kin[st].all():
+                continue
+            if np.all(vlo[v] <= fhi[f]) and np.all(flo[f] <= vhi[v]):
+                out["type"].append(0); out["i"].append(v); out["j"].append(f)
+    for e in range(sc.E):
+        for g in range(e + 1, sc.E):
+            st = np.array([*sc.edges[e], *sc.edges[g]])
+            if len(set(st.tolist())) < 4 or kin[st].all():
+                continue
+            if np.all(elo[e] <= ehi[g]) and np.all(elo[g] <= ehi[e]):
+                out["type"].append(1); out["i"].append(e); out["j"].append(g)
+    return {k: np.array(v, np.int32) for k, v in out.items()}
+
+
+def test_restricted_step_bounds_match_the_full_one():
+    """The sampled forms of the step bound: over a brute-force list of the swept-box
+    candidates, and over the pairs of given query primitives, they reach the full bound
+    exactly (the same pairs advanced the same way)."""
+    sc, x, dx = _sheets()
+    full = oracle.accd(sc, x, dx)
+    assert 0.0 < full["alpha"] < 1.0
+    cand = _swept_candidates(sc, x, dx)
+    assert full["n_candidates"] == len(cand["type"])
+    assert oracle.accd_list(sc, x, dx, cand)["alpha"] == full["alpha"]
+    a_v = oracle.accd_of(sc, x, dx, 0, np.arange(sc.Nv))
+    a_e = oracle.accd_of(sc, x, dx, 1, np.arange(sc.E))
+    assert min(a_v["alpha"], a_e["alpha"]) == full["alpha"]
+    n_pt = int((cand["type"] == 0).sum())
+    assert a_v["n_candidates"] == n_pt and a_e["n_candidates"] == 2 * (len(cand["type"]) - n_pt)
+    # a subset of queries never bounds the step more tightly than all of them
+    assert oracle.accd_of(sc, x, dx, 1, np.arange(0, sc.E, 3))["alpha"] >= full["alpha"]
+
+
+def test_restricted_edge_pairs_match_the_full_set():
+    """EE pairs of sampled edges are exactly the full set's EE pairs that have one of those
+    edges as a side, in (i, j) order with i < j; a pair with both sides among the queries
+    is listed once per side."""
+    sc = _scene(1)
+    x = oracle.embed(sc, sc.iterate(0))
+    prs = oracle.pairs(sc, x)
+    ee = np.nonzero(prs["type"] == 1)[0]
+    i, j, d = prs["i"][ee], prs["j"][ee], prs["d"][ee]
+    q = np.unique(np.concatenate([i[:6], j[-6:], [j[0], 0, 17]]))
+    sub = oracle.pairs_of(sc, x, 1, q)
+    times = np.isin(i, q).astype(int) + np.isin(j, q).astype(int)
+    assert (times > 0).sum() > 6 and (times == 2).any()
+    assert np.array_equal(sub["i"], np.repeat(i, times)) and np.array_equal(sub["j"], np.repeat(j, times))
+    assert np.array_equal(sub["d"], np.repeat(d, times))
+
+
 def test_ca_iteration_cap_returns_safe_time():
     T = np.array([[-1.0, -1.0, 0.0], [2.0, -1.0, 0.0], [-1.0, 2.0, 0.0]])
     x4 = np.concatenate([[0.1, 0.2, 1e-3], T.ravel()])
