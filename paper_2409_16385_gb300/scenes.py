@@ -653,10 +653,17 @@ def plate_in_rack(seed: int = 0, plate_cells=(150, 100), n_tines: int = 10,
 
 
 def _grid_dims(n_nodes: float, ext) -> Tuple[int, int, int]:
-    """Cube counts of a cage grid over a box with extents `ext` holding about n_nodes nodes."""
+    """Cube counts (c_x, c_y, c_z) of a cage grid over a box with extents `ext` whose node
+    count prod(c_i + 1) is closest to n_nodes (in ratio), for near-cubic cells."""
     ext = np.asarray(ext, float)
-    h = (np.prod(ext) / max(n_nodes, 8.0)) ** (1.0 / 3.0)
-    return tuple(int(max(1, round(e / h))) for e in ext)
+    target = max(float(n_nodes), 8.0)
+    best, best_err = (1, 1, 1), np.inf
+    for h in np.geomspace(ext.max(), ext.min() / 64.0, 2000):
+        dims = tuple(int(max(1, round(e / h))) for e in ext)
+        err = abs(np.log(np.prod(np.array(dims) + 1.0) / target))
+        if err < best_err:
+            best, best_err = dims, err
+    return best
 
 
 def batched_grasp(n_scenes: int = 256, seed: int = 0, min_tris: int = 2000, max_tris: int = 50000,
