@@ -49,6 +49,11 @@ enum { PT_FACE = 0 };
 template <class T>
 T point_segment_d2(const V3<T>& p, const V3<T>& a, const V3<T>& b, double* tout) {
   V3<T> e = b - a;
+  if (val(dot(e, e)) == 0.0) {  // a segment of zero length is its point
+    *tout = 0.0;
+    V3<T> r = p - a;
+    return dot(r, r);
+  }
   T t = dot(p - a, e) / dot(e, e);
   if (val(t) <= 0.0) {
     t = T(0.0);

@@ -104,6 +104,26 @@ def test_ee_closed_forms():
     assert np.isclose(d2, 0.25) and reg == 7
 
 
+def test_degenerate_primitives():
+    """A triangle with collinear vertices is the segment they span, and a zero-length edge is
+    its point: the distances reduce to point-segment and point-point closed forms."""
+    # collinear triangle on the x axis from 0 to 2 (vertex t2 in the middle)
+    t0, t1, t2 = np.array([0.0, 0.0, 0.0]), np.array([2.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0])
+    for p, expect in [((0.5, 0.3, 0.4), 0.25), ((-1.0, 0.0, 1.0), 2.0), ((1.5, -0.2, 0.0), 0.04)]:
+        d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t0, t1, t2]))
+        assert np.isfinite(d2) and np.isclose(d2, expect, rtol=1e-14), (p, d2)
+        assert reg != 0 and np.all(np.isfinite(c)) and abs(c.sum()) < 1e-14
+    # a triangle collapsed to one point
+    P = np.array([0.3, -0.2, 0.1])
+    d2, reg, _ = oracle.pair_d2(0, np.concatenate([[1.0, 1.0, 1.0], P, P, P]))
+    assert np.isclose(d2, np.sum((np.array([1.0, 1.0, 1.0]) - P) ** 2), rtol=1e-14) and reg >= 4
+    # edge-edge with one edge of zero length: point-segment distance
+    a0 = a1 = np.array([0.5, 0.7, 0.2])
+    b0, b1 = np.array([0.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0])
+    d2, reg, c = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+    assert np.isclose(d2, 0.49 + 0.04, rtol=1e-14) and np.all(np.isfinite(c))
+
+
 def test_distance_invariant_under_rigid_motion():
     for ptype in (0, 1):
         X = rng.normal(size=(4, 3))
