@@ -35,6 +35,7 @@ GEO_PT = ("test_oracle_geometry", "test_pt_distance_vs_sampling", [(t,) for t in
 GEO_EE = ("test_oracle_geometry", "test_ee_distance_vs_sampling", [(t,) for t in range(40)])
 GEO_PT_CF = ("test_oracle_geometry", "test_pt_closed_forms", [()])
 GEO_EE_CF = ("test_oracle_geometry", "test_ee_closed_forms", [()])
+GEO_DEGEN = ("test_oracle_geometry", "test_degenerate_primitives", [()])
 BARRIER = ("test_oracle_potentials", "test_barrier_closed_form_and_boundary", [()])
 F0 = ("test_oracle_potentials", "test_f0_matches_integral_of_f1", [()])
 PAIR_FD = ("test_oracle_potentials", "test_barrier_derivatives_vs_central_differences",
@@ -110,6 +111,8 @@ MUTANTS = [
      [GEO_EE, GEO_EE_CF, FRICTION, DEDUP_SCENES]),
     ("segment_no_lower_clamp", "geometry.hpp", "  if (val(t) <= 0.0) {\n    t = T(0.0);",
      "  if (val(t) <= -1e300) {\n    t = T(0.0);", [GEO_PT, GEO_EE]),
+    ("segment_zero_length", "geometry.hpp", "if (val(dot(e, e)) == 0.0) {", "if (val(dot(e, e)) < 0.0) {",
+     [GEO_DEGEN]),
     # projection to the nearest PSD matrix (Sec. III-C)
     ("jacobi_rotation_sign", "oracle.cpp", "A[k * n + q] = s * akp + c * akq;",
      "A[k * n + q] = s * akp - c * akq;", [PSD, PSD_PAIR]),
