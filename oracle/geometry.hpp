@@ -7,7 +7,8 @@
 // that minimum:
 //   PT: project p onto the triangle's plane; if the projection's barycentrics are all
 //       >= 0 the projection is the closest point, otherwise the minimum lies on the
-//       boundary and is the smallest of the three point-segment distances.
+//       boundary and is the smallest of the three point-segment distances.  (A triangle
+//       with collinear vertices has no plane: the smallest edge distance decides.)
 //   EE: the squared distance is a convex quadratic in the segment parameters (s,t); if
 //       its unconstrained minimiser lies in [0,1]^2 it is the answer, otherwise (or if the
 //       segments are parallel to within |ea x eb|^2 <= 1e-20 |ea|^2 |eb|^2) the minimum is
@@ -17,6 +18,7 @@
 // second derivatives (AD).  Each routine also reports the closest-point stencil c[4] with
 // r = sum_a c_a x_a = (point on side A) - (point on side B), used for lagged friction.
 #pragma once
+#include <algorithm>
 #include <cmath>
 
 #include "ad.hpp"
@@ -76,9 +78,24 @@ T pt_d2(const V3<T>& p, const V3<T>& t0, const V3<T>& t1, const V3<T>& t2, int* 
   T b2 = (a * e - b * d) / det;
   if (val(b1) >= 0.0 && val(b2) >= 0.0 && val(b1) + val(b2) <= 1.0) {
     V3<T> r = r0 - e1 * b1 - e2 * b2;
-    *region = PT_FACE;
-    c[0] = 1.0; c[1] = -(1.0 - val(b1) - val(b2)); c[2] = -val(b1); c[3] = -val(b2);
-    return dot(r, r);
+    T d2 = dot(r, r);
+    // The face point lies in the closed triangle, so no edge is closer unless the solve
+    // was singular (a triangle with collinear vertices, where det is rounding noise and
+    // any point of the triangle can come out).  The distance is the minimum over the
+    // closed triangle: an edge closer by more than rounding (1e-13 relative; a regular
+    // triangle's edges are never closer than its face point) wins.
+    double t_unused;
+    const V3<double> pv = {val(p.x), val(p.y), val(p.z)};
+    const V3<double> q0 = {val(t0.x), val(t0.y), val(t0.z)}, q1 = {val(t1.x), val(t1.y), val(t1.z)},
+                     q2 = {val(t2.x), val(t2.y), val(t2.z)};
+    const double edges = std::min(point_segment_d2(pv, q0, q1, &t_unused),
+                                  std::min(point_segment_d2(pv, q1, q2, &t_unused),
+                                           point_segment_d2(pv, q2, q0, &t_unused)));
+    if (!(edges < val(d2) * (1.0 - 1e-13))) {
+      *region = PT_FACE;
+      c[0] = 1.0; c[1] = -(1.0 - val(b1) - val(b2)); c[2] = -val(b1); c[3] = -val(b2);
+      return d2;
+    }
   }
   const V3<T>* tv[3] = {&t0, &t1, &t2};
   T best(0.0);

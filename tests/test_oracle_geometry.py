@@ -113,6 +113,18 @@ def test_degenerate_primitives():
         d2, reg, c = oracle.pair_d2(0, np.concatenate([p, t0, t1, t2]))
         assert np.isfinite(d2) and np.isclose(d2, expect, rtol=1e-14), (p, d2)
         assert reg != 0 and np.all(np.isfinite(c)) and abs(c.sum()) < 1e-14
+    # random exactly collinear triangles (the 2x2 solve is singular, its determinant only
+    # rounding): the distance to the segment they span
+    r = np.random.default_rng(8)
+    for _ in range(500):
+        xs = r.uniform(-1e-3, 1e-3, 3)
+        T = np.zeros((3, 3)); T[:, 0] = xs
+        p = r.normal(size=3) * 1e-3
+        d2, _, c = oracle.pair_d2(0, np.concatenate([p, T.ravel()]))
+        t = np.clip(p[0], xs.min(), xs.max())
+        assert np.isclose(d2, (p[0] - t) ** 2 + p[1] ** 2 + p[2] ** 2, rtol=1e-12)
+        # the stencil weights still name the closest point
+        assert np.isclose(np.linalg.norm(c[0] * p + c[1:] @ T), np.sqrt(d2), rtol=1e-9)
     # a triangle collapsed to one point
     P = np.array([0.3, -0.2, 0.1])
     d2, reg, _ = oracle.pair_d2(0, np.concatenate([[1.0, 1.0, 1.0], P, P, P]))
