@@ -167,3 +167,65 @@ def test_pairs_at_the_dhat_boundary_match_the_oracle():
     assert kg == ko
     near = np.abs(o["d"] / dhat - 1.0) < 5e-3
     assert near.sum() >= 100          # the boundary cases really are in the set
+
+
+def test_degenerate_surface_primitives_match_the_oracle():
+    """A kinematic surface of degenerate triangles (three collinear vertices, two coincident
+    vertices, all three coincident) under embedded triangles at 0.3-0.8 dhat.  The
+    distance is the minimum over the closed primitive: a collinear triangle is the segment
+    it spans, a zero-length edge is its point.  Pair set, distances, E, g_r, H_r and the
+    step bound must match the oracle.  The closest-point weights on a degenerate triangle
+    are not unique, so friction is off (mu = 0) and only the embedded DoFs carry
+    derivatives."""
+    from paper_2409_16385_gb300 import ContactScene
+    rng = np.random.default_rng(21)
+    dhat = 1e-3
+    verts, tris, emb = [], [], []
+    for k in range(60):
+        o = np.array([0.01 * (k % 10), 0.01 * (k // 10), 0.0])
+        kind = k % 3
+        if kind == 0:          # collinear along x, middle vertex last
+            T = np.array([[-1e-3, 0, 0], [1e-3, 0, 0], [rng.uniform(-5e-4, 5e-4), 0, 0]])
+        elif kind == 1:        # two coincident vertices: a zero-length edge
+            T = np.array([[-1e-3, 0, 0], [1e-3, 0, 0], [1e-3, 0, 0]])
+        else:                  # all three coincident
+            T = np.zeros((3, 3))
+        h = rng.uniform(0.3, 0.8) * dhat
+        p = np.array([rng.uniform(-8e-4, 8e-4), rng.uniform(-2e-4, 2e-4), h])
+        up = np.array([p, p + [1.5e-3, 2e-4, 2.5e-3], p + [-2e-4, 1.5e-3, 2.5e-3]])
+        base = len(verts)
+        for v in T:
+            verts.append(v + o); emb.append(False)
+        for v in up:
+            verts.append(v + o); emb.append(True)
+        tris += [[base, base + 1, base + 2], [base + 3, base + 4, base + 5]]
+    verts = np.array(verts); tris = np.array(tris, np.int32); emb = np.array(emb)
+    nv = len(verts)
+    idx = np.full((nv, 4), -1, np.int32); w = np.zeros((nv, 4))
+    node_of = np.cumsum(emb) - 1
+    idx[emb, 0] = node_of[emb]; idx[emb, 1:] = node_of[emb][:, None]
+    w[emb, 0] = 1.0
+    xk = np.where(emb[:, None], 0.0, verts)
+    sc = scenes.Scene(name="degenerate", tris=tris, edges=scenes.edges_of(tris), cage_idx=idx, w=w, x_kin=xk,
+                      Ns=int(emb.sum()), cage_tets=np.zeros((0, 4), np.int32), q_rest=verts[emb].copy(),
+                      body=np.zeros(nv, np.int32), params=dict(scenes.DEFAULT_PARAMS, dhat=dhat, mu=0.0))
+    q = verts[emb].copy()
+    dq = np.tile([0.0, 0.0, -1.5e-3], (sc.Ns, 1))
+    from test_gpu_parity import check_eval, check_pairs
+    cs = ContactScene(sc, pair_capacity=1 << 14, bsr_capacity=1 << 14)
+    qd = _t(q)
+    pr = cs.build_candidates(qd)
+    E, g, H = cs.eval_contact(qd, pr, None)
+    x_g = cs.embed(qd)
+    dx_g = cs.embed(_t(dq), displacement=True)
+    a = cs.accd_toi(x_g, dx_g).item()
+    torch.cuda.synchronize()
+    assert cs.status()["flags"] == 0
+    x = oracle.embed(sc, q)
+    po = oracle.pairs(sc, x)
+    assert len(po["type"]) >= 60
+    assert check_pairs(pr.host(), po, dhat) == len(po["type"])
+    ro = oracle.eval_contact(sc, x, po, None)
+    check_eval(E.item(), g.cpu().numpy(), H.host(), ro, sc.Ns)
+    ao = oracle.accd(sc, x, oracle.embed(sc, dq, displacement=True))["alpha"]
+    assert 0.0 < ao < 1.0 and a <= ao and ao - a <= 1e-6
