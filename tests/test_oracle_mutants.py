@@ -111,6 +111,8 @@ MUTANTS = [
      [GEO_EE, GEO_EE_CF, FRICTION, DEDUP_SCENES]),
     ("segment_no_lower_clamp", "geometry.hpp", "  if (val(t) <= 0.0) {\n    t = T(0.0);",
      "  if (val(t) <= -1e300) {\n    t = T(0.0);", [GEO_PT, GEO_EE]),
+    ("pt_face_without_edge_check", "geometry.hpp", "if (!(edges < val(d2) * (1.0 - 1e-13))) {",
+     "if (!(edges < -1.0)) {", [GEO_DEGEN]),
     ("segment_zero_length", "geometry.hpp", "if (val(dot(e, e)) == 0.0) {", "if (val(dot(e, e)) < 0.0) {",
      [GEO_DEGEN]),
     # projection to the nearest PSD matrix (Sec. III-C)
