@@ -65,3 +65,17 @@ def test_block_assembly_equals_the_dense_one():
     assert np.array_equal(dense != 0, cage.assemble_dense(Ht).numpy() != 0)
     assert np.abs(dense - cage.assemble_dense(Ht).numpy()).max() <= 1e-12 * np.abs(dense).max()
     assert np.all(np.diff(rp) > 0) and all(np.all(np.diff(cl[rp[I]:rp[I + 1]]) > 0) for I in range(cage.ns))
+
+
+@pytest.mark.parametrize("phys", [False, True])
+def test_vertex_volumes_match_the_oracle(phys):
+    """Per-vertex volumes (cones of each vertex's triangles to its body's centroid) of the
+    driver against the oracle's, on the pad-lift scene and on the three-body grasp."""
+    from paper_2409_16385_gb300.sim import _vertex_volumes
+    import oracle
+    sc = scenes.bubble_grasp_physical(small=True) if phys else scenes.make_config(5, small=True)
+    x = oracle.embed(sc, sc.q0)
+    V = _vertex_volumes(sc, torch.tensor(x)).numpy()
+    Vo = osim.vertex_volumes(sc)
+    assert np.abs(V - Vo).max() <= 1e-12 * np.abs(Vo).max()
+    assert np.all(V[sc.kinematic] == 0.0)
