@@ -224,6 +224,9 @@ def _build_one(mutant):
     digest = hashlib.sha256("\0".join(texts[f] for f in oracle._SRCS).encode()).hexdigest()[:16]
     so = os.path.join(d, f"liboracle_{digest}.so")       # a new path per source: dlopen caches by path
     if not os.path.exists(so):
+        for old_so in os.listdir(d):                     # builds of earlier sources
+            if old_so.startswith("liboracle_") and old_so.endswith(".so"):
+                os.remove(os.path.join(d, old_so))
         for f in oracle._SRCS:
             with open(os.path.join(d, f), "w") as fh:
                 fh.write(texts[f])
