@@ -223,10 +223,10 @@ def _build_one(mutant):
     texts[fname] = texts[fname].replace(old, new)
     digest = hashlib.sha256("\0".join(texts[f] for f in oracle._SRCS).encode()).hexdigest()[:16]
     so = os.path.join(d, f"liboracle_{digest}.so")       # a new path per source: dlopen caches by path
+    for old_so in os.listdir(d):                         # builds of earlier sources
+        if old_so.startswith("liboracle_") and old_so.endswith(".so") and old_so != os.path.basename(so):
+            os.remove(os.path.join(d, old_so))
     if not os.path.exists(so):
-        for old_so in os.listdir(d):                     # builds of earlier sources
-            if old_so.startswith("liboracle_") and old_so.endswith(".so"):
-                os.remove(os.path.join(d, old_so))
         for f in oracle._SRCS:
             with open(os.path.join(d, f), "w") as fh:
                 fh.write(texts[f])
