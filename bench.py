@@ -240,14 +240,17 @@ def oracle_sample(sc, t, frac, seed=0):
     q, qn = sc.iterate(t), sc.iterate(sc.lag_of(t))
     t0 = time.perf_counter()
     x, xn = oracle.embed(sc, q), oracle.embed(sc, qn)
-    pv = oracle.pairs_of(sc, x, 0, qv)
-    pe = oracle.pairs_of(sc, x, 1, qe)
-    prs = dict(type=np.concatenate([np.zeros(len(pv["i"]), np.int32), np.ones(len(pe["i"]), np.int32)]),
-               i=np.concatenate([pv["i"], pe["i"]]), j=np.concatenate([pv["j"], pe["j"]]))
-    pvn = oracle.pairs_of(sc, xn, 0, qv)
-    pen = oracle.pairs_of(sc, xn, 1, qe)
-    prn = dict(type=np.concatenate([np.zeros(len(pvn["i"]), np.int32), np.ones(len(pen["i"]), np.int32)]),
-               i=np.concatenate([pvn["i"], pen["i"]]), j=np.concatenate([pvn["j"], pen["j"]]))
+    def sampled_pairs(xx):
+        pv = oracle.pairs_of(sc, xx, 0, qv)
+        pe = oracle.pairs_of(sc, xx, 1, qe)
+        # an EE pair with both edges among the queries is listed once per side: keep one
+        ee = np.unique(np.stack([pe["i"], pe["j"]], 1), axis=0).reshape(-1, 2)
+        return dict(type=np.concatenate([np.zeros(len(pv["i"]), np.int32), np.ones(len(ee), np.int32)]),
+                    i=np.concatenate([pv["i"], ee[:, 0]]).astype(np.int32),
+                    j=np.concatenate([pv["j"], ee[:, 1]]).astype(np.int32))
+
+    prs = sampled_pairs(x)
+    prn = sampled_pairs(xn)
     lag = oracle.friction_lag(sc, xn, prn)
     oracle.eval_contact(sc, x, prs, lag)
     dx = oracle.embed(sc, sc.dq(t), displacement=True)

@@ -86,3 +86,14 @@ def test_capacities_grow_only_where_the_device_overflowed():
     assert out["cand"] == int(1.3 * 2000) + 1024
     assert out["bsr"] == max(50, int(1.3 * 40) + 1024)
     assert caps["cand"] == 1000                                 # the input is not modified
+
+
+def test_cpu_leg_sample_with_every_query_is_the_whole_contact_set():
+    """The CPU baseline's sampled stage, given every vertex and edge as a query, evaluates
+    exactly the contact set (EE pairs with both sides queried counted once)."""
+    import oracle
+    from paper_2409_16385_gb300 import scenes
+    sc = scenes.make_config(2, small=True)
+    n, dt, n_cand = bench.oracle_sample(sc, 3, 1.0)
+    full = oracle.pairs(sc, oracle.embed(sc, sc.iterate(3)))
+    assert n == len(full["type"]) > 0 and dt > 0 and n_cand > 0
