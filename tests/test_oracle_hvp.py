@@ -12,7 +12,6 @@ import dataclasses
 import functools
 
 import numpy as np
-import pytest
 
 import oracle
 from paper_2409_16385_gb300 import scenes

@@ -4,7 +4,6 @@ embedding (Eq. 17: grad_q = J^T grad_x, hess_q = J^T hess_x J), its special case
 import functools
 
 import numpy as np
-import pytest
 
 import oracle
 from paper_2409_16385_gb300 import scenes

@@ -12,7 +12,6 @@ import dataclasses
 import functools
 
 import numpy as np
-import pytest
 
 import oracle
 from oracle import sim
