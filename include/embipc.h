@@ -304,7 +304,8 @@ eipc_status eipc_accd_toi_static(int64_t Nv, int64_t F, int64_t E, const double*
                                  eipc_stream stream);
 int64_t eipc_accd_static_max_vertices(void);
 
-/* Library version string. */
+/* Library version string: static, NUL-terminated ASCII owned by the library (never NULL,
+ * never freed by the caller); needs no GPU. */
 const char* eipc_version(void);
 
 #ifdef __cplusplus

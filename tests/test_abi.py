@@ -88,3 +88,26 @@ def test_entry_points_reject_misuse_without_gpu_work():
     assert lib.eipc_bsr_spmv(1, rp.ctypes.data, None, None, x.ctypes.data, float("nan"), 0.0, y.ctypes.data,
                              None) == INVALID
     assert lib.eipc_bsr_spmv(1, None, None, None, x.ctypes.data, 1.0, 0.0, y.ctypes.data, None) == INVALID
+
+
+def test_every_entry_point_is_documented():
+    """Each declared entry point (or the group of declarations it belongs to) follows a
+    comment that states what it computes and how its arguments are laid out."""
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", f)).read().splitlines()
+        for k, line in enumerate(lines):
+            m = re.match(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(eipc_[a-z_0-9]+)\s*\(", line)
+            if not m:
+                continue
+            j = k - 1
+            # skip the other declarations of the same group (and their continuation lines)
+            while j >= 0 and lines[j].strip() and not lines[j].rstrip().endswith("*/"):
+                j -= 1
+            assert j >= 0 and lines[j].rstrip().endswith("*/"), f"{m.group(1)} has no comment above it"
+            start = j
+            while start >= 0 and "/*" not in lines[start]:
+                start -= 1
+            words = " ".join(lines[start:j + 1]).split()
+            assert len(words) >= 6, f"{m.group(1)}: comment too short"
