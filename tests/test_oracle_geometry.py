@@ -144,3 +144,48 @@ def test_distance_invariant_under_rigid_motion():
         Y = X @ Q.T + rng.normal(size=3)
         e2, _, _ = oracle.pair_d2(ptype, Y.ravel())
         assert np.isclose(d2, e2, rtol=1e-12)
+
+
+def _two_tri_scene(V):
+    from paper_2409_16385_gb300 import scenes
+    tris = np.array([[0, 1, 2], [3, 4, 5]], np.int32)
+    return scenes.Scene(name="pair", tris=tris, edges=scenes.edges_of(tris),
+                        cage_idx=np.full((6, 4), -1, np.int32), w=np.zeros((6, 4)), x_kin=V, Ns=0,
+                        cage_tets=np.zeros((0, 4), np.int32), q_rest=np.zeros((0, 3)),
+                        body=np.zeros(6, np.int32), params={})
+
+
+def test_intersection_test_on_exact_configurations():
+    """The exact edge-triangle test behind the no-penetration checks (orientation
+    predicates by expansion arithmetic): configurations decided by their exact geometry,
+    including ones that floating-point rounding of a naive test would get wrong."""
+    T = [[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]
+    cases = [
+        # an edge of the second triangle pierces the first one's interior
+        ([[0.2, 0.2, -0.5], [0.3, 0.2, 0.5], [2.0, 2.0, 2.0]], False),
+        # the same triangle lifted just above the plane: no contact
+        ([[0.2, 0.2, 2.0 ** -50], [0.3, 0.2, 0.5], [2.0, 2.0, 2.0]], True),
+        # a vertex exactly on the first triangle's interior: the closed sets meet
+        ([[0.25, 0.25, 0.0], [0.3, 0.2, 0.5], [2.0, 2.0, 2.0]], False),
+        # coplanar and overlapping
+        ([[0.1, 0.1, 0.0], [2.0, 0.1, 0.0], [0.1, 2.0, 0.0]], False),
+        # coplanar and disjoint (beyond the hypotenuse x + y = 1)
+        ([[0.6, 0.6, 0.0], [2.0, 0.6, 0.0], [0.6, 2.0, 0.0]], True),
+        # an edge passing exactly through the hypotenuse's midpoint, off the plane elsewhere
+        ([[0.5, 0.5, -1.0], [0.5, 0.5, 1.0], [3.0, 3.0, 0.5]], False),
+        # the same edge shifted by the smallest step beyond the hypotenuse
+        ([[0.5, np.nextafter(0.5, 1.0), -1.0], [0.5, np.nextafter(0.5, 1.0), 1.0], [3.0, 3.0, 0.5]], True),
+    ]
+    for upper, free in cases:
+        V = np.array(T + upper, float)
+        assert oracle.intersection_free(_two_tri_scene(V), V) is free, (upper, free)
+    # large integer coordinates: the plane x + y + z = 2^30 holds the first triangle, and a
+    # vertex with coordinate sum exactly 2^30 lies on it.  The orientation determinants
+    # reach 2^90, far beyond what one FP64 rounding can decide.
+    G = 2.0 ** 30
+    T = [[G, 0.0, 0.0], [0.0, G, 0.0], [0.0, 0.0, G]]
+    on = [2.0 ** 29 + 3, 2.0 ** 29 - 5, 2.0]
+    for lift, free in ((0.0, False), (1.0, True), (-1.0, False)):
+        up = [[on[0], on[1], on[2] + lift], [G, G, G], [G, 2 * G, G]]
+        V = np.array(T + up, float)
+        assert oracle.intersection_free(_two_tri_scene(V), V) is free, (lift, free)

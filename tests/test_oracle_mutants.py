@@ -36,6 +36,7 @@ GEO_EE = ("test_oracle_geometry", "test_ee_distance_vs_sampling", [(t,) for t in
 GEO_PT_CF = ("test_oracle_geometry", "test_pt_closed_forms", [()])
 GEO_EE_CF = ("test_oracle_geometry", "test_ee_closed_forms", [()])
 GEO_DEGEN = ("test_oracle_geometry", "test_degenerate_primitives", [()])
+GEO_EXACT = ("test_oracle_geometry", "test_intersection_test_on_exact_configurations", [()])
 BARRIER = ("test_oracle_potentials", "test_barrier_closed_form_and_boundary", [()])
 F0 = ("test_oracle_potentials", "test_f0_matches_integral_of_f1", [()])
 PAIR_FD = ("test_oracle_potentials", "test_barrier_derivatives_vs_central_differences",
@@ -159,6 +160,10 @@ MUTANTS = [
      "int32_t s[4];", [PAIRS_EE_SAMPLED]),
     ("pairs_sampled_range", "oracle.cpp", "if (d > 0.0 && d < dhat) out.push_back",
      "if (d > 0.0 && d < 1.5 * dhat) out.push_back", [PAIRS_EE_SAMPLED, PAIRS]),
+    ("exact_product_error_dropped", "predicates.hpp", "    h = grow(h, err);\n    h = grow(h, p);",
+     "    h = grow(h, p);", [GEO_EXACT]),
+    ("exact_sum_error_dropped", "predicates.hpp", "    if (err != 0.0) h.push_back(err);\n", "",
+     [GEO_EXACT]),
     ("intersection_decision", "predicates.hpp", "return !(has_pos && has_neg);", "return has_pos && has_neg;",
      [ACCD, NO_PENETRATION]),
     # the exact Hessian-vector product
