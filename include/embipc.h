@@ -284,7 +284,10 @@ int64_t eipc_launch_count(void);
  * the LBVH search: for k < n_cand, pair (cand_type[k], cand_i[k], cand_j[k]) is a PT pair
  * (type 0: vertex i, triangle j) or an EE pair (type 1: edges i, j).  Candidates whose
  * closed FP64 swept boxes over [x, x + dx] do not overlap, and incident ones, are skipped,
- * so any superset of the overlapping pairs gives the same alpha.  Inputs (device, caller-
+ * so any superset of the overlapping pairs gives the same alpha.  This call has no
+ * kinematic mask: a pair whose four vertices are all kinematic is advanced like any other
+ * (eipc_accd_toi's search drops such pairs), so to get the scene path's alpha the caller
+ * leaves them out of the list.  Inputs (device, caller-
  * owned): x[Nv*3], dx[Nv*3], tris[F*3], edges[E*2], the three candidate arrays.  Outputs
  * (device, caller-owned): *alpha; *flags (EIPC_FLAG_PENETRATION / NONFINITE / ACCD_CAP /
  * BAD_INDEX, may be NULL); *n_advanced (candidates whose boxes overlap, may be NULL).
@@ -293,7 +296,10 @@ int64_t eipc_launch_count(void);
  * 256-byte header, resident on every device that loads the library until the process
  * exits).  Nv above that returns EIPC_ERR_TOO_LARGE before anything is enqueued.
  * The first call on a device looks up that array's device address with the device
- * current (cudaGetSymbolAddress); make that first call before any stream capture.  Every
+ * current (cudaGetSymbolAddress); make that first call before any stream capture.  The
+ * address is kept for the life of the process: after cudaDeviceReset the library's module
+ * is loaded again and the array may move, so a process that resets a device must not
+ * call this entry point on that device afterwards.  Every
  * call re-initialises the scratch it needs, but all calls share the one array, so calls
  * whose work overlaps on the GPU (different streams, or different host threads) race and
  * must be serialised by the caller. */

@@ -16,6 +16,33 @@ from __future__ import annotations
 import torch
 
 
+class FixedScatter:
+    """out[idx[k]] += v[k] in an order that depends only on idx: every target's
+    contributions, in increasing k, are gathered into one row of an [n, width] table
+    (padded with a zero entry) and summed along the row by a fixed-shape reduction.
+    torch's index_add_ on CUDA adds with atomics, whose order (and so the rounding of the
+    result) changes from run to run; this form gives the same bits on every run."""
+
+    def __init__(self, idx, n: int):
+        idx = idx.reshape(-1).long()
+        self.n, self.m = int(n), int(idx.numel())
+        dev = idx.device
+        counts = torch.bincount(idx, minlength=self.n)
+        width = max(int(counts.max()) if self.m else 0, 1)
+        order = torch.argsort(idx, stable=True)
+        start = torch.cumsum(counts, 0) - counts
+        rank = torch.arange(self.m, device=dev) - start[idx[order]]
+        table = torch.full((self.n, width), self.m, dtype=torch.int64, device=dev)
+        table[idx[order], rank] = order
+        self.table = table
+
+    def __call__(self, v):
+        tail = v.shape[1:]
+        flat = v.reshape(self.m, -1)
+        padded = torch.cat([flat, torch.zeros((1, flat.shape[1]), dtype=v.dtype, device=v.device)])
+        return padded[self.table].sum(1).reshape((self.n,) + tuple(tail))
+
+
 def lame(E: float, nu: float):
     return E / (2.0 * (1.0 + nu)), E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
 
@@ -57,6 +84,9 @@ class CorotationalCage:
                     B[:, 3 * i + j, 3 * a + i] = self.Dm_inv[:, a - 1, j]
         self.B = B
         self.dofs = (3 * self.tets[:, :, None] + torch.arange(3, device=q0.device)[None, None, :]).reshape(T, 12)
+        # node of each (tet, local node) entry, for the deterministic nodal scatter
+        self._node_scatter = FixedScatter(self.tets, self.ns)
+        self._block_scatter = None
 
     def _ds(self, q):
         t = self.tets
@@ -85,12 +115,8 @@ class CorotationalCage:
 
     def _scatter(self, G):
         """dE/dDs per tet [T,3,3] (columns = nodes 1..3) -> nodal vectors [Ns,3]."""
-        out = torch.zeros((self.ns, 3), dtype=G.dtype, device=G.device)
-        t = self.tets
-        for a in range(3):
-            out.index_add_(0, t[:, a + 1], G[:, :, a])
-        out.index_add_(0, t[:, 0], -G.sum(2))
-        return out
+        per_node = torch.cat([-G.sum(2)[:, None, :], G.transpose(1, 2)], dim=1)   # [T,4,3]
+        return self._node_scatter(per_node.reshape(-1, 3))
 
     def energy(self, q) -> torch.Tensor:
         F = self.deformation(q)
@@ -156,9 +182,9 @@ class CorotationalCage:
         """Per-tet 12 x 12 Hessians -> values [nnzb,3,3] on the block pattern."""
         T = Ht.shape[0]
         blocks = Ht.reshape(T, 4, 3, 4, 3).permute(0, 1, 3, 2, 4).reshape(T * 16, 3, 3)
-        out = torch.zeros((nnzb, 3, 3), dtype=Ht.dtype, device=Ht.device)
-        out.index_add_(0, slot.reshape(-1), blocks)
-        return out
+        if self._block_scatter is None or self._block_scatter.n != nnzb:
+            self._block_scatter = FixedScatter(slot, nnzb)
+        return self._block_scatter(blocks)
 
     def assemble_dense(self, Ht):
         n = 3 * self.ns

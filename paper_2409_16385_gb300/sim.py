@@ -31,7 +31,7 @@ import numpy as np
 import torch
 
 from . import binding
-from .elastic import CorotationalCage, lame
+from .elastic import CorotationalCage, FixedScatter, lame
 
 
 def _vertex_volumes(sc, x) -> torch.Tensor:
@@ -50,17 +50,34 @@ def _vertex_volumes(sc, x) -> torch.Tensor:
         vol = (a0 * torch.linalg.cross(a1, a2)).sum(1) / 6.0
         if float(vol.sum()) < 0:
             vol = -vol
-        for k in range(3):
-            V.index_add_(0, t[:, k], vol / 3.0)
+        V = V + FixedScatter(t, sc.Nv)((vol / 3.0)[:, None].expand(-1, 3).reshape(-1))
     return V
 
 
 @dataclass
 class StepInfo:
+    """How a Newton solve ended.  `reason` is "residual" (free residual below rtol times
+    the largest force term), "step" (the Newton step fell below four ulps of the positions:
+    the residual is at its rounding floor), "line_search" (backtracking found no decrease
+    down to alpha < 1e-20) or "max_iter".  Only the first two are converged."""
     iterations: int
     residual: float
     exact_hessian_steps: int
     krylov_iterations: int = 0
+    reason: str = "residual"
+
+    @property
+    def converged(self) -> bool:
+        return self.reason in ("residual", "step")
+
+
+class NewtonError(RuntimeError):
+    """A Newton solve that stopped without converging (line search or iteration cap)."""
+
+    def __init__(self, info: StepInfo):
+        super().__init__(f"Newton step did not converge: {info.reason} after {info.iterations} iterations, "
+                         f"relative residual {info.residual:.3e}")
+        self.info = info
 
 
 class Simulator:
@@ -89,7 +106,7 @@ class Simulator:
         emb_np = ~np.asarray(scene.kinematic)
         tet_of_np = np.array([row_of[tuple(r)] for r in np.asarray(scene.cage_idx)[emb_np].tolist()], np.int64)
         tet_of = torch.as_tensor(tet_of_np, device=self.dev)
-        V_T = torch.zeros(tets.shape[0], **f64).index_add_(0, tet_of, Vk[emb])
+        V_T = FixedScatter(tet_of, tets.shape[0])(Vk[emb])
         # materials: one, or one per body (a tet takes the body of the vertices inside it)
         T = tets.shape[0]
         body_np = np.asarray(scene.body)[emb_np]
@@ -109,10 +126,9 @@ class Simulator:
         self.nnzb = int(self.col.shape[0])
         m = torch.as_tensor(rho_v, **f64) * Vk[emb]
         ie, we = idx[emb], w[emb]
-        Mb = torch.zeros(self.nnzb, **f64)
         vslot = self.slot[tet_of]                                       # [nv_emb,4,4]
         # the vertex's node order is its tet's node order (cage_idx row = tet row)
-        Mb.index_add_(0, vslot.reshape(-1), (m[:, None, None] * we[:, :, None] * we[:, None, :]).reshape(-1))
+        Mb = FixedScatter(vslot, self.nnzb)((m[:, None, None] * we[:, :, None] * we[:, None, :]).reshape(-1))
         self.Mb = Mb
         eye = torch.eye(3, **f64)
         self.M_blocks = Mb[:, None, None] * eye
@@ -120,9 +136,7 @@ class Simulator:
                                        (self.row_ptr[1:] - self.row_ptr[:-1]).long())
         self.diag_slot = torch.nonzero(rows == self.col.long()).squeeze(1)   # one per row
         g = torch.as_tensor(np.asarray(scene.gravity, float), **f64)
-        f = torch.zeros((self.Ns, 3), **f64)
-        f.index_add_(0, ie.reshape(-1), ((m[:, None] * we).reshape(-1, 1)) * g[None, :])
-        self.f_ext = f
+        self.f_ext = FixedScatter(ie, self.Ns)(((m[:, None] * we).reshape(-1, 1)) * g[None, :])
         active = torch.zeros(self.Ns, dtype=torch.bool, device=self.dev)
         active[tets[V_T > 0].reshape(-1)] = True
         fixed = getattr(scene, "prescribed_nodes", None)
@@ -256,7 +270,7 @@ class Simulator:
         rp = Hc.row_ptr.long()
         rows_c = torch.repeat_interleave(torch.arange(self.Ns, device=self.dev), rp[1:] - rp[:-1])
         on_diag = torch.nonzero(rows_c == Hc.col[:nnzb_c].long()).squeeze(1)
-        D.index_add_(0, rows_c[on_diag], h2 * Hc.val[on_diag].reshape(-1, 3, 3))
+        D = D + FixedScatter(rows_c[on_diag], self.Ns)(h2 * Hc.val[on_diag].reshape(-1, 3, 3))
         eye = torch.eye(3, dtype=torch.float64, device=self.dev)
         D = torch.where(self.free[:, None, None], D, eye)
         Dinv = torch.linalg.inv(D)
@@ -293,11 +307,13 @@ class Simulator:
 
     # ---------------------------------------------------------------- one time step
     def step(self, q_prev, q_prev2, shift, kappa: float, lag, rtol: float = 1e-12, max_iter: int = 100,
-             q_fixed=None):
+             q_fixed=None, strict: bool = True):
         """q^{n+1} with the kinematic vertices at `shift` and the Dirichlet nodes at q_fixed
         (their start positions if None): Newton with the CCD step bound and backtracking
         until the free residual is below rtol times the largest force term, or the step is
-        below four ulps of the positions."""
+        below four ulps of the positions.  The returned StepInfo says which; a solve that
+        ends otherwise (backtracking exhausted, iteration cap) raises NewtonError when
+        `strict`, else comes back with that reason."""
         self.set_state(shift, kappa)
         q_tilde = 2.0 * q_prev - q_prev2
         q = q_prev.clone()
@@ -312,7 +328,7 @@ class Simulator:
             phi, g, scale = self._forces(q, q_tilde, lag)
             res = float(g[self.free].abs().max())
             if res <= rtol * scale:
-                return q, StepInfo(it, res / scale, n_exact, n_kry)
+                return q, StepInfo(it, res / scale, n_exact, n_kry, "residual")
             if self.solver == "dense":
                 P, exact, k = self._direction_dense(q, lag, g)
             else:
@@ -320,7 +336,7 @@ class Simulator:
             n_exact += int(exact)
             n_kry += k
             if float(P.abs().max()) <= 4.0 * eps * float(q.abs().max()):
-                return q, StepInfo(it, res / scale, n_exact, n_kry)
+                return q, StepInfo(it, res / scale, n_exact, n_kry, "step")
             x = self.cs.embed(q)
             dx = self.cs.embed(P, displacement=True)
             alpha = float(self.cs.accd_toi(x, dx).item())
@@ -332,9 +348,15 @@ class Simulator:
                     break
                 alpha *= 0.5
                 if alpha < 1e-20:
-                    return q, StepInfo(it, res / scale, n_exact, n_kry)
+                    return q, self._stalled(StepInfo(it, res / scale, n_exact, n_kry, "line_search"), strict)
             q = q + alpha * P
-        return q, StepInfo(max_iter, res / scale, n_exact, n_kry)
+        return q, self._stalled(StepInfo(max_iter, res / scale, n_exact, n_kry, "max_iter"), strict)
+
+    @staticmethod
+    def _stalled(info: StepInfo, strict: bool) -> StepInfo:
+        if strict:
+            raise NewtonError(info)
+        return info
 
     def prescribed(self, n: int):
         """Positions of the Dirichlet nodes at step n (None: their start positions)."""

@@ -57,6 +57,7 @@ def test_pcg_step_matches_dense_step(which):
     qa, ia = a.step(a.q0, a.q0, shift, kappa, a.initial_lag(kappa), q_fixed=a.prescribed(1))
     qb, ib = b.step(b.q0, b.q0, shift, kappa, b.initial_lag(kappa), q_fixed=b.prescribed(1))
     # both stop at this scene's rounding floor (a few 1e-11 of the largest force term)
+    assert ia.converged and ib.converged, (ia, ib)
     assert ia.residual <= 1e-10 and ib.residual <= 1e-10, (ia, ib)
     assert ib.krylov_iterations > 0
     d = (qa - a.q0).abs().max()
@@ -75,4 +76,4 @@ def test_physical_grasp_matches_oracle():
         assert np.abs(qs[n].cpu().numpy() - ref).max() <= 1e-8 * np.abs(ref - sc.q0).max(), n
     x = oracle.embed(sc, qs[2].cpu().numpy())
     assert oracle.intersection_free(sc, x)
-    assert all(i.residual <= 1e-10 for i in infos)
+    assert all(i.converged and i.residual <= 1e-10 for i in infos), infos
