@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="bubble grasp: skip the other workloads reported beside the headline (sphere on pad, "
+                         "plate in rack, exact-Hessian HVP, 256-scene batch vs plain)")
     ap.add_argument("--quick", action="store_true", help="small scene (profiling / smoke)")
     ap.add_argument("--json-out", default="")
     ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
@@ -175,39 +178,58 @@ def measured_peaks():
 
 # Algorithmic work per unit:
 #   eval_barrier  FP64 flops per contact pair, counted by ncu on the bubble-grasp workload
-#                 (2 x DFMA + DMUL + DADD thread instructions / pairs: 373.2e6 / 115,583)
-#   ccd_advance   FP64 flops per CCD candidate (box test, advancement distance evaluations)
+#                 ((2 x DFMA + DMUL + DADD) thread instructions / pairs)
+#   ccd_advance   FP64 flops per advanced CCD candidate (box test, advancement distances)
 #   others        DRAM bytes per unit of their minimum input + output traffic
 FP64_FLOPS_PER_PAIR = 3229.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
-# (eval_barrier at the autotuned launch shape: 117.4 MB + 224.5 MB for 115,583 pairs)
+# (eval_barrier: per contact pair; bvh_query: per launch of the contact traversal)
 NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 2958.0}
 
 
-def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_step, sc):
+def query_bytes(sc, n_cand):
+    """Minimum DRAM bytes of one traversal launch: every query's padded vertex box once
+    (32 B per vertex; edge queries reuse their vertices' boxes, plus 8 B of edge ids), every
+    node of both hierarchies once (64 B; the trees are L2-resident after that), and 8 B per
+    candidate written."""
+    return 32.0 * sc.Nv + 8.0 * sc.E + 64.0 * (2 * sc.F + 2 * sc.E) + 8.0 * n_cand
+
+
+def roofline_figure(name, total_ms, launches, steps, per_step, sc, fp64_probe=None):
+    """Roofline of one kernel from its live event timer: total_ms over `launches` launches in
+    `steps` steps.  per_step: units per step -- pairs (contact pairs evaluated), ccd
+    (candidates the CCD advanced), cand_contact / cand_ccd (broad-phase candidates of the
+    contact and CCD traversals).  FP64 kernels are measured against the FP64 peak derived
+    from the unit counts and the maximum clock; fp64_probe (the live DFMA-chain
+    measurement) is reported beside it."""
     if launches == 0 or total_ms <= 0:
         return dict(bound=None, achieved=None, peak=None, unit=None, frac=None, traffic=None, kernel=name)
     avg_s = total_ms / 1e3 / launches
     per_step_launches = launches / steps
     hbm, src = measured_peaks()
     if name in ("eval_barrier", "ccd_advance"):
-        units = (pairs_per_step if name == "eval_barrier" else cand_per_step) / per_step_launches
+        units = (per_step["pairs"] if name == "eval_barrier" else per_step["ccd"]) / per_step_launches
         per = FP64_FLOPS_PER_PAIR if name == "eval_barrier" else FP64_FLOPS_PER_CCD_CAND
         ach = units * per / avg_s / 1e12
         peak = FP64_PEAK_TFLOPS
         tr = NCU_TRAFFIC_PER_UNIT.get(name)
-        return dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
-                    traffic=(tr * units if tr else None), kernel=name, launch_ms=avg_s * 1e3,
-                    units_per_launch=units, unit_cost=f"{per:.0f} FP64 flop per unit",
-                    peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)")
+        out = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
+                   traffic=(tr * units if tr else None), kernel=name, launch_ms=avg_s * 1e3,
+                   units_per_launch=units, unit_cost=f"{per:.0f} FP64 flop per unit",
+                   peak_source="derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)")
+        if fp64_probe:
+            out["peak_probe"] = fp64_probe["tflops"]
+            out["frac_of_probe"] = ach / fp64_probe["tflops"]
+        return out
     # memory-bound kernels: minimum DRAM bytes per launch
     nv, ne, nf = sc.Nv, sc.E, sc.F
     bytes_model = {
         "bvh_build": 0.5 * (nf + ne) * (24 + 8 + 4 + 4 * 4 * 12 + 64 + 8),
-        "bvh_query": 0.5 * (32 * nv + 72 * ne + 64 * (nf + ne) + 8 * cand_per_step),
-        "narrow_phase": 8 * cand_per_step + 20 * pairs_per_step,
-        "pair_sort": 5 * pairs_per_step * 24 + 20 * pairs_per_step,
+        "bvh_query": (query_bytes(sc, per_step.get("cand_contact", 0.0)) + query_bytes(sc, per_step.get("cand_ccd", 0.0)))
+                     / max(per_step_launches, 1.0),
+        "narrow_phase": 8 * per_step.get("cand_contact", 0.0) + 20 * per_step["pairs"],
+        "pair_sort": 5 * per_step["pairs"] * 24 + 20 * per_step["pairs"],
         "hessian_reduce": 0.0,
         "embed": 32 * nv + 48 * nv,
     }
@@ -217,8 +239,12 @@ def roofline_figure(name, total_ms, launches, steps, pairs_per_step, cand_per_st
                     launch_ms=avg_s * 1e3)
     ach = b / avg_s / 1e9
     tr = NCU_TRAFFIC_PER_UNIT.get(name)
-    return dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=tr, kernel=name,
-                launch_ms=avg_s * 1e3, peak_source=src)
+    out = dict(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=tr, kernel=name,
+               launch_ms=avg_s * 1e3, bytes_per_launch=b, peak_source=src)
+    if name == "bvh_query":
+        out["note"] = ("latency-bound (dependent node fetches; see the ncu summary): the fraction is the minimum "
+                       "DRAM bytes over the launch time, a model, not measured traffic")
+    return out
 
 
 def build_scene(quick):
@@ -260,39 +286,194 @@ def oracle_sample(sc, t, frac, seed=0):
     return len(prs["type"]), dt, a1["n_candidates"] + a2["n_candidates"]
 
 
+def _subset(d, idx):
+    return {k: np.asarray(v)[idx] for k, v in d.items()}
+
+
+def swept_overlap(sc, x, dx, cand):
+    """Mask of the candidates whose closed FP64 swept boxes over [x, x + dx] overlap (the
+    CCD's exact box test), for host arrays x, dx [Nv,3] and cand = (type, i, j)."""
+    ct, ci, cj = (np.asarray(a) for a in (cand["type"], cand["i"], cand["j"]))
+    st = np.zeros((len(ct), 4), np.int64)
+    pt = ct == 0
+    st[pt] = np.c_[ci[pt], np.asarray(sc.tris)[cj[pt]]]
+    st[~pt] = np.c_[np.asarray(sc.edges)[ci[~pt]], np.asarray(sc.edges)[cj[~pt]]]
+    p0, p1 = x[st], x[st] + dx[st]
+    lo, hi = np.minimum(p0, p1), np.maximum(p0, p1)
+    side_a = np.arange(4)[None, :] < np.where(pt, 1, 2)[:, None]
+    loA = np.where(side_a[..., None], lo, np.inf).min(1)
+    hiA = np.where(side_a[..., None], hi, -np.inf).max(1)
+    loB = np.where(~side_a[..., None], lo, np.inf).min(1)
+    hiB = np.where(~side_a[..., None], hi, -np.inf).max(1)
+    return ~((loA > hiB) | (loB > hiA)).any(1)
+
+
+def cpu_stage_baseline(sc, x, xn, dx, pairs, pairs_n, cand, budget_s=8.0, seed=0):
+    """The oracle's two timed stages on the lists the GPU used, on all host cores and on
+    one core:
+      eval: barrier + lagged friction energy, gradient and projected Hessian reduced into
+            g_r and H_r (oracle.eval_contact) over the contact pairs `pairs` and the lag
+            state of `pairs_n` at xn -- pairs/s;
+      ccd:  conservative advancement over the candidates whose swept boxes overlap
+            (oracle.accd_list over `cand`) -- queries/s.
+    Each stage runs on the whole list when it fits in about budget_s seconds, else on a
+    seeded random subset (the same fraction of the friction pairs as of the contact pairs),
+    sized by a first run on up to 2,000 entries."""
+    import oracle
+    oracle.build()
+    lag = oracle.friction_lag(sc, xn, pairs_n)
+    n_all = oracle.num_threads()
+    rng = np.random.default_rng(seed)
+    P, L, C = len(pairs["type"]), len(lag["lam"]), len(cand["type"])
+    res = {}
+
+    def run_eval(m):
+        ip = np.arange(P) if m >= P else np.sort(rng.choice(P, m, replace=False))
+        il = np.arange(L) if m >= P else np.sort(rng.choice(L, min(L, int(round(m * L / max(P, 1)))), replace=False))
+        sp, sl = _subset(pairs, ip), _subset(lag, il)
+        t0 = time.perf_counter()
+        oracle.eval_contact(sc, x, sp, sl)
+        return len(ip), len(il), time.perf_counter() - t0
+
+    def run_ccd(m, repeat=1):
+        ic = np.arange(C) if m >= C else np.sort(rng.choice(C, m, replace=False))
+        sub = _subset(cand, ic)
+        t0 = time.perf_counter()
+        for _ in range(repeat):
+            oracle.accd_list(sc, x, dx, sub)
+        return len(ic) * repeat, time.perf_counter() - t0
+
+    try:
+        for label, threads in (("all", n_all), ("1core", 1)):
+            oracle.set_threads(threads)
+            if P:
+                m0, _, t0 = run_eval(min(P, 2000))
+                n, nl, dt = run_eval(min(P, max(m0, int(m0 * budget_s / max(t0, 1e-6)))))
+                res[f"eval_{label}"] = dict(value=n / dt, pairs=n, friction_pairs=nl, seconds=dt, threads=threads,
+                                            list_pairs=P, list_friction_pairs=L)
+            if C:
+                # the whole list, repeated until about budget_s / 2 has passed (most
+                # candidates settle at their first advancement, so one pass is short)
+                m0, t0 = run_ccd(min(C, 2000))
+                m = min(C, max(m0, int(m0 * budget_s / 2 / max(t0, 1e-6))))
+                n1, t1 = run_ccd(m)
+                rep = max(1, int(budget_s / 2 / max(t1, 1e-6))) if m >= C else 1
+                n, dt = run_ccd(m, rep) if rep > 1 else (n1, t1)
+                res[f"ccd_{label}"] = dict(value=n / dt, queries=n, seconds=dt, threads=threads, list_queries=C,
+                                           passes=rep)
+    finally:
+        oracle.set_threads(n_all)
+    return res
+
+
+def cpu_enumeration(sc, x, n_queries=400, seed=0):
+    """The oracle's brute-force O(n^2) contact-pair enumeration, timed apart (it is the
+    definition of the pair set, not a fair baseline for the LBVH): n_queries vertex queries
+    against every triangle and n_queries edge queries against every edge, and the time a
+    whole-scene enumeration would take at that rate."""
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    qv = np.sort(rng.choice(sc.Nv, min(n_queries, sc.Nv), replace=False)).astype(np.int32)
+    qe = np.sort(rng.choice(sc.E, min(n_queries, sc.E), replace=False)).astype(np.int32)
+    t0 = time.perf_counter()
+    pv = oracle.pairs_of(sc, x, 0, qv)
+    t1 = time.perf_counter()
+    pe = oracle.pairs_of(sc, x, 1, qe)
+    t2 = time.perf_counter()
+    full = (t1 - t0) * sc.Nv / len(qv) + (t2 - t1) * sc.E / len(qe)
+    return dict(vertex_queries=int(len(qv)), edge_queries=int(len(qe)), pairs_found=int(len(pv["i"]) + len(pe["i"])),
+                seconds=t2 - t0, full_enumeration_s_estimate=full, cores=oracle.num_threads(),
+                kind="oracle brute force (not a baseline: the definition of the pair set)")
+
+
+def reference_list(sc, t, frac, seed):
+    """The oracle's own contact list at iterate t for a seeded random fraction of the query
+    primitives (brute force), its lagged list, and the positions: the input of one
+    reference step."""
+    import oracle
+    rng = np.random.default_rng(seed + t)
+    qv = np.sort(rng.choice(sc.Nv, max(1, int(frac * sc.Nv)), replace=False)).astype(np.int32)
+    qe = np.sort(rng.choice(sc.E, max(1, int(frac * sc.E)), replace=False)).astype(np.int32)
+    x, xn = oracle.embed(sc, sc.iterate(t)), oracle.embed(sc, sc.iterate(sc.lag_of(t)))
+
+    def sampled_pairs(xx):
+        pv = oracle.pairs_of(sc, xx, 0, qv)
+        pe = oracle.pairs_of(sc, xx, 1, qe)
+        ee = np.unique(np.stack([pe["i"], pe["j"]], 1), axis=0).reshape(-1, 2)
+        return dict(type=np.concatenate([np.zeros(len(pv["i"]), np.int32), np.ones(len(ee), np.int32)]),
+                    i=np.concatenate([pv["i"], ee[:, 0]]).astype(np.int32),
+                    j=np.concatenate([pv["j"], ee[:, 1]]).astype(np.int32))
+
+    prs = sampled_pairs(x)
+    lag = oracle.friction_lag(sc, xn, sampled_pairs(xn))
+    return x, prs, lag
+
+
 def run_reference(args, ws, rank):
-    """`--impl reference`: the CPU oracle as it stands, on the host cores."""
+    """`--impl reference`: the CPU oracle as it stands, on the host cores.  A step is the
+    oracle's evaluation stage (barrier + lagged friction energy, gradient and projected
+    Hessian reduced into the subspace: the metric's own stage) over the contact list of one
+    iterate.  The lists come from the oracle's own brute-force enumeration for a seeded
+    fraction of the query primitives, found before the timed steps (untimed; their time is
+    reported as enumeration_s)."""
     if rank != 0:
         return
     import oracle
     oracle.build()
     sc = build_scene(args.quick)
-    # size each step's sample so that warm-up + timed steps end within about 3 minutes:
-    # calibrate on a 1/1000 sample, then scale to ~150 s / (steps + warm-up) per step
-    total_steps = args.steps + args.warmup
-    _, t_cal, _ = oracle_sample(sc, 0, 1e-3, seed=999)
-    frac = min(1.0 / 12, 1e-3 * (150.0 / total_steps) / max(t_cal, 1e-3))
+    # the enumeration fraction: about 30 s of brute force per list, calibrated on 1/2000
+    t_cal = time.perf_counter()
+    reference_list(sc, 0, 5e-4, seed=999)
+    t_cal = time.perf_counter() - t_cal
+    frac = 1.0 if args.quick else min(1.0 / 12, 5e-4 * 30.0 / max(t_cal, 1e-3))
+    its = [sc.lag_of(5), sc.lag_of(5) + 1 if sc.lag_of(5) + 1 < sc.n_iterates else sc.lag_of(5)]
+    t_en = time.perf_counter()
+    lists = [reference_list(sc, t, frac, seed=7) for t in its]
+    t_en = time.perf_counter() - t_en
     for k in range(args.warmup):
-        oracle_sample(sc, (7 * k) % sc.n_iterates, frac, seed=k)
-    pairs = 0; secs = 0.0; cand = 0
+        x, prs, lag = lists[k % len(lists)]
+        oracle.eval_contact(sc, x, prs, lag)
+    pairs = 0; secs = 0.0
     for k in range(args.steps):
-        p, dt, c = oracle_sample(sc, (7 * (k + args.warmup)) % sc.n_iterates, frac, seed=100 + k)
-        pairs += p; secs += dt; cand += c
+        x, prs, lag = lists[k % len(lists)]
+        t0 = time.perf_counter()
+        oracle.eval_contact(sc, x, prs, lag)
+        secs += time.perf_counter() - t0
+        pairs += len(prs["type"])
     v = pairs / secs if secs > 0 else 0.0
     cores = oracle.num_threads()
-    sample = f"per step: one iterate, brute-force contact set of {frac:.4f} of the vertices and edges (queries), " \
-             f"lagged friction, evaluation and CCD of those queries"
+    sample = (f"per step: the oracle's evaluation stage over the contact pairs (and lagged friction pairs) of one "
+              f"iterate ({', '.join(str(t) for t in its)}, alternating) found by its own brute force for a "
+              f"{frac:.4f} fraction of the vertices and edges as queries; enumeration untimed ({t_en:.1f} s)")
     line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * secs / max(1, args.steps), higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic (seeded)", impl="reference",
-                config=dict(workload=WORKLOAD, iterates=sc.n_iterates, l2="n/a (host)"),
+                config=dict(workload=WORKLOAD + ("_small" if args.quick else ""), iterates=sc.n_iterates,
+                            l2="n/a (host)", pairs_per_step=pairs / max(1, args.steps)),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0),
-                ccd_candidates_per_s=cand / secs if secs > 0 else 0.0)
+                enumeration_s=t_en)
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- GPU arm
+
+def pair_split(sc, h):
+    """Contact pairs between two bodies and pairs inside one body (self-contact, mostly
+    rest-state neighbours when dhat is near the edge length)."""
+    body = np.asarray(sc.body)
+    t, i, j = (np.asarray(h[k]) for k in ("type", "i", "j"))
+    tris, edges = np.asarray(sc.tris), np.asarray(sc.edges)
+    va = np.where(t == 0, i, 0)
+    vb = np.zeros_like(va)
+    pt = t == 0
+    vb[pt] = tris[j[pt], 0]
+    va[~pt] = edges[i[~pt], 0]
+    vb[~pt] = edges[j[~pt], 0]
+    inter = body[va] != body[vb]
+    return dict(inter_body=int(inter.sum()), intra_body=int((~inter).sum()))
+
 
 def run_ours(args, ws, rank, local):
     import torch
@@ -305,6 +486,8 @@ def run_ours(args, ws, rank, local):
     cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21, cand_capacity=args.cand_cap,
                       rec_capacity=args.rec_cap)
     lib = binding.load()
+    # the device's FP64 rate, measured first, on an idle GPU
+    fp64 = binding.fp64_peak()
     Q = torch.tensor(np.stack([sc.iterate(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
     DQ = torch.tensor(np.stack([sc.dq(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
     lag_of = [sc.lag_of(t) for t in range(n_it)]
@@ -346,7 +529,8 @@ def run_ours(args, ws, rank, local):
         cs.build_candidates(Q[first], out=pairs)
         cs.friction_lag(Q[first], pairs, out=lag)
 
-    # warm-up with every kernel timer on: picks the dominant kernel for the roofline
+    # warm-up with every kernel timer on: the three largest kernels are then timed inside
+    # the timed steps, and the largest of them there is the roofline's kernel
     cs.timing_enable(None)
     start_t = (t0 - args.warmup) % n_it
     for k in range(args.warmup):
@@ -357,9 +541,8 @@ def run_ours(args, ws, rank, local):
         step(t, Q[t], DQ[t])
     torch.cuda.synchronize()
     warm = cs.timing_read()
-    dominant = max(warm.items(), key=lambda kv: kv[1][0])[0] if warm else "eval_barrier"
-    # the dominant kernel's launches, and the FP64 evaluation's when it is not the dominant one
-    timed = [dominant] + (["eval_barrier"] if dominant != "eval_barrier" else [])
+    ranked = sorted(warm, key=lambda k: -warm[k][0])
+    timed = ranked[:3] + ([] if "eval_barrier" in ranked[:3] else ["eval_barrier"])
     cs.timing_enable(timed)
     st = cs.status()
     if st["flags"] & ~64:
@@ -404,20 +587,21 @@ def run_ours(args, ws, rank, local):
     total_cand = float(cnt[:, 1].sum())
     total_s_all, total_pairs_all, total_cand_all = across_ranks(total_s, total_pairs, total_cand, ws, dev)
     value = total_pairs_all / total_s_all
+    dominant = max(timed, key=lambda k: kt.get(k, (0.0, 0))[0])
+    kernel_ms_timed = {k: dict(ms_per_step=kt.get(k, (0.0, 0))[0] / K, launches_per_step=kt.get(k, (0.0, 0))[1] / K)
+                       for k in timed}
 
-    # ---- roofline of the dominant kernel, from its live event timer
-    dom_ms, dom_n = kt.get(dominant, (0.0, 0))
-    roof = roofline_figure(dominant, dom_ms, dom_n, K, total_pairs / K, total_cand / K, sc)
-    roofs = {k: roofline_figure(k, *kt.get(k, (0.0, 0)), K, total_pairs / K, total_cand / K, sc) for k in timed}
-
-    # ---- stage-only throughputs (same iterates, pairs precomputed)
+    # ---- stage-only throughputs (same iterates, pairs precomputed); the broad-phase
+    # candidate counts of both traversals per iterate, for the traversal's bytes
     stage = {}
     cs.timing_enable([])
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev_ms = 0.0; n_p = 0
+    cand_contact = []
     for k in range(K):
         t = (t0 + k) % n_it
         cs.build_candidates(Q[t], out=pairs)
+        cand_contact.append(cs.work_counts()["candidates"])
         n_p += int(pairs.count.item())
         flush.zero_()
         ev0.record(stream)
@@ -427,7 +611,9 @@ def run_ours(args, ws, rank, local):
         ev_ms += ev0.elapsed_time(ev1)
     stage["eval_pairs_per_s"] = n_p / (ev_ms / 1e3)
     work = cs.work_counts()          # the last iterate's contact build and evaluation
+    work.update(pair_split(sc, pairs.host()))
     ac_ms = 0.0; n_c = 0
+    cand_ccd = []
     for k in range(K):
         t = (t0 + k) % n_it
         cs.embed(Q[t], out=x)
@@ -439,28 +625,72 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         ac_ms += ev0.elapsed_time(ev1)
         n_c += int(ncand.item())
+        cand_ccd.append(cs.work_counts()["candidates"])
     stage["ccd_queries_per_s"] = n_c / (ac_ms / 1e3)
     stage["ccd_queries_per_s_in_step"] = total_cand / total_s
     wc = cs.work_counts()
     work["ccd_candidates"], work["ccd_advanced"] = wc["candidates"], wc["ccd_advanced"]
+
+    # ---- rooflines: every kernel timed inside the timed steps; the headline is the one
+    # with the largest time there
+    per_step = dict(pairs=total_pairs / K, ccd=total_cand / K, cand_contact=float(np.mean(cand_contact)),
+                    cand_ccd=float(np.mean(cand_ccd)))
+    roofs = {k: roofline_figure(k, *kt.get(k, (0.0, 0)), K, per_step, sc, fp64) for k in timed}
+    roof = dict(roofs[dominant])
+    roof["chosen_by"] = "largest device time inside the timed steps (per-kernel CUDA events on the launching stream)"
 
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(cs, sc, Q, DQ, lag_of, t0, K, flush, dev)
 
-    # ---- CPU baseline (rank 0, one GPU only)
-    cpu = None
+    # ---- CPU baselines (rank 0, one GPU only): the oracle's stages on the GPU's own lists
+    cpu, cpu_more = None, {}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        # about 20 s of oracle work: calibrate on a 1/1000 sample first
-        _, t_cal, _ = oracle_sample(sc, t0, 1e-3, seed=999)
-        frac = 1.0 if args.quick else min(1.0 / 12, 1e-3 * 20.0 / max(t_cal, 1e-3))
-        p, dt, c = oracle_sample(sc, t0, frac)
-        cpu = dict(value=p / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                   sample=f"iterate {t0}: brute-force contact set of a {frac:.4f} fraction of the vertices and edges"
-                          f" (queries), lagged friction, evaluation and CCD of those queries; {p} pairs in {dt:.1f} s")
+        tl = lag_of[t0]
+        pn = cs.build_candidates(Q[tl], out=cs.new_pairs()).host()
+        pr = cs.build_candidates(Q[t0], out=cs.new_pairs()).host()
+        cs.accd_toi(cs.embed(Q[t0]), cs.embed(DQ[t0], displacement=True))
+        cand = dict(zip(("type", "i", "j"), (a.cpu().numpy() for a in cs.candidates())))
+        xo, xno = oracle.embed(sc, sc.iterate(t0)), oracle.embed(sc, sc.iterate(tl))
+        dxo = oracle.embed(sc, sc.dq(t0), displacement=True)
+        cand = _subset(cand, np.nonzero(swept_overlap(sc, xo, dxo, cand))[0])
+        pl = lambda h: dict(type=h["type"], i=h["i"], j=h["j"])
+        stg = cpu_stage_baseline(sc, xo, xno, dxo, pl(pr), pl(pn), cand, budget_s=1.0 if args.quick else 8.0)
+        cores = oracle.num_threads()
+
+        def entry(key, unit, what):
+            r = stg.get(key)
+            if r is None:
+                return None
+            n = r.get("pairs", r.get("queries"))
+            of = r.get("list_pairs", r.get("list_queries"))
+            reps = f" ({r['passes']} passes over it)" if r.get("passes", 1) > 1 else ""
+            return dict(value=r["value"], unit=unit, cores=r["threads"], kind="oracle",
+                        sample=f"iterate {t0}, {what}: {n // r.get('passes', 1)} of the GPU's {of}{reps} "
+                               f"in {r['seconds']:.2f} s")
+
+        cpu = entry("eval_all", UNIT, "evaluation stage (barrier + lagged friction, gradient, projected Hessian, "
+                                      "reduction) over the GPU's contact and lagged pair lists")
+        cpu_more = dict(
+            cpu_baseline_1core=entry("eval_1core", UNIT, "the same evaluation stage on one core"),
+            cpu_baseline_ccd=entry("ccd_all", "queries/s", "CCD advancement over the GPU's candidates whose swept "
+                                                           "boxes overlap"),
+            cpu_baseline_ccd_1core=entry("ccd_1core", "queries/s", "the same CCD stage on one core"),
+            cpu_enumeration=cpu_enumeration(sc, xo))
+        if cpu is not None:
+            cpu["host_cores"] = cores
+
+    # ---- the other workloads, reported beside the headline (one GPU only)
+    extras = {}
+    if ws == 1 and not args.no_extras:
+        extras["adjoint_hvp"] = dict(workload=WORKLOAD, **hvp_stage(cs, sc, Q, lag_of, t0, min(K, 30), flush, dev))
+        cs.close()
+        extras["sphere_on_pad"] = bench_sphere_on_pad(dev)
+        extras["plate_in_rack"] = bench_plate_in_rack(args, dev, fp64)
+        extras["batched_vs_plain"] = batched_summary(args, ws, rank, local)
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=K, warmup=args.warmup,
                 ms_per_step=float(step_ms.mean()), higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -470,18 +700,135 @@ def run_ours(args, ws, rank, local):
                             dhat=sc.params["dhat"], mu=sc.params["mu"], parallelism=f"replicas x{ws}",
                             l2="flushed between steps (256 MiB rewrite)",
                             pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K,
+                            broad_phase_candidates_per_step=dict(contact=per_step["cand_contact"],
+                                                                 ccd=per_step["cand_ccd"]),
                             work_last_iterate=work),
                 clocks=clk, gpu_launches=int(launches), wall_s=wall, roofline=roof, rooflines=roofs,
+                fp64_probe=fp64, kernel_ms_timed=kernel_ms_timed,
                 ccd_queries_per_s=total_cand_all / total_s_all, stages=stage,
-                e2e=e2e, cpu_baseline=cpu, kernel_ms_warmup={k: v[0] for k, v in warm.items()},
+                e2e=e2e, cpu_baseline=cpu, **cpu_more, kernel_ms_warmup={k: v[0] for k, v in warm.items()},
                 autotune={k: dict(shape=v["shape"], ms=v["ms"], default_ms=v["default_ms"], cached=v["cached"])
-                          for k, v in tuned.items()})
+                          for k, v in tuned.items()},
+                **extras)
     if rank == 0:
         print(json.dumps(line), flush=True)
         if args.json_out:
             with open(args.json_out, "w") as f:
                 json.dump(line, f, indent=1)
+    if not extras:
+        cs.close()
+
+
+def bench_sphere_on_pad(dev, warmup=10, calls=50):
+    """Latency of the sphere-on-pad scene (a few hundred pairs): median over `calls` calls,
+    after `warmup`, of the whole contact stage and of its parts, each call timed with CUDA
+    events and the L2 flushed before it."""
+    import torch
+    from paper_2409_16385_gb300 import ContactScene, scenes
+    sc = scenes.make_config(1)
+    cs = ContactScene(sc, pair_capacity=1 << 16, bsr_capacity=1 << 18)
+    q = torch.tensor(sc.iterate(0), dtype=torch.float64, device=dev)
+    dq = torch.tensor(sc.dq(0), dtype=torch.float64, device=dev)
+    pairs, H = cs.new_pairs(), cs.new_bsr()
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros((sc.Ns, 3), dtype=torch.float64, device=dev)
+    x = torch.empty((sc.Nv, 3), dtype=torch.float64, device=dev)
+    dx = torch.empty_like(x)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    lag = cs.friction_lag(q, cs.build_candidates(q, out=pairs))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    parts = {
+        "build_candidates": lambda: cs.build_candidates(q, out=pairs),
+        "eval_contact": lambda: cs.eval_contact(q, pairs, lag, E=E, g_r=g, H=H),
+        "accd_toi": lambda: (cs.embed(q, out=x), cs.embed(dq, out=dx, displacement=True), cs.accd_toi(x, dx, alpha=alpha)),
+    }
+    parts["whole_stage"] = lambda: (parts["build_candidates"](), parts["eval_contact"](), parts["accd_toi"]())
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, fn in parts.items():
+        for _ in range(warmup):
+            fn()
+        ms = []
+        for _ in range(calls):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[name] = float(np.median(ms))
+    n = int(pairs.count.item())
+    st = cs.status()
     cs.close()
+    if st["flags"] & ~64:
+        raise RuntimeError(f"sphere on pad: device status {st}")
+    return dict(workload=sc.name, triangles=sc.F, vertices=sc.Nv, cage_nodes=sc.Ns, pairs=n,
+                median_ms=out, calls=calls, warmup=warmup, pairs_per_s=n / (out["whole_stage"] / 1e3),
+                timing="CUDA events per call, L2 flushed before each call")
+
+
+def bench_plate_in_rack(args, dev, fp64=None):
+    """The plate-in-rack scene (Sec. IV-B stand-in; many near-parallel edge-edge pairs) over
+    its 100 lowering iterates, one step = one Newton iteration's contact stage as in the
+    headline: pairs/s over whole steps, the evaluation kernel's FP64 roofline."""
+    import torch
+    from paper_2409_16385_gb300 import ContactScene, scenes
+    sc = scenes.make_config(3, small=args.quick)
+    n_it = sc.n_iterates
+    cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21)
+    Q = torch.tensor(np.stack([sc.iterate(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    DQ = torch.tensor(np.stack([sc.dq(t) for t in range(n_it)]), dtype=torch.float64, device=dev)
+    lag_of = [sc.lag_of(t) for t in range(n_it)]
+    pairs, lag, H = cs.new_pairs(), cs.new_lag(), cs.new_bsr()
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.zeros((sc.Ns, 3), dtype=torch.float64, device=dev)
+    x = torch.empty((sc.Nv, 3), dtype=torch.float64, device=dev)
+    dx = torch.empty_like(x)
+    alpha = torch.zeros(1, dtype=torch.float64, device=dev)
+    nc = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(t):
+        cs.build_candidates(Q[t], out=pairs)
+        if lag_of[t] == t:
+            cs.friction_lag(Q[t], pairs, out=lag)
+        cs.eval_contact(Q[t], pairs, lag, E=E, g_r=g, H=H)
+        cs.embed(Q[t], out=x)
+        cs.embed(DQ[t], out=dx, displacement=True)
+        cs.accd_toi(x, dx, alpha=alpha, n_candidates=nc)
+
+    cs.friction_lag(Q[lag_of[0]], cs.build_candidates(Q[lag_of[0]], out=pairs), out=lag)
+    for t in range(min(5, n_it)):
+        step(t)
+    torch.cuda.synchronize()
+    cs.timing_enable(["eval_barrier"])
+    ms, np_, nq = [], 0, 0
+    for t in range(n_it):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        np_ += int(pairs.count.item())
+        nq += int(nc.item())
+    kt = cs.timing_read()
+    work = cs.work_counts()
+    work.update(pair_split(sc, pairs.host()))
+    st = cs.status()
+    cs.close()
+    if st["flags"] & ~64:
+        raise RuntimeError(f"plate in rack: device status {st}")
+    total_s = float(np.sum(ms)) / 1e3
+    per_step = dict(pairs=np_ / n_it, ccd=nq / n_it)
+    roof = roofline_figure("eval_barrier", *kt.get("eval_barrier", (0.0, 0)), n_it, per_step, sc, fp64)
+    return dict(workload=sc.name, triangles=sc.F, vertices=sc.Nv, cage_nodes=sc.Ns, iterates=n_it,
+                value=np_ / total_s, unit=UNIT, ms_per_step=float(np.mean(ms)), pairs_per_step=np_ / n_it,
+                ccd_queries_per_s=nq / total_s, roofline_eval_barrier=roof, work_last_iterate=work,
+                timing="every iterate once, CUDA events per step, L2 flushed before each")
 
 
 def run_e2e(cs, sc, Q, DQ, lag_of, t0, K, flush, dev):
@@ -654,7 +1001,23 @@ def batched_oracle_sample(b, t, budget_s=20.0, seed=0, max_tris=8000):
                        f"{pairs} pairs in {secs:.1f} s")
 
 
-def run_batched(args, ws, rank, local):
+def batched_summary(args, ws, rank, local):
+    """The 256-scene batch beside the headline: 20 graph-replayed steps and the plain
+    per-scene path on the same iterates (no CPU leg, no end-to-end pass)."""
+    import copy
+    a = copy.copy(args)
+    a.steps, a.warmup = 20, max(3, min(args.warmup, 5))
+    a.no_cpu_baseline, a.no_e2e, a.no_plain = True, True, False
+    a.cand_cap, a.rec_cap = 0, 0
+    line = run_batched(a, ws, rank, local, emit=False)
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "plain_per_scene", "speedup_vs_plain", "roofline",
+            "clocks", "gpu_launches", "kernels_per_graph", "autotune", "ccd_queries_per_s", "scene_generation_s")
+    out = {k: line[k] for k in keep if k in line}
+    out["config"] = line["config"]
+    return out
+
+
+def run_batched(args, ws, rank, local, emit=True):
     """256 independent grasp scenes (surface sizes log-uniform in [2k, 50k] triangles, own
     closing phase each) in one scene with one group per scene.  One step is one CUDA graph
     replay of the whole contact stage of all scenes; the plain per-scene path (one
@@ -779,7 +1142,7 @@ def run_batched(args, ws, rank, local):
     st.cs.timing_enable([])
     dominant = max(kt.items(), key=lambda kv: kv[1][0])[0]
     dom_ms, dom_n = kt[dominant]
-    roof = roofline_figure(dominant, dom_ms, dom_n, K, total_pairs / K, total_cand / K, b)
+    roof = roofline_figure(dominant, dom_ms, dom_n, K, dict(pairs=total_pairs / K, ccd=total_cand / K), b)
     roof["timed"] = "eager replay of the timed steps with per-kernel CUDA-event timers"
 
     # ---- end to end: pinned host q, dq in; E per scene, alpha per scene, g_r out
@@ -883,12 +1246,14 @@ def run_batched(args, ws, rank, local):
                 kernels_per_graph={f"lag={a},rebuild={c}": int(n) for (a, c), n in kernels_per_graph.items()},
                 capacities=st.caps, scene_generation_s=gen_s,
                 kernel_ms_eager={k: v[0] for k, v in kt.items()})
+    st.cs.close()
+    if not emit:
+        return line
     if rank == 0:
         print(json.dumps(line), flush=True)
         if args.json_out:
             with open(args.json_out, "w") as f:
                 json.dump(line, f, indent=1)
-    st.cs.close()
 
 
 # --------------------------------------------------------------------------- adjoint

@@ -190,9 +190,13 @@ eipc_status eipc_contact_hvp(eipc_scene* scene, const double* q, const eipc_pair
  * eps_x = factor * rest_len2[i] * rest_len2[j] carries kappa m(c) b(d), m(c) = c (2/eps_x
  * - c/eps_x^2), in every later eval_contact, contact_hvp and friction_lag (whose lambda is
  * scaled by m at x^n); such pairs take a full 12 x 12 Hessian (PSD-projected by Jacobi for
- * eval_contact).  IPC's factor is 1e-3.  rest_len2: HOST [E], squared rest lengths of the
- * edges, all > 0.  factor = 0 turns it off.  Synchronous (copies rest_len2). */
-eipc_status eipc_scene_set_mollifier(eipc_scene* scene, const double* rest_len2, double factor);
+ * eval_contact).  IPC's factor is 1e-3.  x_rest: DEVICE [Nv*3] (caller-owned, read
+ * during the call only), the rest positions the edge lengths |e|^2 are taken from; the
+ * library computes and keeps the squared rest length of every edge.  Returns
+ * EIPC_ERR_INVALID (and leaves the mollifier off) if any edge has a zero or non-finite
+ * rest length.  factor = 0 turns it off (x_rest may then be NULL).  Synchronises `stream`
+ * (the length check is read back). */
+eipc_status eipc_scene_set_mollifier(eipc_scene* scene, const double* x_rest, double factor, eipc_stream stream);
 
 /* y <- alpha A x + beta y for a 3x3-block CSR matrix A with nrows block rows (the eipc_bsr
  * layout: row_ptr[nrows+1], col[nnzb], val[nnzb*9] row-major blocks), for the Krylov
@@ -226,6 +230,17 @@ eipc_status eipc_status_read(eipc_scene* scene, eipc_stream stream, int32_t* fla
  * Values beyond a buffer's capacity are clamped as the kernels clamp them. */
 enum { EIPC_WORK_COUNTS = 9 };
 eipc_status eipc_work_counts(eipc_scene* scene, eipc_stream stream, int64_t* out, int32_t n);
+
+/* The broad-phase candidate list of the scene's last eipc_build_candidates or
+ * eipc_accd_toi call (the pairs whose FP32 boxes overlap, before any exact test), for
+ * inspection and for running another implementation of the same stage on identical input
+ * (the CCD bound of Sec. III-C over the same candidates).  Entry k is a PT pair (type 0:
+ * vertex i[k], triangle j[k]) or an EE pair (type 1: edges i[k] < j[k]) in the list's own
+ * (unsorted) order.  type, i, j: caller-owned DEVICE int32 arrays of `capacity` entries;
+ * *n: DEVICE int64, set to the full count (entries beyond `capacity` are not written).
+ * Asynchronous on `stream`. */
+eipc_status eipc_candidates_read(eipc_scene* scene, int32_t* type, int32_t* i, int32_t* j, int64_t capacity,
+                                 int64_t* n, eipc_stream stream);
 
 /* Tracing: per-kernel CUDA-event timers.  Bit k of mask enables timer k (0 embed,
  * 1 bvh_build, 2 bvh_query, 3 narrow_phase, 4 pair_sort, 5 friction_lag, 6 stencil_nodes,
@@ -264,7 +279,8 @@ eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_strea
  * evaluation, 1 = BVH traversal, 2 = BVH bottom-up refit.  threads per block: 64, 128
  * (eval), 64, 128, 256 (traversal) or 256 (refit); blocks_per_sm: cap on the grid as a
  * multiple of the 152 SMs (1..64; ignored by the refit); variant: eval 2 = no register
- * cap, 3 = at most 170 registers (3 blocks of 128 per SM); refit 0 = arrival counters
+ * cap, 3 = at most 170 registers (3 blocks of 128 per SM); traversal 2 = no register cap,
+ * 3 = at most 40 registers (6 blocks of 256 per SM); refit 0 = arrival counters
  * behind full device fences, 1 = release-acquire arrival counters, 2 = treelets of up to
  * 32 leaves refitted per warp in shared memory below release-acquire counters (default).
  * Results never depend on the shape. */
@@ -309,6 +325,16 @@ eipc_status eipc_accd_toi_static(int64_t Nv, int64_t F, int64_t E, const double*
                                  const eipc_params* p, double* alpha, int32_t* flags, int64_t* n_advanced,
                                  eipc_stream stream);
 int64_t eipc_accd_static_max_vertices(void);
+
+/* FP64 throughput probe, a measurement utility with no counterpart in the paper: one
+ * launch of eight independent DFMA chains per thread, `iters` rounds each, over
+ * 4 x 152 blocks of 256 threads, on `stream`.  The caller times it (CUDA events on the same
+ * stream) and divides eipc_fp64_probe_flops(iters) by the time to get the device's FP64
+ * rate, the denominator of the FP64 rooflines.  sink: caller-owned DEVICE double array of
+ * at least 152 * 4 * 256 entries (only entry 0 is written in practice).  iters in
+ * [1, 2^30], else EIPC_ERR_INVALID.  Asynchronous. */
+eipc_status eipc_fp64_probe(int64_t iters, double* sink, eipc_stream stream);
+int64_t eipc_fp64_probe_flops(int64_t iters);
 
 /* Library version string: static, NUL-terminated ASCII owned by the library (never NULL,
  * never freed by the caller); needs no GPU. */

@@ -1,7 +1,7 @@
 """Launch-shape autotuner for the kernels whose best shape depends on the workload: the
 per-pair barrier evaluation (threads per block, grid cap in blocks per SM, register
-budget), the BVH traversal (threads per block, grid cap) and the BVH refit (how its
-bottom-up arrival counters are ordered).
+budget), the BVH traversal (threads per block, grid cap, register budget) and the BVH
+refit (how its bottom-up arrival counters are ordered).
 
 Results never depend on the shape: every kernel is a grid-stride loop over a device-side
 count, and every reduction order is fixed by sort keys, not by the launch.  So the tuner
@@ -20,7 +20,7 @@ from typing import Callable, Dict, Iterable, Optional, Tuple
 EVAL_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
     (threads, bps, variant) for threads in (64, 128) for bps in (2, 3, 4, 6, 8, 16) for variant in (2, 3))
 QUERY_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
-    (threads, bps, 2) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32))
+    (threads, bps, variant) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32) for variant in (2, 3))
 
 REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1), (256, 8, 2))
 

@@ -26,7 +26,7 @@ EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
            "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
            "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier", "eipc_bsr_spmv",
-           "eipc_work_counts"]
+           "eipc_work_counts", "eipc_candidates_read", "eipc_fp64_probe", "eipc_fp64_probe_flops"]
 
 
 class Params(ctypes.Structure):
@@ -107,10 +107,16 @@ def load(build_if_missing: bool = True):
     L.eipc_contact_hvp.restype = i32
     L.eipc_scene_set_kinematic.argtypes = [P, P, P]
     L.eipc_scene_set_kinematic.restype = i32
-    L.eipc_scene_set_mollifier.argtypes = [P, P, ctypes.c_double]
+    L.eipc_scene_set_mollifier.argtypes = [P, P, ctypes.c_double, P]
     L.eipc_scene_set_mollifier.restype = i32
     L.eipc_bsr_spmv.argtypes = [i64, P, P, P, P, ctypes.c_double, ctypes.c_double, P, P]
     L.eipc_bsr_spmv.restype = i32
+    L.eipc_candidates_read.argtypes = [P, P, P, P, i64, P, P]
+    L.eipc_candidates_read.restype = i32
+    L.eipc_fp64_probe.argtypes = [i64, P, P]
+    L.eipc_fp64_probe.restype = i32
+    L.eipc_fp64_probe_flops.argtypes = [i64]
+    L.eipc_fp64_probe_flops.restype = i64
     _lib = L
     return L
 
@@ -315,14 +321,29 @@ class ContactScene:
 
     def set_mollifier(self, x_rest=None, factor: float = 1e-3):
         """EE mollifier with eps_x = factor |e_i|^2 |e_j|^2 at the rest positions x_rest
-        (host [Nv,3]); x_rest None turns it off."""
+        ([Nv,3], moved to the device); x_rest None turns it off."""
+        import torch
         if x_rest is None:
-            _check(self.lib.eipc_scene_set_mollifier(self.handle, None, 0.0), "eipc_scene_set_mollifier")
+            _check(self.lib.eipc_scene_set_mollifier(self.handle, None, 0.0, _stream()), "eipc_scene_set_mollifier")
             return
-        e = np.asarray(self.scene.edges)
-        xr = np.asarray(x_rest, np.float64)
-        r2 = np.ascontiguousarray(np.sum((xr[e[:, 1]] - xr[e[:, 0]]) ** 2, axis=1), np.float64)
-        _check(self.lib.eipc_scene_set_mollifier(self.handle, r2.ctypes.data, float(factor)), "eipc_scene_set_mollifier")
+        xr = torch.as_tensor(x_rest, dtype=torch.float64, device=self.device).contiguous()
+        _check(self.lib.eipc_scene_set_mollifier(self.handle, _ptr(xr), float(factor), _stream()),
+               "eipc_scene_set_mollifier")
+
+    def candidates(self, capacity: Optional[int] = None):
+        """The broad-phase candidate list of the last build_candidates or accd_toi call, as
+        device int32 tensors (type, i, j) (eipc_candidates_read; synchronises once to size
+        the result)."""
+        import torch
+        n = torch.zeros(1, dtype=torch.int64, device=self.device)
+        _check(self.lib.eipc_candidates_read(self.handle, None, None, None, 0, _ptr(n), _stream()),
+               "eipc_candidates_read")
+        m = int(n.item()) if capacity is None else int(capacity)
+        out = [torch.empty(max(m, 1), dtype=torch.int32, device=self.device) for _ in range(3)]
+        _check(self.lib.eipc_candidates_read(self.handle, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), m, _ptr(n),
+                                             _stream()), "eipc_candidates_read")
+        k = min(m, int(n.item()))
+        return out[0][:k], out[1][:k], out[2][:k]
 
     def set_dedup(self, on: bool = True):
         """Deduplicated contact sets from build_candidates (EIPC_PARAM_DEDUP)."""
@@ -413,6 +434,26 @@ class ContactScene:
 
 WORK_COUNTS = ("candidates", "screened", "pairs", "items", "hessian_records", "gradient_records", "hessian_blocks",
                "gradient_nodes", "ccd_advanced")
+
+
+def fp64_peak(iters: int = 1 << 16, repeats: int = 5) -> dict:
+    """Measured FP64 rate of the current device (eipc_fp64_probe): the best of `repeats`
+    launches timed with CUDA events on the current stream, in TFLOP/s."""
+    import torch
+    L = load()
+    sink = torch.zeros(152 * 4 * 256, dtype=torch.float64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    best = None
+    _check(L.eipc_fp64_probe(1024, _ptr(sink), _stream()), "eipc_fp64_probe")     # warm-up
+    for _ in range(repeats):
+        ev[0].record()
+        _check(L.eipc_fp64_probe(int(iters), _ptr(sink), _stream()), "eipc_fp64_probe")
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1])
+        best = ms if best is None else min(best, ms)
+    flops = L.eipc_fp64_probe_flops(int(iters))
+    return dict(tflops=flops / (best / 1e3) / 1e12, ms=best, flops=int(flops), iters=int(iters))
 
 
 def bsr_spmv(row_ptr, col, val, x, out=None, alpha: float = 1.0, beta: float = 0.0):

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libembipc.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["api.cu", "pairs.cu", "eval.cu", "accd.cu", "bvh.cu", "sort.cu", "accd_static.cu", "groups.cu", "solve.cu"]
+SOURCES = ["api.cu", "pairs.cu", "eval.cu", "accd.cu", "bvh.cu", "sort.cu", "accd_static.cu", "groups.cu", "solve.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -203,7 +203,8 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
   }
   EIPC_TIMED(sc, kKQuery, s,
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
+                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps,
+                       sc->tune.query_variant));
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 
                  sc->topo, sc->x4, sc->dx4, sc->cand, n_cand, sc->cand_cap, p.accd_s, p.accd_max_iter, abits, sc->group_alpha_bits, n_adv,

@@ -296,16 +296,32 @@ eipc_status eipc_bsr_spmv(int64_t nrows, const int32_t* row_ptr, const int32_t* 
   return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
 }
 
-eipc_status eipc_scene_set_mollifier(eipc_scene* sc, const double* rest_len2, double factor) {
-  if (!sc || !(factor >= 0.0) || !std::isfinite(factor) || (factor > 0.0 && !rest_len2)) return EIPC_ERR_INVALID;
-  if (factor > 0.0) {
-    for (int64_t e = 0; e < sc->ne; ++e)
-      if (!(rest_len2[e] > 0.0) || !std::isfinite(rest_len2[e])) return EIPC_ERR_INVALID;
-    if (sc->ne > 0 && cudaMemcpy(sc->moll_r2, rest_len2, sizeof(double) * sc->ne, cudaMemcpyHostToDevice) != cudaSuccess)
+eipc_status eipc_scene_set_mollifier(eipc_scene* sc, const double* x_rest, double factor, eipc_stream stream) {
+  if (!sc || !(factor >= 0.0) || !std::isfinite(factor) || (factor > 0.0 && !x_rest)) return EIPC_ERR_INVALID;
+  if (factor > 0.0 && sc->ne > 0) {
+    // squared rest lengths on the device, then a synchronous check that all are positive
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t* bad = sc->counters + kCntMollBad;
+    if (cudaMemsetAsync(bad, 0, sizeof(int64_t), s) != cudaSuccess) return EIPC_ERR_CUDA;
+    mollifier_rest_launch(sc, x_rest, bad, s);
+    int64_t nbad = -1;
+    if (cudaMemcpyAsync(&nbad, bad, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
       return EIPC_ERR_CUDA;
+    if (nbad != 0) {
+      sc->moll_factor = 0.0;
+      return EIPC_ERR_INVALID;
+    }
   }
   sc->moll_factor = factor;
   return EIPC_OK;
+}
+
+eipc_status eipc_candidates_read(eipc_scene* sc, int32_t* type, int32_t* i, int32_t* j, int64_t capacity,
+                                 int64_t* n, eipc_stream stream) {
+  if (!sc || !n || capacity < 0 || (capacity > 0 && (!type || !i || !j))) return EIPC_ERR_INVALID;
+  candidates_launch(sc, type, i, j, capacity, n, (cudaStream_t)stream);
+  return cudaPeekAtLastError() == cudaSuccess ? EIPC_OK : EIPC_ERR_CUDA;
 }
 
 eipc_status eipc_scene_set_kinematic(eipc_scene* sc, const double* x_kin, eipc_stream stream) {
@@ -427,9 +443,10 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
     return EIPC_OK;
   }
   if (kernel == 1) {
-    if (threads != 64 && threads != 128 && threads != 256) return EIPC_ERR_INVALID;
+    if ((threads != 64 && threads != 128 && threads != 256) || (variant != 2 && variant != 3)) return EIPC_ERR_INVALID;
     sc->tune.query_threads = threads;
     sc->tune.query_bps = blocks_per_sm;
+    sc->tune.query_variant = variant;
     return EIPC_OK;
   }
   if (kernel == 2) {

@@ -460,9 +460,13 @@ __device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_ca
 
 // One launch for both query sets: threads [0, nv) run vertex boxes against the triangle
 // tree (PT), threads [nv, nv + ne) run edge boxes against the edge tree (EE, j > i), the
-// edges in that tree's Morton order so neighbouring threads take similar paths.
-__global__ void __launch_bounds__(256) k_query(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
-                                               uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
+// edges in that tree's Morton order so neighbouring threads take similar paths.  MINB is
+// the minimum number of 256-thread blocks per SM the register allocation must allow: the
+// walk is latency-bound (dependent node fetches), so more resident warps hide more of it;
+// 4 leaves the compiler free (54 registers), 6 caps it at 40 registers.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_query(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
+                                                     uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
   const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);
   const int64_t nv_q = tt.n > 0 ? T.nv : 0;
   for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += grid_stride()) {
@@ -614,10 +618,13 @@ void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const float* vbox, cudaS
 }
 
 void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* vbox_q, uint64_t* cand,
-               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps) {
+               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps, int variant) {
   const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
-  launch(k_query, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
+  if (variant == 3)
+    launch(k_query<6>, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
+  else
+    launch(k_query<4>, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
 }
 
 }  // namespace eipc

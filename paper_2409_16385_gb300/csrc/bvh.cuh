@@ -96,6 +96,6 @@ void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, 
 // are appended as pair keys to cand[0..cap) with the running count in *n_cand, and an
 // overflow raises CAND_OVERFLOW.
 void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* vbox_q, uint64_t* cand,
-               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads = 128, int bps = 24);
+               int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps, int variant);
 
 }  // namespace eipc

@@ -293,7 +293,50 @@ __global__ void __launch_bounds__(kBlock) k_set_kinematic(int64_t nv, const int3
     x_kin4[4 * v + 2] = x_kin[3 * v + 2];
   }
 }
+// squared rest length of every edge, |x_b - x_a|^2 from rest positions x_rest [nv*3]; bad
+// counts the edges whose squared length is not a positive finite number
+__global__ void __launch_bounds__(kBlock) k_edge_rest_len2(int64_t ne, const int32_t* __restrict__ edges,
+                                                           const double* __restrict__ x_rest, double* __restrict__ r2,
+                                                           int64_t* bad) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += grid_stride()) {
+    const int64_t a = edges[2 * e], b = edges[2 * e + 1];
+    const double dx = x_rest[3 * b] - x_rest[3 * a];
+    const double dy = x_rest[3 * b + 1] - x_rest[3 * a + 1];
+    const double dz = x_rest[3 * b + 2] - x_rest[3 * a + 2];
+    const double l2 = dx * dx + dy * dy + dz * dz;
+    r2[e] = l2;
+    if (!(l2 > 0.0 && l2 <= 1.7976931348623157e308)) atomicAdd(reinterpret_cast<unsigned long long*>(bad), 1ull);
+  }
+}
+
+// candidate keys (type << (bits_i + bits_j) | i << bits_j | j) decoded into three arrays
+__global__ void __launch_bounds__(kBlock) k_decode_candidates(Topo T, const uint64_t* __restrict__ cand,
+                                                              const int64_t* n_cand, int64_t cand_cap, int64_t out_cap,
+                                                              int32_t* __restrict__ type, int32_t* __restrict__ ci,
+                                                              int32_t* __restrict__ cj, int64_t* n_out) {
+  const int64_t n = clamp_count(n_cand, cand_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = n;
+  const int64_t m = n < out_cap ? n : out_cap;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += grid_stride()) {
+    const uint64_t key = cand[k];
+    cj[k] = (int32_t)(key & ((1ull << T.bits_j) - 1));
+    ci[k] = (int32_t)((key >> T.bits_j) & ((1ull << T.bits_i) - 1));
+    type[k] = (int32_t)(key >> (T.bits_i + T.bits_j));
+  }
+}
 }  // namespace
+
+void mollifier_rest_launch(eipc_scene* sc, const double* x_rest, int64_t* bad, cudaStream_t s) {
+  launch(k_edge_rest_len2, blocks_for(sc->ne), kBlock, 0, s, sc->ne, static_cast<const int32_t*>(sc->edges), x_rest,
+         sc->moll_r2, bad);
+}
+
+void candidates_launch(eipc_scene* sc, int32_t* type, int32_t* ci, int32_t* cj, int64_t cap, int64_t* n,
+                       cudaStream_t s) {
+  launch(k_decode_candidates, blocks_for(sc->cand_cap), kBlock, 0, s, sc->topo,
+         static_cast<const uint64_t*>(sc->cand), static_cast<const int64_t*>(sc->counters + kCntCand), sc->cand_cap,
+         cap, type, ci, cj, n);
+}
 
 void set_kinematic_launch(eipc_scene* sc, const double* x_kin, cudaStream_t s) {
   launch(k_set_kinematic, blocks_for(sc->nv), kBlock, 0, s, sc->nv, static_cast<const int32_t*>(sc->cage_idx), x_kin,
@@ -325,7 +368,8 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   }
   EIPC_TIMED(sc, kKQuery, s,
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox_pad, sc->cand, n_cand, sc->cand_cap,
-                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps));
+                       sc->status, s, sc->tune.query_threads, sc->tune.query_bps,
+                       sc->tune.query_variant));
   int64_t* n_cand2 = sc->counters + kCntScreened;
   cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
   sc->timers->start(kKNarrow, s);

@@ -85,7 +85,7 @@ struct eipc_scene {
   int rebuild_interval;  // contact LBVH: full rebuild every this many build_candidates calls
   struct {
     int eval_threads = 128, eval_bps = 16, eval_variant = 2;
-    int query_threads = 128, query_bps = 24;
+    int query_threads = 128, query_bps = 24, query_variant = 2;
     int refit_variant = 2;
   } tune;                // launch shapes of the tunable kernels (eipc_set_launch)
   int contact_refits;    // refits since the last full rebuild
@@ -100,7 +100,7 @@ constexpr int kHRecStride = 10, kGRecStride = 4;
 
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
        kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntScreened = 15, kCntDedup = 17, kCntUnitsH = 18,
-       kCntUnitsG = 19,
+       kCntUnitsG = 19, kCntMollBad = 20,
        kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \
@@ -122,6 +122,9 @@ void group_energy_launch(eipc_scene* sc, double* E_groups, cudaStream_t s);
 void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
                 const double* v, const double* kin_dir, double* out_r, double* out_kin, cudaStream_t s);
 void set_kinematic_launch(eipc_scene* sc, const double* x_kin, cudaStream_t s);
+void mollifier_rest_launch(eipc_scene* sc, const double* x_rest, int64_t* bad, cudaStream_t s);
+void candidates_launch(eipc_scene* sc, int32_t* type, int32_t* ci, int32_t* cj, int64_t cap, int64_t* n,
+                       cudaStream_t s);
 void bsr_spmv_launch(int64_t nrows, const int32_t* row_ptr, const int32_t* col, const double* val, const double* x,
                      double alpha, double beta, double* y, cudaStream_t s);
 void group_alpha_launch(eipc_scene* sc, double* alpha_groups, cudaStream_t s);

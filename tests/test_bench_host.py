@@ -42,36 +42,41 @@ class _Sizes:
     Nv, E, F = 1000, 3000, 2000
 
 
+PER_STEP = dict(pairs=1e5, ccd=2e4, cand_contact=1e6, cand_ccd=3e5)
+
+
 def test_roofline_of_the_fp64_evaluation():
     """eval_barrier: achieved = pairs per launch x FP64 flops per pair / launch time, against
     the FP64 peak of 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz; traffic from the per-pair
-    ncu figure."""
-    r = bench.roofline_figure("eval_barrier", total_ms=20.0, launches=10, steps=10,
-                              pairs_per_step=1e5, cand_per_step=1e6, sc=_Sizes)
+    ncu figure; the live probe's rate is reported beside it."""
+    r = bench.roofline_figure("eval_barrier", 20.0, 10, 10, PER_STEP, _Sizes, dict(tflops=1.2))
     ach = 1e5 * bench.FP64_FLOPS_PER_PAIR / 2e-3 / 1e12
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - ach) <= 1e-12 * ach
     assert abs(r["peak"] - 152 * 4 * 2.07e9 / 1e12) <= 1e-12
     assert abs(r["frac"] - ach / r["peak"]) <= 1e-12
+    assert abs(r["frac_of_probe"] - ach / 1.2) <= 1e-12 and r["peak_probe"] == 1.2
     assert r["traffic"] == bench.NCU_TRAFFIC_PER_UNIT["eval_barrier"] * 1e5
     # two launches per step split the step's pairs
-    r2 = bench.roofline_figure("eval_barrier", total_ms=20.0, launches=20, steps=10,
-                               pairs_per_step=1e5, cand_per_step=1e6, sc=_Sizes)
-    assert abs(r2["achieved"] - ach) <= 1e-12 * ach
+    r2 = bench.roofline_figure("eval_barrier", 20.0, 20, 10, PER_STEP, _Sizes)
+    assert abs(r2["achieved"] - ach) <= 1e-12 * ach and "peak_probe" not in r2
 
 
-def test_roofline_of_a_memory_bound_kernel(monkeypatch):
+def test_roofline_of_the_traversal_uses_both_traversals_candidates(monkeypatch):
+    """bvh_query runs twice per step (contact set, CCD): its bytes per launch average the
+    two launches' minimum traffic, each with its own candidate count."""
     monkeypatch.setattr(bench, "measured_peaks", lambda: (6000.0, "measured"))
-    r = bench.roofline_figure("bvh_query", total_ms=5.0, launches=10, steps=10,
-                              pairs_per_step=1e5, cand_per_step=1e6, sc=_Sizes)
-    b = 0.5 * (32 * 1000 + 72 * 3000 + 64 * 5000 + 8 * 1e6)
+    r = bench.roofline_figure("bvh_query", 5.0, 20, 10, PER_STEP, _Sizes)
+    base = 32 * 1000 + 8 * 3000 + 64 * (2 * 2000 + 2 * 3000)
+    b = 0.5 * ((base + 8 * 1e6) + (base + 8 * 3e5))
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == 6000.0
-    assert abs(r["achieved"] - b / 5e-4 / 1e9) <= 1e-9 and abs(r["frac"] - r["achieved"] / 6000.0) <= 1e-15
-    assert r["peak_source"] == "measured"
+    assert abs(r["bytes_per_launch"] - b) <= 1e-9 * b
+    assert abs(r["achieved"] - b / 2.5e-4 / 1e9) <= 1e-9 and abs(r["frac"] - r["achieved"] / 6000.0) <= 1e-15
+    assert r["peak_source"] == "measured" and "latency-bound" in r["note"]
 
 
 def test_roofline_without_launches_and_peak_fallback(monkeypatch, tmp_path):
-    r = bench.roofline_figure("bvh_query", 0.0, 0, 10, 1.0, 1.0, _Sizes)
+    r = bench.roofline_figure("bvh_query", 0.0, 0, 10, PER_STEP, _Sizes)
     assert r["frac"] is None and r["achieved"] is None
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))          # no peaks file there
     assert bench.measured_peaks() == (6800.0, "fallback")
@@ -97,3 +102,73 @@ def test_cpu_leg_sample_with_every_query_is_the_whole_contact_set():
     n, dt, n_cand = bench.oracle_sample(sc, 3, 1.0)
     full = oracle.pairs(sc, oracle.embed(sc, sc.iterate(3)))
     assert n == len(full["type"]) > 0 and dt > 0 and n_cand > 0
+
+
+def test_swept_overlap_matches_a_direct_box_test():
+    """The host-side copy of the CCD's exact FP64 swept-box test, against boxes built
+    pair by pair."""
+    import numpy as np
+    import oracle
+    from paper_2409_16385_gb300 import scenes
+    sc = scenes.make_config(1)
+    x = oracle.embed(sc, sc.iterate(0))
+    dx = oracle.embed(sc, sc.dq(0), displacement=True)
+    rng = np.random.default_rng(1)
+    n = 3000
+    ct = rng.integers(0, 2, n).astype(np.int32)
+    ci = np.where(ct == 0, rng.integers(0, sc.Nv, n), rng.integers(0, sc.E, n)).astype(np.int32)
+    cj = np.where(ct == 0, rng.integers(0, sc.F, n), rng.integers(0, sc.E, n)).astype(np.int32)
+    # random pairs (mostly far apart) and the contact pairs (close: mostly overlapping)
+    near = oracle.pairs(sc, x)
+    ct = np.concatenate([ct, near["type"]]).astype(np.int32)
+    ci = np.concatenate([ci, near["i"]]).astype(np.int32)
+    cj = np.concatenate([cj, near["j"]]).astype(np.int32)
+    n = len(ct)
+    cand = dict(type=ct, i=ci, j=cj)
+    got = bench.swept_overlap(sc, x, dx, cand)
+    for k in range(n):
+        if ct[k] == 0:
+            A, B = [ci[k]], list(sc.tris[cj[k]])
+        else:
+            A, B = list(sc.edges[ci[k]]), list(sc.edges[cj[k]])
+        pa = np.concatenate([x[A], x[A] + dx[A]]); pb = np.concatenate([x[B], x[B] + dx[B]])
+        ov = np.all(pa.min(0) <= pb.max(0)) and np.all(pb.min(0) <= pa.max(0))
+        assert got[k] == ov, k
+    assert 0 < got.sum() < n
+
+
+def test_pair_split_counts_pairs_between_bodies():
+    import numpy as np
+    from paper_2409_16385_gb300 import scenes
+    sc = scenes.make_config(1)                                  # sphere (body 0) on the pad (body 1)
+    body = np.asarray(sc.body)
+    v_sphere = int(np.nonzero(body == 0)[0][0])
+    f_pad = int(np.nonzero(body[sc.tris[:, 0]] == 1)[0][0])
+    f_sphere = int(np.nonzero(body[sc.tris[:, 0]] == 0)[0][-1])
+    e_pad = int(np.nonzero(body[sc.edges[:, 0]] == 1)[0][0])
+    e_sph = int(np.nonzero(body[sc.edges[:, 0]] == 0)[0][0])
+    h = dict(type=np.array([0, 0, 1, 1]), i=np.array([v_sphere, v_sphere, e_sph, e_sph]),
+             j=np.array([f_pad, f_sphere, e_pad, e_sph + 1]))
+    assert bench.pair_split(sc, h) == dict(inter_body=2, intra_body=2)
+
+
+def test_cpu_stage_baseline_runs_each_stage_on_the_given_lists():
+    """The CPU legs time the oracle's evaluation and CCD stages over given lists (here the
+    oracle's own, standing in for the GPU's), on all cores and on one core, and restore the
+    thread count."""
+    import oracle
+    from paper_2409_16385_gb300 import scenes
+    sc = scenes.make_config(2, small=True)
+    x, xn = oracle.embed(sc, sc.iterate(3)), oracle.embed(sc, sc.iterate(sc.lag_of(3)))
+    dx = oracle.embed(sc, sc.dq(3), displacement=True)
+    prs, pn = oracle.pairs(sc, x), oracle.pairs(sc, xn)
+    cand = dict(type=prs["type"], i=prs["i"], j=prs["j"])
+    n0 = oracle.num_threads()
+    r = bench.cpu_stage_baseline(sc, x, xn, dx, prs, pn, cand, budget_s=0.2)
+    assert oracle.num_threads() == n0
+    assert set(r) == {"eval_all", "eval_1core", "ccd_all", "ccd_1core"}
+    assert r["eval_1core"]["threads"] == 1 and r["eval_all"]["threads"] == n0
+    assert all(v["value"] > 0 for v in r.values())
+    assert r["eval_all"]["list_pairs"] == len(prs["type"])
+    e = bench.cpu_enumeration(sc, x, n_queries=50)
+    assert e["pairs_found"] >= 0 and e["full_enumeration_s_estimate"] > 0

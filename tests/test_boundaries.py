@@ -67,7 +67,8 @@ def test_oracle_includes_and_imports_nothing_of_the_library():
 
 def test_bench_reaches_the_oracle_only_in_its_cpu_legs():
     tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
-    allowed = {"oracle_sample", "run_reference", "batched_oracle_sample", "cpu_baseline"}
+    allowed = {"oracle_sample", "run_reference", "batched_oracle_sample", "cpu_baseline", "cpu_stage_baseline",
+               "cpu_enumeration", "reference_list"}
     for node in tree.body:
         if isinstance(node, (ast.Import, ast.ImportFrom)):
             names = [a.name for a in node.names] if isinstance(node, ast.Import) else [node.module or ""]

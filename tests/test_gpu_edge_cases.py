@@ -229,3 +229,44 @@ def test_degenerate_surface_primitives_match_the_oracle():
     check_eval(E.item(), g.cpu().numpy(), H.host(), ro, sc.Ns)
     ao = oracle.accd(sc, x, oracle.embed(sc, dq, displacement=True))["alpha"]
     assert 0.0 < ao < 1.0 and a <= ao and ao - a <= 1e-6
+
+
+def test_candidate_readout_covers_the_pairs_and_the_ccd_input():
+    """eipc_candidates_read returns the broad phase of the last call: after
+    build_candidates a superset of the contact pairs; after accd_toi the list whose exact
+    FP64 swept-box overlaps are the candidates the CCD advanced, and the oracle's
+    advancement over exactly those gives the oracle's step bound."""
+    from paper_2409_16385_gb300 import ContactScene
+    sc = scenes.make_config(1)
+    cs = ContactScene(sc, pair_capacity=1 << 14, bsr_capacity=1 << 16)
+    q = sc.iterate(0)
+    pairs = cs.build_candidates(_t(q))
+    ct, ci, cj = (a.cpu().numpy() for a in cs.candidates())
+    h = pairs.host()
+    cand = set(zip(ct.tolist(), ci.tolist(), cj.tolist()))
+    assert len(h["type"]) > 0
+    assert set(zip(h["type"].tolist(), h["i"].tolist(), h["j"].tolist())) <= cand
+    x = cs.embed(_t(q))
+    dx = cs.embed(_t(sc.dq(0)), displacement=True)
+    nadv = torch.zeros(1, dtype=torch.int64, device="cuda")
+    a = cs.accd_toi(x, dx, n_candidates=nadv).item()
+    ct, ci, cj = (a_.cpu().numpy() for a_ in cs.candidates())
+    xo = oracle.embed(sc, q)
+    dxo = oracle.embed(sc, sc.dq(0), displacement=True)
+    st = np.zeros((len(ct), 4), np.int64)                       # stencil vertices
+    pt = ct == 0
+    st[pt] = np.c_[ci[pt], sc.tris[cj[pt]]]
+    st[~pt] = np.c_[sc.edges[ci[~pt]], sc.edges[cj[~pt]]]
+    na = np.where(ct == 0, 1, 2)
+    p0, p1 = xo[st], xo[st] + dxo[st]
+    lo, hi = np.minimum(p0, p1), np.maximum(p0, p1)
+    side_a = np.arange(4)[None, :] < na[:, None]
+    big = np.inf
+    loA = np.where(side_a[..., None], lo, big).min(1); hiA = np.where(side_a[..., None], hi, -big).max(1)
+    loB = np.where(~side_a[..., None], lo, big).min(1); hiB = np.where(~side_a[..., None], hi, -big).max(1)
+    ov = ~((loA > hiB) | (loB > hiA)).any(1)
+    assert int(ov.sum()) == int(nadv.item())
+    ao = oracle.accd(sc, xo, dxo)
+    al = oracle.accd_list(sc, xo, dxo, dict(type=ct[ov], i=ci[ov], j=cj[ov]))
+    assert al["alpha"] == ao["alpha"]
+    assert a <= ao["alpha"] and ao["alpha"] - a <= 1e-6

@@ -85,3 +85,25 @@ def test_mollified_hvp_matches_oracle(sheets):
     ro, rk = oracle.hvp(sc, x1, prs, lo, u)
     assert np.abs(out.cpu().numpy() - ro).max() <= TOL * np.abs(ro).max()
     assert np.abs(out_kin.cpu().numpy() - rk).max() <= TOL * np.abs(rk).max()
+
+
+def test_mollifier_rest_lengths_are_checked_in_the_library():
+    """The library takes the rest positions and computes the edges' squared rest lengths
+    itself; a zero-length edge at rest is refused and leaves the mollifier off."""
+    from paper_2409_16385_gb300 import ContactScene
+    sc = scenes.parallel_sheets()
+    xr = oracle.embed(sc, sc.q_rest)
+    cs = ContactScene(sc, pair_capacity=1 << 18, bsr_capacity=1 << 19, rec_capacity=1 << 22)
+    q1 = _t(sc.iterate(1))
+    pairs = cs.build_candidates(q1)
+    E_off, _, _ = cs.eval_contact(q1, pairs)
+    bad = xr.copy()
+    a, b = sc.edges[7]
+    bad[b] = bad[a]
+    with pytest.raises(RuntimeError):
+        cs.set_mollifier(bad)
+    E_bad, _, _ = cs.eval_contact(q1, pairs)
+    assert E_bad.item() == E_off.item()
+    cs.set_mollifier(xr)
+    E_on, _, _ = cs.eval_contact(q1, pairs)
+    assert E_on.item() != E_off.item()
