@@ -628,6 +628,9 @@ def run_ours(args, ws, rank, local):
         cand_ccd.append(cs.work_counts()["candidates"])
     stage["ccd_queries_per_s"] = n_c / (ac_ms / 1e3)
     stage["ccd_queries_per_s_in_step"] = total_cand / total_s
+    if ws == 1:
+        stage["graph_replay"] = graph_steps(sc, Q, DQ, lag_of, t0, K, flush, dev,
+                                            {k: v["shape"] for k, v in tuned.items()})
     wc = cs.work_counts()
     work["ccd_candidates"], work["ccd_advanced"] = wc["candidates"], wc["ccd_advanced"]
 
@@ -915,7 +918,7 @@ class _Stage:
     def __init__(self, sc, caps, groups, dev):
         import torch
         from paper_2409_16385_gb300 import ContactScene
-        self.sc, self.caps = sc, caps
+        self.sc, self.caps, self.groups = sc, caps, groups is not None
         self.cs = ContactScene(sc, pair_capacity=caps["pair"], bsr_capacity=caps["bsr"], cand_capacity=caps["cand"],
                                rec_capacity=caps["rec"])
         ng = 1
@@ -941,11 +944,79 @@ class _Stage:
         if lag_step:
             cs.friction_lag(self.q, self.pairs, out=self.lag)
         cs.eval_contact(self.q, self.pairs, self.lag, E=self.E, g_r=self.g, H=self.H)
-        cs.group_energy(out=self.Eg)
+        if self.groups:
+            cs.group_energy(out=self.Eg)
         cs.embed(self.q, out=self.x)
         cs.embed(self.dq, out=self.dx, displacement=True)
         cs.accd_toi(self.x, self.dx, alpha=self.alpha, n_candidates=self.ncand)
-        cs.group_alpha(out=self.ag)
+        if self.groups:
+            cs.group_alpha(out=self.ag)
+
+
+def capture_step_graphs(st, q_warm, dq_warm, R):
+    """One CUDA graph of the whole contact stage per (lag step, hierarchy rebuild) case:
+    the rebuild-or-refit choice is made on the host when a call is enqueued, so each case is
+    captured with the rebuild interval forced to it.  Returns ({case: graph}, {case: kernels})."""
+    import torch
+    from paper_2409_16385_gb300 import binding
+    lib = binding.load()
+    graphs, kernels = {}, {}
+    side = torch.cuda.Stream()
+    for lag_step in (False, True):
+        for rebuild in (True, False):
+            st.cs.set_rebuild_interval(1 if rebuild else 1 << 30)
+            st.q.copy_(q_warm); st.dq.copy_(dq_warm)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                st(lag_step)                      # warm-up on the side stream
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            n0 = lib.eipc_launch_count()
+            with torch.cuda.graph(g):
+                st(lag_step)
+            kernels[(lag_step, rebuild)] = lib.eipc_launch_count() - n0
+            graphs[(lag_step, rebuild)] = g
+    st.cs.set_rebuild_interval(R)
+    torch.cuda.synchronize()
+    return graphs, kernels
+
+
+def graph_steps(sc, Q, DQ, lag_of, t0, K, flush, dev, shapes):
+    """The headline's steps replayed from CUDA graphs (the library's calls are capturable:
+    no host read-back), with the same launch shapes, iterates, L2 flush and CUDA-event
+    timing: how much of the eager step is host launch overhead."""
+    import torch
+    n_it = sc.n_iterates
+    R = 8
+    st = _Stage(sc, dict(pair=1 << 21, bsr=1 << 21, cand=0, rec=0), None, dev)
+    for k, shape in shapes.items():
+        st.cs.set_launch(k, *shape)
+    graphs, kernels = capture_step_graphs(st, Q[t0], DQ[t0], R)
+    st.q.copy_(Q[lag_of[t0]])
+    st(True)
+    stream = torch.cuda.current_stream()
+    ms, n_p = [], torch.zeros(K, dtype=torch.int64, device=dev)
+    for k in range(K):
+        t = (t0 + k) % n_it
+        st.q.copy_(Q[t]); st.dq.copy_(DQ[t])
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graphs[(lag_of[t] == t, k % R == 0)].replay()
+        e1.record(stream)
+        n_p[k].copy_(st.pairs.count[0])
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ms])
+    stt = st.cs.status()
+    st.cs.close()
+    if stt["flags"] & ~64:
+        raise RuntimeError(f"graph steps: device status {stt}")
+    pairs = float(n_p.sum().item())
+    return dict(ms_per_step=float(step_ms.mean()), pairs_per_s=pairs / (step_ms.sum() / 1e3),
+                kernels_per_step={f"lag={a},rebuild={c}": int(n) for (a, c), n in kernels.items()},
+                timing="CUDA events around each replay, L2 flushed before each, the headline's iterates")
 
 
 def _sized_stage(sc, caps, groups, dev, Q, DQ, lag_of, ts):
@@ -1054,23 +1125,7 @@ def run_batched(args, ws, rank, local, emit=True):
 
     # ---- one graph per (lag step, hierarchy rebuild) combination
     R = 8
-    graphs, kernels_per_graph = {}, {}
-    side = torch.cuda.Stream()
-    for lag_step in (False, True):
-        for rebuild in (True, False):
-            st.cs.set_rebuild_interval(1 if rebuild else 1 << 30)
-            side.wait_stream(torch.cuda.current_stream())
-            with torch.cuda.stream(side):
-                st(lag_step)                      # warm-up on the side stream
-            torch.cuda.current_stream().wait_stream(side)
-            torch.cuda.synchronize()
-            g = torch.cuda.CUDAGraph()
-            n0 = lib.eipc_launch_count()
-            with torch.cuda.graph(g):
-                st(lag_step)
-            kernels_per_graph[(lag_step, rebuild)] = lib.eipc_launch_count() - n0
-            graphs[(lag_step, rebuild)] = g
-    torch.cuda.synchronize()
+    graphs, kernels_per_graph = capture_step_graphs(st, Q[t0], DQ[t0], R)
 
     def replay(k, t):
         st.q.copy_(Q[t]); st.dq.copy_(DQ[t])

@@ -504,39 +504,46 @@ __global__ void __launch_bounds__(256, MINB) k_query(Bvh tt, Bvh te, Topo T, con
       if (box_overlap(b, b + 3, qlo, qhi)) leaf(0);
       continue;
     }
-    // stack of (node, last leaf position under it); EE queries skip subtrees that lie
-    // entirely at or before their own leaf
+    // Depth-first walk that descends into an overlapping child directly and pushes only
+    // the second child when both overlap, so a descent costs one node fetch and no stack
+    // round trip; leaves are handled where they are found.  The stack holds (node, last
+    // leaf position under it); EE queries skip subtrees that lie entirely at or before
+    // their own leaf.
     int32_t stack[64], smax[64];
     int sp = 0;
-    stack[sp] = 0;
-    smax[sp++] = (int32_t)(t.n - 1);
-    // a tree of n leaves has n-1 internal nodes, each popped at most once
+    int32_t node = 0;
+    int32_t nmax = (int32_t)(t.n - 1);
+    // a tree of n leaves has n-1 internal nodes, each fetched at most once
     int64_t visits = 0;
-    while (sp > 0) {
+    while (true) {
       if (++visits > t.n) {
         raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
         break;
       }
-      --sp;
-      const int32_t node = stack[sp];
-      const int32_t nmax = smax[sp];
       const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
       const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
       const int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
       const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
       const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
       const int32_t c0 = f3.x, c1 = f3.y, kin = f3.z, split = f3.w;
-      const bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
-      const bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
+      bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
+      bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
+      if (o0 && c0 < 0) { leaf(~c0); o0 = false; }
+      if (o1 && c1 < 0) { leaf(~c1); o1 = false; }
       if (o0) {
-        if (c0 < 0) leaf(~c0);
-        else if (sp < 64) { stack[sp] = c0; smax[sp++] = split; }
-        else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
-      }
-      if (o1) {
-        if (c1 < 0) leaf(~c1);
-        else if (sp < 64) { stack[sp] = c1; smax[sp++] = nmax; }
-        else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+        if (o1) {
+          if (sp < 64) { stack[sp] = c1; smax[sp++] = nmax; }
+          else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+        }
+        node = c0;
+        nmax = split;
+      } else if (o1) {
+        node = c1;
+      } else {
+        if (sp == 0) break;
+        --sp;
+        node = stack[sp];
+        nmax = smax[sp];
       }
     }
   }

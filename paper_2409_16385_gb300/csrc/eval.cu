@@ -174,84 +174,104 @@ __device__ __forceinline__ void rotate_sym(T A[N][N], T V[N][N], int p, int q, T
   }
 }
 
-// Fixed number of cyclic Jacobi sweeps in FP32 (62x the FP64 rate on this part): a cheap
-// approximate eigenbasis V of the symmetric matrix A (scaled to unit norm beforehand).
-template <int N>
-__device__ __forceinline__ void jacobi_f32(float A[N][N], float V[N][N], int sweeps) {
+// Sweep order of the 5 x 5 Jacobi solvers: five rounds of two rotations in disjoint
+// planes (a round-robin schedule covering all ten index pairs once).  The two rotations
+// of a round commute and their angles depend only on entries the other does not touch,
+// so both angles are computed before either is applied: two independent dependency
+// chains instead of one.
+__device__ constexpr int kRound5[5][2][2] = {{{1, 4}, {2, 3}}, {{0, 4}, {1, 2}}, {{0, 3}, {2, 4}},
+                                             {{0, 2}, {1, 3}}, {{0, 1}, {3, 4}}};
+
+// FP32 rotation angle zeroing a_pq: t = tan, c = cos, s = sin; false when a_pq is negligible
+__device__ __forceinline__ bool angle_f32(float app, float aqq, float apq, float* t, float* c, float* s) {
+  if (!(fabsf(apq) > 1e-30f)) return false;
+  const float theta = (aqq - app) / (2.f * apq);
+  const float at = fabsf(theta);
+  float tt = at > 1e18f ? 0.5f / at : 1.f / (at + sqrtf(at * at + 1.f));
+  tt = theta < 0.f ? -tt : tt;
+  *t = tt;
+  *c = 1.f / sqrtf(tt * tt + 1.f);
+  *s = tt * *c;
+  return true;
+}
+
+// Fixed number of Jacobi sweeps in FP32 (62x the FP64 rate on this part): a cheap
+// approximate eigenbasis V of the symmetric 5 x 5 matrix A (scaled to unit norm beforehand).
+__device__ __forceinline__ void jacobi_f32_5(float A[5][5], float V[5][5], int sweeps) {
 #pragma unroll
-  for (int i = 0; i < N; ++i)
+  for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
+    for (int j = 0; j < 5; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
+    for (int r = 0; r < 5; ++r)
 #pragma unroll
-      for (int q = p + 1; q < N; ++q) {
+      for (int h = 0; h < 2; ++h) {
+        const int p = kRound5[r][h][0], q = kRound5[r][h][1];
         const float apq = A[p][q];
-        if (fabsf(apq) > 1e-30f) {
-          const float theta = (A[q][q] - A[p][p]) / (2.f * apq);
-          const float at = fabsf(theta);
-          float t = at > 1e18f ? 0.5f / at : 1.f / (at + sqrtf(at * at + 1.f));
-          t = theta < 0.f ? -t : t;
-          const float c = 1.f / sqrtf(t * t + 1.f);
-          const float s = t * c;
-          rotate_sym<float, N>(A, V, p, q, c, s, t, apq);
-        }
+        float t, c, sn;
+        if (angle_f32(A[p][p], A[q][q], apq, &t, &c, &sn)) rotate_sym<float, 5>(A, V, p, q, c, sn, t, apq);
       }
-    }
   }
 }
 
-// Cyclic Jacobi on a symmetric N x N matrix held in registers; A becomes diagonal
-// (eigenvalues), V accumulates the rotations (columns = eigenvectors).  V is taken as the
-// starting basis when `seeded` (the caller has already rotated A into it).
-template <int N>
-__device__ __forceinline__ void jacobi(double A[N][N], double V[N][N], bool seeded = false) {
-  if (!seeded) {
-#pragma unroll
-    for (int i = 0; i < N; ++i)
-#pragma unroll
-      for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+// FP64 rotation angle zeroing a_pq (t, c), false when a_pq is exactly zero.  The zero test
+// and the small-angle test read the exponent fields with integer instructions, keeping them
+// off the FP64 pipe.
+__device__ __forceinline__ bool angle_f64(double app, double aqq, double apq, double* t_out, double* c_out) {
+  const int hi_a = __double2hiint(apq);
+  if (((hi_a & 0x7fffffff) | __double2loint(apq)) == 0) return false;
+  const double gap = aqq - app;
+  const int ea = (hi_a >> 20) & 0x7ff, eg = (__double2hiint(gap) >> 20) & 0x7ff;
+  double t, c;
+  if (eg - ea >= 21 && eg > 1023 - 120 && eg < 1023 + 120) {
+    // small angle, |apq| < 2^-20 |gap| (the usual case after the FP32
+    // pre-diagonalisation): t = apq / gap to relative O(t^2) <= 2^-40, with 1/gap to FP32
+    // precision (the exponent range check keeps gap a normal float).  Any t gives an exact
+    // rotation (c = 1 - t^2 / 2 and s = t c are orthonormal to O(t^4)); the approximate t
+    // leaves an off-diagonal residual of about 2^-24 |apq|, far below the sweep's stopping
+    // threshold
+    t = apq * (double)__frcp_rn((float)gap);
+    c = 1.0 - 0.5 * t * t;
+  } else {
+    const double theta = gap / (2.0 * apq);
+    const double at = fabs(theta);
+    t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
+    t = theta < 0.0 ? -t : t;
+    c = rsqrt(t * t + 1.0);
   }
+  *t_out = t;
+  *c_out = c;
+  return true;
+}
+
+// Jacobi on the symmetric 5 x 5 A held in registers, from the basis V the caller has
+// already rotated A into; A becomes diagonal (eigenvalues), V accumulates the rotations
+// (columns = eigenvectors).
+__device__ __forceinline__ void jacobi_5(double A[5][5], double V[5][5]) {
   double fro = 0.0;
 #pragma unroll
-  for (int i = 0; i < N; ++i)
+  for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j < N; ++j) fro += A[i][j] * A[i][j];
+    for (int j = 0; j < 5; ++j) fro += A[i][j] * A[i][j];
   // stop once the off-diagonal norm is below 1e-13 of the matrix norm
   const double tol = 1e-26 * fro;
   for (int sweep = 0; sweep < 12; ++sweep) {
     double off = 0.0;
 #pragma unroll
-    for (int p = 0; p < N; ++p)
+    for (int p = 0; p < 5; ++p)
 #pragma unroll
-      for (int q = p + 1; q < N; ++q) off += A[p][q] * A[p][q];
+      for (int q = p + 1; q < 5; ++q) off += A[p][q] * A[p][q];
     if (off <= tol) break;
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
+    for (int r = 0; r < 5; ++r)
 #pragma unroll
-      for (int q = p + 1; q < N; ++q) {
+      for (int h = 0; h < 2; ++h) {
+        const int p = kRound5[r][h][0], q = kRound5[r][h][1];
         const double apq = A[p][q];
-        if (apq != 0.0) {
-          const double gap = A[q][q] - A[p][p];
-          double t, c;
-          if (fabs(apq) < 1e-6 * fabs(gap)) {
-            // small angle (the usual case after the FP32 pre-diagonalisation):
-            // t = apq / gap to O(t^3), c = 1 - t^2 / 2 to O(t^4), both below 1e-17
-            t = apq / gap;
-            c = 1.0 - 0.5 * t * t;
-          } else {
-            const double theta = gap / (2.0 * apq);
-            const double at = fabs(theta);
-            t = at > 1e150 ? 0.5 / at : 1.0 / (at + sqrt(at * at + 1.0));
-            t = theta < 0.0 ? -t : t;
-            c = rsqrt(t * t + 1.0);
-          }
-          const double s = t * c;
-          rotate_sym<double, N>(A, V, p, q, c, s, t, apq);
-        }
+        double t, c;
+        if (angle_f64(A[p][p], A[q][q], apq, &t, &c)) rotate_sym<double, 5>(A, V, p, q, c, t * c, t, apq);
       }
-    }
   }
 }
 
@@ -308,13 +328,14 @@ __device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
       for (int q = 0; q < 5; ++q) V[p][q] = (p == q) ? 1.0 : 0.0;
     return;
   }
-  const double inv = rsqrt(fro);
+  // 1/|K| only scales the FP32 stage: FP32 precision is enough when |K|^2 is a normal float
+  const double inv = (fro > 1e-36 && fro < 1e36) ? (double)rsqrtf((float)fro) : rsqrt(fro);
   float Af[5][5], Vf[5][5];
 #pragma unroll
   for (int p = 0; p < 5; ++p)
 #pragma unroll
     for (int q = 0; q < 5; ++q) Af[p][q] = (float)(K[p][q] * inv);
-  jacobi_f32<5>(Af, Vf, 4);
+  jacobi_f32_5(Af, Vf, 4);
   // FP64 orthonormal basis from the FP32 eigenvectors (columns)
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
@@ -331,7 +352,10 @@ __device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
     double nn = 0.0;
 #pragma unroll
     for (int p = 0; p < 5; ++p) nn += V[p][j] * V[p][j];
-    const double r = rsqrt(nn);
+    // the FP32 eigenvectors are orthonormal to FP32 precision, so |nn - 1| is about 1e-7:
+    // two Newton steps for 1/sqrt(nn) from 1 leave an error of order (nn - 1)^4
+    double r = 1.5 - 0.5 * nn;
+    r = r * (1.5 - 0.5 * nn * r * r);
 #pragma unroll
     for (int p = 0; p < 5; ++p) V[p][j] *= r;
   }
@@ -356,17 +380,18 @@ __device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
       K[i][j] = s;
       K[j][i] = s;
     }
-  jacobi<5>(K, V, true);
+  jacobi_5(K, V);
 }
 
 // one upper-triangle record: key (min, max) of the two cage nodes, block transposed when
-// the first node is the larger one
+// the first node is the larger one.  With presorted records the sorted position is
+// hinv[pos]; a caller that has already loaded it passes it as `pre` (else pass -1).
 __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32_t Iu, int32_t Iv,
-                                           const double B[3][3]) {
+                                           const double B[3][3], int64_t pre = -1) {
   const bool swap = Iu > Iv;
   int64_t dst = pos;
   if (A.hinv) {
-    dst = A.hinv[pos];
+    dst = pre >= 0 ? pre : (int64_t)A.hinv[pos];
   } else {
     A.hkeys[pos] = swap ? (uint64_t)Iv * (uint64_t)A.ns + (uint64_t)Iu : (uint64_t)Iu * (uint64_t)A.ns + (uint64_t)Iv;
     A.hvals[pos] = (uint32_t)pos;
@@ -421,13 +446,13 @@ __device__ __forceinline__ void barrier_span(const V3 Y[4], const Stencil& S, do
   // r and r^
   V3 r = {0.0, 0.0, 0.0};
   for (int a = 0; a < 4; ++a) r = r + Y[a] * S.c[a];
-  const double rn = sqrt(dot(r, r));
-  B.rh = r * (1.0 / rn);
+  B.rh = r * rsqrt(dot(r, r));
   const V3 rh = B.rh;
   // orthonormal 4-vectors c^, a^_1, a^_2
-  const double cn = sqrt(S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3]);
+  const double cc = S.c[0] * S.c[0] + S.c[1] * S.c[1] + S.c[2] * S.c[2] + S.c[3] * S.c[3];
+  const double inv_cn = rsqrt(cc);
+  const double cn = cc * inv_cn;
   B.cn = cn;
-  const double inv_cn = 1.0 / cn;
   for (int a = 0; a < 4; ++a) B.basis[0][a] = S.c[a] * inv_cn;
   for (int j = 0; j < 2; ++j) {
     if (j < S.m) {
@@ -727,6 +752,15 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   // (min(I_u, I_v), max(I_u, I_v)) and transposed when I_u > I_v
   const double rhv[3] = {rh.x, rh.y, rh.z};
   int64_t pos = oh;
+  // the sorted position of the next record is loaded one record ahead, so its latency
+  // overlaps the current block's arithmetic
+  const int64_t pend = min(oh + (int64_t)n * (n + 1) / 2, A.rec_cap);
+  int64_t nxt = (A.hinv && pos < pend) ? (int64_t)__ldg(A.hinv + pos) : -1;
+  auto advance = [&]() {
+    const int64_t cur = nxt;
+    nxt = (A.hinv && pos + 1 < pend) ? (int64_t)__ldg(A.hinv + pos + 1) : -1;
+    return cur;
+  };
   for (int u = 0; u < n; ++u) {
     double Bu[3][5];
     if (active) {
@@ -735,8 +769,28 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
       for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 5; ++q) Bu[p][q] = nw[u][0] * Kp[p][q] + rhv[p] * t[q];
     }
-    for (int w2 = u; w2 < n; ++w2, ++pos) {
+    // the diagonal block (u, u) is symmetric: its upper triangle, mirrored
+    if (pos < A.rec_cap) {
+      const int64_t dst = advance();
+      double B[3][3];
+      if (active) {
+        for (int p = 0; p < 3; ++p) {
+          const double s = nw[u][1] * Bu[p][3] + nw[u][2] * Bu[p][4];
+          for (int q = p; q < 3; ++q) {
+            B[p][q] = nw[u][0] * Bu[p][q] + s * rhv[q];
+            B[q][p] = B[p][q];
+          }
+        }
+      } else {
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
+      }
+      emit_upper(A, pos, nodes[u], nodes[u], B, dst);
+    }
+    ++pos;
+    for (int w2 = u + 1; w2 < n; ++w2, ++pos) {
       if (pos >= A.rec_cap) continue;
+      const int64_t dst = advance();
       double B[3][3];
       if (active) {
         for (int p = 0; p < 3; ++p) {
@@ -747,7 +801,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
       }
-      emit_upper(A, pos, nodes[u], nodes[w2], B);
+      emit_upper(A, pos, nodes[u], nodes[w2], B, dst);
     }
   }
 }

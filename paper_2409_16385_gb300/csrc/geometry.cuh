@@ -70,12 +70,15 @@ __device__ __forceinline__ double pt_distance(V3 p, V3 t0, V3 t1, V3 t2, Stencil
   V3 e1 = t1 - t0, e2 = t2 - t0, w = p - t0;
   V3 n = cross(e1, e2);
   double nn = dot(n, n);
-  // barycentric coordinates of the projection: beta1 = ((w x e2) . n)/nn, etc.
-  double b1 = dot(cross(w, e2), n) / nn;
-  double b2 = dot(cross(e1, w), n) / nn;
+  // barycentric coordinates of the projection: beta1 = ((w x e2) . n)/nn, etc., with one
+  // reciprocal of nn for the three quotients (nn = 0 gives infinite or NaN barycentrics,
+  // which fail the face test, as the quotients would)
+  const double inv_nn = 1.0 / nn;
+  double b1 = dot(cross(w, e2), n) * inv_nn;
+  double b2 = dot(cross(e1, w), n) * inv_nn;
   if (b1 >= 0.0 && b2 >= 0.0 && b1 + b2 <= 1.0) {
     double h = dot(w, n);
-    double d2 = h * h / nn;
+    double d2 = h * h * inv_nn;
     if (kStencil) {
       set_zero(*S);
       S->c[0] = 1.0; S->c[1] = -(1.0 - b1 - b2); S->c[2] = -b1; S->c[3] = -b2;
@@ -109,11 +112,12 @@ __device__ __forceinline__ double ee_distance(V3 a0, V3 a1, V3 b0, V3 b1, Stenci
   V3 n = cross(ea, eb);
   double nn = dot(n, n);
   if (nn > 1e-20 * A * C) {
-    double s = (B * E - C * D) / nn;
-    double t = (A * E - B * D) / nn;
+    const double inv_nn = 1.0 / nn;
+    double s = (B * E - C * D) * inv_nn;
+    double t = (A * E - B * D) * inv_nn;
     if (s >= 0.0 && s <= 1.0 && t >= 0.0 && t <= 1.0) {
       double h = dot(w, n);
-      double d2 = h * h / nn;
+      double d2 = h * h * inv_nn;
       if (kStencil) {
         set_zero(*S);
         S->c[0] = 1.0 - s; S->c[1] = s; S->c[2] = -(1.0 - t); S->c[3] = -t;
