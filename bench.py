@@ -58,7 +58,9 @@ def parse():
     ap.add_argument("--json-out", default="")
     ap.add_argument("--cand-cap", type=int, default=0, help="broad-phase candidate capacity (0: library default)")
     ap.add_argument("--rec-cap", type=int, default=0, help="reduction record capacity (0: library default)")
-    ap.add_argument("--workload", choices=["bubble_grasp", "batched", "adjoint", "physical"], default="bubble_grasp",
+    ap.add_argument("--profile-once", action="store_true", help="eval_by_type: one evaluation per class (for ncu)")
+    ap.add_argument("--workload", choices=["bubble_grasp", "batched", "adjoint", "physical", "eval_by_type"],
+                    default="bubble_grasp",
                     help="bubble_grasp: one scene; batched: 256 grasp scenes in one CUDA graph per step; "
                          "adjoint: trajectory gradient of the sphere on a rising pad")
     ap.add_argument("--no-plain", action="store_true", help="batched: skip the plain per-scene comparison")
@@ -473,6 +475,119 @@ def pair_split(sc, h):
     vb[~pt] = edges[j[~pt], 0]
     inter = body[va] != body[vb]
     return dict(inter_body=int(inter.sum()), intra_body=int((~inter).sum()))
+
+
+PAIR_CLASSES = ("pt_face", "pt_edge", "pt_vertex", "ee_interior", "ee_edge", "ee_vertex")
+
+
+def _seg_param(p, e0, e1):
+    """Closest-point parameter t in [0, 1] of points p on segments e0 -> e1 and the squared
+    distance (vectorised)."""
+    e, w = e1 - e0, p - e0
+    ee = np.einsum("ij,ij->i", e, e)
+    t = np.clip(np.einsum("ij,ij->i", w, e) / np.where(ee > 0, ee, 1.0), 0.0, 1.0)
+    r = w - e * t[:, None]
+    return t, np.einsum("ij,ij->i", r, r)
+
+
+def classify_pairs(sc, x, h):
+    """Closest-feature class of each contact pair (index into PAIR_CLASSES) and its number
+    of distinct cage nodes: the minimum of the distance over the closed primitives is
+    attained inside the face / on an edge interior / at a vertex (point-triangle), or at
+    interior points of both edges / an endpoint against an edge interior / two endpoints
+    (edge-edge).  Host-side numpy, for reporting work per pair type."""
+    t, i, j = (np.asarray(h[k]) for k in ("type", "i", "j"))
+    tris, edges = np.asarray(sc.tris), np.asarray(sc.edges)
+    cls = np.zeros(len(t), np.int32)
+    st = np.zeros((len(t), 4), np.int64)
+    pt = t == 0
+    st[pt] = np.c_[i[pt], tris[j[pt]]]
+    st[~pt] = np.c_[edges[i[~pt]], edges[j[~pt]]]
+    if pt.any():
+        p, a, b, c = (x[st[pt, k]] for k in range(4))
+        e1, e2, w = b - a, c - a, p - a
+        n = np.cross(e1, e2)
+        nn = np.einsum("ij,ij->i", n, n)
+        b1 = np.einsum("ij,ij->i", np.cross(w, e2), n) / nn
+        b2 = np.einsum("ij,ij->i", np.cross(e1, w), n) / nn
+        face = (b1 >= 0) & (b2 >= 0) & (b1 + b2 <= 1)
+        segs = [_seg_param(p, a, b), _seg_param(p, b, c), _seg_param(p, c, a)]
+        d2 = np.stack([s_[1] for s_ in segs], 1)
+        tt = np.stack([s_[0] for s_ in segs], 1)
+        kbest = np.argmin(d2, 1)
+        tb = tt[np.arange(len(kbest)), kbest]
+        inner = (tb > 0) & (tb < 1)
+        cls[pt] = np.where(face, 0, np.where(inner, 1, 2))
+    if (~pt).any():
+        a0, a1, b0, b1_ = (x[st[~pt, k]] for k in range(4))
+        ea, eb, w = a1 - a0, b1_ - b0, a0 - b0
+        A = np.einsum("ij,ij->i", ea, ea); B = np.einsum("ij,ij->i", ea, eb); C = np.einsum("ij,ij->i", eb, eb)
+        D = np.einsum("ij,ij->i", ea, w); E = np.einsum("ij,ij->i", eb, w)
+        n = np.cross(ea, eb)
+        nn = np.einsum("ij,ij->i", n, n)
+        ok = nn > 1e-20 * A * C
+        nns = np.where(ok, nn, 1.0)
+        s_ = (B * E - C * D) / nns
+        t_ = (A * E - B * D) / nns
+        interior = ok & (s_ >= 0) & (s_ <= 1) & (t_ >= 0) & (t_ <= 1)
+        segs = [_seg_param(a0, b0, b1_), _seg_param(a1, b0, b1_), _seg_param(b0, a0, a1), _seg_param(b1_, a0, a1)]
+        d2 = np.stack([q[1] for q in segs], 1)
+        tt = np.stack([q[0] for q in segs], 1)
+        kbest = np.argmin(d2, 1)
+        tb = tt[np.arange(len(kbest)), kbest]
+        inner = (tb > 0) & (tb < 1)
+        cls[~pt] = np.where(interior, 3, np.where(inner, 4, 5))
+    ci = np.asarray(sc.cage_idx)[st]                       # [n, 4 vertices, 4 nodes]
+    nodes = np.array([len({int(v) for v in row.ravel() if v >= 0}) for row in ci])
+    return cls, nodes
+
+
+def run_eval_by_type(args, ws, rank, local):
+    """The barrier evaluation stage on the bubble grasp's contact pairs split by closest-
+    feature class (PAIR_CLASSES): one list per class, evaluated without friction; device
+    time per class from the kernel's event timer.  With --profile-once each class is
+    evaluated exactly once, in PAIR_CLASSES order, so that an ncu launch list of
+    k_eval_barrier gives each class's FP64 instruction counts (launch k = class k)."""
+    import torch
+    from paper_2409_16385_gb300 import ContactScene, PairList
+    dev = torch.device("cuda", local)
+    sc = build_scene(args.quick)
+    cs = ContactScene(sc, pair_capacity=1 << 21, bsr_capacity=1 << 21)
+    t0 = 5 % sc.n_iterates
+    q = torch.tensor(sc.iterate(t0), dtype=torch.float64, device=dev)
+    h = cs.build_candidates(q).host()
+    cls, nodes = classify_pairs(sc, cs.embed(q).cpu().numpy(), h)
+    out = {}
+    reps = 1 if args.profile_once else 10
+    for c, name in enumerate(PAIR_CLASSES):
+        sel = np.nonzero(cls == c)[0]
+        if len(sel) == 0:
+            continue
+        m = len(sel)
+        pl = PairList(torch.tensor(h["type"][sel], dtype=torch.int32, device=dev),
+                      torch.tensor(h["i"][sel], dtype=torch.int32, device=dev),
+                      torch.tensor(h["j"][sel], dtype=torch.int32, device=dev),
+                      torch.zeros(m, dtype=torch.float64, device=dev),
+                      torch.tensor([m], dtype=torch.int64, device=dev))
+        if not args.profile_once:
+            cs.eval_contact(q, pl, None)
+        cs.timing_enable(["eval_barrier"])
+        for _ in range(reps):
+            cs.eval_contact(q, pl, None)
+        torch.cuda.synchronize()
+        ms, n_l = cs.timing_read().get("eval_barrier", (0.0, 0))
+        cs.timing_enable([])
+        out[name] = dict(pairs=m, mean_cage_nodes=float(nodes[sel].mean()), kernel_ms=ms / max(n_l, 1),
+                         pairs_per_s=m / (ms / max(n_l, 1) / 1e3) if ms > 0 else None)
+    st = cs.status()
+    cs.close()
+    if st["flags"] & ~64:
+        raise RuntimeError(f"eval by type: device status {st}")
+    line = dict(workload=sc.name, iterate=t0, classes=out, reps=reps,
+                note="k_eval_barrier time per class (no friction items); FP64 instruction counts per class "
+                     "come from an ncu launch list of the --profile-once run")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, ws, rank, local):
@@ -915,10 +1030,10 @@ class _Stage:
     that it can be captured in a CUDA graph: static inputs q, dq; outputs E, g_r, H_r,
     per-group energy, alpha and per-group alpha."""
 
-    def __init__(self, sc, caps, groups, dev):
+    def __init__(self, sc, caps, groups, dev, group_outputs=True):
         import torch
         from paper_2409_16385_gb300 import ContactScene
-        self.sc, self.caps, self.groups = sc, caps, groups is not None
+        self.sc, self.caps, self.groups = sc, caps, group_outputs
         self.cs = ContactScene(sc, pair_capacity=caps["pair"], bsr_capacity=caps["bsr"], cand_capacity=caps["cand"],
                                rec_capacity=caps["rec"])
         ng = 1
@@ -989,7 +1104,7 @@ def graph_steps(sc, Q, DQ, lag_of, t0, K, flush, dev, shapes):
     import torch
     n_it = sc.n_iterates
     R = 8
-    st = _Stage(sc, dict(pair=1 << 21, bsr=1 << 21, cand=0, rec=0), None, dev)
+    st = _Stage(sc, dict(pair=1 << 21, bsr=1 << 21, cand=0, rec=0), None, dev, group_outputs=False)
     for k, shape in shapes.items():
         st.cs.set_launch(k, *shape)
     graphs, kernels = capture_step_graphs(st, Q[t0], DQ[t0], R)
@@ -1482,6 +1597,8 @@ def main():
         run_adjoint(args, ws, rank, local)
     elif args.workload == "physical":
         run_physical(args, ws, rank, local)
+    elif args.workload == "eval_by_type":
+        run_eval_by_type(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

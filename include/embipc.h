@@ -276,14 +276,18 @@ eipc_status eipc_group_energy(eipc_scene* scene, double* E_groups, eipc_stream s
 eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_stream stream);
 
 /* Launch shape of a tunable kernel (the autotuner's knobs).  kernel: 0 = per-pair barrier
- * evaluation, 1 = BVH traversal, 2 = BVH bottom-up refit.  threads per block: 64, 128
- * (eval), 64, 128, 256 (traversal) or 256 (refit); blocks_per_sm: cap on the grid as a
- * multiple of the 152 SMs (1..64; ignored by the refit); variant: eval 2 = no register
- * cap, 3 = at most 170 registers (3 blocks of 128 per SM); traversal 2 = no register cap,
- * 3 = at most 40 registers (6 blocks of 256 per SM); refit 0 = arrival counters
- * behind full device fences, 1 = release-acquire arrival counters, 2 = treelets of up to
- * 32 leaves refitted per warp in shared memory below release-acquire counters (default).
- * Results never depend on the shape. */
+ * evaluation, 1 = BVH traversal, 2 = BVH bottom-up refit, 3 = the evaluation's work-queue
+ * tile, 4 = the CCD advancement's work-queue tile.  threads per block: 64, 128 (eval), 64,
+ * 128, 256 (traversal) or 256 (refit); for kernels 3 and 4 `threads` is instead the number
+ * of items a warp claims from the kernel's work queue at a time (32, 64, 128 or 256;
+ * defaults 32 and 128), and the other two arguments are ignored.  blocks_per_sm: cap on the
+ * grid as a multiple of the 152 SMs (1..64; ignored by the refit); variant: eval 2 = no
+ * register cap, 3 = at most 170 registers (3 blocks of 128 per SM), 4 = at most 128
+ * registers (4 blocks of 128 per SM); traversal 2 = no register cap, 3 = at most 40
+ * registers (6 blocks of 256 per SM); refit 0 = arrival counters behind full device
+ * fences, 1 = release-acquire arrival counters, 2 = treelets of up to 32 leaves refitted per
+ * warp in shared memory below release-acquire counters (default).  Results never depend on
+ * the shape. */
 eipc_status eipc_set_launch(eipc_scene* scene, int32_t kernel, int32_t threads, int32_t blocks_per_sm,
                             int32_t variant);
 

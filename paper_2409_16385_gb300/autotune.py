@@ -1,6 +1,7 @@
 """Launch-shape autotuner for the kernels whose best shape depends on the workload: the
 per-pair barrier evaluation (threads per block, grid cap in blocks per SM, register
-budget), the BVH traversal (threads per block, grid cap, register budget) and the BVH
+budget), the pair tile of its work queue and of the CCD advancement's (items a warp claims
+at a time), the BVH traversal (threads per block, grid cap, register budget) and the BVH
 refit (how its bottom-up arrival counters are ordered).
 
 Results never depend on the shape: every kernel is a grid-stride loop over a device-side
@@ -18,15 +19,19 @@ import os
 from typing import Callable, Dict, Iterable, Optional, Tuple
 
 EVAL_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
-    (threads, bps, variant) for threads in (64, 128) for bps in (2, 3, 4, 6, 8, 16) for variant in (2, 3))
+    (threads, bps, variant) for threads in (64, 128) for bps in (2, 3, 4, 6, 8, 16) for variant in (2, 3, 4))
+# items a warp claims from the evaluation's / CCD advancement's work queue at a time
+TILE_SPACE: Tuple[Tuple[int, int, int], ...] = tuple((items, 1, 0) for items in (32, 64, 128, 256))
 QUERY_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
     (threads, bps, variant) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32) for variant in (2, 3))
 
 REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1), (256, 8, 2))
 
-SPACES = {"eval_barrier": EVAL_SPACE, "bvh_query": QUERY_SPACE, "bvh_refit": REFIT_SPACE}
+SPACES = {"eval_barrier": EVAL_SPACE, "bvh_query": QUERY_SPACE, "bvh_refit": REFIT_SPACE, "eval_tile": TILE_SPACE,
+          "ccd_tile": TILE_SPACE}
 # the library timer that brackets each tunable kernel's launches
-TIMERS = {"eval_barrier": "eval_barrier", "bvh_query": "bvh_query", "bvh_refit": "bvh_build"}
+TIMERS = {"eval_barrier": "eval_barrier", "bvh_query": "bvh_query", "bvh_refit": "bvh_build",
+          "eval_tile": "eval_barrier", "ccd_tile": "ccd_advance"}
 
 
 def default_cache_path() -> str:
@@ -73,7 +78,7 @@ def time_kernel(cs, stage: Callable[[], None], kernel: str, reps: int = 3) -> fl
 
 
 def tune(cs, stage: Callable[[], None], workload_key: str,
-         kernels: Iterable[str] = ("eval_barrier", "bvh_query", "bvh_refit"),
+         kernels: Iterable[str] = ("eval_barrier", "eval_tile", "bvh_query", "bvh_refit", "ccd_tile"),
          cache_path: Optional[str] = None, reps: int = 3, force: bool = False) -> Dict[str, dict]:
     """Chooses and applies a launch shape for each kernel on `cs` (a ContactScene).
 

@@ -392,7 +392,7 @@ class ContactScene:
         _check(self.lib.eipc_group_alpha(self.handle, _ptr(out), _stream()), "eipc_group_alpha")
         return out
 
-    LAUNCH_KERNELS = {"eval_barrier": 0, "bvh_query": 1, "bvh_refit": 2}
+    LAUNCH_KERNELS = {"eval_barrier": 0, "bvh_query": 1, "bvh_refit": 2, "eval_tile": 3, "ccd_tile": 4}
 
     def set_launch(self, kernel: str, threads: int, blocks_per_sm: int, variant: int = 2):
         """Launch shape of a tunable kernel; results do not depend on it."""

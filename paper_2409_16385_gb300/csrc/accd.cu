@@ -54,11 +54,26 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
                                                      const int64_t* n_cand, int64_t cap, double s, int max_iter,
                                                      unsigned long long* alpha_bits,
                                                      unsigned long long* __restrict__ group_bits, int64_t* n_adv,
-                                                     DevStatus* st) {
+                                                     DevStatus* st, int64_t* queue, int tile_req) {
   const int64_t n = clamp_count(n_cand, cap);
+  const int tile = tile_req >= 32 ? (tile_req & ~31) : 32;
   const int lane = threadIdx.x & 31;
-  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += grid_stride()) {
-    const int64_t k = base + threadIdx.x;
+  // persistent work queue over candidate tiles: each warp claims the next `tile`
+  // candidates (tile / 32 per lane), so warps whose candidates settled at once come back for
+  // more while a few run long advancements
+  // every claim takes `tile` candidates, so n / tile + 2 claims cover all a warp can make
+  const int64_t max_rounds = n / tile + 2;
+  for (int64_t round = 0;; ++round) {
+    if (round > max_rounds) {
+      raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+      break;
+    }
+    unsigned long long qb = 0;
+    if (lane == 0) qb = atomicAdd(reinterpret_cast<unsigned long long*>(queue), (unsigned long long)tile);
+    const int64_t tbase = (int64_t)__shfl_sync(0xffffffffu, qb, 0);
+    if (tbase >= n) break;
+  for (int o = 0; o < tile; o += 32) {
+    const int64_t k = tbase + o + lane;
     bool adv = false;
     int iters = 0;
     if (k < n) {
@@ -157,11 +172,12 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
     }
     const uint32_t m = __ballot_sync(0xffffffffu, adv);
     int tot = iters;
-    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    for (int sh = 16; sh > 0; sh >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, sh);
     if (lane == 0) {
       if (m) atomicAdd(reinterpret_cast<unsigned long long*>(n_adv), (unsigned long long)__popc(m));
       if (tot) atomicAdd(&st->accd_iters, (unsigned long long)tot);
     }
+  }
   }
 }
 
@@ -205,10 +221,12 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps,
                        sc->tune.query_variant));
+  int64_t* queue = sc->counters + kCntCcdQueue;
+  cudaMemsetAsync(queue, 0, sizeof(int64_t), s);
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 
                  sc->topo, sc->x4, sc->dx4, sc->cand, n_cand, sc->cand_cap, p.accd_s, p.accd_max_iter, abits, sc->group_alpha_bits, n_adv,
-                 sc->status)));
+                 sc->status, queue, sc->tune.ccd_tile)));
   launch(k_alpha_out, 1, 32, 0, s, abits, alpha, n_adv, n_candidates);
 }
 

@@ -436,7 +436,7 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
                             int32_t variant) {
   if (!sc || blocks_per_sm < 1 || blocks_per_sm > 64) return EIPC_ERR_INVALID;
   if (kernel == 0) {
-    if ((threads != 64 && threads != 128) || (variant != 2 && variant != 3)) return EIPC_ERR_INVALID;
+    if ((threads != 64 && threads != 128) || variant < 2 || variant > 4) return EIPC_ERR_INVALID;
     sc->tune.eval_threads = threads;
     sc->tune.eval_bps = blocks_per_sm;
     sc->tune.eval_variant = variant;
@@ -452,6 +452,13 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
   if (kernel == 2) {
     if (threads != 256 || variant < 0 || variant > 2) return EIPC_ERR_INVALID;
     sc->tune.refit_variant = variant;
+    return EIPC_OK;
+  }
+  if (kernel == 3 || kernel == 4) {
+    // work-queue tiles: `threads` = items a warp claims at a time (32, 64, 128 or 256)
+    if (threads != 32 && threads != 64 && threads != 128 && threads != 256) return EIPC_ERR_INVALID;
+    if (kernel == 3) sc->tune.eval_tile = threads;
+    else sc->tune.ccd_tile = threads;
     return EIPC_OK;
   }
   return EIPC_ERR_INVALID;

@@ -302,6 +302,7 @@ struct EvalArgs {
   const double* moll_r2;   // EE mollifier: rest squared edge lengths (null: off)
   double moll_factor;      // eps_x = moll_factor |e_i|^2 |e_j|^2
   int64_t* queue;          // next unclaimed position of `order` (work queue)
+  int tile;                // items a warp claims from the queue at a time (multiple of 32)
   const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
   double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
   // Presorted records (energy/gradient/Hessian evaluation): the keys were written and
@@ -806,9 +807,11 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   }
 }
 
-// MINB = 2: no register cap (248 registers, 2 blocks of 128 per SM); MINB = 3: at most 170
-// registers (3 blocks per SM, a few hundred bytes of spills).  Chosen at run time.  With
-// A.project false the pair Hessians are kept as they are (no PSD projection).
+// MINB = 2: no register cap (about 200 registers, 2 blocks of 128 per SM); MINB = 3: at
+// most 170 registers (3 blocks per SM, a few hundred bytes of spills); MINB = 4: at most
+// 128 registers (4 blocks per SM, spilling a few KB to L1-resident local memory).  Chosen at
+// run time.  With A.project false the pair Hessians are kept as they are (no PSD
+// projection).
 template <int MINB>
 __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A) {
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
@@ -819,16 +822,31 @@ __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A)
       eval_barrier_item(A, k);
     return;
   }
-  // scheduled: each warp takes the next 32 items of the order from a queue, so warps
-  // that drew light items come back for more (dynamic balance)
+  // scheduled: a persistent work queue over pair tiles -- each warp claims the next
+  // A.tile items of the order (one to several per lane), so warps that drew light items come
+  // back for more (dynamic balance); in a batch the tiles run across scene boundaries
   const int lane = threadIdx.x & 31;
-  for (int round = 0; round < (1 << 30); ++round) {
-    unsigned long long b = 0;
-    if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(A.queue), 32ull);
-    const int64_t base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+  const int tile = A.tile >= 32 ? (A.tile & ~31) : 32;
+  int64_t base = 0;
+  int left = 0;                  // items of the claimed tile not yet taken (a multiple of 32)
+  // a warp takes 32 items per round, so np / 32 + 2 rounds cover every claim it can make
+  const int64_t max_rounds = np / 32 + 2;
+  for (int64_t round = 0;; ++round) {
+    if (round > max_rounds) {
+      raise_flag(A.st, EIPC_FLAG_STACK_OVERFLOW);
+      break;
+    }
+    if (left == 0) {
+      unsigned long long b = 0;
+      if (lane == 0) b = atomicAdd(reinterpret_cast<unsigned long long*>(A.queue), (unsigned long long)tile);
+      base = (int64_t)__shfl_sync(0xffffffffu, b, 0);
+      left = tile;
+    }
     if (base >= np) break;
     const int64_t idx = base + lane;
     if (idx < np) eval_barrier_item(A, (int64_t)A.order[idx]);
+    base += 32;
+    left -= 32;
   }
 }
 
@@ -1715,10 +1733,14 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                   sc->sort_hist, s);
     A.order = wo ? sc->svals_alt : sc->svals;
     A.queue = cnt + kCntEvalQueue;
+    A.tile = sc->tune.eval_tile;
     cudaMemsetAsync(A.queue, 0, sizeof(int64_t), s);
   }
   EIPC_TIMED(sc, kKEvalBarrier, s,
-             (sc->tune.eval_variant == 3
+             (sc->tune.eval_variant == 4
+                  ? launch(k_eval_barrier<4>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
+                           sc->tune.eval_threads, 0, s, A)
+              : sc->tune.eval_variant == 3
                   ? launch(k_eval_barrier<3>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
                            sc->tune.eval_threads, 0, s, A)
                   : launch(k_eval_barrier<2>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
@@ -1786,6 +1808,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.moll_factor = sc->moll_factor;
   A.order = nullptr;
   A.queue = nullptr;
+  A.tile = 32;
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
   A.hinv = nullptr; A.ginv = nullptr;

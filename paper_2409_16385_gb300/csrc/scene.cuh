@@ -84,7 +84,8 @@ struct eipc_scene {
   int bits_h, bits_g;    // key widths of the reduction sorts
   int rebuild_interval;  // contact LBVH: full rebuild every this many build_candidates calls
   struct {
-    int eval_threads = 128, eval_bps = 16, eval_variant = 2;
+    int eval_threads = 128, eval_bps = 16, eval_variant = 2, eval_tile = 32;
+    int ccd_tile = 128;
     int query_threads = 128, query_bps = 24, query_variant = 2;
     int refit_variant = 2;
   } tune;                // launch shapes of the tunable kernels (eipc_set_launch)
@@ -100,7 +101,7 @@ constexpr int kHRecStride = 10, kGRecStride = 4;
 
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
        kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntScreened = 15, kCntDedup = 17, kCntUnitsH = 18,
-       kCntUnitsG = 19, kCntMollBad = 20,
+       kCntUnitsG = 19, kCntMollBad = 20, kCntCcdQueue = 21,
        kCntN = 24 };
 
 #define EIPC_TIMED(sc, id, s, ...)        \

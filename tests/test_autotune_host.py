@@ -24,14 +24,18 @@ class FakeScene:
 
     def set_launch(self, kernel, threads, bps, variant=2):
         self.shape[kernel] = (threads, bps, variant)
+        self.last = kernel
 
     def timing_enable(self, names=None):
         self.enabled = list(names or [])
 
     def timing_read(self):
+        # a timer can bracket several knobs (the evaluation's shape and its queue tile):
+        # the cost is that of the knob set last among those the timer covers
         out = {}
         for timer in self.enabled:
-            kernel = next(k for k, t in autotune.TIMERS.items() if t == timer)
+            knobs = [k for k, t in autotune.TIMERS.items() if t == timer]
+            kernel = self.last if getattr(self, "last", None) in knobs else knobs[0]
             out[timer] = (self.cost(kernel, self.shape.get(kernel)), 1)
         return out
 
@@ -40,7 +44,8 @@ def _cost(kernel, shape):
     if shape is None:
         return 10.0
     threads, bps, variant = shape
-    best = {"eval_barrier": (64, 4, 3), "bvh_query": (256, 12, 2), "bvh_refit": (256, 8, 1)}[kernel]
+    best = {"eval_barrier": (64, 4, 3), "bvh_query": (256, 12, 2), "bvh_refit": (256, 8, 1),
+            "eval_tile": (64, 1, 0), "ccd_tile": (128, 1, 0)}[kernel]
     return 1.0 + abs(threads - best[0]) / 64 + abs(bps - best[1]) + abs(variant - best[2])
 
 
@@ -55,7 +60,9 @@ def test_picks_the_fastest_shape_and_caches_it(tmp_path):
     assert res["eval_barrier"]["shape"] == [64, 4, 3] and not res["eval_barrier"]["cached"]
     assert res["bvh_query"]["shape"] == [256, 12, 2]
     assert res["bvh_refit"]["shape"] == [256, 8, 1]
-    assert cs.shape == {"eval_barrier": (64, 4, 3), "bvh_query": (256, 12, 2), "bvh_refit": (256, 8, 1)}
+    assert res["eval_tile"]["shape"] == [64, 1, 0] and res["ccd_tile"]["shape"] == [128, 1, 0]
+    assert cs.shape == {"eval_barrier": (64, 4, 3), "bvh_query": (256, 12, 2), "bvh_refit": (256, 8, 1),
+                        "eval_tile": (64, 1, 0), "ccd_tile": (128, 1, 0)}
     assert res["eval_barrier"]["ms"] == 1.0
     assert len(res["eval_barrier"]["candidates"]) == len(autotune.EVAL_SPACE)
     table = json.load(open(cache))

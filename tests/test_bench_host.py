@@ -172,3 +172,29 @@ def test_cpu_stage_baseline_runs_each_stage_on_the_given_lists():
     assert r["eval_all"]["list_pairs"] == len(prs["type"])
     e = bench.cpu_enumeration(sc, x, n_queries=50)
     assert e["pairs_found"] >= 0 and e["full_enumeration_s_estimate"] > 0
+
+
+def test_classify_pairs_on_hand_built_configurations():
+    """The bench's closest-feature classes on configurations whose answer is known."""
+    import numpy as np
+
+    class Sc:
+        pass
+    sc = Sc()
+    x = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0],              # triangle 0
+                  [0.2, 0.2, 0.1],                              # 3: above the face
+                  [0.5, -0.3, 0.1],                             # 4: beyond edge (0,1)
+                  [-0.3, -0.3, 0.1],                            # 5: beyond vertex 0
+                  [0.5, 0.5, 1.0], [0.5, 0.5, 2.0],             # 6-7: unused
+                  [0.5, -1, 0.2], [0.5, 1, 0.2],                # 8-9: edge crossing over edge (0,1)
+                  [0.5, 0.2, 0.3], [0.5, 2.0, 0.3],             # 10-11: T: endpoint 10 above edge (0,1) interior
+                  [-1, 3, 0], [-1, 4, 0]], float)               # 12-13: edge beyond vertex 2 of edge (1,2)
+    sc.tris = np.array([[0, 1, 2]])
+    sc.edges = np.array([[0, 1], [8, 9], [10, 11], [12, 13], [1, 2]])
+    sc.cage_idx = np.tile(np.arange(4), (len(x), 1))
+    sc.cage_idx[12:] = -1
+    h = dict(type=np.array([0, 0, 0, 1, 1, 1]), i=np.array([3, 4, 5, 0, 0, 4]), j=np.array([0, 0, 0, 1, 2, 3]))
+    cls, nodes = bench.classify_pairs(sc, x, h)
+    names = [bench.PAIR_CLASSES[c] for c in cls]
+    assert names == ["pt_face", "pt_edge", "pt_vertex", "ee_interior", "ee_edge", "ee_vertex"], names
+    assert list(nodes) == [4, 4, 4, 4, 4, 4]
