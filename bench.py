@@ -183,11 +183,13 @@ def measured_peaks():
 #                 ((2 x DFMA + DMUL + DADD) thread instructions / pairs)
 #   ccd_advance   FP64 flops per advanced CCD candidate (box test, advancement distances)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-FP64_FLOPS_PER_PAIR = 3229.0
+# eval_barrier: 291.28e6 flops over the 115,699 pairs of bubble-grasp iterate 2 (ncu, the
+# autotuned shape 128 threads x 6 blocks/SM, 128-register variant); see profiles/
+FP64_FLOPS_PER_PAIR = 2518.0
 FP64_FLOPS_PER_CCD_CAND = 420.0
-# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code
-# (eval_barrier: per contact pair; bvh_query: per launch of the contact traversal)
-NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 2958.0}
+# DRAM bytes (read + write) per unit from one ncu capture of the same kernel code and shape
+# (eval_barrier: 122.8 MB + 237.7 MB for the same 115,699 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3116.0}
 
 
 def query_bytes(sc, n_cand):

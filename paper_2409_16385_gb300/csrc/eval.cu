@@ -174,13 +174,18 @@ __device__ __forceinline__ void rotate_sym(T A[N][N], T V[N][N], int p, int q, T
   }
 }
 
-// Sweep order of the 5 x 5 Jacobi solvers: five rounds of two rotations in disjoint
-// planes (a round-robin schedule covering all ten index pairs once).  The two rotations
-// of a round commute and their angles depend only on entries the other does not touch,
-// so both angles are computed before either is applied: two independent dependency
-// chains instead of one.
+// Sweep orders of the Jacobi solvers: rounds of two rotations in disjoint planes covering
+// every index pair once (a round-robin schedule: 5 rounds for N = 5, 3 for N = 4).  The
+// rotations of a round commute, so their order inside the round does not matter.
 __device__ constexpr int kRound5[5][2][2] = {{{1, 4}, {2, 3}}, {{0, 4}, {1, 2}}, {{0, 3}, {2, 4}},
                                              {{0, 2}, {1, 3}}, {{0, 1}, {3, 4}}};
+__device__ constexpr int kRound4[3][2][2] = {{{0, 1}, {2, 3}}, {{0, 2}, {1, 3}}, {{0, 3}, {1, 2}}};
+template <int N>
+__device__ __forceinline__ int round_entry(int r, int h, int w) {
+  return N == 5 ? kRound5[r][h][w] : kRound4[r][h][w];
+}
+template <int N>
+constexpr int kRounds = N == 5 ? 5 : 3;
 
 // FP32 rotation angle zeroing a_pq: t = tan, c = cos, s = sin; false when a_pq is negligible
 __device__ __forceinline__ bool angle_f32(float app, float aqq, float apq, float* t, float* c, float* s) {
@@ -196,21 +201,22 @@ __device__ __forceinline__ bool angle_f32(float app, float aqq, float apq, float
 }
 
 // Fixed number of Jacobi sweeps in FP32 (62x the FP64 rate on this part): a cheap
-// approximate eigenbasis V of the symmetric 5 x 5 matrix A (scaled to unit norm beforehand).
-__device__ __forceinline__ void jacobi_f32_5(float A[5][5], float V[5][5], int sweeps) {
+// approximate eigenbasis V of the symmetric N x N matrix A (scaled to unit norm beforehand).
+template <int N>
+__device__ __forceinline__ void jacobi_f32(float A[N][N], float V[N][N], int sweeps) {
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int j = 0; j < 5; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
+    for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.f : 0.f;
   for (int sweep = 0; sweep < sweeps; ++sweep) {
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
+    for (int r = 0; r < kRounds<N>; ++r)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int p = kRound5[r][h][0], q = kRound5[r][h][1];
+        const int p = round_entry<N>(r, h, 0), q = round_entry<N>(r, h, 1);
         const float apq = A[p][q];
         float t, c, sn;
-        if (angle_f32(A[p][p], A[q][q], apq, &t, &c, &sn)) rotate_sym<float, 5>(A, V, p, q, c, sn, t, apq);
+        if (angle_f32(A[p][p], A[q][q], apq, &t, &c, &sn)) rotate_sym<float, N>(A, V, p, q, c, sn, t, apq);
       }
   }
 }
@@ -245,32 +251,33 @@ __device__ __forceinline__ bool angle_f64(double app, double aqq, double apq, do
   return true;
 }
 
-// Jacobi on the symmetric 5 x 5 A held in registers, from the basis V the caller has
+// Jacobi on the symmetric N x N A held in registers, from the basis V the caller has
 // already rotated A into; A becomes diagonal (eigenvalues), V accumulates the rotations
 // (columns = eigenvectors).
-__device__ __forceinline__ void jacobi_5(double A[5][5], double V[5][5]) {
+template <int N>
+__device__ __forceinline__ void jacobi(double A[N][N], double V[N][N]) {
   double fro = 0.0;
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int j = 0; j < 5; ++j) fro += A[i][j] * A[i][j];
+    for (int j = 0; j < N; ++j) fro += A[i][j] * A[i][j];
   // stop once the off-diagonal norm is below 1e-13 of the matrix norm
   const double tol = 1e-26 * fro;
   for (int sweep = 0; sweep < 12; ++sweep) {
     double off = 0.0;
 #pragma unroll
-    for (int p = 0; p < 5; ++p)
+    for (int p = 0; p < N; ++p)
 #pragma unroll
-      for (int q = p + 1; q < 5; ++q) off += A[p][q] * A[p][q];
+      for (int q = p + 1; q < N; ++q) off += A[p][q] * A[p][q];
     if (off <= tol) break;
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
+    for (int r = 0; r < kRounds<N>; ++r)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int p = kRound5[r][h][0], q = kRound5[r][h][1];
+        const int p = round_entry<N>(r, h, 0), q = round_entry<N>(r, h, 1);
         const double apq = A[p][q];
         double t, c;
-        if (angle_f64(A[p][p], A[q][q], apq, &t, &c)) rotate_sym<double, 5>(A, V, p, q, c, t * c, t, apq);
+        if (angle_f64(A[p][p], A[q][q], apq, &t, &c)) rotate_sym<double, N>(A, V, p, q, c, t * c, t, apq);
       }
   }
 }
@@ -312,76 +319,109 @@ struct EvalArgs {
   const uint32_t* ginv;
 };
 
-// Eigen-decomposition of the symmetric 5x5 K: an FP32 Jacobi pre-diagonalisation of K/|K|,
-// its eigenvectors re-orthonormalised in FP64 (modified Gram-Schmidt), K rotated into that
-// basis in FP64, then FP64 Jacobi sweeps to full precision (quadratic convergence from the
-// ~1e-7 residual leaves one or two sweeps).  On return K is diagonal, V its eigenvectors.
-__device__ __forceinline__ void eigen5(double K[5][5], double V[5][5]) {
+// Eigen-decomposition of the symmetric N x N K (N = 5, or 4 when the span has four
+// dimensions): an FP32 Jacobi pre-diagonalisation of K/|K|, its eigenvectors
+// re-orthonormalised in FP64 (modified Gram-Schmidt), K rotated into that basis in FP64,
+// then FP64 Jacobi sweeps to full precision (quadratic convergence from the ~1e-7 residual
+// leaves one or two sweeps).  On return K is diagonal, V its eigenvectors.
+template <int N>
+__device__ __forceinline__ void eigen_sym(double K[N][N], double V[N][N]) {
   double fro = 0.0;
 #pragma unroll
-  for (int p = 0; p < 5; ++p)
+  for (int p = 0; p < N; ++p)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) fro += K[p][q] * K[p][q];
+    for (int q = 0; q < N; ++q) fro += K[p][q] * K[p][q];
   if (fro == 0.0) {
 #pragma unroll
-    for (int p = 0; p < 5; ++p)
+    for (int p = 0; p < N; ++p)
 #pragma unroll
-      for (int q = 0; q < 5; ++q) V[p][q] = (p == q) ? 1.0 : 0.0;
+      for (int q = 0; q < N; ++q) V[p][q] = (p == q) ? 1.0 : 0.0;
     return;
   }
   // 1/|K| only scales the FP32 stage: FP32 precision is enough when |K|^2 is a normal float
   const double inv = (fro > 1e-36 && fro < 1e36) ? (double)rsqrtf((float)fro) : rsqrt(fro);
-  float Af[5][5], Vf[5][5];
+  float Af[N][N], Vf[N][N];
 #pragma unroll
-  for (int p = 0; p < 5; ++p)
+  for (int p = 0; p < N; ++p)
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Af[p][q] = (float)(K[p][q] * inv);
-  jacobi_f32_5(Af, Vf, 4);
+    for (int q = 0; q < N; ++q) Af[p][q] = (float)(K[p][q] * inv);
+  jacobi_f32<N>(Af, Vf, 4);
   // FP64 orthonormal basis from the FP32 eigenvectors (columns)
 #pragma unroll
-  for (int j = 0; j < 5; ++j) {
+  for (int j = 0; j < N; ++j) {
 #pragma unroll
-    for (int p = 0; p < 5; ++p) V[p][j] = (double)Vf[p][j];
+    for (int p = 0; p < N; ++p) V[p][j] = (double)Vf[p][j];
 #pragma unroll
     for (int i = 0; i < j; ++i) {
       double pr = 0.0;
 #pragma unroll
-      for (int p = 0; p < 5; ++p) pr += V[p][i] * V[p][j];
+      for (int p = 0; p < N; ++p) pr += V[p][i] * V[p][j];
 #pragma unroll
-      for (int p = 0; p < 5; ++p) V[p][j] -= pr * V[p][i];
+      for (int p = 0; p < N; ++p) V[p][j] -= pr * V[p][i];
     }
     double nn = 0.0;
 #pragma unroll
-    for (int p = 0; p < 5; ++p) nn += V[p][j] * V[p][j];
+    for (int p = 0; p < N; ++p) nn += V[p][j] * V[p][j];
     // the FP32 eigenvectors are orthonormal to FP32 precision, so |nn - 1| is about 1e-7:
     // two Newton steps for 1/sqrt(nn) from 1 leave an error of order (nn - 1)^4
     double r = 1.5 - 0.5 * nn;
     r = r * (1.5 - 0.5 * nn * r * r);
 #pragma unroll
-    for (int p = 0; p < 5; ++p) V[p][j] *= r;
+    for (int p = 0; p < N; ++p) V[p][j] *= r;
   }
   // K <- V^T K V
-  double T[5][5];
+  double T[N][N];
 #pragma unroll
-  for (int p = 0; p < 5; ++p)
+  for (int p = 0; p < N; ++p)
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
+    for (int j = 0; j < N; ++j) {
       double s = 0.0;
 #pragma unroll
-      for (int q = 0; q < 5; ++q) s += K[p][q] * V[q][j];
+      for (int q = 0; q < N; ++q) s += K[p][q] * V[q][j];
       T[p][j] = s;
     }
 #pragma unroll
-  for (int i = 0; i < 5; ++i)
+  for (int i = 0; i < N; ++i)
 #pragma unroll
-    for (int j = i; j < 5; ++j) {
+    for (int j = i; j < N; ++j) {
       double s = 0.0;
 #pragma unroll
-      for (int p = 0; p < 5; ++p) s += V[p][i] * T[p][j];
+      for (int p = 0; p < N; ++p) s += V[p][i] * T[p][j];
       K[i][j] = s;
       K[j][i] = s;
     }
-  jacobi_5(K, V);
+  jacobi<N>(K, V);
+}
+
+// K+ = (V max(Lambda, 0)) V^T of the leading N x N block of the 5 x 5 K (rows and columns
+// beyond N are zero in K and in K+)
+template <int N>
+__device__ __forceinline__ void psd_span(const double K[5][5], double Kp[5][5]) {
+  double Kn[N][N], V[N][N];
+#pragma unroll
+  for (int p = 0; p < N; ++p)
+#pragma unroll
+    for (int q = 0; q < N; ++q) Kn[p][q] = K[p][q];
+  eigen_sym<N>(Kn, V);
+  double W[N][N];
+#pragma unroll
+  for (int e = 0; e < N; ++e) {
+    const double le = Kn[e][e] > 0.0 ? Kn[e][e] : 0.0;
+#pragma unroll
+    for (int p = 0; p < N; ++p) W[p][e] = V[p][e] * le;
+  }
+#pragma unroll
+  for (int p = 0; p < 5; ++p)
+#pragma unroll
+    for (int q = p; q < 5; ++q) {
+      double s = 0.0;
+      if (p < N && q < N) {
+#pragma unroll
+        for (int e = 0; e < N; ++e) s += W[p][e] * V[q][e];
+      }
+      Kp[p][q] = s;
+      Kp[q][p] = s;
+    }
 }
 
 // one upper-triangle record: key (min, max) of the two cage nodes, block transposed when
@@ -712,21 +752,12 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
       for (int c = 0; c < 3; ++c)
         for (int a = 0; a < 4; ++a) basis[c][a] = B.basis[c][a];
       if (A.project) {
-        double V[5][5];
-        eigen5(B.K, V);
-        // K+ = (V max(Lambda, 0)) V^T, upper triangle mirrored
-        double W[5][5];
-        for (int e = 0; e < 5; ++e) {
-          const double le = B.K[e][e] > 0.0 ? B.K[e][e] : 0.0;
-          for (int p = 0; p < 5; ++p) W[p][e] = V[p][e] * le;
-        }
-        for (int p = 0; p < 5; ++p)
-          for (int q = p; q < 5; ++q) {
-            double s = 0.0;
-            for (int e = 0; e < 5; ++e) s += W[p][e] * V[q][e];
-            Kp[p][q] = s;
-            Kp[q][p] = s;
-          }
+        // K+ in the span.  With fewer than two free closest-point parameters (an edge or a
+        // vertex of the triangle, an endpoint against an edge or two endpoints) the fifth
+        // basis vector is zero, so K's last row and column are zero and the projection is a
+        // 4 x 4 eigenproblem
+        if (S.m == 2) psd_span<5>(B.K, Kp);
+        else psd_span<4>(B.K, Kp);
       } else {
         for (int p = 0; p < 5; ++p)
           for (int q = 0; q < 5; ++q) Kp[p][q] = B.K[p][q];
