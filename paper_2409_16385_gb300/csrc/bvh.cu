@@ -458,94 +458,145 @@ __device__ __forceinline__ void emit(uint64_t key, uint64_t* cand, int64_t* n_ca
   }
 }
 
+// Candidates found during one round of a warp's queries are appended to the warp's own
+// slice of shared memory (a shared-memory atomic per candidate) and written out when the
+// round ends: one global atomic per warp per round reserves their positions, and the
+// copy is coalesced.  A round's candidates beyond the slice's capacity go straight to
+// global memory through emit().  Without this, every leaf hit waited for a global
+// atomic's returned position.
+constexpr int kQueryWarpBuf = 256;
+
+__device__ __forceinline__ void flush_warp_candidates(uint64_t* buf, int* count, uint64_t* cand, int64_t* n_cand,
+                                                      int64_t cap, DevStatus* st, int lane) {
+  __syncwarp();
+  int c = *count;
+  if (c > kQueryWarpBuf) c = kQueryWarpBuf;
+  if (c > 0) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(n_cand), (unsigned long long)c);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int k = lane; k < c; k += 32) {
+      const int64_t pos = (int64_t)base + k;
+      if (pos < cap) cand[pos] = buf[k];
+    }
+    if (lane == 0 && (int64_t)base + c > cap) {
+      raise_flag(st, EIPC_FLAG_CAND_OVERFLOW);
+      raise_need(st, &st->need_cand, (int64_t)base + c);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) *count = 0;
+  __syncwarp();
+}
+
 // One launch for both query sets: threads [0, nv) run vertex boxes against the triangle
 // tree (PT), threads [nv, nv + ne) run edge boxes against the edge tree (EE, j > i), the
-// edges in that tree's Morton order so neighbouring threads take similar paths.  MINB is
-// the minimum number of 256-thread blocks per SM the register allocation must allow: the
-// walk is latency-bound (dependent node fetches), so more resident warps hide more of it;
-// 4 leaves the compiler free (54 registers), 6 caps it at 40 registers.
+// edges in that tree's Morton order so neighbouring threads take similar paths.  A warp's
+// 32 lanes take rounds of 32 consecutive queries together (lanes past the end idle), so
+// the warp can write out its round's candidates at the round's end.  MINB is the minimum
+// number of 256-thread blocks per SM the register allocation must allow: the walk is
+// latency-bound (dependent node fetches), so more resident warps hide more of it; 4 leaves
+// the compiler free (48 registers), 6 caps it at 40 registers.  Dynamic shared memory:
+// kQueryWarpBuf 8-byte keys per warp.
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_query(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
                                                      uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
+  extern __shared__ uint64_t qbuf[];
+  __shared__ int qcount[8];
   const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);
   const int64_t nv_q = tt.n > 0 ? T.nv : 0;
-  for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < nq; qi += grid_stride()) {
-    const bool is_pt = qi < nv_q;
-    const Bvh& t = is_pt ? tt : te;
-    const PrimKind qkind = is_pt ? kVertex : kEdge;
-    const int64_t qpos = is_pt ? -1 : qi - nv_q;     // EE: the query's own leaf position
-    const int64_t q = is_pt ? qi : (int64_t)te.leaf_prim[qpos];
-    float qlo[3], qhi[3];
-    prim_box_v(qkind, q, T, vbox_q, qlo, qhi);
-    int32_t qa, qb;
-    if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
-    else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
-    const bool qkin = prim_kin(qkind, T, q);
-    const int32_t qgroup = T.vgroup[qa];   // primitives of different scenes never pair
-    auto leaf = [&](int32_t lpos) {
-      const int4 info = __ldg(t.leaf_info + lpos);
-      if (is_pt) {
-        if (info.x == qa || info.y == qa || info.z == qa) return;
-        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
-        const int32_t p = t.leaf_prim[lpos];
-        emit(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j), cand, n_cand, cap, st);
-      } else {
-        // each EE pair is found once, from the edge earlier in Morton order
-        if (lpos <= qpos) return;
-        if (info.x == qa || info.x == qb || info.y == qa || info.y == qb) return;
-        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
-        const int32_t p = t.leaf_prim[lpos];
-        const uint32_t lo = (uint32_t)(p < q ? p : q), hi = (uint32_t)(p < q ? q : p);
-        emit(pair_key(1, lo, hi, T.bits_i, T.bits_j), cand, n_cand, cap, st);
-      }
-    };
-    if (t.n == 1) {
-      const float* b = t.leaf_box + 6 * (int64_t)t.leaf_prim[0];
-      if (box_overlap(b, b + 3, qlo, qhi)) leaf(0);
-      continue;
-    }
-    // Depth-first walk that descends into an overlapping child directly and pushes only
-    // the second child when both overlap, so a descent costs one node fetch and no stack
-    // round trip; leaves are handled where they are found.  The stack holds (node, last
-    // leaf position under it); EE queries skip subtrees that lie entirely at or before
-    // their own leaf.
-    int32_t stack[64], smax[64];
-    int sp = 0;
-    int32_t node = 0;
-    int32_t nmax = (int32_t)(t.n - 1);
-    // a tree of n leaves has n-1 internal nodes, each fetched at most once
-    int64_t visits = 0;
-    while (true) {
-      if (++visits > t.n) {
-        raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
-        break;
-      }
-      const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
-      const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-      const int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
-      const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-      const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-      const int32_t c0 = f3.x, c1 = f3.y, kin = f3.z, split = f3.w;
-      bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
-      bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
-      if (o0 && c0 < 0) { leaf(~c0); o0 = false; }
-      if (o1 && c1 < 0) { leaf(~c1); o1 = false; }
-      if (o0) {
-        if (o1) {
-          if (sp < 64) { stack[sp] = c1; smax[sp++] = nmax; }
-          else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  uint64_t* wbuf = qbuf + (size_t)wib * kQueryWarpBuf;
+  int* wcount = qcount + wib;
+  if (lane == 0) *wcount = 0;
+  __syncwarp();
+  const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t wbase = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); wbase < nq; wbase += wstride) {
+    const int64_t qi = wbase + lane;
+    if (qi < nq) {
+      const bool is_pt = qi < nv_q;
+      const Bvh& t = is_pt ? tt : te;
+      const PrimKind qkind = is_pt ? kVertex : kEdge;
+      const int64_t qpos = is_pt ? -1 : qi - nv_q;     // EE: the query's own leaf position
+      const int64_t q = is_pt ? qi : (int64_t)te.leaf_prim[qpos];
+      float qlo[3], qhi[3];
+      prim_box_v(qkind, q, T, vbox_q, qlo, qhi);
+      int32_t qa, qb;
+      if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
+      else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
+      const bool qkin = prim_kin(qkind, T, q);
+      const int32_t qgroup = T.vgroup[qa];   // primitives of different scenes never pair
+      auto put = [&](uint64_t key) {
+        const int slot = atomicAdd(wcount, 1);
+        if (slot < kQueryWarpBuf) wbuf[slot] = key;
+        else emit(key, cand, n_cand, cap, st);
+      };
+      auto leaf = [&](int32_t lpos) {
+        const int4 info = __ldg(t.leaf_info + lpos);
+        if (is_pt) {
+          if (info.x == qa || info.y == qa || info.z == qa) return;
+          if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
+          const int32_t p = t.leaf_prim[lpos];
+          put(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j));
+        } else {
+          // each EE pair is found once, from the edge earlier in Morton order
+          if (lpos <= qpos) return;
+          if (info.x == qa || info.x == qb || info.y == qa || info.y == qb) return;
+          if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
+          const int32_t p = t.leaf_prim[lpos];
+          const uint32_t lo = (uint32_t)(p < q ? p : q), hi = (uint32_t)(p < q ? q : p);
+          put(pair_key(1, lo, hi, T.bits_i, T.bits_j));
         }
-        node = c0;
-        nmax = split;
-      } else if (o1) {
-        node = c1;
+      };
+      if (t.n == 1) {
+        const float* b = t.leaf_box + 6 * (int64_t)t.leaf_prim[0];
+        if (box_overlap(b, b + 3, qlo, qhi)) leaf(0);
       } else {
-        if (sp == 0) break;
-        --sp;
-        node = stack[sp];
-        nmax = smax[sp];
+        // Depth-first walk that descends into an overlapping child directly and pushes only
+        // the second child when both overlap, so a descent costs one node fetch and no stack
+        // round trip; leaves are handled where they are found.  The stack holds (node, last
+        // leaf position under it); EE queries skip subtrees that lie entirely at or before
+        // their own leaf.
+        int32_t stack[64], smax[64];
+        int sp = 0;
+        int32_t node = 0;
+        int32_t nmax = (int32_t)(t.n - 1);
+        // a tree of n leaves has n-1 internal nodes, each fetched at most once
+        int64_t visits = 0;
+        while (true) {
+          if (++visits > t.n) {
+            raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+            break;
+          }
+          const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
+          const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+          const int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
+          const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
+          const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
+          const int32_t c0 = f3.x, c1 = f3.y, kin = f3.z, split = f3.w;
+          bool o0 = box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
+          bool o1 = box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
+          if (o0 && c0 < 0) { leaf(~c0); o0 = false; }
+          if (o1 && c1 < 0) { leaf(~c1); o1 = false; }
+          if (o0) {
+            if (o1) {
+              if (sp < 64) { stack[sp] = c1; smax[sp++] = nmax; }
+              else raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
+            }
+            node = c0;
+            nmax = split;
+          } else if (o1) {
+            node = c1;
+          } else {
+            if (sp == 0) break;
+            --sp;
+            node = stack[sp];
+            nmax = smax[sp];
+          }
+        }
       }
     }
+    flush_warp_candidates(wbuf, wcount, cand, n_cand, cap, st, lane);
   }
 }
 
@@ -628,10 +679,11 @@ void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* v
                int64_t* n_cand, int64_t cap, DevStatus* st, cudaStream_t s, int threads, int bps, int variant) {
   const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
+  const size_t smem = (size_t)(threads / 32) * kQueryWarpBuf * sizeof(uint64_t);
   if (variant == 3)
-    launch(k_query<6>, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
+    launch(k_query<6>, blocks_for(nq, bps, threads), threads, smem, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
   else
-    launch(k_query<4>, blocks_for(nq, bps, threads), threads, 0, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
+    launch(k_query<4>, blocks_for(nq, bps, threads), threads, smem, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
 }
 
 }  // namespace eipc
