@@ -396,7 +396,7 @@ __device__ __forceinline__ void eigen_sym(double K[N][N], double V[N][N]) {
 // K+ = (V max(Lambda, 0)) V^T of the leading N x N block of the 5 x 5 K (rows and columns
 // beyond N are zero in K and in K+)
 template <int N>
-__device__ __forceinline__ void psd_span(const double K[5][5], double Kp[5][5]) {
+__device__ __forceinline__ void psd_span_inl(const double K[5][5], double Kp[5][5]) {
   double Kn[N][N], V[N][N];
 #pragma unroll
   for (int p = 0; p < N; ++p)
@@ -423,6 +423,13 @@ __device__ __forceinline__ void psd_span(const double K[5][5], double Kp[5][5]) 
       Kp[q][p] = s;
     }
 }
+
+// The 4 x 4 projection (99 % of the pairs of the benchmark workloads) is inlined; the
+// 5 x 5 one, for pairs with two free closest-point parameters, is a separate function, so
+// its larger register footprint (the 5 x 5 eigensolver's matrices) does not set the
+// register allocation of the common path: under a register cap only the rare call spills.
+__device__ __noinline__ void psd_span5(const double K[5][5], double Kp[5][5]) { psd_span_inl<5>(K, Kp); }
+__device__ __forceinline__ void psd_span4(const double K[5][5], double Kp[5][5]) { psd_span_inl<4>(K, Kp); }
 
 // one upper-triangle record: key (min, max) of the two cage nodes, block transposed when
 // the first node is the larger one.  With presorted records the sorted position is
@@ -756,8 +763,8 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
         // vertex of the triangle, an endpoint against an edge or two endpoints) the fifth
         // basis vector is zero, so K's last row and column are zero and the projection is a
         // 4 x 4 eigenproblem
-        if (S.m == 2) psd_span<5>(B.K, Kp);
-        else psd_span<4>(B.K, Kp);
+        if (S.m == 2) psd_span5(B.K, Kp);
+        else psd_span4(B.K, Kp);
       } else {
         for (int p = 0; p < 5; ++p)
           for (int q = 0; q < 5; ++q) Kp[p][q] = B.K[p][q];
