@@ -226,8 +226,10 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
     s->feat_bits = bits_for((uint64_t)mx);
   }
   s->rebuild_interval = 8;
-  s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2;
-  s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.refit_variant = 2;
+  // the scene was zero-filled after construction: every launch-shape default is set here
+  s->tune.eval_threads = 128; s->tune.eval_bps = 16; s->tune.eval_variant = 2; s->tune.eval_tile = 32;
+  s->tune.ccd_tile = 128;
+  s->tune.query_threads = 128; s->tune.query_bps = 24; s->tune.query_variant = 2; s->tune.refit_variant = 2;
   s->contact_refits = 0;
   *out = s;
   return EIPC_OK;
