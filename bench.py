@@ -186,10 +186,15 @@ def measured_peaks():
 # eval_barrier: 291.28e6 flops over the 115,699 pairs of bubble-grasp iterate 2 (ncu, the
 # autotuned shape 128 threads x 6 blocks/SM, 128-register variant); see profiles/
 FP64_FLOPS_PER_PAIR = 2518.0
+# eval_friction: FP64 flops per lagged friction item (ncu, the third launch of the same
+# command: 39.00e6 flops over 115,221 items)
+FP64_FLOPS_PER_FRICTION_ITEM = 338.5
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code and shape
 # (eval_barrier: 122.8 MB + 237.7 MB for the same 115,699 pairs)
 NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3116.0}
+# eval_friction: 113.9 MB + 140.6 MB for the same 115,221 items
+NCU_TRAFFIC_PER_FRICTION_ITEM = 2209.0
 
 
 def query_bytes(sc, n_cand):
@@ -212,12 +217,18 @@ def roofline_figure(name, total_ms, launches, steps, per_step, sc, fp64_probe=No
     avg_s = total_ms / 1e3 / launches
     per_step_launches = launches / steps
     hbm, src = measured_peaks()
-    if name in ("eval_barrier", "ccd_advance"):
-        units = (per_step["pairs"] if name == "eval_barrier" else per_step["ccd"]) / per_step_launches
-        per = FP64_FLOPS_PER_PAIR if name == "eval_barrier" else FP64_FLOPS_PER_CCD_CAND
+    if name in ("eval_barrier", "ccd_advance", "eval_kernels"):
+        units = (per_step["ccd"] if name == "ccd_advance" else per_step["pairs"]) / per_step_launches
+        per = FP64_FLOPS_PER_CCD_CAND if name == "ccd_advance" else FP64_FLOPS_PER_PAIR
+        tr = NCU_TRAFFIC_PER_UNIT.get(name)
+        if name == "eval_kernels":
+            # barrier and friction evaluation, overlapped on two streams: both kernels' FP64
+            # work (and DRAM traffic) over the span from the fork to the join, per contact pair
+            fr = per_step.get("friction_items", 0.0) / max(per_step["pairs"], 1.0)
+            per += FP64_FLOPS_PER_FRICTION_ITEM * fr
+            tr = NCU_TRAFFIC_PER_UNIT["eval_barrier"] + NCU_TRAFFIC_PER_FRICTION_ITEM * fr
         ach = units * per / avg_s / 1e12
         peak = FP64_PEAK_TFLOPS
-        tr = NCU_TRAFFIC_PER_UNIT.get(name)
         out = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,
                    traffic=(tr * units if tr else None), kernel=name, launch_ms=avg_s * 1e3,
                    units_per_launch=units, unit_cost=f"{per:.0f} FP64 flop per unit",
@@ -715,6 +726,7 @@ def run_ours(args, ws, rank, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev_ms = 0.0; n_p = 0
     cand_contact = []
+    fric_items = []
     for k in range(K):
         t = (t0 + k) % n_it
         cs.build_candidates(Q[t], out=pairs)
@@ -726,6 +738,8 @@ def run_ours(args, ws, rank, local):
         ev1.record(stream)
         torch.cuda.synchronize()
         ev_ms += ev0.elapsed_time(ev1)
+        wk = cs.work_counts()
+        fric_items.append(wk["items"] - wk["pairs"])
     stage["eval_pairs_per_s"] = n_p / (ev_ms / 1e3)
     work = cs.work_counts()          # the last iterate's contact build and evaluation
     work.update(pair_split(sc, pairs.host()))
@@ -754,7 +768,7 @@ def run_ours(args, ws, rank, local):
     # ---- rooflines: every kernel timed inside the timed steps; the headline is the one
     # with the largest time there
     per_step = dict(pairs=total_pairs / K, ccd=total_cand / K, cand_contact=float(np.mean(cand_contact)),
-                    cand_ccd=float(np.mean(cand_ccd)))
+                    cand_ccd=float(np.mean(cand_ccd)), friction_items=float(np.mean(fric_items)))
     roofs = {k: roofline_figure(k, *kt.get(k, (0.0, 0)), K, per_step, sc, fp64) for k in timed}
     roof = dict(roofs[dominant])
     roof["chosen_by"] = "largest device time inside the timed steps (per-kernel CUDA events on the launching stream)"

@@ -245,8 +245,9 @@ eipc_status eipc_candidates_read(eipc_scene* scene, int32_t* type, int32_t* i, i
 /* Tracing: per-kernel CUDA-event timers.  Bit k of mask enables timer k (0 embed,
  * 1 bvh_build, 2 bvh_query, 3 narrow_phase, 4 pair_sort, 5 friction_lag, 6 stencil_nodes,
  * 7 eval_barrier, 8 eval_friction, 9 hessian_reduce, 10 gradient_reduce, 11 energy_sum,
- * 12 ccd_advance; eipc_kernel_name(k) names them): each launch is bracketed by two events on
- * its stream.  eipc_timing_read synchronises, writes the summed milliseconds and launch
+ * 12 ccd_advance, 13 eval_kernels -- the barrier and friction evaluations together, which
+ * run side by side on two streams; eipc_kernel_name(k) names them): each launch is
+ * bracketed by two events on its stream.  eipc_timing_read synchronises, writes the summed milliseconds and launch
  * counts of the first n timers and resets them. */
 eipc_status eipc_timing_enable(eipc_scene* scene, uint32_t mask);
 eipc_status eipc_timing_read(eipc_scene* scene, double* total_ms, int64_t* launches, int32_t n);

@@ -399,7 +399,7 @@ class ContactScene:
         _check(self.lib.eipc_set_launch(self.handle, self.LAUNCH_KERNELS[kernel], int(threads), int(blocks_per_sm),
                                         int(variant)), "eipc_set_launch")
 
-    N_TIMERS = 13
+    N_TIMERS = 14
 
     def timing_enable(self, names=None):
         """Brackets every launch of the named kernels (all if None, none if []) with CUDA

@@ -41,6 +41,9 @@ void free_scene(eipc_scene* s) {
     s->timers->destroy();
     delete s->timers;
   }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->aux) cudaStreamDestroy(s->aux);
   delete s;
 }
 
@@ -171,6 +174,9 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->moll_r2, E > 0 ? E : 1));
   ok(dalloc(&s->scan_partial, kScanBlocks + 1)); ok(dalloc(&s->sum_partial, kScanBlocks));
   ok(dalloc(&s->status, 1));
+  ok(cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
+  ok(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+  ok(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
   if (e != cudaSuccess) {
     free_scene(s);
     cudaGetLastError();
@@ -478,7 +484,7 @@ int64_t eipc_launch_count(void) { return (int64_t)g_launches.load(); }
 const char* eipc_kernel_name(int32_t id) {
   static const char* names[kKNum] = {"embed", "bvh_build", "bvh_query", "narrow_phase", "pair_sort", "friction_lag",
                                      "stencil_nodes", "eval_barrier", "eval_friction", "hessian_reduce",
-                                     "gradient_reduce", "energy_sum", "ccd_advance"};
+                                     "gradient_reduce", "energy_sum", "ccd_advance", "eval_kernels"};
   return (id >= 0 && id < kKNum) ? names[id] : "";
 }
 

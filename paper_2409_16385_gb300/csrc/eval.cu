@@ -1774,6 +1774,18 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
     A.tile = sc->tune.eval_tile;
     cudaMemsetAsync(A.queue, 0, sizeof(int64_t), s);
   }
+  // friction items on the scene's second stream, beside the barrier items: the two
+  // kernels write disjoint records and item energies, and the barrier kernel leaves most
+  // warp slots and part of the FP64 pipe free
+  sc->timers->start(kKEvalPair, s);
+  if (fr) {
+    cudaEventRecord(sc->ev_fork, s);
+    cudaStreamWaitEvent(sc->aux, sc->ev_fork, 0);
+    EIPC_TIMED(sc, kKEvalFriction, sc->aux,
+               (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, sc->aux, A,
+                       *lag, p.mu, p.eps_v * p.h)));
+    cudaEventRecord(sc->ev_join, sc->aux);
+  }
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (sc->tune.eval_variant == 4
                   ? launch(k_eval_barrier<4>, blocks_for(pr.capacity, sc->tune.eval_bps, sc->tune.eval_threads),
@@ -1785,10 +1797,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                            sc->tune.eval_threads, 0, s, A)));
   if (A.moll_r2)
     EIPC_TIMED(sc, kKEvalBarrier, s, (launch(k_mollified<false>, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
-  if (fr)
-    EIPC_TIMED(sc, kKEvalFriction, s,
-               (launch(k_eval_friction, blocks_for(lag->capacity, 8, kEvalThreads), kEvalThreads, 0, s, A, *lag, p.mu,
-                                                                                                    p.eps_v * p.h)));
+  if (fr) cudaStreamWaitEvent(s, sc->ev_join, 0);
+  sc->timers->stop(kKEvalPair, s);
   // sums over the contiguous presorted records, in sorted order
   sc->timers->start(kKHReduce, s);
   launch(k_seg_pieces<9, kHRecStride>, blocks_for(sc->rec_cap / kSegChunk + 1, 8), kBlock, 0, s, static_cast<const double*>(sc->hrec),

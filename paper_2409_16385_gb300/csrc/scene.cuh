@@ -92,6 +92,11 @@ struct eipc_scene {
   int contact_refits;    // refits since the last full rebuild
   eipc::DevStatus* status;
   eipc::Timers* timers;   // host-side event timers (off unless enabled)
+  // a second stream of the scene's device: the friction evaluation runs on it beside the
+  // barrier evaluation (they write disjoint records), forked from and joined back to the
+  // caller's stream with two events, which also works inside a graph capture
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 namespace eipc {

@@ -21,7 +21,8 @@ enum KernelId {
   kKGReduce = 10,    // sort-and-reduce of the reduced gradient (group)
   kKEnergy = 11,
   kKCa = 12,         // conservative advancement of CCD candidates
-  kKNum = 13
+  kKEvalPair = 13,   // barrier and friction evaluation together (they overlap on two streams)
+  kKNum = 14
 };
 
 constexpr int kTimerRing = 512;
