@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes (no autotuning)")
     ap.add_argument("--solver", choices=["auto", "dense", "pcg"], default="auto", help="physical: linear solver")
+    ap.add_argument("--launch-mode", choices=["programmatic", "stream"], default="programmatic",
+                    help="kernel launch mode: programmatic dependent launch (default) or plain stream order")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 300 if args.workload == "bubble_grasp" and args.impl == "ours" else 20
@@ -832,7 +834,7 @@ def run_ours(args, ws, rank, local):
                 config=dict(workload=WORKLOAD + ("_small" if args.quick else ""), iterates=n_it,
                             triangles=sc.F, vertices=sc.Nv, edges=sc.E, cage_nodes=sc.Ns,
                             dhat=sc.params["dhat"], mu=sc.params["mu"], parallelism=f"replicas x{ws}",
-                            l2="flushed between steps (256 MiB rewrite)",
+                            l2="flushed between steps (256 MiB rewrite)", launch_mode=args.launch_mode,
                             pairs_per_step=total_pairs / K, ccd_candidates_per_step=total_cand / K,
                             broad_phase_candidates_per_step=dict(contact=per_step["cand_contact"],
                                                                  ccd=per_step["cand_ccd"]),
@@ -1607,7 +1609,10 @@ def main():
     ws, rank, local = dist_setup(backend)
     if args.impl == "reference":
         run_reference(args, ws, rank)
-    elif args.workload == "batched":
+        return finish(ws)
+    from paper_2409_16385_gb300 import binding
+    binding.set_programmatic_launch(args.launch_mode == "programmatic")
+    if args.workload == "batched":
         run_batched(args, ws, rank, local)
     elif args.workload == "adjoint":
         run_adjoint(args, ws, rank, local)
@@ -1617,6 +1622,10 @@ def main():
         run_eval_by_type(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
+    finish(ws)
+
+
+def finish(ws):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

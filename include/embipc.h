@@ -295,6 +295,15 @@ eipc_status eipc_set_launch(eipc_scene* scene, int32_t kernel, int32_t threads, 
 /* Number of kernel launches the library has enqueued in this process (all scenes). */
 int64_t eipc_launch_count(void);
 
+/* Launch mode of every later kernel launch of the library, process-wide (all scenes and
+ * streams).  on != 0 (the default): programmatic dependent launch -- each kernel may be
+ * scheduled while its predecessor in the stream still runs and waits on the device for
+ * that predecessor's completion before its first memory access, which hides the launch
+ * latency between the short kernels of a step.  on == 0: plain stream order.  Results are
+ * the same bits either way.  Graphs keep the mode they were captured with.  Not thread-
+ * safe against launches in flight on other host threads (they see either mode). */
+void eipc_set_programmatic_launch(int32_t on);
+
 /* CCD step bound without any device allocation.  The paper has no counterpart: this
  * exists for callers that cannot call cudaMalloc -- code running under another framework's
  * device-memory allocator or pool that must own every allocation, or a control loop that

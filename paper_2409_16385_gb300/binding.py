@@ -26,7 +26,8 @@ EXPORTS = ["eipc_scene_create", "eipc_scene_destroy", "eipc_embed", "eipc_build_
            "eipc_timing_read", "eipc_kernel_name", "eipc_launch_count", "eipc_set_rebuild_interval",
            "eipc_scene_set_groups", "eipc_group_energy", "eipc_group_alpha", "eipc_set_launch",
            "eipc_contact_hvp", "eipc_scene_set_kinematic", "eipc_scene_set_mollifier", "eipc_bsr_spmv",
-           "eipc_work_counts", "eipc_candidates_read", "eipc_fp64_probe", "eipc_fp64_probe_flops"]
+           "eipc_work_counts", "eipc_candidates_read", "eipc_fp64_probe", "eipc_fp64_probe_flops",
+           "eipc_set_programmatic_launch"]
 
 
 class Params(ctypes.Structure):
@@ -94,6 +95,8 @@ def load(build_if_missing: bool = True):
     L.eipc_set_rebuild_interval.argtypes = [P, i32]
     L.eipc_set_rebuild_interval.restype = i32
     L.eipc_launch_count.restype = i64
+    L.eipc_set_programmatic_launch.argtypes = [i32]
+    L.eipc_set_programmatic_launch.restype = None
     L.eipc_scene_set_groups.argtypes = [P, P, i32]
     L.eipc_scene_set_groups.restype = i32
     L.eipc_group_energy.argtypes = [P, P, P]
@@ -454,6 +457,12 @@ def fp64_peak(iters: int = 1 << 16, repeats: int = 5) -> dict:
         best = ms if best is None else min(best, ms)
     flops = L.eipc_fp64_probe_flops(int(iters))
     return dict(tflops=flops / (best / 1e3) / 1e12, ms=best, flops=int(flops), iters=int(iters))
+
+
+def set_programmatic_launch(on: bool = True):
+    """Process-wide launch mode of the library's kernels (eipc_set_programmatic_launch):
+    programmatic dependent launch (the default) or plain stream order."""
+    load().eipc_set_programmatic_launch(1 if on else 0)
 
 
 def bsr_spmv(row_ptr, col, val, x, out=None, alpha: float = 1.0, beta: float = 0.0):

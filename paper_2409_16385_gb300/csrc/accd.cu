@@ -24,6 +24,7 @@ constexpr double kMargin = 1.0 - 9.313225746154785e-10;   // 1 - 2^-30
 __global__ void __launch_bounds__(kBlock) k_pad(const double* __restrict__ x, const double* __restrict__ dx,
                                                 int64_t nv, double* __restrict__ x4, double* __restrict__ dx4,
                                                 DevStatus* st) {
+  pdl_entry();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     const double a = x[3 * v], b = x[3 * v + 1], c = x[3 * v + 2];
     const double e = dx[3 * v], f = dx[3 * v + 1], g = dx[3 * v + 2];
@@ -37,6 +38,7 @@ __global__ void __launch_bounds__(kBlock) k_pad(const double* __restrict__ x, co
 }
 
 __global__ void k_alpha_init(unsigned long long* bits, unsigned long long* group_bits, int32_t ng) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) *bits = __double_as_longlong(1.0);
   for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
     group_bits[g] = __double_as_longlong(1.0);
@@ -55,6 +57,7 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
                                                      unsigned long long* alpha_bits,
                                                      unsigned long long* __restrict__ group_bits, int64_t* n_adv,
                                                      DevStatus* st, int64_t* queue, int tile_req) {
+  pdl_entry();
   const int64_t n = clamp_count(n_cand, cap);
   const int tile = tile_req >= 32 ? (tile_req & ~31) : 32;
   const int lane = threadIdx.x & 31;
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(kAccdThreads) k_ca(Topo T, const double* __res
 }
 
 __global__ void k_alpha_out(const unsigned long long* bits, double* alpha, const int64_t* n_adv, int64_t* n_out) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *alpha = __longlong_as_double((long long)*bits);
     if (n_out) *n_out = *n_adv;

@@ -46,6 +46,7 @@ __host__ __device__ inline StaticView view_of(unsigned char* base) {
 
 // every call starts from alpha = 1, no flags, no advanced pairs
 __global__ void k_static_init(unsigned char* base) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     StaticView v = view_of(base);
     *v.alpha_bits = (unsigned long long)__double_as_longlong(1.0);
@@ -56,6 +57,7 @@ __global__ void k_static_init(unsigned char* base) {
 
 __global__ void __launch_bounds__(256) k_static_pad(const double* __restrict__ x, const double* __restrict__ dx,
                                                     int64_t nv, unsigned char* base) {
+  pdl_entry();
   StaticView sv = view_of(base);
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
     const double a = x[3 * v], b = x[3 * v + 1], c = x[3 * v + 2];
@@ -82,6 +84,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_ca(int64_t nv, int64_
                                                               const int32_t* __restrict__ ci,
                                                               const int32_t* __restrict__ cj, double s, int max_iter,
                                                               unsigned char* base) {
+  pdl_entry();
   StaticView sv = view_of(base);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nc; k += gridDim.x * blockDim.x) {
     const int type = ctype[k];
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_static_ca(int64_t nv, int64_
 }
 
 __global__ void k_static_out(const unsigned char* base, double* alpha, int32_t* flags, int64_t* n_adv) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     StaticView v = view_of(const_cast<unsigned char*>(base));
     *alpha = __longlong_as_double((long long)*v.alpha_bits);

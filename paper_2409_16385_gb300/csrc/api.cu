@@ -481,6 +481,8 @@ eipc_status eipc_set_rebuild_interval(eipc_scene* sc, int32_t n) {
 
 int64_t eipc_launch_count(void) { return (int64_t)g_launches.load(); }
 
+void eipc_set_programmatic_launch(int32_t on) { g_programmatic.store(on ? 1 : 0); }
+
 const char* eipc_kernel_name(int32_t id) {
   static const char* names[kKNum] = {"embed", "bvh_build", "bvh_query", "narrow_phase", "pair_sort", "friction_lag",
                                      "stencil_nodes", "eval_barrier", "eval_friction", "hessian_reduce",

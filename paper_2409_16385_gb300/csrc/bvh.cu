@@ -13,6 +13,7 @@ __device__ __forceinline__ int32_t f2ord(float f) {
 __device__ __forceinline__ float ord2f(int32_t i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
 __global__ void k_bounds_init(int32_t* b) {
+  pdl_entry();
   if (threadIdx.x < 3) b[threadIdx.x] = 0x7fffffff;
   else if (threadIdx.x < 6) b[threadIdx.x] = (int32_t)0x80000000;
 }
@@ -20,6 +21,7 @@ __global__ void k_bounds_init(int32_t* b) {
 // scene box over all vertex positions (and their swept ends)
 __global__ void __launch_bounds__(kBlock) k_bounds(const double* __restrict__ x4, const double* __restrict__ dx4,
                                                    int64_t nv, int32_t* __restrict__ b) {
+  pdl_entry();
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     V3 p = load_x(x4, (int32_t)v);
@@ -69,6 +71,7 @@ __device__ __forceinline__ uint32_t spread10(uint32_t v) {
 __global__ void __launch_bounds__(kBlock) k_vertex_boxes(int64_t nv, const double* __restrict__ x4,
                                                          const double* __restrict__ dx4, double pad,
                                                          float* __restrict__ vbox, float* __restrict__ vbox_pad) {
+  pdl_entry();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     const V3 p = load_x(x4, (int32_t)v);
     double lo[3] = {p.x, p.y, p.z}, hi[3] = {p.x, p.y, p.z};
@@ -116,6 +119,7 @@ __global__ void __launch_bounds__(kBlock) k_leaves(PrimKind kind, int64_t n, Top
                                                    const int32_t* __restrict__ b,
                                                    float* __restrict__ leaf_box, uint64_t* __restrict__ keys,
                                                    uint32_t* __restrict__ vals) {
+  pdl_entry();
   float blo[3], bext[3];
   for (int k = 0; k < 3; ++k) {
     blo[k] = ord2f(b[k]);
@@ -149,6 +153,7 @@ __device__ __forceinline__ int delta(const uint64_t* __restrict__ k, int64_t n, 
 __global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict__ keys, int64_t n,
                                                      BvhNode* __restrict__ nodes, int32_t* __restrict__ parent,
                                                      int2* __restrict__ range) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 1; i += grid_stride()) {
     int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = delta(keys, n, i, i - dir);
@@ -217,6 +222,7 @@ __device__ __forceinline__ void leaf_box_of(int4 li, const float* __restrict__ v
 
 __global__ void __launch_bounds__(kBlock) k_leaf_boxes(int64_t n, const int4* __restrict__ leaf_info,
                                                        const float* __restrict__ vbox, float* __restrict__ leaf_box) {
+  pdl_entry();
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
     float lo[3], hi[3];
     leaf_box_of(leaf_info[l], vbox, lo, hi);
@@ -237,6 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
                                                   const float* __restrict__ leaf_box, BvhNode* nodes,
                                                   const int32_t* __restrict__ parent, int32_t* leaf_prim,
                                                   int4* __restrict__ leaf_info, int32_t* flag) {
+  pdl_entry();
   for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n; l += grid_stride()) {
     int kin = 0;
     float lo[3], hi[3];
@@ -296,6 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
 __global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2* __restrict__ range,
                                                           const int32_t* __restrict__ parent, int32_t* __restrict__ tl_root,
                                                           int32_t* __restrict__ up_start, int32_t* __restrict__ count) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n - 1; i += grid_stride()) {
     if (i < n - 1) {                              // internal node i
       const int2 r = range[i];
@@ -336,6 +344,7 @@ __host__ __device__ __forceinline__ RefitView refit_view(const Bvh& t) {
 // computing leaf l's box from the positions and climbing in shared memory.  The grid also
 // clears both trees' arrival counters for phase B.
 __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
+  pdl_entry();
   __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
   __shared__ int scnt[kTreeletWarps][kTreelet];
   __shared__ int spar[kTreeletWarps][kTreelet];
@@ -396,6 +405,7 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
 // directly under a larger node, its box from the positions) climbs with release-acquire
 // arrival counters; the two trees' climbs run side by side.
 __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
+  pdl_entry();
   const int64_t nuA = A.n > 1 ? A.count[1] : 0, nuB = B.n > 1 ? B.count[1] : 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nuA + nuB; k += grid_stride()) {
     const bool inA = k < nuA;
@@ -501,6 +511,7 @@ __device__ __forceinline__ void flush_warp_candidates(uint64_t* buf, int* count,
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) k_query(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
                                                      uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
+  pdl_entry();
   extern __shared__ uint64_t qbuf[];
   __shared__ int qcount[8];
   const int64_t nq = (tt.n > 0 ? T.nv : 0) + (te.n > 0 ? T.ne : 0);

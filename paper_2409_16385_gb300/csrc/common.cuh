@@ -14,12 +14,40 @@ namespace eipc {
 
 // Process-wide count of kernel launches enqueued by the library (eipc_launch_count).
 inline std::atomic<long long> g_launches{0};
+// Process-wide launch mode (eipc_set_programmatic_launch): 1 = programmatic dependent
+// launch, 0 = plain stream order.
+inline std::atomic<int> g_programmatic{1};
 
-// Every kernel of the library is launched through here.
+// Every kernel of the library is launched through here.  With programmatic stream
+// serialisation a kernel may be scheduled while the kernel before it in the stream is
+// still running (its CTAs occupy free slots and its launch latency overlaps the
+// predecessor's tail); correctness rests on pdl_entry() below being the first statement
+// of every kernel.
 template <class... KArgs, class... Args>
 inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
-  kernel<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = g_programmatic.load(std::memory_order_relaxed);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
   g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+// First statement of every kernel.  griddepcontrol.wait returns once the grids this one
+// depends on (the previous kernel in the stream, when launched programmatically) have
+// completed and their memory operations are visible; it returns at once otherwise.  Since
+// every kernel waits before it can complete, completion stays transitive along the stream.
+// launch_dependents then lets the next kernel's CTAs be scheduled once every CTA of this
+// grid has started, so they never compete with this grid's own unscheduled CTAs.
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 constexpr int kSMs = 152;          // GB300: 2 dies x 76 SMs

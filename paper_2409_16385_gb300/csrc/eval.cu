@@ -71,6 +71,7 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
                                                        int32_t* __restrict__ item_group, const int32_t* __restrict__ vgroup,
                                                        int64_t* __restrict__ rc_h, int64_t* __restrict__ rc_g,
                                                        int64_t* n_items, DevStatus* st) {
+  pdl_entry();
   const int64_t P = clamp_count(pr.count, pr.capacity);
   const int64_t L = lag_v ? clamp_count(lag_count, lag_cap) : 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -852,6 +853,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
 // projection).
 template <int MINB>
 __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A) {
+  pdl_entry();
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t np = P < nit ? P : nit;
@@ -889,6 +891,7 @@ __global__ void __launch_bounds__(kEvalThreads, MINB) k_eval_barrier(EvalArgs A)
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc_lag lag, double mu, double eps) {
+  pdl_entry();
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t L = nit - P;
@@ -983,6 +986,7 @@ __device__ __forceinline__ bool item_has_kinematic(const Topo& T, const eipc_pai
 __global__ void k_hvp_counts(Topo T, eipc_pairs pr, const int32_t* lag_v, const int64_t* lag_count, int64_t lag_cap,
                              const int32_t* __restrict__ cage_idx, const int32_t* __restrict__ item_n,
                              const int64_t* n_items, int64_t cap, int64_t* __restrict__ rc_g) {
+  pdl_entry();
   const int64_t n = clamp_count(n_items, cap);
   const int64_t P = clamp_count(pr.count, pr.capacity);
   const int64_t L = lag_v ? clamp_count(lag_count, lag_cap) : 0;
@@ -991,6 +995,7 @@ __global__ void k_hvp_counts(Topo T, eipc_pairs pr, const int32_t* lag_v, const 
 }
 
 __global__ void k_hvp_kin_sum(const double* __restrict__ rows, double* __restrict__ out_kin) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     double a[3] = {0.0, 0.0, 0.0};
     for (int s = 0; s < kKinSlots; ++s)
@@ -1019,6 +1024,7 @@ __device__ __forceinline__ void emit_g(const EvalArgs& A, int64_t pos, uint64_t 
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
+  pdl_entry();
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t np = P < nit ? P : nit;
@@ -1089,6 +1095,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_barrier(EvalArgs A) {
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_lag lag, double mu, double eps) {
+  pdl_entry();
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t L = nit - P;
@@ -1141,6 +1148,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_hvp_friction(EvalArgs A, eipc_
 // as for every other item.
 template <bool hvp>
 __global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
+  pdl_entry();
   const int64_t P = clamp_count(A.pr.count, A.pr.capacity);
   const int64_t nit = *A.n_items;
   const int64_t np = P < nit ? P : nit;
@@ -1228,6 +1236,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
 __global__ void __launch_bounds__(kBlock) k_eval_order_keys(const int32_t* __restrict__ type, const int32_t* __restrict__ item_n,
                                                             const int64_t* n_pairs, int64_t pair_cap, const int64_t* n_items,
                                                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  pdl_entry();
   const int64_t P = clamp_count(n_pairs, pair_cap);
   const int64_t n = *n_items;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
@@ -1239,6 +1248,7 @@ __global__ void __launch_bounds__(kBlock) k_eval_order_keys(const int32_t* __res
 // record totals -> overflow flags and clamped sort counts
 __global__ void k_rec_check(const int64_t* rh_total, const int64_t* rg_total, int64_t rec_cap, int64_t gcap,
                             int64_t* n_rh, int64_t* n_rg, DevStatus* st) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t a = *rh_total, b = *rg_total;
     if (a > rec_cap || b > gcap) {
@@ -1271,6 +1281,7 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restr
                                                          uint64_t* __restrict__ fkey, uint32_t* __restrict__ fval,
                                                          int64_t* n_full_sort, int64_t* n_diag, DevStatus* st,
                                                          int32_t* __restrict__ dst) {
+  pdl_entry();
   const int64_t S0 = *n_seg;
   const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1298,6 +1309,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict
                                                       const double* __restrict__ rec, const int64_t* __restrict__ start,
                                                       const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
                                                       double* __restrict__ g) {
+  pdl_entry();
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
   const int lane = threadIdx.x & 31;
@@ -1333,6 +1345,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
                                                      int64_t rec_cap, int64_t gcap, int64_t ns,
                                                      uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hvals,
                                                      uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gvals) {
+  pdl_entry();
   const int64_t nit = *n_items;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1362,6 +1375,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
 // inverse of the sort permutation: record perm[p] sits at sorted position p
 __global__ void __launch_bounds__(kBlock) k_inverse(const uint32_t* __restrict__ perm, const int64_t* n_dev, int64_t cap,
                                                     uint32_t* __restrict__ inv) {
+  pdl_entry();
   const int64_t n = clamp_count(n_dev, cap);
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += grid_stride()) inv[perm[p]] = (uint32_t)p;
 }
@@ -1369,6 +1383,7 @@ __global__ void __launch_bounds__(kBlock) k_inverse(const uint32_t* __restrict__
 // key of each segment
 __global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict__ keys, const int64_t* __restrict__ start,
                                                      const int64_t* n_seg, uint64_t* __restrict__ ukey) {
+  pdl_entry();
   const int64_t S = *n_seg;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) ukey[s] = keys[start[s]];
 }
@@ -1380,6 +1395,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restri
                                                         const int64_t* n_full_sort, const int64_t* n_diag, int br,
                                                         eipc_bsr H, int64_t* __restrict__ row_count,
                                                         int32_t* __restrict__ dst, DevStatus* st) {
+  pdl_entry();
   const int64_t nnzb = *n_full_sort - *n_diag;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *H.nnzb = nnzb;
@@ -1410,6 +1426,7 @@ constexpr int kSegChunk = 32;
 // units per segment: unit[s] = ceil(len_s / kSegChunk) (exclusive-scanned afterwards)
 __global__ void __launch_bounds__(kBlock) k_seg_units(const int64_t* __restrict__ start, const int64_t* n_rec,
                                                       const int64_t* n_seg, int64_t cap, int64_t* __restrict__ unit) {
+  pdl_entry();
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
@@ -1470,6 +1487,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_pieces(const double* __restrict_
                                                        const int64_t* __restrict__ unit, const int64_t* n_units,
                                                        const int64_t* n_rec, const int64_t* n_seg, int64_t cap,
                                                        double* __restrict__ piece) {
+  pdl_entry();
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
   const int64_t U = *n_units;
@@ -1520,6 +1538,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __res
                                                              const int64_t* __restrict__ unit, const int64_t* n_units,
                                                              const int64_t* n_seg, int64_t cap,
                                                              const int32_t* __restrict__ dst, eipc_bsr H) {
+  pdl_entry();
   const int64_t S0 = *n_seg;
   const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;      // the segments k_full_entries kept
   const int64_t U = *n_units;
@@ -1551,6 +1570,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g_pieces(const uint64_t* __r
                                                              const int64_t* __restrict__ start,
                                                              const int64_t* __restrict__ unit, const int64_t* n_units,
                                                              const int64_t* n_seg, double* __restrict__ g) {
+  pdl_entry();
   const int64_t S = *n_seg;
   const int64_t U = *n_units;
   const int lane = threadIdx.x & 31;
@@ -1569,6 +1589,7 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g_pieces(const uint64_t* __r
 }
 
 __global__ void k_rowptr(const int64_t* __restrict__ row_off, int64_t ns, int32_t* __restrict__ row_ptr) {
+  pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= ns; i += grid_stride())
     row_ptr[i] = (int32_t)row_off[i];
 }
@@ -1576,6 +1597,7 @@ __global__ void k_rowptr(const int64_t* __restrict__ row_off, int64_t ns, int32_
 // deterministic sum: fixed chunk per block, fixed in-block tree, partials summed in order
 __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict__ x, const int64_t* n_dev,
                                                         int64_t cap, double* __restrict__ partial) {
+  pdl_entry();
   const int64_t n = clamp_count(n_dev, cap);
   const int64_t per = (n + gridDim.x - 1) / gridDim.x;
   const int64_t b = blockIdx.x * per, e = (b + per < n) ? b + per : n;
@@ -1594,6 +1616,7 @@ __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict
 
 // one warp: lane l adds partials l, l + 32, ... in order, then a fixed shuffle tree
 __global__ void k_sum_final(const double* __restrict__ partial, int nb, double* out) {
+  pdl_entry();
   if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const int lane = threadIdx.x;
   double t = 0.0;
@@ -1606,6 +1629,7 @@ __global__ void k_sum_final(const double* __restrict__ partial, int nb, double* 
 __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __restrict__ x4, eipc_pairs pr,
                                                       double dhat, double kappa, eipc_lag out, DevStatus* st,
                                                       const double* __restrict__ moll_r2, double moll_factor) {
+  pdl_entry();
   const int64_t P = clamp_count(pr.count, pr.capacity);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *out.count = P < out.capacity ? P : out.capacity;
@@ -1651,6 +1675,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __re
 }
 
 __global__ void k_set_count(int64_t* c, int64_t v) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) *c = v;
 }
 

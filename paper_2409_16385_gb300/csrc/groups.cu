@@ -16,6 +16,7 @@ namespace {
 __global__ void __launch_bounds__(kBlock) k_group_keys(const int32_t* __restrict__ item_group, const int64_t* n_items,
                                                        int64_t cap, int32_t ng, uint64_t* __restrict__ keys,
                                                        uint32_t* __restrict__ vals, int64_t* __restrict__ counts) {
+  pdl_entry();
   const int64_t n = clamp_count(n_items, cap);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
     int32_t g = item_group[k];
@@ -27,6 +28,7 @@ __global__ void __launch_bounds__(kBlock) k_group_keys(const int32_t* __restrict
 }
 
 __global__ void k_group_prefix(const int64_t* __restrict__ counts, int32_t ng, int64_t* __restrict__ offsets) {
+  pdl_entry();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t run = 0;
     for (int32_t g = 0; g < ng; ++g) {
@@ -40,6 +42,7 @@ __global__ void k_group_prefix(const int64_t* __restrict__ counts, int32_t ng, i
 __global__ void __launch_bounds__(kBlock) k_group_sum(const uint32_t* __restrict__ sorted, const double* __restrict__ item_E,
                                                       const int64_t* __restrict__ offsets, int32_t ng,
                                                       double* __restrict__ E_groups) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(kBlock) k_group_sum(const uint32_t* __restrict
 }
 
 __global__ void k_group_alpha_out(const unsigned long long* __restrict__ bits, int32_t ng, double* __restrict__ out) {
+  pdl_entry();
   for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
     out[g] = __longlong_as_double((long long)bits[g]);
 }

@@ -14,6 +14,7 @@ __global__ void __launch_bounds__(kBlock) k_embed(int64_t nv, const int32_t* __r
                                                   const double* __restrict__ q, double* __restrict__ out,
                                                   int padded, int displacement, float* __restrict__ outf,
                                                   DevStatus* st) {
+  pdl_entry();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     const int4 id = __ldg(reinterpret_cast<const int4*>(idx) + v);
     double r[3];
@@ -71,6 +72,7 @@ __global__ void __launch_bounds__(kBlock) k_screen(Topo T, const float* __restri
                                                    const uint64_t* __restrict__ cand,
                                                    const int64_t* n_cand, int64_t cap, double dhat,
                                                    uint64_t* __restrict__ out, int64_t* n_out) {
+  pdl_entry();
   const int64_t n = clamp_count(n_cand, cap);
   const float dhat_up = __double2float_ru(dhat);
   const int lane = threadIdx.x & 31;
@@ -114,6 +116,7 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
                                                    int64_t cand_cap, double dhat, uint64_t* __restrict__ skeys,
                                                    uint32_t* __restrict__ svals, double* __restrict__ sd,
                                                    int64_t* n_surv, DevStatus* st) {
+  pdl_entry();
   const int64_t n = clamp_count(n_cand, cand_cap);
   const int lane = threadIdx.x & 31;
   // d2 at or above this has sqrt(d2) > dhat: rejected without the square root, the rest
@@ -181,6 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_feature_keys(Topo T, const double* _
                                                          const int32_t* __restrict__ eid, int B,
                                                          uint64_t* __restrict__ fkeys, uint32_t* __restrict__ fvals,
                                                          DevStatus* st) {
+  pdl_entry();
   const int64_t n = clamp_count(n_surv, cap);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
     int type; int32_t i, j;
@@ -230,6 +234,7 @@ __global__ void __launch_bounds__(kBlock) k_feature_keys(Topo T, const double* _
 __global__ void __launch_bounds__(kBlock) k_feature_firsts(const uint64_t* __restrict__ fkeys,
                                                            const uint32_t* __restrict__ fvals, const int64_t* n_surv,
                                                            int64_t cap, int64_t* __restrict__ keep) {
+  pdl_entry();
   const int64_t n = clamp_count(n_surv, cap);
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += grid_stride())
     keep[fvals[s]] = (s == 0 || fkeys[s] != fkeys[s - 1]) ? 1 : 0;
@@ -241,6 +246,7 @@ __global__ void __launch_bounds__(kBlock) k_feature_compact(const uint64_t* __re
                                                             const int64_t* __restrict__ pos, const int64_t* n_surv,
                                                             int64_t cap, uint64_t* __restrict__ keys2,
                                                             uint32_t* __restrict__ vals2) {
+  pdl_entry();
   const int64_t n = clamp_count(n_surv, cap);
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride())
     if (keep[k]) {
@@ -254,6 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_emit_pairs(Topo T, const uint64_t* _
                                                        const uint32_t* __restrict__ vals, const double* __restrict__ sd,
                                                        const int64_t* n_surv, int64_t cand_cap, eipc_pairs out,
                                                        DevStatus* st) {
+  pdl_entry();
   const int64_t n = clamp_count(n_surv, cand_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *out.count = n;
@@ -286,6 +293,7 @@ namespace {
 // new prescribed positions for the kinematic rows (cage_idx[4v] < 0) only
 __global__ void __launch_bounds__(kBlock) k_set_kinematic(int64_t nv, const int32_t* __restrict__ cage_idx,
                                                           const double* __restrict__ x_kin, double* __restrict__ x_kin4) {
+  pdl_entry();
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += grid_stride()) {
     if (cage_idx[4 * v] >= 0) continue;
     x_kin4[4 * v] = x_kin[3 * v];
@@ -298,6 +306,7 @@ __global__ void __launch_bounds__(kBlock) k_set_kinematic(int64_t nv, const int3
 __global__ void __launch_bounds__(kBlock) k_edge_rest_len2(int64_t ne, const int32_t* __restrict__ edges,
                                                            const double* __restrict__ x_rest, double* __restrict__ r2,
                                                            int64_t* bad) {
+  pdl_entry();
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne; e += grid_stride()) {
     const int64_t a = edges[2 * e], b = edges[2 * e + 1];
     const double dx = x_rest[3 * b] - x_rest[3 * a];
@@ -314,6 +323,7 @@ __global__ void __launch_bounds__(kBlock) k_decode_candidates(Topo T, const uint
                                                               const int64_t* n_cand, int64_t cand_cap, int64_t out_cap,
                                                               int32_t* __restrict__ type, int32_t* __restrict__ ci,
                                                               int32_t* __restrict__ cj, int64_t* n_out) {
+  pdl_entry();
   const int64_t n = clamp_count(n_cand, cand_cap);
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_out = n;
   const int64_t m = n < out_cap ? n : out_cap;

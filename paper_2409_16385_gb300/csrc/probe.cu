@@ -13,6 +13,7 @@ constexpr int kProbeThreads = 256;
 constexpr int kProbeBlocksPerSM = 4;
 
 __global__ void __launch_bounds__(kProbeThreads) k_fp64_probe(int64_t iters, double m, double c, double* sink) {
+  pdl_entry();
   double a[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) a[k] = 1.0 + 1e-3 * (threadIdx.x + k);

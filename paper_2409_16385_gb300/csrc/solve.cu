@@ -11,6 +11,7 @@ __global__ void __launch_bounds__(kBlock) k_bsr_spmv(int64_t nrows, const int32_
                                                      const int32_t* __restrict__ col, const double* __restrict__ val,
                                                      const double* __restrict__ x, double alpha, double beta,
                                                      double* __restrict__ y) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {

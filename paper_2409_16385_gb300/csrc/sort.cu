@@ -26,6 +26,7 @@ __device__ __forceinline__ void chunk_range(int64_t n, int64_t* beg, int64_t* en
 __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restrict__ keys,
                                                        const int64_t* n_dev, int64_t cap, int shift,
                                                        uint32_t* __restrict__ hist) {
+  pdl_entry();
   __shared__ uint32_t h[256];
   for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
   __syncthreads();
@@ -44,6 +45,7 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restric
 // consecutive counters [t * per, (t + 1) * per); a block scan of the threads' sums gives
 // each its starting offset.
 __global__ void __launch_bounds__(256) k_hist_digits(uint32_t* hist) {
+  pdl_entry();
   constexpr int per = (kSortBlocks + 255) / 256;
   __shared__ uint32_t wsum[8];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(const uint64_t* __rest
                                                           uint32_t* __restrict__ vout,
                                                           const int64_t* n_dev, int64_t cap, int shift,
                                                           const uint32_t* __restrict__ offs) {
+  pdl_entry();
   constexpr int W = kSortThreads / 32;
   __shared__ uint32_t base[256];
   __shared__ uint32_t wcnt[W][257];
@@ -172,6 +175,7 @@ __device__ int64_t block_sum_i64(int64_t v) {
 
 __global__ void __launch_bounds__(256) k_scan_partial(const int64_t* __restrict__ in, const int64_t* n_dev,
                                                       int64_t cap, int64_t* __restrict__ partial) {
+  pdl_entry();
   int64_t n = *n_dev;
   if (n > cap) n = cap;
   int64_t beg, end;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(256) k_scan_partial(const int64_t* __restrict_
 
 // exclusive scan of the kScanBlocks partial sums by one warp (chunks of 32 with a carry)
 __global__ void k_scan_partials(int64_t* partial, int64_t* total) {
+  pdl_entry();
   const int lane = threadIdx.x & 31;
   if (threadIdx.x >= 32 || blockIdx.x != 0) return;
   int64_t run = 0;
@@ -208,6 +213,7 @@ __global__ void k_scan_partials(int64_t* partial, int64_t* total) {
 __global__ void __launch_bounds__(256) k_scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out,
                                                     const int64_t* n_dev, int64_t cap,
                                                     const int64_t* __restrict__ partial) {
+  pdl_entry();
   __shared__ int64_t tile_sum[256];
   int64_t n = *n_dev;
   if (n > cap) n = cap;
@@ -242,6 +248,7 @@ __device__ __forceinline__ int64_t seg_head(const uint64_t* __restrict__ keys, i
 // per-chunk number of segment heads (chunks of scan_range)
 __global__ void __launch_bounds__(256) k_seg_heads_partial(const uint64_t* __restrict__ keys, const int64_t* n_dev,
                                                            int64_t cap, int64_t* __restrict__ partial) {
+  pdl_entry();
   int64_t n = *n_dev;
   if (n > cap) n = cap;
   int64_t beg, end;
@@ -257,6 +264,7 @@ __global__ void __launch_bounds__(256) k_seg_heads_partial(const uint64_t* __res
 __global__ void __launch_bounds__(256) k_seg_heads_write(const uint64_t* __restrict__ keys, const int64_t* n_dev,
                                                          int64_t cap, const int64_t* __restrict__ partial,
                                                          int64_t* __restrict__ start) {
+  pdl_entry();
   __shared__ int32_t wsum[8];
   int64_t n = *n_dev;
   if (n > cap) n = cap;

@@ -175,6 +175,33 @@ def test_bitwise_repeatable():
     assert outs[0] == outs[1] == outs[2]
 
 
+def test_launch_modes_agree_bitwise():
+    """Programmatic dependent launch (the default) and plain stream order give the same
+    bits for the pair set, E, g_r, H_r and the CCD step bound."""
+    from paper_2409_16385_gb300 import binding
+    sc = _scene(2, True)
+    cs = _cs(sc)
+    q = _t(sc.iterate(9))
+    qn = _t(sc.iterate(sc.lag_of(9)))
+    dq = _t(sc.dq(9))
+    outs = []
+    try:
+        for on in (False, True, False, True):
+            binding.set_programmatic_launch(on)
+            lag = cs.friction_lag(qn, cs.build_candidates(qn, out=cs.new_pairs()))
+            pr = cs.build_candidates(q)
+            E, g, H = cs.eval_contact(q, pr, lag)
+            a = cs.accd_toi(cs.embed(q), cs.embed(dq, displacement=True))
+            h = H.host()
+            ph = pr.host()
+            outs.append((ph["i"].tobytes(), ph["j"].tobytes(), ph["d"].tobytes(), E.cpu().numpy().tobytes(),
+                         g.cpu().numpy().tobytes(), h["val"].tobytes(), h["col"].tobytes(), float(a)))
+            assert cs.status()["flags"] == 0
+    finally:
+        binding.set_programmatic_launch(True)
+    assert outs[0] == outs[1] == outs[2] == outs[3]
+
+
 def test_refitted_and_rebuilt_hierarchies_agree_bitwise():
     """The contact set and the reduced outputs do not depend on whether the LBVH was
     rebuilt for these positions or refitted from another configuration's hierarchy."""
