@@ -14,6 +14,7 @@
 // differences between this FP64 arithmetic and any other evaluation of the same bound.
 #include "geometry.cuh"
 #include "scene.cuh"
+#include "sort.cuh"
 
 namespace eipc {
 namespace {
@@ -200,8 +201,8 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
   int64_t* n_cand = sc->counters + kCntCand;
   int64_t* n_adv = sc->counters + kCntAccd;
   unsigned long long* abits = reinterpret_cast<unsigned long long*>(sc->counters + 12);
-  cudaMemsetAsync(n_cand, 0, sizeof(int64_t), s);
-  cudaMemsetAsync(n_adv, 0, sizeof(int64_t), s);
+  int64_t* queue = sc->counters + kCntCcdQueue;
+  zero_ranges(s, {{n_cand, sizeof(int64_t)}, {n_adv, sizeof(int64_t)}, {queue, sizeof(int64_t)}});
   launch(k_alpha_init, blocks_for(sc->n_groups), kBlock, 0, s, abits, sc->group_alpha_bits, sc->n_groups);
   // swept per-vertex boxes over [x, x + dx]; the hierarchies of the last contact-set build
   // are refitted with them when they exist (the topology is reused; only the boxes change)
@@ -225,8 +226,6 @@ void accd_launch(eipc_scene* sc, const double* x, const double* dx, const eipc_p
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps,
                        sc->tune.query_variant));
-  int64_t* queue = sc->counters + kCntCcdQueue;
-  cudaMemsetAsync(queue, 0, sizeof(int64_t), s);
   EIPC_TIMED(sc, kKCa, s,
              (launch(k_ca, blocks_for(sc->cand_cap, 16, kAccdThreads), kAccdThreads, 0, s, 
                  sc->topo, sc->x4, sc->dx4, sc->cand, n_cand, sc->cand_cap, p.accd_s, p.accd_max_iter, abits, sc->group_alpha_bits, n_adv,

@@ -172,7 +172,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->row_count, Ns + 1));
   ok(dalloc(&s->edge_key, E > 0 ? E : 1)); ok(dalloc(&s->edge_id, E > 0 ? E : 1));
   ok(dalloc(&s->moll_r2, E > 0 ? E : 1));
-  ok(dalloc(&s->scan_partial, kScanBlocks + 1)); ok(dalloc(&s->sum_partial, kScanBlocks));
+  ok(dalloc(&s->scan_partial, 2 * (kScanBlocks + 1))); ok(dalloc(&s->sum_partial, kScanBlocks));
   ok(dalloc(&s->status, 1));
   ok(cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking));
   ok(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));

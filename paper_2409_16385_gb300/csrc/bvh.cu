@@ -622,6 +622,8 @@ void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double 
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, const float* vbox,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant) {
   if (t.n <= 0) return;
+  zero_ranges(s, {{t.nodes, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1)}, {t.refit_flag, sizeof(int32_t) * t.n},
+                  {t.n > 1 ? t.tl_count : nullptr, 2 * sizeof(int32_t)}});
   launch(k_bounds_init, 1, 32, 0, s, bounds_ws);
   launch(k_bounds, blocks_for(topo.nv, 4), kBlock, 0, s, x4, dx4, topo.nv, bounds_ws);
   launch(k_leaves, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, vbox, static_cast<const int32_t*>(bounds_ws),
@@ -630,8 +632,6 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   const uint64_t* sk = which ? t.keys_alt : t.keys;
   const uint32_t* sv = which ? t.vals_alt : t.vals;
   t.sorted = sv;
-  cudaMemsetAsync(t.nodes, 0, sizeof(BvhNode) * (t.n > 1 ? t.n - 1 : 1), s);
-  cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
   if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent, t.range);
   if (refit_variant == 0)
     launch(k_refit<true, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
@@ -642,7 +642,6 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
            t.leaf_info, t.refit_flag);
   if (t.n > 1) {
-    cudaMemsetAsync(t.tl_count, 0, 2 * sizeof(int32_t), s);
     launch(k_treelet_lists, blocks_for(2 * t.n), kBlock, 0, s, t.n, static_cast<const int2*>(t.range),
            static_cast<const int32_t*>(t.parent), t.tl_root, t.up_start, t.tl_count);
   }
@@ -675,7 +674,7 @@ void bvh_refit(Bvh& t, PrimKind kind, const Topo& topo, const float* vbox, cudaS
     return;
   }
   launch(k_leaf_boxes, blocks_for(t.n), kBlock, 0, s, t.n, static_cast<const int4*>(t.leaf_info), vbox, t.leaf_box);
-  cudaMemsetAsync(t.refit_flag, 0, sizeof(int32_t) * t.n, s);
+  zero_ranges(s, {{t.refit_flag, sizeof(int32_t) * t.n}});
   if (refit_variant == 0)
     launch(k_refit<false, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, t.sorted,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,

@@ -1228,19 +1228,83 @@ __global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
   }
 }
 
+// FP32 guess of a stencil's number of free closest-point parameters (2: projection inside
+// the triangle / both segment parameters inside; 1: an edge interior; 0: two vertices), by
+// the same region rules as pt_distance / ee_distance.  Only a scheduling hint: a wrong
+// guess near a region boundary costs a divergent branch, never a different result.
+__device__ __forceinline__ int seg_hint_f32(F3 w, F3 e, float* d2) {
+  const float we = fdot(w, e), ee = fdot(e, e);
+  const float t = we > 0.f ? (we < ee ? we / ee : 1.f) : 0.f;
+  const F3 r = w - e * t;
+  *d2 = fdot(r, r);
+  return (t > 0.f && t < 1.f) ? 1 : 0;
+}
+
+__device__ __forceinline__ int span_hint_f32(const Topo& T, const double* __restrict__ x4, int type, int32_t i,
+                                             int32_t j) {
+  int32_t v[4];
+  stencil_vertices(T, type, i, j, v);
+  const V3 X0 = load_x(x4, v[0]);
+  F3 Y[4];
+  Y[0] = {0.f, 0.f, 0.f};
+  for (int a = 1; a < 4; ++a) {
+    const V3 d = load_x(x4, v[a]) - X0;
+    Y[a] = {(float)d.x, (float)d.y, (float)d.z};
+  }
+  float best, d2;
+  int m, mk;
+  if (type == 0) {
+    const F3 e1 = Y[2] - Y[1], e2 = Y[3] - Y[1], w = Y[0] - Y[1];
+    const F3 n = fcross(e1, e2);
+    const float nn = fdot(n, n);
+    const float b1 = fdot(fcross(w, e2), n) / nn, b2 = fdot(fcross(e1, w), n) / nn;
+    if (b1 >= 0.f && b2 >= 0.f && b1 + b2 <= 1.f) return 2;
+    m = seg_hint_f32(w, e1, &best);
+    mk = seg_hint_f32(Y[0] - Y[2], Y[3] - Y[2], &d2);
+    if (d2 < best) { best = d2; m = mk; }
+    mk = seg_hint_f32(Y[0] - Y[3], Y[1] - Y[3], &d2);
+    if (d2 < best) m = mk;
+    return m;
+  }
+  const F3 ea = Y[1] - Y[0], eb = Y[3] - Y[2], w = Y[0] - Y[2];
+  const float A = fdot(ea, ea), B = fdot(ea, eb), C = fdot(eb, eb), D = fdot(ea, w), E = fdot(eb, w);
+  const F3 n = fcross(ea, eb);
+  const float nn = fdot(n, n);
+  if (nn > 1e-12f * A * C) {
+    const float sa = (B * E - C * D) / nn, tb = (A * E - B * D) / nn;
+    if (sa >= 0.f && sa <= 1.f && tb >= 0.f && tb <= 1.f) return 2;
+  }
+  m = seg_hint_f32(Y[0] - Y[2], eb, &best);
+  mk = seg_hint_f32(Y[1] - Y[2], eb, &d2);
+  if (d2 < best) { best = d2; m = mk; }
+  mk = seg_hint_f32(Y[2] - Y[0], ea, &d2);
+  if (d2 < best) { best = d2; m = mk; }
+  mk = seg_hint_f32(Y[3] - Y[0], ea, &d2);
+  if (d2 < best) m = mk;
+  return m;
+}
+
 // Schedule of the barrier evaluation: items keyed by (number of cage nodes, descending;
-// pair type), friction items last.  A warp's lanes then take the same branch and emit
-// the same number of blocks, and the heaviest items go first so the tail is light.  Only
-// the processing order changes: every item writes its records at offsets fixed by its
-// own index.
-__global__ void __launch_bounds__(kBlock) k_eval_order_keys(const int32_t* __restrict__ type, const int32_t* __restrict__ item_n,
-                                                            const int64_t* n_pairs, int64_t pair_cap, const int64_t* n_items,
+// pair type; hinted number of free closest-point parameters), friction items last.  A
+// warp's lanes then take the same branches, project in the same dimension and emit the
+// same number of blocks, and the heaviest items go first so the tail is light.  Only the
+// processing order changes: every item writes its records at offsets fixed by its own
+// index.  Keys fit in 8 bits: (16 - n) << 3 | type << 2 | m with 1 <= n <= 16, and 128
+// for friction items.
+__global__ void __launch_bounds__(kBlock) k_eval_order_keys(Topo T, const double* __restrict__ x4, eipc_pairs pr,
+                                                            const int32_t* __restrict__ item_n, const int64_t* n_items,
                                                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   pdl_entry();
-  const int64_t P = clamp_count(n_pairs, pair_cap);
+  const int64_t P = clamp_count(pr.count, pr.capacity);
   const int64_t n = *n_items;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
-    keys[k] = k < P ? (uint64_t)((31 - (item_n[k] & 31)) << 1 | (type[k] & 1)) : (uint64_t)(1u << 7);
+    uint64_t key = 128;
+    if (k < P) {
+      const int ty = pr.type[k] & 1;
+      const int nn = min(max(item_n[k], 1), kMaxNodes);
+      key = (uint64_t)((kMaxNodes - nn) << 3 | ty << 2 | span_hint_f32(T, x4, ty, pr.i[k], pr.j[k]));
+    }
+    keys[k] = key;
     vals[k] = (uint32_t)k;
   }
 }
@@ -1701,7 +1765,12 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
   const bool fr = lag && p.mu > 0.0;
   int64_t* cnt = sc->counters;
-  cudaMemsetAsync(cnt + kCntItems, 0, 5 * sizeof(int64_t), s);
+  int64_t* n_full = cnt + 13;
+  int64_t* n_diag = cnt + 14;
+  // counters, the BSR row counts, the evaluation queue and g_r, all reset up front
+  zero_ranges(s, {{cnt + kCntItems, 5 * sizeof(int64_t)}, {n_diag, sizeof(int64_t)},
+                  {sc->row_count, sizeof(int64_t) * (sc->ns + 1)}, {cnt + kCntEvalQueue, sizeof(int64_t)},
+                  {g_r, sizeof(double) * 3 * sc->ns}});
   const int64_t item_cap = sc->item_cap;
   sc->timers->start(kKItems, s);
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
@@ -1711,8 +1780,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                                            cnt + kCntItems, sc->status);
   int64_t* tot_h = cnt + 9;
   int64_t* tot_g = cnt + 10;
-  exclusive_scan_i64(sc->rc_h, sc->ro_h, cnt + kCntItems, item_cap, tot_h, sc->scan_partial, s);
-  exclusive_scan_i64(sc->rc_g, sc->ro_g, cnt + kCntItems, item_cap, tot_g, sc->scan_partial, s);
+  exclusive_scan2_i64(sc->rc_h, sc->ro_h, tot_h, sc->rc_g, sc->ro_g, tot_g, cnt + kCntItems, item_cap,
+                      sc->scan_partial, s);
   launch(k_rec_check, 1, 32, 0, s, tot_h, tot_g, sc->rec_cap, sc->gcap, cnt + kCntRecH, cnt + kCntRecG, sc->status);
   sc->timers->stop(kKItems, s);
 
@@ -1740,9 +1809,6 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   int32_t* dst = reinterpret_cast<int32_t*>(sc->seg_id);
   launch(k_seg_keys, blocks_for(sc->rec_cap), kBlock, 0, s, hk, static_cast<const int64_t*>(sc->seg_start),
          static_cast<const int64_t*>(cnt + kCntSegH), ukey);
-  int64_t* n_full = cnt + 13;
-  int64_t* n_diag = cnt + 14;
-  cudaMemsetAsync(n_diag, 0, sizeof(int64_t), s);
   // row field: bits_g rounded up to whole radix digits (the sort passes cover whole bytes,
   // so the column must start on a byte); 2^bits_g > ns, so the all-ones row of the
   // diagonal twins is above every row
@@ -1754,7 +1820,6 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                 sc->sort_hist, s);
   const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
-  cudaMemsetAsync(sc->row_count, 0, sizeof(int64_t) * (sc->ns + 1), s);
   launch(k_bsr_pattern, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const int64_t*>(n_full),
          static_cast<const int64_t*>(n_diag), rb, H, sc->row_count, dst, sc->status);
   int64_t* nrow = cnt + 11;
@@ -1789,15 +1854,14 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.hinv = sc->hinv; A.ginv = sc->ginv;
   {
     // (node count, type) schedule; the pair-sort buffers are free once the pairs are built
-    launch(k_eval_order_keys, blocks_for(item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(pr.type),
-           static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(pr.count), pr.capacity,
-           static_cast<const int64_t*>(cnt + kCntItems), sc->skeys, sc->svals);
+    launch(k_eval_order_keys, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, static_cast<const double*>(sc->x4), pr,
+           static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(cnt + kCntItems), sc->skeys,
+           sc->svals);
     const int wo = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, cnt + kCntItems, item_cap, 8,
                                   sc->sort_hist, s);
     A.order = wo ? sc->svals_alt : sc->svals;
     A.queue = cnt + kCntEvalQueue;
     A.tile = sc->tune.eval_tile;
-    cudaMemsetAsync(A.queue, 0, sizeof(int64_t), s);
   }
   // friction items on the scene's second stream, beside the barrier items: the two
   // kernels write disjoint records and item energies, and the barrier kernel leaves most
@@ -1835,7 +1899,6 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
          static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, static_cast<const int32_t*>(dst), H);
   sc->timers->stop(kKHReduce, s);
   sc->timers->start(kKGReduce, s);
-  cudaMemsetAsync(g_r, 0, sizeof(double) * 3 * sc->ns, s);
   launch(k_seg_pieces<3, kGRecStride>, blocks_for(sc->gcap / kSegChunk + 1, 8), kBlock, 0, s, static_cast<const double*>(sc->grec),
          static_cast<const int64_t*>(sc->gseg_start), static_cast<const int64_t*>(sc->gunit),
          static_cast<const int64_t*>(cnt + kCntUnitsG), static_cast<const int64_t*>(cnt + kCntRecG),
@@ -1856,8 +1919,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
   const bool fr = lag && p.mu > 0.0;
   int64_t* cnt = sc->counters;
-  cudaMemsetAsync(cnt + kCntItems, 0, 5 * sizeof(int64_t), s);
-  cudaMemsetAsync(cnt + kCntZero, 0, sizeof(int64_t), s);
+  zero_ranges(s, {{cnt + kCntItems, 5 * sizeof(int64_t)}, {cnt + kCntZero, sizeof(int64_t)}});
   const int64_t item_cap = sc->item_cap;
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
          fr ? lag->capacity : 0, sc->cage_idx, item_cap, sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
@@ -1899,7 +1961,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
   const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
   segment_starts(gk, cnt + kCntRecG, sc->gcap, sc->gseg_start, cnt + kCntSegG, sc->scan_partial, s);
-  cudaMemsetAsync(sc->hvp_out, 0, sizeof(double) * 3 * (sc->ns + kKinSlots), s);
+  zero_ranges(s, {{sc->hvp_out, sizeof(double) * 3 * (sc->ns + kKinSlots)}});
   launch(k_seg_sum_g, blocks_for(sc->gcap, 16), kBlock, 0, s, gk, gv, sc->grec, sc->gseg_start, cnt + kCntRecG,
          cnt + kCntSegG, sc->gcap, sc->hvp_out);
   cudaMemcpyAsync(out_r, sc->hvp_out, sizeof(double) * 3 * sc->ns, cudaMemcpyDeviceToDevice, s);

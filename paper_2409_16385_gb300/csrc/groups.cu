@@ -67,7 +67,7 @@ void group_energy_launch(eipc_scene* sc, double* E_groups, cudaStream_t s) {
   const int32_t ng = sc->n_groups;
   int64_t* counts = sc->group_count;
   int64_t* offsets = sc->group_count + (ng + 1);
-  cudaMemsetAsync(counts, 0, sizeof(int64_t) * (ng + 1), s);
+  zero_ranges(s, {{counts, sizeof(int64_t) * (ng + 1)}});
   const int64_t* n_items = sc->counters + kCntItems;
   launch(k_group_keys, blocks_for(sc->item_cap), kBlock, 0, s, static_cast<const int32_t*>(sc->item_group), n_items,
          sc->item_cap, ng, sc->gkeys, sc->gvals, counts);

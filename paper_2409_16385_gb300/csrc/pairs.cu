@@ -357,7 +357,8 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
   int64_t* n_cand = sc->counters + kCntCand;
   int64_t* n_surv = sc->counters + kCntSurv;
-  cudaMemsetAsync(sc->counters + kCntCand, 0, 2 * sizeof(int64_t), s);
+  int64_t* n_cand2 = sc->counters + kCntScreened;
+  zero_ranges(s, {{sc->counters + kCntCand, 2 * sizeof(int64_t)}, {n_cand2, sizeof(int64_t)}});
   // LBVHs over triangles and edges, then one traversal: vertex boxes grown by dhat against
   // the triangle tree (PT) and edge boxes grown by dhat against the edge tree (EE, j > i)
   // full rebuild every `rebuild_interval` calls, refit of the same hierarchy in between (the
@@ -380,8 +381,6 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
              bvh_query(sc->tri_bvh, sc->edge_bvh, sc->topo, sc->vbox_pad, sc->cand, n_cand, sc->cand_cap,
                        sc->status, s, sc->tune.query_threads, sc->tune.query_bps,
                        sc->tune.query_variant));
-  int64_t* n_cand2 = sc->counters + kCntScreened;
-  cudaMemsetAsync(n_cand2, 0, sizeof(int64_t), s);
   sc->timers->start(kKNarrow, s);
   launch(k_screen, blocks_for(sc->cand_cap, 16), kBlock, 0, s, sc->topo, static_cast<const float*>(sc->x4f),
          static_cast<const uint64_t*>(sc->cand),

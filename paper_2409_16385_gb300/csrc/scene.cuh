@@ -79,7 +79,7 @@ struct eipc_scene {
   double* grec;          // [gcap*kGRecStride] 3-vectors, 16-byte aligned rows
   int64_t* gseg_start;
   int64_t* row_count;    // [ns+1]
-  int64_t* scan_partial; // [kScanBlocks+1]
+  int64_t* scan_partial; // [2 (kScanBlocks+1)] scan partials (two arrays for exclusive_scan2_i64)
   double* sum_partial;   // [kScanBlocks]
   int bits_h, bits_g;    // key widths of the reduction sorts
   int rebuild_interval;  // contact LBVH: full rebuild every this many build_candidates calls

@@ -239,6 +239,91 @@ __global__ void __launch_bounds__(256) k_scan_apply(const int64_t* __restrict__ 
   }
 }
 
+// ---- two exclusive scans of the same length in the launches of one: partial holds
+// 2 (kScanBlocks + 1) entries, the first array's partials then the second's
+__global__ void __launch_bounds__(256) k_scan2_partial(const int64_t* __restrict__ a, const int64_t* __restrict__ b,
+                                                       const int64_t* n_dev, int64_t cap, int64_t* __restrict__ partial) {
+  pdl_entry();
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t sa = 0, sb = 0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    sa += a[i];
+    sb += b[i];
+  }
+  sa = block_sum_i64(sa);
+  sb = block_sum_i64(sb);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = sa;
+    partial[kScanBlocks + 1 + blockIdx.x] = sb;
+  }
+}
+
+// exclusive scans of both partial arrays, one warp each
+__global__ void k_scan2_partials(int64_t* partial, int64_t* total_a, int64_t* total_b) {
+  pdl_entry();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w > 1 || blockIdx.x != 0) return;
+  int64_t* p = partial + w * (kScanBlocks + 1);
+  int64_t* total = w == 0 ? total_a : total_b;
+  int64_t run = 0;
+  for (int b0 = 0; b0 < kScanBlocks; b0 += 32) {
+    const int b = b0 + lane;
+    const int64_t c = b < kScanBlocks ? p[b] : 0;
+    int64_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (b < kScanBlocks) p[b] = run + x - c;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (lane == 0) {
+    p[kScanBlocks] = run;
+    if (total) *total = run;
+  }
+}
+
+// both arrays' tiles: one block-wide scan of (a, b) pairs per tile
+__global__ void __launch_bounds__(256) k_scan2_apply(const int64_t* __restrict__ a, int64_t* __restrict__ out_a,
+                                                     const int64_t* __restrict__ b, int64_t* __restrict__ out_b,
+                                                     const int64_t* n_dev, int64_t cap,
+                                                     const int64_t* __restrict__ partial) {
+  pdl_entry();
+  __shared__ int64_t ta[256], tb[256];
+  int64_t n = *n_dev;
+  if (n > cap) n = cap;
+  int64_t beg, end;
+  scan_range(n, &beg, &end);
+  int64_t run_a = partial[blockIdx.x], run_b = partial[kScanBlocks + 1 + blockIdx.x];
+  const int t = threadIdx.x;
+  for (int64_t tile = beg; tile < end; tile += 256) {
+    const int64_t i = tile + t;
+    const int64_t va = (i < end) ? a[i] : 0, vb = (i < end) ? b[i] : 0;
+    ta[t] = va;
+    tb[t] = vb;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+      const int64_t ua = (t >= off) ? ta[t - off] : 0, ub = (t >= off) ? tb[t - off] : 0;
+      __syncthreads();
+      ta[t] += ua;
+      tb[t] += ub;
+      __syncthreads();
+    }
+    if (i < end) {
+      out_a[i] = run_a + ta[t] - va;
+      out_b[i] = run_b + tb[t] - vb;
+    }
+    const int64_t sa = ta[255], sb = tb[255];
+    __syncthreads();
+    run_a += sa;
+    run_b += sb;
+  }
+}
+
 // ---- segment starts of a sorted key array (a segment = a run of equal keys)
 
 __device__ __forceinline__ int64_t seg_head(const uint64_t* __restrict__ keys, int64_t i) {
@@ -290,7 +375,36 @@ __global__ void __launch_bounds__(256) k_seg_heads_write(const uint64_t* __restr
   }
 }
 
+struct ZeroArgs {
+  uint32_t* p[kZeroRanges];
+  int64_t n[kZeroRanges];
+  int count;
+};
+
+__global__ void __launch_bounds__(kBlock) k_zero_ranges(ZeroArgs z) {
+  pdl_entry();
+  for (int r = 0; r < z.count; ++r)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < z.n[r]; i += grid_stride()) z.p[r][i] = 0u;
+}
+
 }  // namespace
+
+void zero_ranges(cudaStream_t s, std::initializer_list<ZeroRange> ranges) {
+  ZeroArgs z{};
+  int64_t most = 0;
+  for (const ZeroRange& r : ranges) {
+    if (r.ptr == nullptr || r.bytes == 0) continue;
+    z.p[z.count] = static_cast<uint32_t*>(r.ptr);
+    z.n[z.count] = (int64_t)(r.bytes / 4);
+    if (z.n[z.count] > most) most = z.n[z.count];
+    if (++z.count == kZeroRanges) {          // more ranges than one launch takes
+      launch(k_zero_ranges, blocks_for(most, 4), kBlock, 0, s, z);
+      z = ZeroArgs{};
+      most = 0;
+    }
+  }
+  if (z.count > 0) launch(k_zero_ranges, blocks_for(most, 4), kBlock, 0, s, z);
+}
 
 int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
                    const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s) {
@@ -313,6 +427,13 @@ void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64
   launch(k_scan_partial, kScanBlocks, 256, 0, s, in, n, cap, partial);
   launch(k_scan_partials, 1, 32, 0, s, partial, total);
   launch(k_scan_apply, kScanBlocks, 256, 0, s, in, out, n, cap, partial);
+}
+
+void exclusive_scan2_i64(const int64_t* in_a, int64_t* out_a, int64_t* total_a, const int64_t* in_b, int64_t* out_b,
+                         int64_t* total_b, const int64_t* n, int64_t cap, int64_t* partial, cudaStream_t s) {
+  launch(k_scan2_partial, kScanBlocks, 256, 0, s, in_a, in_b, n, cap, partial);
+  launch(k_scan2_partials, 1, 64, 0, s, partial, total_a, total_b);
+  launch(k_scan2_apply, kScanBlocks, 256, 0, s, in_a, out_a, in_b, out_b, n, cap, static_cast<const int64_t*>(partial));
 }
 
 void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,

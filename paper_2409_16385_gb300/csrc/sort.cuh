@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
+
 namespace eipc {
 
 constexpr int kSortBlocks = 1216;  // 8 per SM; each block owns one contiguous chunk
@@ -26,10 +28,26 @@ constexpr int kScanBlocks = 304;
 void exclusive_scan_i64(const int64_t* in, int64_t* out, const int64_t* n, int64_t cap,
                         int64_t* total, int64_t* partial, cudaStream_t s);
 
+// Two exclusive scans over the same count in three launches (as two exclusive_scan_i64
+// calls).  partial needs 2 (kScanBlocks + 1) entries.
+void exclusive_scan2_i64(const int64_t* in_a, int64_t* out_a, int64_t* total_a, const int64_t* in_b, int64_t* out_b,
+                         int64_t* total_b, const int64_t* n, int64_t cap, int64_t* partial, cudaStream_t s);
+
 // Segments of a sorted key array keys[0 .. min(*n, cap)), a segment being a run of equal
 // keys: start[s] = position of segment s's first element, *n_seg = the number of segments.
 // partial needs kScanBlocks + 1 entries.
 void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,
                     int64_t* partial, cudaStream_t s);
+
+// Zeroes up to kZeroRanges byte ranges in one launch (each range 4-byte aligned, its
+// length a multiple of 4 bytes).  The library resets its counters and accumulators with
+// this kernel rather than cudaMemsetAsync, so the reset stays on the programmatic-launch
+// chain of the stream instead of breaking it.
+constexpr int kZeroRanges = 6;
+struct ZeroRange {
+  void* ptr;
+  size_t bytes;
+};
+void zero_ranges(cudaStream_t s, std::initializer_list<ZeroRange> ranges);
 
 }  // namespace eipc
