@@ -182,21 +182,17 @@ def measured_peaks():
 
 # Algorithmic work per unit:
 #   eval_barrier  FP64 flops per contact pair, counted by ncu on the bubble-grasp workload
-#                 ((2 x DFMA + DMUL + DADD) thread instructions / pairs)
+#                 ((2 x DFMA + DMUL + DADD) thread instructions / pairs), the lagged
+#                 friction of the pairs that carry it included
 #   ccd_advance   FP64 flops per advanced CCD candidate (box test, advancement distances)
 #   others        DRAM bytes per unit of their minimum input + output traffic
-# eval_barrier: 291.28e6 flops over the 115,699 pairs of bubble-grasp iterate 2 (ncu, the
-# autotuned shape 128 threads x 6 blocks/SM, 128-register variant); see profiles/
-FP64_FLOPS_PER_PAIR = 2518.0
-# eval_friction: FP64 flops per lagged friction item (ncu, the third launch of the same
-# command: 39.00e6 flops over 115,221 items)
-FP64_FLOPS_PER_FRICTION_ITEM = 338.5
+# eval_barrier: 349.71e6 flops over the 115,699 pairs of bubble-grasp iterate 2 (ncu, the
+# autotuned shape 64 threads x 16 blocks/SM, 128-register variant); see profiles/
+FP64_FLOPS_PER_PAIR = 3022.6
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code and shape
-# (eval_barrier: 122.8 MB + 237.7 MB for the same 115,699 pairs)
-NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3116.0}
-# eval_friction: 113.9 MB + 140.6 MB for the same 115,221 items
-NCU_TRAFFIC_PER_FRICTION_ITEM = 2209.0
+# (eval_barrier: 152.0 MB + 273.2 MB for the same 115,699 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3675.5}
 
 
 def query_bytes(sc, n_cand):
@@ -224,11 +220,10 @@ def roofline_figure(name, total_ms, launches, steps, per_step, sc, fp64_probe=No
         per = FP64_FLOPS_PER_CCD_CAND if name == "ccd_advance" else FP64_FLOPS_PER_PAIR
         tr = NCU_TRAFFIC_PER_UNIT.get(name)
         if name == "eval_kernels":
-            # barrier and friction evaluation, overlapped on two streams: both kernels' FP64
-            # work (and DRAM traffic) over the span from the fork to the join, per contact pair
-            fr = per_step.get("friction_items", 0.0) / max(per_step["pairs"], 1.0)
-            per += FP64_FLOPS_PER_FRICTION_ITEM * fr
-            tr = NCU_TRAFFIC_PER_UNIT["eval_barrier"] + NCU_TRAFFIC_PER_FRICTION_ITEM * fr
+            # barrier evaluation (with the friction of the pairs that carry it) and the
+            # friction items without a contact pair beside it on a second stream, from the
+            # fork to the join; the latter's few flops are not counted
+            tr = NCU_TRAFFIC_PER_UNIT["eval_barrier"]
         ach = units * per / avg_s / 1e12
         peak = FP64_PEAK_TFLOPS
         out = dict(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak,

@@ -22,7 +22,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->x4, s->dx4, s->x4f, s->vbox, s->vbox_pad, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->fric_of_pair, s->pair_of_fric, s->x4, s->dx4, s->x4f, s->vbox, s->vbox_pad, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->tri_bvh.range, s->tri_bvh.tl_root, s->tri_bvh.up_start,
@@ -34,7 +34,7 @@ void free_scene(eipc_scene* s) {
                   s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
                   s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start, s->hinv, s->ginv, s->piece, s->hunit, s->gunit,
                   s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec,
-                  s->gseg_start, s->row_count, s->scan_partial, s->sum_partial, s->status};
+                  s->gseg_start, s->scan_partial, s->sum_partial, s->status};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->timers) {
@@ -154,6 +154,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->svals, s->cand_cap)); ok(dalloc(&s->svals_alt, s->cand_cap)); ok(dalloc(&s->sd, s->cand_cap));
   ok(dalloc(&s->item_nodes, 16 * s->item_cap)); ok(dalloc(&s->item_n, s->item_cap));
   ok(dalloc(&s->item_group, s->item_cap));
+  ok(dalloc(&s->fric_of_pair, s->item_cap)); ok(dalloc(&s->pair_of_fric, s->item_cap));
   ok(dalloc(&s->rc_h, s->item_cap)); ok(dalloc(&s->ro_h, s->item_cap));
   ok(dalloc(&s->rc_g, s->item_cap)); ok(dalloc(&s->ro_g, s->item_cap)); ok(dalloc(&s->item_E, s->item_cap));
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));
@@ -169,7 +170,6 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, kGRecStride * s->gcap));
   ok(dalloc(&s->gseg_start, s->gcap));
-  ok(dalloc(&s->row_count, Ns + 1));
   ok(dalloc(&s->edge_key, E > 0 ? E : 1)); ok(dalloc(&s->edge_id, E > 0 ? E : 1));
   ok(dalloc(&s->moll_r2, E > 0 ? E : 1));
   ok(dalloc(&s->scan_partial, 2 * (kScanBlocks + 1))); ok(dalloc(&s->sum_partial, kScanBlocks));

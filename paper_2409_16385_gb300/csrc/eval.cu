@@ -63,6 +63,68 @@ __device__ __forceinline__ bool item_vertices(const Topo& T, const eipc_pairs& p
   return false;
 }
 
+// Friction merged into contact pairs with the same stencil: for pair k,
+// fric_of_pair[k] = INT32_MAX - f when lagged friction item f takes k's records (0: none);
+// pair_of_fric[f] = that pair + 1 (0: none).  The claim holds only if both agree.
+// friction item f rides on pair kp's records (both arrays as in EvalArgs)
+__device__ __forceinline__ bool friction_merged(const int32_t* __restrict__ fric_of_pair,
+                                                const int32_t* __restrict__ pair_of_fric, int64_t f) {
+  if (!pair_of_fric) return false;
+  const int32_t kp = pair_of_fric[f] - 1;
+  return kp >= 0 && fric_of_pair[kp] == INT32_MAX - (int32_t)f;
+}
+
+// first pair position k in [0, P) with (type[k], i[k]) >= (type, i) (the pair list is in
+// (type, i, j) order)
+__device__ __forceinline__ int64_t pair_lower_bound(const eipc_pairs& pr, int64_t P, int type, int32_t i) {
+  int64_t lo = 0, hi = P;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const int t = pr.type[mid];
+    if (t < type || (t == type && pr.i[mid] < i)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Friction items that ride on a contact pair: lagged item f and pair k share their records
+// when their stencils have the same four vertices in the same order (then the same cage
+// nodes in the same order, so the same record keys).  The candidates are the PT pairs of
+// vertex v0 and the EE pairs of edge (v0, v1).  When several items find the same pair (a
+// lag list with repeated stencils), the lowest f wins; the others keep their own records.
+__global__ void __launch_bounds__(kBlock) k_fric_match(Topo T, eipc_pairs pr, eipc_lag lag, int64_t item_cap,
+                                                       const uint64_t* __restrict__ ekey,
+                                                       const int32_t* __restrict__ eid,
+                                                       int32_t* __restrict__ fric_of_pair,
+                                                       int32_t* __restrict__ pair_of_fric) {
+  pdl_entry();
+  int64_t P = clamp_count(pr.count, pr.capacity);
+  if (P > item_cap) P = item_cap;
+  int64_t L = clamp_count(lag.count, lag.capacity);
+  if (P + L > item_cap) L = item_cap - P;
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < L; f += grid_stride()) {
+    const int4 q = reinterpret_cast<const int4*>(lag.v)[f];
+    int64_t found = -1;
+    for (int64_t k = pair_lower_bound(pr, P, 0, q.x); k < P && found < 0; ++k) {
+      if (pr.type[k] != 0 || pr.i[k] != q.x) break;
+      const int64_t j = pr.j[k];
+      if (T.tris[3 * j] == q.y && T.tris[3 * j + 1] == q.z && T.tris[3 * j + 2] == q.w) found = k;
+    }
+    if (found < 0) {
+      const int32_t e = edge_id_of(q.x, q.y, T.nv, ekey, eid, T.ne);
+      if (e >= 0 && T.edges[2 * (int64_t)e] == q.x) {
+        for (int64_t k = pair_lower_bound(pr, P, 1, e); k < P && found < 0; ++k) {
+          if (pr.type[k] != 1 || pr.i[k] != e) break;
+          const int64_t j = pr.j[k];
+          if (T.edges[2 * j] == q.z && T.edges[2 * j + 1] == q.w) found = k;
+        }
+      }
+    }
+    pair_of_fric[f] = (int32_t)(found + 1);
+    if (found >= 0) atomicMax(fric_of_pair + found, INT32_MAX - (int32_t)f);
+  }
+}
+
 // unique cage nodes of each item (kinematic vertices carry none), record counts
 __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, const int32_t* lag_v,
                                                        const int64_t* lag_count, int64_t lag_cap,
@@ -70,7 +132,9 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
                                                        int32_t* __restrict__ item_nodes, int32_t* __restrict__ item_n,
                                                        int32_t* __restrict__ item_group, const int32_t* __restrict__ vgroup,
                                                        int64_t* __restrict__ rc_h, int64_t* __restrict__ rc_g,
-                                                       int64_t* n_items, DevStatus* st) {
+                                                       int64_t* n_items, DevStatus* st,
+                                                       const int32_t* __restrict__ fric_of_pair,
+                                                       const int32_t* __restrict__ pair_of_fric) {
   pdl_entry();
   const int64_t P = clamp_count(pr.count, pr.capacity);
   const int64_t L = lag_v ? clamp_count(lag_count, lag_cap) : 0;
@@ -86,6 +150,13 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
     int32_t v[4];
     item_vertices(T, pr, P, lag_v, L, k, v);
+    item_group[k] = vgroup[v[0]];
+    if (k >= P && friction_merged(fric_of_pair, pair_of_fric, k - P)) {
+      item_n[k] = 0;               // evaluated in its contact pair's records
+      rc_h[k] = 0;
+      rc_g[k] = 0;
+      continue;
+    }
     int32_t nodes[kMaxNodes];
     int cnt = 0;
     for (int a = 0; a < 4; ++a) {
@@ -100,7 +171,6 @@ __global__ void __launch_bounds__(kBlock) k_item_nodes(Topo T, eipc_pairs pr, co
     }
     for (int u = 0; u < cnt; ++u) item_nodes[kMaxNodes * k + u] = nodes[u];
     item_n[k] = cnt;
-    item_group[k] = vgroup[v[0]];
     rc_h[k] = (int64_t)cnt * (cnt + 1) / 2;
     rc_g[k] = cnt;
   }
@@ -318,7 +388,66 @@ struct EvalArgs {
   // without a key.  Null: record r is written at r with its key (Hessian-vector products).
   const uint32_t* hinv;
   const uint32_t* ginv;
+  // friction merged into contact pairs (friction_merged; null: no merging); lag, mu and
+  // eps_f are the friction parameters
+  const int32_t* fric_of_pair;
+  const int32_t* pair_of_fric;
+  eipc_lag lag;
+  double mu, eps_f;
 };
+
+// Lagged friction of item f at the current positions (Sec. III-B, Eq. 8-9): energy
+// mu lambda f0(|u|), the gradient scale mu lambda f1(y)/y along u, the symmetric 3 x 3
+// F = mu lambda (f1(y)/y (I - n n^T) + (f1'(y) - f1(y)/y) u u^T / y^2), and the per-node
+// weights of gamma for the item's cage nodes.
+struct FrictionTerms {
+  double E, gs;
+  double u[3];
+  double F[3][3];
+};
+
+__device__ __forceinline__ void friction_terms(const double* __restrict__ x4, const eipc_lag& lag, int64_t f,
+                                               const int32_t v[4], double mu, double eps, FrictionTerms& R,
+                                               double gam[4]) {
+  for (int a = 0; a < 4; ++a) gam[a] = lag.gamma[4 * f + a];
+  const V3 nrm = {lag.n[3 * f], lag.n[3 * f + 1], lag.n[3 * f + 2]};
+  const V3 anc = {lag.anchor[3 * f], lag.anchor[3 * f + 1], lag.anchor[3 * f + 2]};
+  const double ml = mu * lag.lambda[f];
+  V3 vs = {0.0, 0.0, 0.0};
+  for (int a = 0; a < 4; ++a) vs = vs + load_x(x4, v[a]) * gam[a];
+  vs = vs - anc;
+  const V3 u = vs - nrm * dot(nrm, vs);
+  const double y2 = dot(u, u);
+  // f0(y), f1(y)/y and (f1'(y) - f1(y)/y) / y^2, with one division for 1/eps (or 1/y)
+  // and one for 1/y^2
+  double f0, f1y, c2;
+  if (y2 == 0.0) {
+    f0 = eps / 3.0; f1y = 2.0 / eps; c2 = 0.0;
+  } else {
+    const double y = sqrt(y2);
+    double f1p_minus;
+    if (y < eps) {
+      const double ie = 1.0 / eps, yie2 = y * ie * ie;
+      f0 = y2 * (ie - yie2 / 3.0) + eps / 3.0;    // -y^3 / (3 eps^2) + y^2 / eps + eps / 3
+      f1y = 2.0 * ie - yie2;
+      f1p_minus = -yie2;                          // (2/eps - 2y/eps^2) - (2/eps - y/eps^2)
+    } else {
+      const double iy = 1.0 / y;
+      f0 = y; f1y = iy; f1p_minus = -iy;
+    }
+    c2 = f1p_minus / y2;
+  }
+  R.E = ml * f0;
+  R.gs = ml * f1y;
+  R.u[0] = u.x; R.u[1] = u.y; R.u[2] = u.z;
+  const double nn[3] = {nrm.x, nrm.y, nrm.z};
+  for (int p = 0; p < 3; ++p)
+    for (int q = p; q < 3; ++q) {
+      const double s = ml * (f1y * ((p == q ? 1.0 : 0.0) - nn[p] * nn[q]) + c2 * R.u[p] * R.u[q]);
+      R.F[p][q] = s;
+      R.F[q][p] = s;
+    }
+}
 
 // Eigen-decomposition of the symmetric N x N K (N = 5, or 4 when the span has four
 // dimensions): an FP32 Jacobi pre-diagonalisation of K/|K|, its eigenvectors
@@ -772,6 +901,18 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
       }
     }
   }
+  // the lagged friction item on this pair's stencil, if any, goes into the same records:
+  // its blocks w_u w_v F are added to the barrier blocks (Sec. III-B, Eq. 8-9)
+  const int32_t fenc = A.fric_of_pair ? A.fric_of_pair[k] : 0;
+  const bool fr = fenc > 0;
+  FrictionTerms R;
+  double nwf[kMaxNodes];
+  if (fr) {
+    double gam[4];
+    friction_terms(A.x4, A.lag, (int64_t)(INT32_MAX - fenc), v, A.mu, A.eps_f, R, gam);
+    E += R.E;
+    node_weights1(v, A.cage_idx, A.w, nodes, n, gam, nwf);
+  }
   A.item_E[k] = E;
   // per-node scalars omega, alpha_1, alpha_2
   double nw[kMaxNodes][3];
@@ -780,12 +921,17 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   } else {
     for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
   }
-  // gradient records: kappa b' |c| omega_I r^
+  // gradient records: kappa b' |c| omega_I r^ (+ mu lambda f1/y w_I u)
   for (int u = 0; u < n; ++u) {
     const int64_t pos = og + u;
     if (pos < A.gcap) {
       const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
-      emit_grad(A, pos, (uint64_t)nodes[u], s * rh.x, s * rh.y, s * rh.z);
+      double gx = s * rh.x, gy = s * rh.y, gz = s * rh.z;
+      if (fr) {
+        const double sf = R.gs * nwf[u];
+        gx += sf * R.u[0]; gy += sf * R.u[1]; gz += sf * R.u[2];
+      }
+      emit_grad(A, pos, (uint64_t)nodes[u], gx, gy, gz);
     }
   }
   // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
@@ -825,6 +971,11 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
       }
+      if (fr) {
+        const double ww = nwf[u] * nwf[u];
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) B[p][q] += ww * R.F[p][q];
+      }
       emit_upper(A, pos, nodes[u], nodes[u], B, dst);
     }
     ++pos;
@@ -840,6 +991,11 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
       } else {
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
+      }
+      if (fr) {
+        const double ww = nwf[u] * nwf[w2];
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) B[p][q] += ww * R.F[p][q];
       }
       emit_upper(A, pos, nodes[u], nodes[w2], B, dst);
     }
@@ -897,48 +1053,16 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
   const int64_t L = nit - P;
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < L; f += grid_stride()) {
     const int64_t k = P + f;
+    if (friction_merged(A.fric_of_pair, A.pair_of_fric, f)) {
+      A.item_E[k] = 0.0;           // evaluated with its contact pair, in that pair's records
+      continue;
+    }
     const int4 q4 = reinterpret_cast<const int4*>(lag.v)[f];
     const int32_t v[4] = {q4.x, q4.y, q4.z, q4.w};
+    FrictionTerms R;
     double gam[4];
-    for (int a = 0; a < 4; ++a) gam[a] = lag.gamma[4 * f + a];
-    const V3 nrm = {lag.n[3 * f], lag.n[3 * f + 1], lag.n[3 * f + 2]};
-    const V3 anc = {lag.anchor[3 * f], lag.anchor[3 * f + 1], lag.anchor[3 * f + 2]};
-    const double ml = mu * lag.lambda[f];
-    V3 vs = {0.0, 0.0, 0.0};
-    for (int a = 0; a < 4; ++a) vs = vs + load_x(A.x4, v[a]) * gam[a];
-    vs = vs - anc;
-    const V3 u = vs - nrm * dot(nrm, vs);
-    const double y2 = dot(u, u);
-    // f0(y), f1(y)/y and (f1'(y) - f1(y)/y) / y^2, with one division for 1/eps (or 1/y)
-    // and one for 1/y^2
-    double f0, f1y, c2;
-    if (y2 == 0.0) {
-      f0 = eps / 3.0; f1y = 2.0 / eps; c2 = 0.0;
-    } else {
-      const double y = sqrt(y2);
-      double f1p_minus;
-      if (y < eps) {
-        const double ie = 1.0 / eps, yie2 = y * ie * ie;
-        f0 = y2 * (ie - yie2 / 3.0) + eps / 3.0;    // -y^3 / (3 eps^2) + y^2 / eps + eps / 3
-        f1y = 2.0 * ie - yie2;
-        f1p_minus = -yie2;                          // (2/eps - 2y/eps^2) - (2/eps - y/eps^2)
-      } else {
-        const double iy = 1.0 / y;
-        f0 = y; f1y = iy; f1p_minus = -iy;
-      }
-      c2 = f1p_minus / y2;
-    }
-    A.item_E[k] = ml * f0;
-    const double uu[3] = {u.x, u.y, u.z};
-    const double nn[3] = {nrm.x, nrm.y, nrm.z};
-    // F = ml (f1(y)/y (I - n n^T) + (f1'(y) - f1(y)/y) u u^T / y^2), symmetric
-    double F[3][3];
-    for (int p = 0; p < 3; ++p)
-      for (int q = p; q < 3; ++q) {
-        const double s = ml * (f1y * ((p == q ? 1.0 : 0.0) - nn[p] * nn[q]) + c2 * uu[p] * uu[q]);
-        F[p][q] = s;
-        F[q][p] = s;
-      }
+    friction_terms(A.x4, lag, f, v, mu, eps, R, gam);
+    A.item_E[k] = R.E;
     const int n = A.item_n[k];
     const int32_t* nodes = A.item_nodes + kMaxNodes * k;
     double nw[kMaxNodes];
@@ -948,8 +1072,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
     for (int a = 0; a < n; ++a) {
       const int64_t pos = og + a;
       if (pos < A.gcap) {
-        const double s = ml * f1y * nw[a];
-        emit_grad(A, pos, (uint64_t)nodes[a], s * u.x, s * u.y, s * u.z);
+        const double s = R.gs * nw[a];
+        emit_grad(A, pos, (uint64_t)nodes[a], s * R.u[0], s * R.u[1], s * R.u[2]);
       }
       for (int b = a; b < n; ++b, ++pos2) {
         if (pos2 >= A.rec_cap) continue;
@@ -957,7 +1081,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
         const double ww = nw[a] * nw[b];
         for (int p = 0; p < 3; ++p)
           for (int q = p; q < 3; ++q) {
-            B[p][q] = ww * F[p][q];
+            B[p][q] = ww * R.F[p][q];
             B[q][p] = B[p][q];
           }
         emit_upper(A, pos2, nodes[a], nodes[b], B);
@@ -1285,14 +1409,15 @@ __device__ __forceinline__ int span_hint_f32(const Topo& T, const double* __rest
 }
 
 // Schedule of the barrier evaluation: items keyed by (number of cage nodes, descending;
-// pair type; hinted number of free closest-point parameters), friction items last.  A
-// warp's lanes then take the same branches, project in the same dimension and emit the
-// same number of blocks, and the heaviest items go first so the tail is light.  Only the
-// processing order changes: every item writes its records at offsets fixed by its own
-// index.  Keys fit in 8 bits: (16 - n) << 3 | type << 2 | m with 1 <= n <= 16, and 128
-// for friction items.
+// a merged friction item or not; pair type; two free closest-point parameters (hinted) or
+// fewer), friction items last.  A warp's lanes then take the same branches, project in the
+// same dimension and emit the same number of blocks, and the heaviest items go first so
+// the tail is light.  Only the processing order changes: every item writes its records at
+// offsets fixed by its own index.  Keys fit in 8 bits: (16 - n) << 3 | fr << 2 | type << 1
+// | (m == 2) with 1 <= n <= 16, and 128 for friction items.
 __global__ void __launch_bounds__(kBlock) k_eval_order_keys(Topo T, const double* __restrict__ x4, eipc_pairs pr,
                                                             const int32_t* __restrict__ item_n, const int64_t* n_items,
+                                                            const int32_t* __restrict__ fric_of_pair,
                                                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   pdl_entry();
   const int64_t P = clamp_count(pr.count, pr.capacity);
@@ -1302,7 +1427,9 @@ __global__ void __launch_bounds__(kBlock) k_eval_order_keys(Topo T, const double
     if (k < P) {
       const int ty = pr.type[k] & 1;
       const int nn = min(max(item_n[k], 1), kMaxNodes);
-      key = (uint64_t)((kMaxNodes - nn) << 3 | ty << 2 | span_hint_f32(T, x4, ty, pr.i[k], pr.j[k]));
+      const int fr = (fric_of_pair && fric_of_pair[k] > 0) ? 1 : 0;
+      const int m2 = span_hint_f32(T, x4, ty, pr.i[k], pr.j[k]) == 2 ? 1 : 0;
+      key = (uint64_t)((kMaxNodes - nn) << 3 | fr << 2 | ty << 1 | m2);
     }
     keys[k] = key;
     vals[k] = (uint32_t)k;
@@ -1457,21 +1584,29 @@ __global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict_
 // beyond the capacity)
 __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
                                                         const int64_t* n_full_sort, const int64_t* n_diag, int br,
-                                                        eipc_bsr H, int64_t* __restrict__ row_count,
-                                                        int32_t* __restrict__ dst, DevStatus* st) {
+                                                        int64_t ns, eipc_bsr H, int32_t* __restrict__ dst,
+                                                        DevStatus* st) {
   pdl_entry();
   const int64_t nnzb = *n_full_sort - *n_diag;
+  const uint64_t rmask = (1ull << br) - 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *H.nnzb = nnzb;
     if (nnzb > H.capacity) {
       raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
       raise_need(st, &st->need_bsr, nnzb);
     }
+    if (nnzb == 0)
+      for (int64_t r = 0; r <= ns; ++r) H.row_ptr[r] = 0;
   }
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnzb; e += grid_stride()) {
     const uint64_t key = fkey[e];
-    const int64_t row = (int64_t)(key & ((1ull << br) - 1));
-    atomicAdd(reinterpret_cast<unsigned long long*>(row_count + row), 1ull);
+    const int64_t row = (int64_t)(key & rmask);
+    // the entries are sorted by row: entry e starts every row after the previous entry's
+    // row up to its own, and the last entry closes the rows after its own
+    const int64_t prev = e > 0 ? (int64_t)(fkey[e - 1] & rmask) : -1;
+    for (int64_t r = prev + 1; r <= row; ++r) H.row_ptr[r] = (int32_t)e;
+    if (e == nnzb - 1)
+      for (int64_t r = row + 1; r <= ns; ++r) H.row_ptr[r] = (int32_t)nnzb;
     const uint32_t v = fval[e];
     dst[2 * (int64_t)(v >> 1) + (v & 1u)] = e < H.capacity ? (int32_t)e : -1;
     if (e < H.capacity) H.col[e] = (int32_t)(key >> br);
@@ -1652,12 +1787,6 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g_pieces(const uint64_t* __r
   }
 }
 
-__global__ void k_rowptr(const int64_t* __restrict__ row_off, int64_t ns, int32_t* __restrict__ row_ptr) {
-  pdl_entry();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= ns; i += grid_stride())
-    row_ptr[i] = (int32_t)row_off[i];
-}
-
 // deterministic sum: fixed chunk per block, fixed in-block tree, partials summed in order
 __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict__ x, const int64_t* n_dev,
                                                         int64_t cap, double* __restrict__ partial) {
@@ -1738,11 +1867,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __re
   }
 }
 
-__global__ void k_set_count(int64_t* c, int64_t v) {
-  pdl_entry();
-  if (threadIdx.x == 0 && blockIdx.x == 0) *c = v;
-}
-
 }  // namespace
 
 int bits_for(uint64_t maxval) {
@@ -1764,20 +1888,30 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                  double* E, double* g_r, const eipc_bsr& H, cudaStream_t s) {
   EIPC_TIMED(sc, kKEmbed, s, embed_launch(sc, q, sc->x4, 1, 0, s));
   const bool fr = lag && p.mu > 0.0;
+  // friction items ride on the contact pairs with the same stencil (not with the EE
+  // mollifier, whose pairs are evaluated by their own kernel)
+  const bool merge = fr && !(sc->moll_factor > 0.0);
   int64_t* cnt = sc->counters;
   int64_t* n_full = cnt + 13;
   int64_t* n_diag = cnt + 14;
-  // counters, the BSR row counts, the evaluation queue and g_r, all reset up front
-  zero_ranges(s, {{cnt + kCntItems, 5 * sizeof(int64_t)}, {n_diag, sizeof(int64_t)},
-                  {sc->row_count, sizeof(int64_t) * (sc->ns + 1)}, {cnt + kCntEvalQueue, sizeof(int64_t)},
-                  {g_r, sizeof(double) * 3 * sc->ns}});
   const int64_t item_cap = sc->item_cap;
+  const int64_t pcap = pr.capacity < item_cap ? pr.capacity : item_cap;
+  // counters, the evaluation queue, g_r and the friction claims, all reset up front
+  zero_ranges(s, {{cnt + kCntItems, 5 * sizeof(int64_t)}, {n_diag, sizeof(int64_t)},
+                  {cnt + kCntEvalQueue, sizeof(int64_t)}, {g_r, sizeof(double) * 3 * sc->ns},
+                  {merge ? sc->fric_of_pair : nullptr, sizeof(int32_t) * pcap}});
+  const int32_t* fop = merge ? sc->fric_of_pair : nullptr;
+  const int32_t* pof = merge ? sc->pair_of_fric : nullptr;
   sc->timers->start(kKItems, s);
+  if (merge)
+    launch(k_fric_match, blocks_for(lag->capacity, 8), kBlock, 0, s, sc->topo, pr, *lag, item_cap,
+           static_cast<const uint64_t*>(sc->edge_key), static_cast<const int32_t*>(sc->edge_id), sc->fric_of_pair,
+           sc->pair_of_fric);
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
                                                            fr ? lag->capacity : 0, sc->cage_idx, item_cap,
                                                            sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
                                                            sc->rc_h, sc->rc_g,
-                                                           cnt + kCntItems, sc->status);
+                                                           cnt + kCntItems, sc->status, fop, pof);
   int64_t* tot_h = cnt + 9;
   int64_t* tot_g = cnt + 10;
   exclusive_scan2_i64(sc->rc_h, sc->ro_h, tot_h, sc->rc_g, sc->ro_g, tot_g, cnt + kCntItems, item_cap,
@@ -1821,11 +1955,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
   launch(k_bsr_pattern, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const int64_t*>(n_full),
-         static_cast<const int64_t*>(n_diag), rb, H, sc->row_count, dst, sc->status);
-  int64_t* nrow = cnt + 11;
-  launch(k_set_count, 1, 1, 0, s, nrow, sc->ns + 1);
-  exclusive_scan_i64(sc->row_count, sc->row_count + 0, nrow, sc->ns + 1, nullptr, sc->scan_partial, s);
-  launch(k_rowptr, blocks_for(sc->ns + 1), kBlock, 0, s, sc->row_count, sc->ns, H.row_ptr);
+         static_cast<const int64_t*>(n_diag), rb, sc->ns, H, dst, sc->status);
   sc->timers->stop(kKHReduce, s);
   // gradient segments (one per node)
   sc->timers->start(kKGReduce, s);
@@ -1852,10 +1982,13 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.moll_factor = sc->moll_factor;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
   A.hinv = sc->hinv; A.ginv = sc->ginv;
+  A.fric_of_pair = fop; A.pair_of_fric = pof;
+  A.lag = fr ? *lag : eipc_lag{};
+  A.mu = p.mu; A.eps_f = p.eps_v * p.h;
   {
     // (node count, type) schedule; the pair-sort buffers are free once the pairs are built
     launch(k_eval_order_keys, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, static_cast<const double*>(sc->x4), pr,
-           static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(cnt + kCntItems), sc->skeys,
+           static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(cnt + kCntItems), fop, sc->skeys,
            sc->svals);
     const int wo = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, cnt + kCntItems, item_cap, 8,
                                   sc->sort_hist, s);
@@ -1923,7 +2056,8 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   const int64_t item_cap = sc->item_cap;
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
          fr ? lag->capacity : 0, sc->cage_idx, item_cap, sc->item_nodes, sc->item_n, sc->item_group, sc->vgroup,
-         sc->rc_h, sc->rc_g, cnt + kCntItems, sc->status);
+         sc->rc_h, sc->rc_g, cnt + kCntItems, sc->status, static_cast<const int32_t*>(nullptr),
+         static_cast<const int32_t*>(nullptr));
   launch(k_hvp_counts, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr,
          fr ? static_cast<const int64_t*>(lag->count) : nullptr, fr ? lag->capacity : 0,
          static_cast<const int32_t*>(sc->cage_idx), static_cast<const int32_t*>(sc->item_n),
@@ -1947,6 +2081,9 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
   A.hinv = nullptr; A.ginv = nullptr;
+  A.fric_of_pair = nullptr; A.pair_of_fric = nullptr;
+  A.lag = fr ? *lag : eipc_lag{};
+  A.mu = p.mu; A.eps_f = p.eps_v * p.h;
   EIPC_TIMED(sc, kKEvalBarrier, s,
              (launch(k_hvp_barrier, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, A)));
   if (A.moll_r2)

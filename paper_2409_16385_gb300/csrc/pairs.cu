@@ -162,18 +162,6 @@ __global__ void __launch_bounds__(kBlock) k_narrow(Topo T, const double* __restr
 // Feature keys: kind << 2B | id1 << B | id2, B bits per id.
 enum { kFeatFV = 0, kFeatVE = 1, kFeatVV = 2, kFeatEE = 3 };
 
-__device__ __forceinline__ int32_t edge_id_of(int32_t a, int32_t b, int64_t nv, const uint64_t* __restrict__ ekey,
-                                              const int32_t* __restrict__ eid, int64_t ne) {
-  if (a > b) { const int32_t t = a; a = b; b = t; }
-  const uint64_t key = (uint64_t)a * (uint64_t)nv + (uint64_t)b;
-  int64_t lo = 0, hi = ne;                 // first position with ekey >= key
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (ekey[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  return (lo < ne && ekey[lo] == key) ? eid[lo] : -1;
-}
-
 __device__ __forceinline__ uint64_t feature_key(int kind, uint32_t a, uint32_t b, int B) {
   return ((uint64_t)kind << (2 * B)) | ((uint64_t)a << B) | (uint64_t)b;
 }

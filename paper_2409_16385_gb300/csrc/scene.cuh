@@ -21,6 +21,8 @@ struct eipc_scene {
   unsigned long long* group_alpha_bits;   // [n_groups] CCD bound per group (IEEE bits)
   int64_t* group_count;  // [n_groups + 1] items per group, then offsets
   int32_t* item_group;   // [item_cap] group of each evaluated item
+  int32_t* fric_of_pair; // [item_cap] friction item riding on each contact pair (see eval.cu)
+  int32_t* pair_of_fric; // [item_cap] contact pair found for each friction item
   eipc::Topo topo;
   // positions (padded, 4 doubles per vertex)
   double* x4;
@@ -78,7 +80,6 @@ struct eipc_scene {
   uint32_t* gvals_alt;
   double* grec;          // [gcap*kGRecStride] 3-vectors, 16-byte aligned rows
   int64_t* gseg_start;
-  int64_t* row_count;    // [ns+1]
   int64_t* scan_partial; // [2 (kScanBlocks+1)] scan partials (two arrays for exclusive_scan2_i64)
   double* sum_partial;   // [kScanBlocks]
   int bits_h, bits_g;    // key widths of the reduction sorts
@@ -108,6 +109,20 @@ enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kC
        kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntScreened = 15, kCntDedup = 17, kCntUnitsH = 18,
        kCntUnitsG = 19, kCntMollBad = 20, kCntCcdQueue = 21,
        kCntN = 24 };
+
+// id of the edge with end vertices {a, b} from the scene's sorted edge keys a * nv + b
+// (a < b), or -1 if there is none
+__device__ __forceinline__ int32_t edge_id_of(int32_t a, int32_t b, int64_t nv, const uint64_t* __restrict__ ekey,
+                                              const int32_t* __restrict__ eid, int64_t ne) {
+  if (a > b) { const int32_t t = a; a = b; b = t; }
+  const uint64_t key = (uint64_t)a * (uint64_t)nv + (uint64_t)b;
+  int64_t lo = 0, hi = ne;                 // first position with ekey >= key
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (ekey[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < ne && ekey[lo] == key) ? eid[lo] : -1;
+}
 
 #define EIPC_TIMED(sc, id, s, ...)        \
   do {                                    \

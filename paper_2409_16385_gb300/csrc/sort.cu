@@ -34,8 +34,15 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(const uint64_t* __restric
   if (n > cap) n = cap;
   int64_t beg, end;
   chunk_range(n, &beg, &end);
-  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x)
-    atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+  // one shared-memory atomic per distinct digit of a warp's 32 elements (the record keys of
+  // the reduction are heavily skewed: a few thousand distinct keys over millions)
+  const uint32_t lt_mask = (1u << (threadIdx.x & 31)) - 1u;
+  for (int64_t i0 = beg; i0 < end; i0 += blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    const uint32_t d = i < end ? (uint32_t)((keys[i] >> shift) & 255u) : 256u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (d < 256u && (peers & lt_mask) == 0u) atomicAdd(&h[d], (uint32_t)__popc(peers));
+  }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[d * kSortBlocks + blockIdx.x] = h[d];
 }

@@ -201,12 +201,11 @@ def test_classify_pairs_on_hand_built_configurations():
 
 
 def test_roofline_of_the_overlapped_evaluation():
-    """eval_kernels: the barrier and friction kernels' FP64 flops (and DRAM bytes) per
-    contact pair, over the span of the overlapped pair of launches."""
+    """eval_kernels: the barrier kernel's FP64 flops (friction of the pairs that carry it
+    included) and DRAM bytes per contact pair, over the span of the overlapped launches."""
     ps = dict(PER_STEP, friction_items=0.5e5)
     r = bench.roofline_figure("eval_kernels", 20.0, 10, 10, ps, _Sizes)
-    per = bench.FP64_FLOPS_PER_PAIR + 0.5 * bench.FP64_FLOPS_PER_FRICTION_ITEM
-    ach = 1e5 * per / 2e-3 / 1e12
+    ach = 1e5 * bench.FP64_FLOPS_PER_PAIR / 2e-3 / 1e12
     assert abs(r["achieved"] - ach) <= 1e-12 * ach and r["bound"] == "alu"
-    tr = (bench.NCU_TRAFFIC_PER_UNIT["eval_barrier"] + 0.5 * bench.NCU_TRAFFIC_PER_FRICTION_ITEM) * 1e5
+    tr = bench.NCU_TRAFFIC_PER_UNIT["eval_barrier"] * 1e5
     assert abs(r["traffic"] - tr) <= 1e-9 * tr

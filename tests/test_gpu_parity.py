@@ -252,8 +252,19 @@ def test_work_counts_match_the_outputs():
                 out += [n for n in ci[v] if n not in out]
         return len(out)
 
-    ns = [nodes([i, *sc.tris[j]] if ty == 0 else [*sc.edges[i], *sc.edges[j]])
-          for ty, i, j in zip(ph["type"], ph["i"], ph["j"])] + [nodes(v) for v in lh["v"]]
+    st = [tuple(int(a) for a in ([i, *sc.tris[j]] if ty == 0 else [*sc.edges[i], *sc.edges[j]]))
+          for ty, i, j in zip(ph["type"], ph["i"], ph["j"])]
+    # a friction pair with the stencil of a contact pair (the first such, in lag order)
+    # writes into that pair's records
+    free, claimed, pairs = [], set(), set(st)
+    for v in lh["v"]:
+        t = tuple(int(a) for a in v)
+        if t in pairs and t not in claimed:
+            claimed.add(t)
+        else:
+            free.append(v)
+    assert len(claimed) > 0.5 * L
+    ns = [nodes(s) for s in st] + [nodes(v) for v in free]
     assert wc["hessian_records"] == sum(n * (n + 1) // 2 for n in ns)
     assert wc["gradient_records"] == sum(ns)
     rows = np.repeat(np.arange(sc.Ns), np.diff(hh["row_ptr"]))
