@@ -224,7 +224,8 @@ eipc_status eipc_status_read(eipc_scene* scene, eipc_stream stream, int32_t* fla
  *          exact FP64 test;
  *   out[2] contact pairs it kept (before deduplication);
  *   out[3] items of the last evaluation (contact pairs + friction pairs);
- *   out[4] its Hessian block records, out[5] its gradient records (a friction pair whose
+ *   out[4] its Hessian block records, out[5] its gradient contributions, one per item and
+ *          cage node, carried in the item's diagonal block records (a friction pair whose
  *          stencil has the same four vertices as a contact pair's is evaluated with that
  *          pair, into its records, and adds none);
  *   out[6] distinct upper-triangle Hessian blocks, out[7] distinct gradient nodes;

@@ -585,6 +585,22 @@ __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32
   A.hrec[kHRecStride * dst + 8] = v[8];
 }
 
+// The diagonal record (I, I) of a presorted item: the block is symmetric, so its six
+// upper entries B00 B01 B02 B11 B12 B22 take the first six values of the row and the item's
+// gradient at node I the next three.  The segment sums of the diagonal records are then
+// the reduced Hessian's diagonal blocks and g_r together, with no gradient records, sort or
+// reduction of their own.
+__device__ __forceinline__ void emit_diag(const EvalArgs& A, int64_t pos, const double B[3][3], double g0, double g1,
+                                          double g2, int64_t pre = -1) {
+  const int64_t dst = pre >= 0 ? pre : (int64_t)A.hinv[pos];
+  double2* p = reinterpret_cast<double2*>(A.hrec + kHRecStride * dst);
+  p[0] = make_double2(B[0][0], B[0][1]);
+  p[1] = make_double2(B[0][2], B[1][1]);
+  p[2] = make_double2(B[1][2], B[2][2]);
+  p[3] = make_double2(g0, g1);
+  A.hrec[kHRecStride * dst + 8] = g2;
+}
+
 // one gradient record (presorted or keyed, as emit_upper)
 __device__ __forceinline__ void emit_grad(const EvalArgs& A, int64_t pos, uint64_t key, double y0, double y1, double y2) {
   int64_t dst = pos;
@@ -868,7 +884,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   else ee_distance<true>(Y[0], Y[1], Y[2], Y[3], &S);
   const int n = A.item_n[k];
   const int32_t* nodes = A.item_nodes + kMaxNodes * k;
-  const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+  const int64_t oh = A.ro_h[k];
   double E = 0.0;
   double Kp[5][5];
   double cn = 0.0, b1 = 0.0;
@@ -921,19 +937,6 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   } else {
     for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
   }
-  // gradient records: kappa b' |c| omega_I r^ (+ mu lambda f1/y w_I u)
-  for (int u = 0; u < n; ++u) {
-    const int64_t pos = og + u;
-    if (pos < A.gcap) {
-      const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
-      double gx = s * rh.x, gy = s * rh.y, gz = s * rh.z;
-      if (fr) {
-        const double sf = R.gs * nwf[u];
-        gx += sf * R.u[0]; gy += sf * R.u[1]; gz += sf * R.u[2];
-      }
-      emit_grad(A, pos, (uint64_t)nodes[u], gx, gy, gz);
-    }
-  }
   // Hessian records, upper triangle only: block(u,v) = A_u K+ A_v^T for u <= v, keyed by
   // (min(I_u, I_v), max(I_u, I_v)) and transposed when I_u > I_v
   const double rhv[3] = {rh.x, rh.y, rh.z};
@@ -976,7 +979,14 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] += ww * R.F[p][q];
       }
-      emit_upper(A, pos, nodes[u], nodes[u], B, dst);
+      // the gradient at node u: kappa b' |c| omega_u r^ (+ mu lambda f1/y w_u u)
+      const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
+      double gx = s * rh.x, gy = s * rh.y, gz = s * rh.z;
+      if (fr) {
+        const double sf = R.gs * nwf[u];
+        gx += sf * R.u[0]; gy += sf * R.u[1]; gz += sf * R.u[2];
+      }
+      emit_diag(A, pos, B, gx, gy, gz, dst);
     }
     ++pos;
     for (int w2 = u + 1; w2 < n; ++w2, ++pos) {
@@ -1067,14 +1077,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
     const int32_t* nodes = A.item_nodes + kMaxNodes * k;
     double nw[kMaxNodes];
     node_weights1(v, A.cage_idx, A.w, nodes, n, gam, nw);
-    const int64_t oh = A.ro_h[k], og = A.ro_g[k];
+    const int64_t oh = A.ro_h[k];
     int64_t pos2 = oh;
     for (int a = 0; a < n; ++a) {
-      const int64_t pos = og + a;
-      if (pos < A.gcap) {
-        const double s = R.gs * nw[a];
-        emit_grad(A, pos, (uint64_t)nodes[a], s * R.u[0], s * R.u[1], s * R.u[2]);
-      }
       for (int b = a; b < n; ++b, ++pos2) {
         if (pos2 >= A.rec_cap) continue;
         double B[3][3];
@@ -1084,7 +1089,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_eval_friction(EvalArgs A, eipc
             B[p][q] = ww * R.F[p][q];
             B[q][p] = B[p][q];
           }
-        emit_upper(A, pos2, nodes[a], nodes[b], B);
+        if (b == a) {
+          const double s = R.gs * nw[a];
+          emit_diag(A, pos2, B, s * R.u[0], s * R.u[1], s * R.u[2]);
+        } else {
+          emit_upper(A, pos2, nodes[a], nodes[b], B);
+        }
       }
     }
   }
@@ -1329,12 +1339,6 @@ __global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
     }
     if (A.project) psd_project_mem(H12, 12);
     A.item_E[k] = Em;
-    for (int u = 0; u < n; ++u) {
-      double y[3] = {0.0, 0.0, 0.0};
-      for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 3; ++c) y[c] += W[a][u] * g12[3 * a + c];
-      emit_g(A, og + u, (uint64_t)nodes[u], V3{y[0], y[1], y[2]});
-    }
     int64_t pos = A.ro_h[k];
     for (int u = 0; u < n; ++u)
       for (int w2 = u; w2 < n; ++w2, ++pos) {
@@ -1347,7 +1351,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_mollified(EvalArgs A) {
             for (int p = 0; p < 3; ++p)
               for (int q = 0; q < 3; ++q) Bk[p][q] += ww * H12[12 * (3 * a + p) + 3 * b + q];
           }
-        emit_upper(A, pos, nodes[u], nodes[w2], Bk);
+        if (w2 == u) {
+          // the diagonal record carries the gradient at node u
+          double y[3] = {0.0, 0.0, 0.0};
+          for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 3; ++c) y[c] += W[a][u] * g12[3 * a + c];
+          emit_diag(A, pos, Bk, y[0], y[1], y[2]);
+        } else {
+          emit_upper(A, pos, nodes[u], nodes[w2], Bk);
+        }
       }
   }
 }
@@ -1544,7 +1556,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
     const int n = item_n[k];
     const int32_t* nodes = item_nodes + kMaxNodes * k;
     const int64_t og = ro_g[k], oh = ro_h[k];
-    if (lane < n && og + lane < gcap) {
+    if (gkeys && lane < n && og + lane < gcap) {
       gkeys[og + lane] = (uint64_t)nodes[lane];
       gvals[og + lane] = (uint32_t)(og + lane);
     }
@@ -1585,12 +1597,13 @@ __global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict_
 __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restrict__ fkey, const uint32_t* __restrict__ fval,
                                                         const int64_t* n_full_sort, const int64_t* n_diag, int br,
                                                         int64_t ns, eipc_bsr H, int32_t* __restrict__ dst,
-                                                        DevStatus* st) {
+                                                        DevStatus* st, int64_t* __restrict__ n_gnodes) {
   pdl_entry();
   const int64_t nnzb = *n_full_sort - *n_diag;
   const uint64_t rmask = (1ull << br) - 1;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *H.nnzb = nnzb;
+    *n_gnodes = *n_diag;           // nodes with a gradient: one diagonal block each
     if (nnzb > H.capacity) {
       raise_flag(st, EIPC_FLAG_BSR_OVERFLOW);
       raise_need(st, &st->need_bsr, nnzb);
@@ -1732,11 +1745,15 @@ __device__ __forceinline__ double warp_reduce_scatter(double (&a)[L], int lane) 
 
 // Hessian pass 2, one warp per segment: lane l adds unit sums l, l+32, ... of its segment
 // in order, then warp_reduce_scatter; the block goes into the BSR values at dst[2s] and,
-// transposed, at dst[2s+1]
+// transposed, at dst[2s+1].  A diagonal segment (I, I) holds the six upper entries of its
+// symmetric block and then the gradient at node I (emit_diag): the block is written whole
+// and the gradient goes to g_r[I].
 __global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __restrict__ piece,
                                                              const int64_t* __restrict__ unit, const int64_t* n_units,
                                                              const int64_t* n_seg, int64_t cap,
-                                                             const int32_t* __restrict__ dst, eipc_bsr H) {
+                                                             const int32_t* __restrict__ dst, eipc_bsr H,
+                                                             const uint64_t* __restrict__ ukey, int64_t ns,
+                                                             double* __restrict__ g_r) {
   pdl_entry();
   const int64_t S0 = *n_seg;
   const int64_t S = (2 * S0 <= cap) ? S0 : cap / 2;      // the segments k_full_entries kept
@@ -1757,8 +1774,22 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __res
     const int c = lane >> 1;
     if ((lane & 1) == 0 && c < 9) {
       const int32_t du = dst[2 * s], dl = dst[2 * s + 1];
-      if (du >= 0 && du < nnzb) H.val[9 * (int64_t)du + c] = v;
-      if (dl >= 0 && dl < nnzb) H.val[9 * (int64_t)dl + 3 * (c % 3) + c / 3] = v;
+      const uint64_t key = ukey[s];
+      const uint64_t I = key / (uint64_t)ns;
+      if (I != key % (uint64_t)ns) {
+        if (du >= 0 && du < nnzb) H.val[9 * (int64_t)du + c] = v;
+        if (dl >= 0 && dl < nnzb) H.val[9 * (int64_t)dl + 3 * (c % 3) + c / 3] = v;
+      } else if (c < 6) {
+        // upper entry c of the symmetric block: (0,0) (0,1) (0,2) (1,1) (1,2) (2,2)
+        const int p = c < 3 ? 0 : (c < 5 ? 1 : 2);
+        const int q = c < 3 ? c : (c < 5 ? c - 2 : 2);
+        if (du >= 0 && du < nnzb) {
+          H.val[9 * (int64_t)du + 3 * p + q] = v;
+          H.val[9 * (int64_t)du + 3 * q + p] = v;
+        }
+      } else {
+        g_r[3 * I + (c - 6)] = v;
+      }
     }
   }
 }
@@ -1927,7 +1958,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   launch(k_rec_keys, blocks_for(32 * item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(sc->item_nodes),
          static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(sc->ro_h),
          static_cast<const int64_t*>(sc->ro_g), static_cast<const int64_t*>(cnt + kCntItems), sc->rec_cap, sc->gcap,
-         sc->ns, sc->hkeys, sc->hvals, sc->gkeys, sc->gvals);
+         sc->ns, sc->hkeys, sc->hvals, static_cast<uint64_t*>(nullptr), static_cast<uint32_t*>(nullptr));
   const int wh = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, cnt + kCntRecH, sc->rec_cap,
                                 sc->bits_h, sc->sort_hist, s);
   const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
@@ -1955,21 +1986,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   const uint64_t* fk = wf ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* fv = wf ? sc->hvals_alt : sc->hvals;
   launch(k_bsr_pattern, blocks_for(sc->rec_cap), kBlock, 0, s, fk, fv, static_cast<const int64_t*>(n_full),
-         static_cast<const int64_t*>(n_diag), rb, sc->ns, H, dst, sc->status);
+         static_cast<const int64_t*>(n_diag), rb, sc->ns, H, dst, sc->status, cnt + kCntSegG);
   sc->timers->stop(kKHReduce, s);
-  // gradient segments (one per node)
-  sc->timers->start(kKGReduce, s);
-  const int wg = radix_sort_u64(sc->gkeys, sc->gvals, sc->gkeys_alt, sc->gvals_alt, cnt + kCntRecG, sc->gcap,
-                                sc->bits_g, sc->sort_hist, s);
-  const uint64_t* gk = wg ? sc->gkeys_alt : sc->gkeys;
-  const uint32_t* gv = wg ? sc->gvals_alt : sc->gvals;
-  segment_starts(gk, cnt + kCntRecG, sc->gcap, sc->gseg_start, cnt + kCntSegG, sc->scan_partial, s);
-  launch(k_inverse, blocks_for(sc->gcap), kBlock, 0, s, gv, static_cast<const int64_t*>(cnt + kCntRecG), sc->gcap,
-         sc->ginv);
-  launch(k_seg_units, blocks_for(sc->gcap), kBlock, 0, s, static_cast<const int64_t*>(sc->gseg_start),
-         static_cast<const int64_t*>(cnt + kCntRecG), static_cast<const int64_t*>(cnt + kCntSegG), sc->gcap, sc->gunit);
-  exclusive_scan_i64(sc->gunit, sc->gunit, cnt + kCntSegG, sc->gcap, cnt + kCntUnitsG, sc->scan_partial, s);
-  sc->timers->stop(kKGReduce, s);
 
   EvalArgs A;
   A.T = sc->topo; A.pr = pr; A.cage_idx = sc->cage_idx; A.w = sc->w; A.x4 = sc->x4; A.ns = sc->ns;
@@ -1981,7 +1999,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.moll_r2 = sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr;
   A.moll_factor = sc->moll_factor;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
-  A.hinv = sc->hinv; A.ginv = sc->ginv;
+  A.hinv = sc->hinv; A.ginv = nullptr;       // gradients ride in the diagonal records
   A.fric_of_pair = fop; A.pair_of_fric = pof;
   A.lag = fr ? *lag : eipc_lag{};
   A.mu = p.mu; A.eps_f = p.eps_v * p.h;
@@ -2027,19 +2045,12 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
          static_cast<const int64_t*>(sc->seg_start), static_cast<const int64_t*>(sc->hunit),
          static_cast<const int64_t*>(cnt + kCntUnitsH), static_cast<const int64_t*>(cnt + kCntRecH),
          static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->piece);
+  // blocks into the BSR values; the diagonal segments' gradients into g_r
   launch(k_seg_sum_h_pieces, blocks_for(32 * sc->rec_cap, 8), kBlock, 0, s, static_cast<const double*>(sc->piece),
          static_cast<const int64_t*>(sc->hunit), static_cast<const int64_t*>(cnt + kCntUnitsH),
-         static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, static_cast<const int32_t*>(dst), H);
+         static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, static_cast<const int32_t*>(dst), H,
+         static_cast<const uint64_t*>(ukey), sc->ns, g_r);
   sc->timers->stop(kKHReduce, s);
-  sc->timers->start(kKGReduce, s);
-  launch(k_seg_pieces<3, kGRecStride>, blocks_for(sc->gcap / kSegChunk + 1, 8), kBlock, 0, s, static_cast<const double*>(sc->grec),
-         static_cast<const int64_t*>(sc->gseg_start), static_cast<const int64_t*>(sc->gunit),
-         static_cast<const int64_t*>(cnt + kCntUnitsG), static_cast<const int64_t*>(cnt + kCntRecG),
-         static_cast<const int64_t*>(cnt + kCntSegG), sc->gcap, sc->piece);
-  launch(k_seg_sum_g_pieces, blocks_for(32 * sc->gcap, 8), kBlock, 0, s, gk, static_cast<const double*>(sc->piece),
-         static_cast<const int64_t*>(sc->gseg_start), static_cast<const int64_t*>(sc->gunit),
-         static_cast<const int64_t*>(cnt + kCntUnitsG), static_cast<const int64_t*>(cnt + kCntSegG), g_r);
-  sc->timers->stop(kKGReduce, s);
   // energy
   sc->timers->start(kKEnergy, s);
   launch(k_sum_partial, kScanBlocks, kBlock, 0, s, sc->item_E, cnt + kCntItems, item_cap, sc->sum_partial);
