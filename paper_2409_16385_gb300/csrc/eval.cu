@@ -1575,21 +1575,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
   }
 }
 
-// inverse of the sort permutation: record perm[p] sits at sorted position p
-__global__ void __launch_bounds__(kBlock) k_inverse(const uint32_t* __restrict__ perm, const int64_t* n_dev, int64_t cap,
-                                                    uint32_t* __restrict__ inv) {
-  pdl_entry();
-  const int64_t n = clamp_count(n_dev, cap);
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += grid_stride()) inv[perm[p]] = (uint32_t)p;
-}
 
-// key of each segment
-__global__ void __launch_bounds__(kBlock) k_seg_keys(const uint64_t* __restrict__ keys, const int64_t* __restrict__ start,
-                                                     const int64_t* n_seg, uint64_t* __restrict__ ukey) {
-  pdl_entry();
-  const int64_t S = *n_seg;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) ukey[s] = keys[start[s]];
-}
 
 // sorted full entries -> BSR columns, row counts, and for each upper segment s the BSR
 // entry of its block (dst[2s]) and of its transpose (dst[2s+1]; -1 on the diagonal or
@@ -1635,15 +1621,19 @@ __global__ void __launch_bounds__(kBlock) k_bsr_pattern(const uint64_t* __restri
 // many threads.
 constexpr int kSegChunk = 32;
 
-// units per segment: unit[s] = ceil(len_s / kSegChunk) (exclusive-scanned afterwards)
+// units per segment: unit[s] = ceil(len_s / kSegChunk) (exclusive-scanned afterwards),
+// and, when keys is given, the segment's key ukey[s]
 __global__ void __launch_bounds__(kBlock) k_seg_units(const int64_t* __restrict__ start, const int64_t* n_rec,
-                                                      const int64_t* n_seg, int64_t cap, int64_t* __restrict__ unit) {
+                                                      const int64_t* n_seg, int64_t cap, int64_t* __restrict__ unit,
+                                                      const uint64_t* __restrict__ keys, uint64_t* __restrict__ ukey) {
   pdl_entry();
   const int64_t R = clamp_count(n_rec, cap);
   const int64_t S = *n_seg;
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
-    const int64_t len = ((s + 1 < S) ? start[s + 1] : R) - start[s];
+    const int64_t b = start[s];
+    const int64_t len = ((s + 1 < S) ? start[s + 1] : R) - b;
     unit[s] = (len + kSegChunk - 1) / kSegChunk;
+    if (keys) ukey[s] = keys[b];
   }
 }
 
@@ -1963,17 +1953,15 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
                                 sc->bits_h, sc->sort_hist, s);
   const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
   const uint32_t* hv = wh ? sc->hvals_alt : sc->hvals;
-  segment_starts(hk, cnt + kCntRecH, sc->rec_cap, sc->seg_start, cnt + kCntSegH, sc->scan_partial, s);
-  launch(k_inverse, blocks_for(sc->rec_cap), kBlock, 0, s, hv, static_cast<const int64_t*>(cnt + kCntRecH), sc->rec_cap,
-         sc->hinv);
-  launch(k_seg_units, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const int64_t*>(sc->seg_start),
-         static_cast<const int64_t*>(cnt + kCntRecH), static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->hunit);
-  exclusive_scan_i64(sc->hunit, sc->hunit, cnt + kCntSegH, sc->rec_cap, cnt + kCntUnitsH, sc->scan_partial, s);
+  // segment starts, and the inverse permutation (each record's sorted position)
+  segment_starts(hk, cnt + kCntRecH, sc->rec_cap, sc->seg_start, cnt + kCntSegH, sc->scan_partial, s, hv, sc->hinv);
   // seg_flag and seg_id hold the segment keys and the segments' BSR entries
   uint64_t* ukey = reinterpret_cast<uint64_t*>(sc->seg_flag);
   int32_t* dst = reinterpret_cast<int32_t*>(sc->seg_id);
-  launch(k_seg_keys, blocks_for(sc->rec_cap), kBlock, 0, s, hk, static_cast<const int64_t*>(sc->seg_start),
-         static_cast<const int64_t*>(cnt + kCntSegH), ukey);
+  launch(k_seg_units, blocks_for(sc->rec_cap), kBlock, 0, s, static_cast<const int64_t*>(sc->seg_start),
+         static_cast<const int64_t*>(cnt + kCntRecH), static_cast<const int64_t*>(cnt + kCntSegH), sc->rec_cap, sc->hunit,
+         hk, ukey);
+  exclusive_scan_i64(sc->hunit, sc->hunit, cnt + kCntSegH, sc->rec_cap, cnt + kCntUnitsH, sc->scan_partial, s);
   // row field: bits_g rounded up to whole radix digits (the sort passes cover whole bytes,
   // so the column must start on a byte); 2^bits_g > ns, so the all-ones row of the
   // diagonal twins is above every row

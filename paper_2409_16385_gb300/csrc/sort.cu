@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(256) k_seg_heads_partial(const uint64_t* __res
 // exclusive partial
 __global__ void __launch_bounds__(256) k_seg_heads_write(const uint64_t* __restrict__ keys, const int64_t* n_dev,
                                                          int64_t cap, const int64_t* __restrict__ partial,
-                                                         int64_t* __restrict__ start) {
+                                                         int64_t* __restrict__ start, const uint32_t* __restrict__ perm,
+                                                         uint32_t* __restrict__ inv) {
   pdl_entry();
   __shared__ int32_t wsum[8];
   int64_t n = *n_dev;
@@ -366,6 +367,7 @@ __global__ void __launch_bounds__(256) k_seg_heads_write(const uint64_t* __restr
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   for (int64_t tile = beg; tile < end; tile += 256) {
     const int64_t i = tile + t;
+    if (inv && i < end) inv[perm[i]] = (uint32_t)i;
     const bool h = i < end && seg_head(keys, i);
     const unsigned m = __ballot_sync(0xffffffffu, h);
     if (lane == 0) wsum[warp] = __popc(m);
@@ -444,10 +446,10 @@ void exclusive_scan2_i64(const int64_t* in_a, int64_t* out_a, int64_t* total_a, 
 }
 
 void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,
-                    int64_t* partial, cudaStream_t s) {
+                    int64_t* partial, cudaStream_t s, const uint32_t* perm, uint32_t* inv) {
   launch(k_seg_heads_partial, kScanBlocks, 256, 0, s, keys, n, cap, partial);
   launch(k_scan_partials, 1, 32, 0, s, partial, n_seg);
-  launch(k_seg_heads_write, kScanBlocks, 256, 0, s, keys, n, cap, static_cast<const int64_t*>(partial), start);
+  launch(k_seg_heads_write, kScanBlocks, 256, 0, s, keys, n, cap, static_cast<const int64_t*>(partial), start, perm, inv);
 }
 
 }  // namespace eipc

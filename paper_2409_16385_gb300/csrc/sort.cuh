@@ -35,9 +35,10 @@ void exclusive_scan2_i64(const int64_t* in_a, int64_t* out_a, int64_t* total_a, 
 
 // Segments of a sorted key array keys[0 .. min(*n, cap)), a segment being a run of equal
 // keys: start[s] = position of segment s's first element, *n_seg = the number of segments.
-// partial needs kScanBlocks + 1 entries.
+// With perm (the sort's values: the original index of each sorted element), also the
+// inverse permutation inv[perm[i]] = i.  partial needs kScanBlocks + 1 entries.
 void segment_starts(const uint64_t* keys, const int64_t* n, int64_t cap, int64_t* start, int64_t* n_seg,
-                    int64_t* partial, cudaStream_t s);
+                    int64_t* partial, cudaStream_t s, const uint32_t* perm = nullptr, uint32_t* inv = nullptr);
 
 // Zeroes up to kZeroRanges byte ranges in one launch (each range 4-byte aligned, its
 // length a multiple of 4 bytes).  The library resets its counters and accumulators with
