@@ -22,7 +22,7 @@ cudaError_t dalloc(T** p, int64_t n) {
 
 void free_scene(eipc_scene* s) {
   if (!s) return;
-  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->fric_of_pair, s->pair_of_fric, s->x4, s->dx4, s->x4f, s->vbox, s->vbox_pad, s->cand2,
+  void* ptrs[] = {s->tris, s->edges, s->cage_idx, s->w, s->x_kin4, s->hvp_out, s->edge_key, s->edge_id, s->moll_r2, s->vkin, s->ekin, s->fkin, s->vgroup, s->group_alpha_bits, s->group_count, s->item_group, s->fric_of_pair, s->pair_of_fric, s->lag_key, s->x4, s->dx4, s->x4f, s->vbox, s->vbox_pad, s->cand2,
                   s->tri_bvh.n_dev, s->tri_bvh.nodes, s->tri_bvh.parent, s->tri_bvh.leaf_prim, s->tri_bvh.leaf_info,
                   s->tri_bvh.leaf_box, s->tri_bvh.refit_flag, s->tri_bvh.keys, s->tri_bvh.vals,
                   s->tri_bvh.keys_alt, s->tri_bvh.vals_alt, s->tri_bvh.range, s->tri_bvh.tl_root, s->tri_bvh.up_start,
@@ -155,6 +155,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->item_nodes, 16 * s->item_cap)); ok(dalloc(&s->item_n, s->item_cap));
   ok(dalloc(&s->item_group, s->item_cap));
   ok(dalloc(&s->fric_of_pair, s->item_cap)); ok(dalloc(&s->pair_of_fric, s->item_cap));
+  ok(dalloc(&s->lag_key, s->item_cap));
   ok(dalloc(&s->rc_h, s->item_cap)); ok(dalloc(&s->ro_h, s->item_cap));
   ok(dalloc(&s->rc_g, s->item_cap)); ok(dalloc(&s->ro_g, s->item_cap)); ok(dalloc(&s->item_E, s->item_cap));
   ok(dalloc(&s->hkeys, s->rec_cap)); ok(dalloc(&s->hkeys_alt, s->rec_cap));

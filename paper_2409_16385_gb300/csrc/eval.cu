@@ -74,6 +74,11 @@ __device__ __forceinline__ bool friction_merged(const int32_t* __restrict__ fric
   return kp >= 0 && fric_of_pair[kp] == INT32_MAX - (int32_t)f;
 }
 
+// (type, i, j) of a pair as one ordered 64-bit key (i, j < 2^31)
+__device__ __forceinline__ uint64_t lag_pair_key(int type, int32_t i, int32_t j) {
+  return ((uint64_t)(type & 1) << 62) | ((uint64_t)(uint32_t)i << 31) | (uint64_t)(uint32_t)j;
+}
+
 // first pair position k in [0, P) with (type[k], i[k]) >= (type, i) (the pair list is in
 // (type, i, j) order)
 __device__ __forceinline__ int64_t pair_lower_bound(const eipc_pairs& pr, int64_t P, int type, int32_t i) {
@@ -95,6 +100,7 @@ __device__ __forceinline__ int64_t pair_lower_bound(const eipc_pairs& pr, int64_
 __global__ void __launch_bounds__(kBlock) k_fric_match(Topo T, eipc_pairs pr, eipc_lag lag, int64_t item_cap,
                                                        const uint64_t* __restrict__ ekey,
                                                        const int32_t* __restrict__ eid,
+                                                       const uint64_t* __restrict__ lag_key,
                                                        int32_t* __restrict__ fric_of_pair,
                                                        int32_t* __restrict__ pair_of_fric) {
   pdl_entry();
@@ -105,6 +111,25 @@ __global__ void __launch_bounds__(kBlock) k_fric_match(Topo T, eipc_pairs pr, ei
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < L; f += grid_stride()) {
     const int4 q = reinterpret_cast<const int4*>(lag.v)[f];
     int64_t found = -1;
+    if (lag_key) {
+      // the item's own pair key (type, i, j), recorded when the scene built this lag state:
+      // one search in the pair list's order, then the same check of the four vertices
+      const uint64_t key = lag_key[f];
+      int64_t lo = 0, hi = P;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (lag_pair_key(pr.type[mid], pr.i[mid], pr.j[mid]) < key) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < P && lag_pair_key(pr.type[lo], pr.i[lo], pr.j[lo]) == key) {
+        int32_t v[4];
+        stencil_vertices(T, pr.type[lo], pr.i[lo], pr.j[lo], v);
+        if (v[0] == q.x && v[1] == q.y && v[2] == q.z && v[3] == q.w) found = lo;
+      }
+      pair_of_fric[f] = (int32_t)(found + 1);
+      if (found >= 0) atomicMax(fric_of_pair + found, INT32_MAX - (int32_t)f);
+      continue;
+    }
     for (int64_t k = pair_lower_bound(pr, P, 0, q.x); k < P && found < 0; ++k) {
       if (pr.type[k] != 0 || pr.i[k] != q.x) break;
       const int64_t j = pr.j[k];
@@ -1842,7 +1867,8 @@ __global__ void k_sum_final(const double* __restrict__ partial, int nb, double* 
 // ------------------------------------------------------------------ friction lag
 __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __restrict__ x4, eipc_pairs pr,
                                                       double dhat, double kappa, eipc_lag out, DevStatus* st,
-                                                      const double* __restrict__ moll_r2, double moll_factor) {
+                                                      const double* __restrict__ moll_r2, double moll_factor,
+                                                      uint64_t* __restrict__ key_out, int64_t key_cap) {
   pdl_entry();
   const int64_t P = clamp_count(pr.count, pr.capacity);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1873,6 +1899,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_lag(Topo T, const double* __re
     V3 anc = {0.0, 0.0, 0.0};
     for (int a = 0; a < 4; ++a) anc = anc + X[a] * S.c[a];
     reinterpret_cast<int4*>(out.v)[k] = make_int4(v[0], v[1], v[2], v[3]);
+    if (k < key_cap) key_out[k] = lag_pair_key(type, pr.i[k], pr.j[k]);
     for (int a = 0; a < 4; ++a) out.gamma[4 * k + a] = S.c[a];
     out.n[3 * k] = rrel.x / rn; out.n[3 * k + 1] = rrel.y / rn; out.n[3 * k + 2] = rrel.z / rn;
     out.anchor[3 * k] = anc.x; out.anchor[3 * k + 1] = anc.y; out.anchor[3 * k + 2] = anc.z;
@@ -1902,7 +1929,8 @@ void lag_launch(eipc_scene* sc, const double* q_n, const eipc_pairs& pr, const e
   EIPC_TIMED(sc, kKLag, s,
              (launch(k_lag, blocks_for(pr.capacity, 8, kEvalThreads), kEvalThreads, 0, s, sc->topo, sc->x4, pr, p.dhat,
                      p.kappa, out, sc->status, static_cast<const double*>(sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr),
-                     sc->moll_factor)));
+                     sc->moll_factor, sc->lag_key, sc->item_cap)));
+  sc->lag_src = out.v;   // the lag state whose pair keys lag_key now holds
 }
 
 void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eipc_lag* lag, const eipc_params& p,
@@ -1926,7 +1954,8 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   sc->timers->start(kKItems, s);
   if (merge)
     launch(k_fric_match, blocks_for(lag->capacity, 8), kBlock, 0, s, sc->topo, pr, *lag, item_cap,
-           static_cast<const uint64_t*>(sc->edge_key), static_cast<const int32_t*>(sc->edge_id), sc->fric_of_pair,
+           static_cast<const uint64_t*>(sc->edge_key), static_cast<const int32_t*>(sc->edge_id),
+           static_cast<const uint64_t*>(lag->v == sc->lag_src ? sc->lag_key : nullptr), sc->fric_of_pair,
            sc->pair_of_fric);
   launch(k_item_nodes, blocks_for(item_cap, 8), kBlock, 0, s, sc->topo, pr, fr ? lag->v : nullptr, fr ? lag->count : nullptr,
                                                            fr ? lag->capacity : 0, sc->cage_idx, item_cap,

@@ -23,6 +23,8 @@ struct eipc_scene {
   int32_t* item_group;   // [item_cap] group of each evaluated item
   int32_t* fric_of_pair; // [item_cap] friction item riding on each contact pair (see eval.cu)
   int32_t* pair_of_fric; // [item_cap] contact pair found for each friction item
+  uint64_t* lag_key;     // [item_cap] (type, i, j) of each item of the last lag state built here
+  const int32_t* lag_src; // that lag state's v array (identifies it at evaluation)
   eipc::Topo topo;
   // positions (padded, 4 doubles per vertex)
   double* x4;

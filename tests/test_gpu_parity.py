@@ -202,6 +202,36 @@ def test_launch_modes_agree_bitwise():
     assert outs[0] == outs[1] == outs[2] == outs[3]
 
 
+def test_friction_match_by_key_and_by_stencil_agree():
+    """A lag state built by the scene is matched to the contact pairs by its recorded pair
+    keys; a copy of it in other buffers (no keys) by the stencils' vertices.  The key also
+    tells a PT pair from an EE pair with the same four vertices, so it merges at least as
+    many items.  Either way E, g_r and H_r are the same sums up to rounding, on the same
+    pattern, and each way repeats bitwise."""
+    import dataclasses
+    sc = _scene(2, True)
+    cs = _cs(sc)
+    t = 9
+    q, qn = _t(sc.iterate(t)), _t(sc.iterate(sc.lag_of(t)))
+    lag = cs.friction_lag(qn, cs.build_candidates(qn, out=cs.new_pairs()))
+    pr = cs.build_candidates(q)
+    copy = dataclasses.replace(lag, **{f.name: getattr(lag, f.name).clone() for f in dataclasses.fields(lag)})
+    outs = []
+    for lg in (lag, copy, lag, copy):
+        E, g, H = cs.eval_contact(q, pr, lg)
+        h = H.host()
+        outs.append((E.cpu().numpy(), g.cpu().numpy(), h["val"], h["col"], h["row_ptr"],
+                     cs.work_counts()["hessian_records"]))
+        assert cs.status()["flags"] == 0
+    for a, b in ((outs[0], outs[2]), (outs[1], outs[3])):
+        assert all(np.array_equal(x, y) for x, y in zip(a[:5], b[:5])) and a[5] == b[5]
+    key, vert = outs[0], outs[1]
+    assert key[5] <= vert[5]
+    assert np.array_equal(key[3], vert[3]) and np.array_equal(key[4], vert[4])
+    for x, y in zip(key[:3], vert[:3]):
+        assert np.max(np.abs(x - y)) <= 1e-12 * max(np.max(np.abs(y)), 1e-300)
+
+
 def test_refitted_and_rebuilt_hierarchies_agree_bitwise():
     """The contact set and the reduced outputs do not depend on whether the LBVH was
     rebuilt for these positions or refitted from another configuration's hierarchy."""
