@@ -288,8 +288,7 @@ eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_strea
  * grid as a multiple of the 152 SMs (1..64; ignored by the refit); variant: eval 2 = no
  * register cap, 3 = at most 170 registers (3 blocks of 128 per SM), 4 = at most 128
  * registers (4 blocks of 128 per SM); traversal 2 = no register cap, 3 = at most 40
- * registers (6 blocks of 256 per SM), 4 = warp-cooperative (a warp walks the union of 32
- * queries' paths with one stack); refit 0 = arrival counters behind full device
+ * registers (6 blocks of 256 per SM); refit 0 = arrival counters behind full device
  * fences, 1 = release-acquire arrival counters, 2 = treelets of up to 32 leaves refitted per
  * warp in shared memory below release-acquire counters (default).  Results never depend on
  * the shape. */

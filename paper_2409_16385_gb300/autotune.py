@@ -23,7 +23,7 @@ EVAL_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
 # items a warp claims from the evaluation's / CCD advancement's work queue at a time
 TILE_SPACE: Tuple[Tuple[int, int, int], ...] = tuple((items, 1, 0) for items in (32, 64, 128, 256))
 QUERY_SPACE: Tuple[Tuple[int, int, int], ...] = tuple(
-    (threads, bps, variant) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32) for variant in (2, 3, 4))
+    (threads, bps, variant) for threads in (64, 128, 256) for bps in (2, 4, 8, 12, 16, 24, 32) for variant in (2, 3))
 
 REFIT_SPACE: Tuple[Tuple[int, int, int], ...] = ((256, 8, 0), (256, 8, 1), (256, 8, 2))
 

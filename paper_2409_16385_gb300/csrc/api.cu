@@ -452,7 +452,7 @@ eipc_status eipc_set_launch(eipc_scene* sc, int32_t kernel, int32_t threads, int
     return EIPC_OK;
   }
   if (kernel == 1) {
-    if ((threads != 64 && threads != 128 && threads != 256) || variant < 2 || variant > 4) return EIPC_ERR_INVALID;
+    if ((threads != 64 && threads != 128 && threads != 256) || (variant != 2 && variant != 3)) return EIPC_ERR_INVALID;
     sc->tune.query_threads = threads;
     sc->tune.query_bps = blocks_per_sm;
     sc->tune.query_variant = variant;

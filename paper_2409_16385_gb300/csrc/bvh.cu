@@ -611,125 +611,6 @@ __global__ void __launch_bounds__(256, MINB) k_query(Bvh tt, Bvh te, Topo T, con
   }
 }
 
-// Warp-cooperative variant of the same search: a warp takes 32 queries of one kind at a
-// time (vertex queries in index order, edge queries in the edge tree's Morton order, so the
-// 32 are close in space) and walks the union of their paths once, with one stack in
-// shared memory.  At each node every lane tests its own box against both children
-// (with the same kinematic, Morton-order and group rules as k_query); the warp descends
-// into a child if any lane overlaps it.  Node fetches are one broadcast per warp instead
-// of one per lane, and the lanes stay converged.  The candidates are the same set.
-constexpr int kCoopStack = 64;
-
-template <int MINB>
-__global__ void __launch_bounds__(256, MINB) k_query_warp(Bvh tt, Bvh te, Topo T, const float* __restrict__ vbox_q,
-                                                          uint64_t* cand, int64_t* n_cand, int64_t cap, DevStatus* st) {
-  pdl_entry();
-  extern __shared__ uint64_t qbuf[];
-  __shared__ int qcount[8];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int nwb = blockDim.x >> 5;
-  uint64_t* wbuf = qbuf + (size_t)wib * kQueryWarpBuf;
-  int2* wstack = reinterpret_cast<int2*>(qbuf + (size_t)nwb * kQueryWarpBuf) + (size_t)wib * kCoopStack;
-  int* wcount = qcount + wib;
-  if (lane == 0) *wcount = 0;
-  __syncwarp();
-  const int64_t nv_q = tt.n > 0 ? T.nv : 0;
-  const int64_t ne_q = te.n > 0 ? T.ne : 0;
-  const int64_t r_pt = (nv_q + 31) / 32;
-  const int64_t rounds = r_pt + (ne_q + 31) / 32;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rounds; r += nw) {
-    const bool is_pt = r < r_pt;                     // warp-uniform
-    const Bvh& t = is_pt ? tt : te;
-    const int64_t idx = (is_pt ? r : r - r_pt) * 32 + lane;
-    const bool act = idx < (is_pt ? nv_q : ne_q);
-    float qlo[3] = {0.f, 0.f, 0.f}, qhi[3] = {-1.f, -1.f, -1.f};
-    int64_t q = 0, qpos = -1;
-    int32_t qa = -1, qb = -1, qgroup = -1;
-    bool qkin = false;
-    if (act) {
-      const PrimKind qkind = is_pt ? kVertex : kEdge;
-      qpos = is_pt ? -1 : idx;
-      q = is_pt ? idx : (int64_t)te.leaf_prim[idx];
-      prim_box_v(qkind, q, T, vbox_q, qlo, qhi);
-      if (is_pt) { qa = (int32_t)q; qb = (int32_t)q; }
-      else { qa = T.edges[2 * q]; qb = T.edges[2 * q + 1]; }
-      qkin = prim_kin(qkind, T, q);
-      qgroup = T.vgroup[qa];
-    }
-    auto put = [&](uint64_t key) {
-      const int slot = atomicAdd(wcount, 1);
-      if (slot < kQueryWarpBuf) wbuf[slot] = key;
-      else emit(key, cand, n_cand, cap, st);
-    };
-    auto leaf = [&](int32_t lpos) {
-      const int4 info = __ldg(t.leaf_info + lpos);
-      if (is_pt) {
-        if (info.x == qa || info.y == qa || info.z == qa) return;
-        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
-        const int32_t p = t.leaf_prim[lpos];
-        put(pair_key(0, (uint32_t)q, (uint32_t)p, T.bits_i, T.bits_j));
-      } else {
-        if (lpos <= qpos) return;
-        if (info.x == qa || info.x == qb || info.y == qa || info.y == qb) return;
-        if ((qkin && (info.w & 1)) || (info.w >> 1) != qgroup) return;
-        const int32_t p = t.leaf_prim[lpos];
-        const uint32_t lo = (uint32_t)(p < q ? p : q), hi = (uint32_t)(p < q ? q : p);
-        put(pair_key(1, lo, hi, T.bits_i, T.bits_j));
-      }
-    };
-    if (t.n == 1) {
-      const float* b = t.leaf_box + 6 * (int64_t)t.leaf_prim[0];
-      if (act && box_overlap(b, b + 3, qlo, qhi)) leaf(0);
-    } else {
-      int sp = 0;                                    // warp-uniform stack depth
-      int32_t node = 0;
-      int32_t nmax = (int32_t)(t.n - 1);
-      int64_t visits = 0;                            // each node is visited at most once
-      while (true) {
-        if (++visits > t.n) {
-          if (lane == 0) raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
-          break;
-        }
-        const float4* np = reinterpret_cast<const float4*>(&t.nodes[node]);
-        const float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-        const int4 f3 = __ldg(reinterpret_cast<const int4*>(np + 3));
-        const float lo0[3] = {f0.x, f0.y, f0.z}, hi0[3] = {f0.w, f1.x, f1.y};
-        const float lo1[3] = {f1.z, f1.w, f2.x}, hi1[3] = {f2.y, f2.z, f2.w};
-        const int32_t c0 = f3.x, c1 = f3.y, kin = f3.z, split = f3.w;
-        bool o0 = act && box_overlap(lo0, hi0, qlo, qhi) && !(qkin && (kin & 1)) && (split > qpos);
-        bool o1 = act && box_overlap(lo1, hi1, qlo, qhi) && !(qkin && (kin & 2)) && (nmax > qpos);
-        if (o0 && c0 < 0) { leaf(~c0); o0 = false; }
-        if (o1 && c1 < 0) { leaf(~c1); o1 = false; }
-        const bool a0 = __any_sync(0xffffffffu, o0), a1 = __any_sync(0xffffffffu, o1);
-        if (a0) {
-          if (a1) {
-            if (sp < kCoopStack) {
-              if (lane == 0) wstack[sp] = make_int2(c1, nmax);
-              ++sp;
-            } else if (lane == 0) {
-              raise_flag(st, EIPC_FLAG_STACK_OVERFLOW);
-            }
-          }
-          node = c0;
-          nmax = split;
-        } else if (a1) {
-          node = c1;
-        } else {
-          if (sp == 0) break;
-          --sp;
-          __syncwarp();
-          const int2 e = wstack[sp];
-          node = e.x;
-          nmax = e.y;
-        }
-        __syncwarp();
-      }
-    }
-    flush_warp_candidates(wbuf, wcount, cand, n_cand, cap, st, lane);
-  }
-}
-
 }  // namespace
 
 void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double pad, float* vbox, float* vbox_pad,
@@ -809,10 +690,7 @@ void bvh_query(const Bvh& tri, const Bvh& edge, const Topo& topo, const float* v
   const int64_t nq = (tri.n > 0 ? topo.nv : 0) + (edge.n > 0 ? topo.ne : 0);
   if (nq <= 0) return;
   const size_t smem = (size_t)(threads / 32) * kQueryWarpBuf * sizeof(uint64_t);
-  if (variant == 4)
-    launch(k_query_warp<4>, blocks_for(nq / 32 + 1, bps, threads / 32), threads,
-           smem + (size_t)(threads / 32) * kCoopStack * sizeof(int2), s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
-  else if (variant == 3)
+  if (variant == 3)
     launch(k_query<6>, blocks_for(nq, bps, threads), threads, smem, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);
   else
     launch(k_query<4>, blocks_for(nq, bps, threads), threads, smem, s, tri, edge, topo, vbox_q, cand, n_cand, cap, st);

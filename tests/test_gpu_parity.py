@@ -202,26 +202,6 @@ def test_launch_modes_agree_bitwise():
     assert outs[0] == outs[1] == outs[2] == outs[3]
 
 
-def test_warp_cooperative_traversal_finds_the_same_sets():
-    """Traversal variant 4 (a warp walks the union of its 32 queries' paths) gives the same
-    pair list, CCD candidate count and step bound as the per-lane walk."""
-    sc = _scene(2, True)
-    outs = []
-    for variant in (2, 4, 2):
-        cs = _cs(sc)
-        cs.set_launch("bvh_query", 128, 8, variant)
-        q = _t(sc.iterate(7))
-        pr = cs.build_candidates(q)
-        ph = pr.host()
-        wc = cs.work_counts()
-        a = cs.accd_toi(cs.embed(q), cs.embed(_t(sc.dq(7)), displacement=True))
-        wa = cs.work_counts()
-        outs.append((ph["type"].tobytes(), ph["i"].tobytes(), ph["j"].tobytes(), ph["d"].tobytes(),
-                     wc["candidates"], wc["screened"], wa["candidates"], wa["ccd_advanced"], float(a)))
-        assert cs.status()["flags"] == 0
-    assert outs[0] == outs[1] == outs[2]
-
-
 def test_friction_match_by_key_and_by_stencil_agree():
     """A lag state built by the scene is matched to the contact pairs by its recorded pair
     keys; a copy of it in other buffers (no keys) by the stencils' vertices.  The key also
