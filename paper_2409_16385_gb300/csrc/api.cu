@@ -225,7 +225,7 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   T.vgroup = s->vgroup;
   T.bits_i = bits_for((uint64_t)(Nv > E ? Nv : E));
   T.bits_j = bits_for((uint64_t)(F > E ? F : E));
-  s->bits_h = bits_for((uint64_t)Ns * (uint64_t)Ns);
+  s->bits_h = bits_for((uint64_t)Ns * (uint64_t)(Ns + 1) / 2);    // upper keys (eval.cu)
   s->bits_g = bits_for((uint64_t)Ns);
   {
     int64_t mx = Nv > E ? Nv : E;

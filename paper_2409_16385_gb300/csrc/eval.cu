@@ -37,6 +37,27 @@ namespace {
 constexpr int kMaxNodes = 16;
 constexpr int kEvalThreads = 128;
 
+// Key of the upper block (I, J), I <= J < ns: its row-major position in the upper triangle,
+// I ns - I (I - 1) / 2 + (J - I).  Ordered like (I, J), and below ns (ns + 1) / 2, so the
+// record sort covers fewer bits than with I ns + J (24 instead of 25 for 5,664 nodes).
+__host__ __device__ __forceinline__ uint64_t upper_key(uint64_t I, uint64_t J, uint64_t ns) {
+  return I * ns - I * (I - 1) / 2 + (J - I);
+}
+
+// (I, J) of an upper key: I is the last row whose first key is at most the key; an FP64
+// estimate from the quadratic, then exact integer correction
+__device__ __forceinline__ void upper_decode(uint64_t key, uint64_t ns, uint64_t* I, uint64_t* J) {
+  const double b = 2.0 * (double)ns + 1.0;
+  double r = 0.5 * (b - sqrt(fmax(b * b - 8.0 * (double)key, 0.0)));
+  int64_t i = (int64_t)r;
+  if (i < 0) i = 0;
+  if (i > (int64_t)ns - 1) i = (int64_t)ns - 1;
+  while (i > 0 && upper_key((uint64_t)i, (uint64_t)i, ns) > key) --i;
+  while (i + 1 < (int64_t)ns && upper_key((uint64_t)(i + 1), (uint64_t)(i + 1), ns) <= key) ++i;
+  *I = (uint64_t)i;
+  *J = key - upper_key((uint64_t)i, (uint64_t)i, ns) + (uint64_t)i;
+}
+
 // stencil vertex ids of pair (type, i, j)
 __device__ __forceinline__ void stencil_vertices(const Topo& T, int type, int32_t i, int32_t j, int32_t v[4]) {
   if (type == 0) {
@@ -596,7 +617,8 @@ __device__ __forceinline__ void emit_upper(const EvalArgs& A, int64_t pos, int32
   if (A.hinv) {
     dst = pre >= 0 ? pre : (int64_t)A.hinv[pos];
   } else {
-    A.hkeys[pos] = swap ? (uint64_t)Iv * (uint64_t)A.ns + (uint64_t)Iu : (uint64_t)Iu * (uint64_t)A.ns + (uint64_t)Iv;
+    A.hkeys[pos] = swap ? upper_key((uint64_t)Iv, (uint64_t)Iu, (uint64_t)A.ns)
+                        : upper_key((uint64_t)Iu, (uint64_t)Iv, (uint64_t)A.ns);
     A.hvals[pos] = (uint32_t)pos;
   }
   double v[9];
@@ -1518,7 +1540,8 @@ __global__ void __launch_bounds__(kBlock) k_full_entries(const uint64_t* __restr
   }
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < S; s += grid_stride()) {
     const uint64_t key = ukey[s];
-    const uint64_t I = key / (uint64_t)ns, J = key % (uint64_t)ns;
+    uint64_t I, J;
+    upper_decode(key, (uint64_t)ns, &I, &J);
     fkey[2 * s] = I | (J << br);
     fval[2 * s] = (uint32_t)(s << 1);
     if (I != J) {
@@ -1594,7 +1617,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
       const int64_t pos = oh + l;
       if (pos >= rec_cap) continue;
       const uint64_t Iu = (uint64_t)nodes[u], Iv = (uint64_t)nodes[w2];
-      hkeys[pos] = Iu <= Iv ? Iu * (uint64_t)ns + Iv : Iv * (uint64_t)ns + Iu;
+      hkeys[pos] = Iu <= Iv ? upper_key(Iu, Iv, (uint64_t)ns) : upper_key(Iv, Iu, (uint64_t)ns);
       hvals[pos] = (uint32_t)pos;
     }
   }
@@ -1790,8 +1813,9 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __res
     if ((lane & 1) == 0 && c < 9) {
       const int32_t du = dst[2 * s], dl = dst[2 * s + 1];
       const uint64_t key = ukey[s];
-      const uint64_t I = key / (uint64_t)ns;
-      if (I != key % (uint64_t)ns) {
+      uint64_t I, J;
+      upper_decode(key, (uint64_t)ns, &I, &J);
+      if (I != J) {
         if (du >= 0 && du < nnzb) H.val[9 * (int64_t)du + c] = v;
         if (dl >= 0 && dl < nnzb) H.val[9 * (int64_t)dl + 3 * (c % 3) + c / 3] = v;
       } else if (c < 6) {
