@@ -244,6 +244,31 @@ __device__ __forceinline__ void node_weights(const int32_t v[4], const int32_t* 
   }
 }
 
+// node_weights for NC (3 or 4) coefficient sets into rows of four: the barrier's c^, a^_1,
+// a^_2 and, with NC = 4, the lagged friction's gamma, in one pass over the stencil's cage
+// slots
+template <int NC>
+__device__ __forceinline__ void node_weights4(const int32_t v[4], const int32_t* __restrict__ cage_idx,
+                                              const double* __restrict__ w, const int32_t* nodes, int n,
+                                              const double coef[4][4], double out[kMaxNodes][4]) {
+  for (int u = 0; u < n; ++u)
+    for (int c = 0; c < NC; ++c) out[u][c] = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    const int4 id = __ldg(reinterpret_cast<const int4*>(cage_idx) + v[a]);
+    if (id.x < 0) continue;
+    const int ids[4] = {id.x, id.y, id.z, id.w};
+    const double2 w01 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a]);
+    const double2 w23 = __ldg(reinterpret_cast<const double2*>(w) + 2 * (int64_t)v[a] + 1);
+    const double ws[4] = {w01.x, w01.y, w23.x, w23.y};
+    for (int s = 0; s < 4; ++s) {
+      int u = 0;
+      while (u < n - 1 && nodes[u] != ids[s]) ++u;
+#pragma unroll
+      for (int c = 0; c < NC; ++c) out[u][c] += coef[c][a] * ws[s];
+    }
+  }
+}
+
 // node_weights for one coefficient set: out[u] = sum over (a, slot) with idx == node_u of
 // coef[a] * w[a][slot]
 __device__ __forceinline__ void node_weights1(const int32_t v[4], const int32_t* __restrict__ cage_idx,
@@ -969,18 +994,20 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
   const int32_t fenc = A.fric_of_pair ? A.fric_of_pair[k] : 0;
   const bool fr = fenc > 0;
   FrictionTerms R;
-  double nwf[kMaxNodes];
+  // per-node scalars omega, alpha_1, alpha_2 and the friction weight w_u (nw[u][3])
+  double coef[4][4];
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 4; ++a) coef[c][a] = basis[c][a];      // zero when not active
   if (fr) {
-    double gam[4];
-    friction_terms(A.x4, A.lag, (int64_t)(INT32_MAX - fenc), v, A.mu, A.eps_f, R, gam);
+    friction_terms(A.x4, A.lag, (int64_t)(INT32_MAX - fenc), v, A.mu, A.eps_f, R, coef[3]);
     E += R.E;
-    node_weights1(v, A.cage_idx, A.w, nodes, n, gam, nwf);
   }
   A.item_E[k] = E;
-  // per-node scalars omega, alpha_1, alpha_2
-  double nw[kMaxNodes][3];
-  if (active) {
-    node_weights(v, A.cage_idx, A.w, nodes, n, basis, 3, nw);
+  double nw[kMaxNodes][4];
+  if (fr) {
+    node_weights4<4>(v, A.cage_idx, A.w, nodes, n, coef, nw);
+  } else if (active) {
+    node_weights4<3>(v, A.cage_idx, A.w, nodes, n, coef, nw);
   } else {
     for (int u = 0; u < n; ++u) nw[u][0] = nw[u][1] = nw[u][2] = 0.0;
   }
@@ -1022,7 +1049,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
           for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
       }
       if (fr) {
-        const double ww = nwf[u] * nwf[u];
+        const double ww = nw[u][3] * nw[u][3];
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] += ww * R.F[p][q];
       }
@@ -1030,7 +1057,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
       const double s = active ? A.kappa * b1 * cn * nw[u][0] : 0.0;
       double gx = s * rh.x, gy = s * rh.y, gz = s * rh.z;
       if (fr) {
-        const double sf = R.gs * nwf[u];
+        const double sf = R.gs * nw[u][3];
         gx += sf * R.u[0]; gy += sf * R.u[1]; gz += sf * R.u[2];
       }
       emit_diag(A, pos, B, gx, gy, gz, dst);
@@ -1050,7 +1077,7 @@ __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) 
           for (int q = 0; q < 3; ++q) B[p][q] = 0.0;
       }
       if (fr) {
-        const double ww = nwf[u] * nwf[w2];
+        const double ww = nw[u][3] * nw[w2][3];
         for (int p = 0; p < 3; ++p)
           for (int q = 0; q < 3; ++q) B[p][q] += ww * R.F[p][q];
       }
