@@ -187,12 +187,12 @@ def measured_peaks():
 #   ccd_advance   FP64 flops per advanced CCD candidate (box test, advancement distances)
 #   others        DRAM bytes per unit of their minimum input + output traffic
 # eval_barrier: 345.20e6 flops over the 115,699 pairs of bubble-grasp iterate 2 (ncu, the
-# autotuned shape 128 threads x 6 blocks/SM, 170-register variant); see profiles/
+# autotuned shape 64 threads, 170-register variant); see profiles/
 FP64_FLOPS_PER_PAIR = 2983.6
 FP64_FLOPS_PER_CCD_CAND = 420.0
 # DRAM bytes (read + write) per unit from one ncu capture of the same kernel code and shape
-# (eval_barrier: 114.4 MB + 239.3 MB for the same 115,699 pairs)
-NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3057.1}
+# (eval_barrier: 112.4 MB + 239.7 MB for the same 115,699 pairs)
+NCU_TRAFFIC_PER_UNIT = {"eval_barrier": 3043.1}
 
 
 def query_bytes(sc, n_cand):
