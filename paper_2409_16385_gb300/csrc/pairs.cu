@@ -244,6 +244,57 @@ __global__ void __launch_bounds__(kBlock) k_feature_compact(const uint64_t* __re
 }
 
 // Sorted survivors -> caller's pair arrays.
+// The pair keys after a stable sort by (type, i) only: each run of one (type, i) -- the
+// pairs one query found, a handful -- is put in j order by the thread at its head, in
+// place (key order within a run is the whole key's order).  Runs longer than kRunMax are
+// sorted the same way with a selection pass per element.
+constexpr int kRunMax = 32;
+
+__global__ void __launch_bounds__(kBlock) k_sort_runs(uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                      const int64_t* n_dev, int64_t cap, int shift) {
+  pdl_entry();
+  const int64_t n = clamp_count(n_dev, cap);
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += grid_stride()) {
+    const uint64_t head = keys[k] >> shift;
+    if (k > 0 && (keys[k - 1] >> shift) == head) continue;
+    int64_t e = k + 1;
+    while (e < n && (keys[e] >> shift) == head) ++e;
+    const int64_t len = e - k;
+    if (len == 1) continue;
+    if (len <= kRunMax) {
+      uint64_t kk[kRunMax];
+      uint32_t vv[kRunMax];
+      for (int a = 0; a < (int)len; ++a) {
+        const uint64_t x = keys[k + a];
+        const uint32_t y = vals[k + a];
+        int b = a;
+        while (b > 0 && kk[b - 1] > x) {
+          kk[b] = kk[b - 1];
+          vv[b] = vv[b - 1];
+          --b;
+        }
+        kk[b] = x;
+        vv[b] = y;
+      }
+      for (int a = 0; a < (int)len; ++a) {
+        keys[k + a] = kk[a];
+        vals[k + a] = vv[a];
+      }
+    } else {
+      // in-place selection sort (keys are distinct)
+      for (int64_t a = k; a < e; ++a) {
+        int64_t m = a;
+        for (int64_t b = a + 1; b < e; ++b)
+          if (keys[b] < keys[m]) m = b;
+        if (m != a) {
+          const uint64_t tk = keys[a]; keys[a] = keys[m]; keys[m] = tk;
+          const uint32_t tv = vals[a]; vals[a] = vals[m]; vals[m] = tv;
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_emit_pairs(Topo T, const uint64_t* __restrict__ keys,
                                                        const uint32_t* __restrict__ vals, const double* __restrict__ sd,
                                                        const int64_t* n_surv, int64_t cand_cap, eipc_pairs out,
@@ -377,11 +428,17 @@ void pairs_launch(eipc_scene* sc, const double* q, const eipc_params& p, const e
          p.dhat, sc->skeys, sc->svals, sc->sd, n_surv, sc->status);
   sc->timers->stop(kKNarrow, s);
   sc->timers->start(kKPairSort, s);
-  int bits = 1 + sc->topo.bits_i + sc->topo.bits_j;
-  int which = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, n_surv, sc->cand_cap, bits,
-                             sc->sort_hist, s);
-  const uint64_t* k = which ? sc->skeys_alt : sc->skeys;
-  const uint32_t* v = which ? sc->svals_alt : sc->svals;
+  // (type, i, j) order: a stable sort by (type, i), the key's bits above j, then each
+  // run of one (type, i) sorted by j in place (three passes instead of five)
+  const int bj = sc->topo.bits_j;
+  int which = radix_sort_u64(sc->skeys, sc->svals, sc->skeys_alt, sc->svals_alt, n_surv, sc->cand_cap,
+                             1 + sc->topo.bits_i, sc->sort_hist, s, bj);
+  uint64_t* ks = which ? sc->skeys_alt : sc->skeys;
+  uint32_t* vs = which ? sc->svals_alt : sc->svals;
+  launch(k_sort_runs, blocks_for(sc->cand_cap, 8), kBlock, 0, s, ks, vs, static_cast<const int64_t*>(n_surv),
+         sc->cand_cap, bj);
+  const uint64_t* k = ks;
+  const uint32_t* v = vs;
   const int64_t* n_out = n_surv;
   if (p.flags & EIPC_PARAM_DEDUP) {
     // feature keys in the record buffers (free until the evaluation), stable sort, firsts,

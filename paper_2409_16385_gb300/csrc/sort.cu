@@ -416,9 +416,9 @@ void zero_ranges(cudaStream_t s, std::initializer_list<ZeroRange> ranges) {
 }
 
 int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s) {
+                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s, int start_bit) {
   int which = 0;
-  for (int shift = 0; shift < bits; shift += 8) {
+  for (int shift = start_bit; shift < start_bit + bits; shift += 8) {
     uint64_t* ki = which ? keys_alt : keys;
     uint32_t* vi = which ? vals_alt : vals;
     uint64_t* ko = which ? keys : keys_alt;

@@ -14,13 +14,14 @@ constexpr int kSortThreads = 256;  // 8 warps, one element per thread per tile
 // Scratch: 256 * kSortBlocks digit counters followed by 256 digit totals.
 inline size_t sort_hist_entries() { return 256u * kSortBlocks + 256u; }
 
-// Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), by key: 8-bit digits over
-// bits [0, 8 ceil(bits / 8)), so every key must be below 2^bits (bits above the last whole
-// digit are ignored, bits inside it are not).
+// Stable LSD radix sort of (keys[i], vals[i]), i < min(*n, cap), by the key's bits
+// [start_bit, start_bit + 8 ceil(bits / 8)) in 8-bit digits: bits below start_bit are
+// ignored (equal there keeps the input order), and every key must be below
+// 2^(start_bit + bits) (bits above the last whole digit are ignored, bits inside it are not).
 // Ping-pongs between (keys, vals) and (keys_alt, vals_alt); returns 0 if the sorted
 // result ends in (keys, vals), 1 if it ends in the alternate buffers.
 int radix_sort_u64(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt,
-                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s);
+                   const int64_t* n, int64_t cap, int bits, uint32_t* hist, cudaStream_t s, int start_bit = 0);
 
 // out[i] = sum_{k<i} in[k] for i < min(*n, cap); *total = the full sum.
 // partial needs kScanBlocks + 1 entries.
