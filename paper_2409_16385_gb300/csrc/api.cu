@@ -32,7 +32,7 @@ void free_scene(eipc_scene* s) {
                   s->edge_bvh.tl_root, s->edge_bvh.up_start, s->edge_bvh.tl_count, s->bounds_ws,
                   s->sort_hist, s->cand, s->counters, s->skeys, s->skeys_alt, s->svals, s->svals_alt, s->sd,
                   s->item_nodes, s->item_n, s->rc_h, s->ro_h, s->rc_g, s->ro_g, s->item_E, s->hkeys,
-                  s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start, s->hinv, s->ginv, s->piece, s->hunit, s->gunit,
+                  s->hkeys_alt, s->hvals, s->hvals_alt, s->hrec, s->seg_flag, s->seg_id, s->seg_start, s->hinv, s->piece, s->hunit,
                   s->gkeys, s->gkeys_alt, s->gvals, s->gvals_alt, s->grec,
                   s->gseg_start, s->scan_partial, s->sum_partial, s->status};
   for (void* p : ptrs)
@@ -162,12 +162,12 @@ eipc_status eipc_scene_create(int64_t Nv, int64_t F, int64_t E, int64_t Ns, cons
   ok(dalloc(&s->hvals, s->rec_cap)); ok(dalloc(&s->hvals_alt, s->rec_cap)); ok(dalloc(&s->hrec, kHRecStride * s->rec_cap));
   ok(dalloc(&s->hvp_out, 3 * (Ns + 64)));
   ok(dalloc(&s->seg_flag, s->rec_cap)); ok(dalloc(&s->seg_id, s->rec_cap)); ok(dalloc(&s->seg_start, s->rec_cap));
-  ok(dalloc(&s->hinv, s->rec_cap)); ok(dalloc(&s->ginv, s->gcap));
+  ok(dalloc(&s->hinv, s->rec_cap));
   {
-    const int64_t pr = s->rec_cap + s->rec_cap / 32 + 2, pg = s->gcap + s->gcap / 32 + 2;
-    ok(dalloc(&s->piece, 9 * pr > 3 * pg ? 9 * pr : 3 * pg));
+    const int64_t pr = s->rec_cap + s->rec_cap / 32 + 2;
+    ok(dalloc(&s->piece, 9 * pr));
   }
-  ok(dalloc(&s->hunit, s->rec_cap + 1)); ok(dalloc(&s->gunit, s->gcap + 1));
+  ok(dalloc(&s->hunit, s->rec_cap + 1));
   ok(dalloc(&s->gkeys, s->gcap)); ok(dalloc(&s->gkeys_alt, s->gcap));
   ok(dalloc(&s->gvals, s->gcap)); ok(dalloc(&s->gvals_alt, s->gcap)); ok(dalloc(&s->grec, kGRecStride * s->gcap));
   ok(dalloc(&s->gseg_start, s->gcap));

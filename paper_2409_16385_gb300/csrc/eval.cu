@@ -454,11 +454,11 @@ struct EvalArgs {
   int tile;                // items a warp claims from the queue at a time (multiple of 32)
   const double* hv_dir;    // Hessian-vector product: reduced direction [ns*3]
   double kin_dir[3];       // ... and the rigid direction of the kinematic vertices
-  // Presorted records (energy/gradient/Hessian evaluation): the keys were written and
-  // sorted before the evaluation, and record r goes to its sorted position hinv[r] (ginv[r])
-  // without a key.  Null: record r is written at r with its key (Hessian-vector products).
+  // Presorted Hessian records (energy/gradient/Hessian evaluation): the keys were written
+  // and sorted before the evaluation, and record r goes to its sorted position hinv[r]
+  // without a key.  Gradient records (Hessian-vector products only) are written at r with
+  // their key.
   const uint32_t* hinv;
-  const uint32_t* ginv;
   // friction merged into contact pairs (friction_merged; null: no merging); lag, mu and
   // eps_f are the friction parameters
   const int32_t* fric_of_pair;
@@ -673,17 +673,12 @@ __device__ __forceinline__ void emit_diag(const EvalArgs& A, int64_t pos, const 
   A.hrec[kHRecStride * dst + 8] = g2;
 }
 
-// one gradient record (presorted or keyed, as emit_upper)
+// one keyed gradient record (Hessian-vector products)
 __device__ __forceinline__ void emit_grad(const EvalArgs& A, int64_t pos, uint64_t key, double y0, double y1, double y2) {
-  int64_t dst = pos;
-  if (A.ginv) {
-    dst = A.ginv[pos];
-  } else {
-    A.gkeys[pos] = key;
-    A.gvals[pos] = (uint32_t)pos;
-  }
-  *reinterpret_cast<double2*>(A.grec + kGRecStride * dst) = make_double2(y0, y1);
-  A.grec[kGRecStride * dst + 2] = y2;
+  A.gkeys[pos] = key;
+  A.gvals[pos] = (uint32_t)pos;
+  *reinterpret_cast<double2*>(A.grec + kGRecStride * pos) = make_double2(y0, y1);
+  A.grec[kGRecStride * pos + 2] = y2;
 }
 
 // The barrier Hessian of one active pair in its span (Sec. III-B, Eq. 7; the 12 x 12
@@ -1860,30 +1855,6 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_h_pieces(const double* __res
   }
 }
 
-// gradient pass 2, one warp per segment (node), as the Hessian's
-__global__ void __launch_bounds__(kBlock) k_seg_sum_g_pieces(const uint64_t* __restrict__ keys,
-                                                             const double* __restrict__ piece,
-                                                             const int64_t* __restrict__ start,
-                                                             const int64_t* __restrict__ unit, const int64_t* n_units,
-                                                             const int64_t* n_seg, double* __restrict__ g) {
-  pdl_entry();
-  const int64_t S = *n_seg;
-  const int64_t U = *n_units;
-  const int lane = threadIdx.x & 31;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < S; s += nw) {
-    const int64_t u1 = (s + 1 < S) ? unit[s + 1] : U;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int64_t k = unit[s] + lane; k < u1; k += 32) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] += __ldg(piece + 3 * k + c);
-    }
-    const double v = warp_reduce_scatter<4>(acc, lane);
-    const int c = lane >> 3;
-    if ((lane & 7) == 0 && c < 3) g[3 * (int64_t)keys[start[s]] + c] = v;
-  }
-}
-
 // deterministic sum: fixed chunk per block, fixed in-block tree, partials summed in order
 __global__ void __launch_bounds__(kBlock) k_sum_partial(const double* __restrict__ x, const int64_t* n_dev,
                                                         int64_t cap, double* __restrict__ partial) {
@@ -2067,7 +2038,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   A.moll_r2 = sc->moll_factor > 0.0 ? sc->moll_r2 : nullptr;
   A.moll_factor = sc->moll_factor;
   A.hv_dir = nullptr; A.kin_dir[0] = A.kin_dir[1] = A.kin_dir[2] = 0.0;
-  A.hinv = sc->hinv; A.ginv = nullptr;       // gradients ride in the diagonal records
+  A.hinv = sc->hinv;                         // gradients ride in the diagonal records
   A.fric_of_pair = fop; A.pair_of_fric = pof;
   A.lag = fr ? *lag : eipc_lag{};
   A.mu = p.mu; A.eps_f = p.eps_v * p.h;
@@ -2159,7 +2130,7 @@ void hvp_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const eip
   A.tile = 32;
   A.hv_dir = v;
   for (int c = 0; c < 3; ++c) A.kin_dir[c] = kin_dir ? kin_dir[c] : 0.0;
-  A.hinv = nullptr; A.ginv = nullptr;
+  A.hinv = nullptr;
   A.fric_of_pair = nullptr; A.pair_of_fric = nullptr;
   A.lag = fr ? *lag : eipc_lag{};
   A.mu = p.mu; A.eps_f = p.eps_v * p.h;

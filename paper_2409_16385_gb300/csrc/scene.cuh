@@ -71,10 +71,8 @@ struct eipc_scene {
   int64_t* seg_id;       // [rec_cap] BSR entries of each segment's block and transpose, as int32 pairs
   int64_t* seg_start;    // [rec_cap]
   uint32_t* hinv;        // [rec_cap] sorted position of each Hessian record
-  uint32_t* ginv;        // [gcap] sorted position of each gradient record
-  double* piece;         // [9 * (rec_cap + rec_cap / 32 + 2)] partial segment sums (Hessian, then gradient)
+  double* piece;         // [9 * (rec_cap + rec_cap / 32 + 2)] partial segment sums of the Hessian records
   int64_t* hunit;        // [rec_cap + 1] first summation unit of each Hessian segment
-  int64_t* gunit;        // [gcap + 1] ... of each gradient segment
   int64_t gcap;          // gradient records
   uint64_t* gkeys;
   uint64_t* gkeys_alt;
@@ -109,7 +107,7 @@ constexpr int kHRecStride = 10, kGRecStride = 4;
 
 enum { kCntCand = 0, kCntSurv = 1, kCntItems = 2, kCntRecH = 3, kCntRecG = 4, kCntSegH = 5, kCntSegG = 6,
        kCntAccd = 7, kCntZero = 8, kCntEvalQueue = 16, kCntScreened = 15, kCntDedup = 17, kCntUnitsH = 18,
-       kCntUnitsG = 19, kCntMollBad = 20, kCntCcdQueue = 21,
+       kCntMollBad = 20, kCntCcdQueue = 21,
        kCntN = 24 };
 
 // id of the edge with end vertices {a, b} from the scene's sorted edge keys a * nv + b
