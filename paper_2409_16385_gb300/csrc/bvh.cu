@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kBlock) k_internal(const uint64_t* __restrict_
     nodes[i].c1 = c1;
     nodes[i].split = (int32_t)gamma;   // last leaf position under child 0
     range[i] = make_int2((int32_t)lo, (int32_t)hi);
-    parent[c0 >= 0 ? c0 : (n - 1 + ~c0)] = (int32_t)i;
-    parent[c1 >= 0 ? c1 : (n - 1 + ~c1)] = (int32_t)i;
+    parent[c0 >= 0 ? c0 : (n - 1 + ~c0)] = (int32_t)(i << 1);
+    parent[c1 >= 0 ? c1 : (n - 1 + ~c1)] = (int32_t)(i << 1) | 1;
   }
 }
 
@@ -268,9 +268,10 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
       lo[0] = a0.x; lo[1] = a0.y; lo[2] = a1.x; hi[0] = a1.y; hi[1] = a2.x; hi[2] = a2.y;
     }
     if (n == 1) continue;
-    int32_t node = parent[n - 1 + l];
-    int slot = (nodes[node].c0 == ~(int32_t)l) ? 0 : 1;
-    write_child<first>(&nodes[node], slot, lo, hi, kin);
+    int32_t ps = parent[n - 1 + l];
+    int32_t node = ps >> 1;
+    write_child<first>(&nodes[node], ps & 1, lo, hi, kin);
+    int32_t up = node ? parent[node] : 0;       // fetched before the arrival, not after it
     if (arrive<fences>(&flag[node]) == 0) continue;
     for (int64_t step = 0; step < n; ++step) {   // a root path has at most n-1 nodes
       if (fences) __threadfence();
@@ -281,11 +282,11 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
       }
       if (first) kin = (__ldcg(&nd->kin) & 3) == 3;
       if (node == 0) break;
-      int32_t p = parent[node];
-      slot = (nodes[p].c0 == node) ? 0 : 1;
-      write_child<first>(&nodes[p], slot, lo, hi, kin);
-      if (arrive<fences>(&flag[p]) == 0) break;
-      node = p;
+      ps = up;
+      node = ps >> 1;
+      write_child<first>(&nodes[node], ps & 1, lo, hi, kin);
+      up = node ? parent[node] : 0;
+      if (arrive<fences>(&flag[node]) == 0) break;
     }
   }
 }
@@ -308,14 +309,14 @@ __global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2*
     if (i < n - 1) {                              // internal node i
       const int2 r = range[i];
       const int64_t size = (int64_t)r.y - r.x + 1;
-      const int64_t psize = (i == 0) ? INT64_MAX : (int64_t)range[parent[i]].y - range[parent[i]].x + 1;
+      const int64_t psize = (i == 0) ? INT64_MAX : (int64_t)range[parent[i] >> 1].y - range[parent[i] >> 1].x + 1;
       if (size <= kTreelet && psize > kTreelet) {
         tl_root[atomicAdd(&count[0], 1)] = (int32_t)i;
         up_start[atomicAdd(&count[1], 1)] = (int32_t)i;
       }
     } else {                                      // leaf l = i - (n - 1)
       const int64_t l = i - (n - 1);
-      const int32_t p = parent[i];
+      const int32_t p = parent[i] >> 1;
       if ((int64_t)range[p].y - range[p].x + 1 > kTreelet) up_start[atomicAdd(&count[1], 1)] = ~(int32_t)l;
     }
   }
@@ -348,7 +349,6 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
   __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
   __shared__ int scnt[kTreeletWarps][kTreelet];
   __shared__ int spar[kTreeletWarps][kTreelet];
-  __shared__ int sc0[kTreeletWarps][kTreelet];
   const int nA = A.n > 1 ? (int)A.n : 0, nB = B.n > 1 ? (int)B.n : 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nA + nB; i += grid_stride()) {
     if (i < nA) A.flag[i] = 0;
@@ -364,23 +364,20 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
     const int32_t root = T.tl_root[inA ? w : w - ntA];
     const int2 rg = T.range[root];
     const int lo = rg.x, m = rg.y - rg.x + 1;           // m <= kTreelet leaves, m - 1 internal nodes
-    // node links of the indices lo .. hi (the treelet's internal nodes are among them)
-    if (lane < m && lo + lane < n - 1) {
-      spar[wib][lane] = T.parent[lo + lane];
-      sc0[wib][lane] = T.nodes[lo + lane].c0;
-    }
+    // parent links (parent << 1 | slot) of the indices lo .. hi (the treelet's internal
+    // nodes are among them)
+    if (lane < m && lo + lane < n - 1) spar[wib][lane] = T.parent[lo + lane];
     scnt[wib][lane] = 0;
     __syncwarp();
     if (lane < m) {
       const int32_t l = lo + lane;
       float b[6];
       leaf_box_of(T.leaf_info[l], vbox, b, b + 3);
-      int32_t child = ~l;
-      int32_t node = T.parent[n - 1 + l];
+      int32_t ps = T.parent[n - 1 + l];
       for (int step = 0; step < kTreelet; ++step) {  // a treelet is at most kTreelet - 1 deep
-        const int off = node - lo;
+        const int32_t node = ps >> 1;
+        const int off = node - lo, slot = ps & 1;
         if (off < 0 || off >= m) break;              // (a subtree's nodes lie in its leaf range)
-        const int slot = (sc0[wib][off] == child) ? 0 : 1;
         float* dl = slot ? T.nodes[node].lo1 : T.nodes[node].lo0;
         float* dh = slot ? T.nodes[node].hi1 : T.nodes[node].hi0;
         for (int k = 0; k < 3; ++k) { __stcg(&dl[k], b[k]); __stcg(&dh[k], b[3 + k]); }
@@ -393,8 +390,7 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
           b[3 + k] = fmaxf(sbox[wib][off][0][3 + k], sbox[wib][off][1][3 + k]);
         }
         if (node == root) break;                     // its box goes up in phase B
-        child = node;
-        node = spar[wib][off];
+        ps = spar[wib][off];
       }
     }
     __syncwarp();
@@ -413,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
     const int64_t n = T.n;
     const int32_t st = T.up_start[inA ? k : k - nuA];
     float lo[3], hi[3];
-    int32_t child, node;
+    int32_t ps;                                      // parent << 1 | slot of the climbing box
     if (st >= 0) {                                   // a treelet root: its box from its children
       const BvhNode* nd = &T.nodes[st];
       for (int q = 0; q < 3; ++q) {
@@ -421,28 +417,33 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
         hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
       }
       if (st == 0) continue;                         // the whole tree was one treelet
-      child = st;
-      node = T.parent[st];
+      ps = __ldg(T.parent + st);
     } else {                                         // a leaf under a larger node
       const int32_t l = ~st;
       leaf_box_of(T.leaf_info[l], vbox, lo, hi);
-      child = st;
-      node = T.parent[n - 1 + l];
+      ps = __ldg(T.parent + n - 1 + l);
     }
+    // Per level: store this box into its slot, arrive, and (second arrival) take the union
+    // with the sibling's box.  The slot comes with the parent link, and the next link is
+    // fetched before the arrival, so the climb waits on the arrival and the sibling's box
+    // only.
     for (int64_t step = 0; step < n; ++step) {       // a root path has at most n-1 nodes
-      const int slot = (T.nodes[node].c0 == child) ? 0 : 1;
-      float* dl = slot ? T.nodes[node].lo1 : T.nodes[node].lo0;
-      float* dh = slot ? T.nodes[node].hi1 : T.nodes[node].hi0;
+      const int32_t node = ps >> 1, slot = ps & 1;
+      BvhNode* nd = &T.nodes[node];
+      float* dl = slot ? nd->lo1 : nd->lo0;
+      float* dh = slot ? nd->hi1 : nd->hi0;
       for (int q = 0; q < 3; ++q) { __stcg(&dl[q], lo[q]); __stcg(&dh[q], hi[q]); }
+      const int32_t up = node ? __ldg(T.parent + node) : 0;
       if (arrive<false>(&T.flag[node]) == 0) break;
-      const BvhNode* nd = &T.nodes[node];
-      for (int q = 0; q < 3; ++q) {
-        lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
-        hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
+      const float* sl = slot ? nd->lo0 : nd->lo1;
+      const float* sh = slot ? nd->hi0 : nd->hi1;
+      for (int q = 0; q < 3; ++q) {                // operands in slot order, as in the build
+        const float a = __ldcg(&sl[q]), b = __ldcg(&sh[q]);
+        lo[q] = slot ? fminf(a, lo[q]) : fminf(lo[q], a);
+        hi[q] = slot ? fmaxf(b, hi[q]) : fmaxf(hi[q], b);
       }
       if (node == 0) break;
-      child = node;
-      node = T.parent[node];
+      ps = up;
     }
   }
 }

@@ -21,7 +21,7 @@ struct Bvh {
   int64_t n;             // primitives (static per scene)
   int64_t* n_dev;        // [1] device copy of n (element count for the Morton sort)
   BvhNode* nodes;        // [n-1]
-  int32_t* parent;       // [2n-1]: internal i at i, leaf l at n-1+l
+  int32_t* parent;       // [2n-1]: parent << 1 | slot (0: child c0, 1: c1); internal i at i, leaf l at n-1+l
   int32_t* leaf_prim;    // [n]
   int4* leaf_info;       // [n] per leaf (Morton order): vertex ids (-1 if unused), kinematic flag
   float* leaf_box;       // [6n], by primitive id (lo xyz, hi xyz)
