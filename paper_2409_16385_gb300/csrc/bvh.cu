@@ -187,6 +187,22 @@ __device__ __forceinline__ uint8_t prim_kin(PrimKind kind, const Topo& T, int64_
   return kind == kTri ? T.fkin[p] : (kind == kEdge ? T.ekin[p] : T.vkin[p]);
 }
 
+// The per-leaf records of a build, in leaf (Morton) order for the traversal: the primitive,
+// and its vertex ids with (kinematic flag | scene group << 1).  Returns the kinematic flag.
+__device__ __forceinline__ int write_leaf_record(PrimKind kind, const Topo& T, int32_t prim, int64_t l,
+                                                 int32_t* __restrict__ leaf_prim, int4* __restrict__ leaf_info) {
+  leaf_prim[l] = prim;
+  const int kin = prim_kin(kind, T, prim);
+  if (kind == kTri) {
+    const int32_t v0 = T.tris[3 * (int64_t)prim];
+    leaf_info[l] = make_int4(v0, T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2], kin | (T.vgroup[v0] << 1));
+  } else {
+    const int32_t v0 = T.edges[2 * (int64_t)prim];
+    leaf_info[l] = make_int4(v0, T.edges[2 * (int64_t)prim + 1], -1, kin | (T.vgroup[v0] << 1));
+  }
+  return kin;
+}
+
 template <bool first>
 __device__ __forceinline__ void write_child(BvhNode* nd, int slot, const float lo[3], const float hi[3], int kin) {
   float* l = slot ? nd->lo1 : nd->lo0;
@@ -249,18 +265,7 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
     float lo[3], hi[3];
     if (first) {
       const int32_t prim = (int32_t)sorted[l];
-      leaf_prim[l] = prim;
-      kin = prim_kin(kind, T, prim);
-      // the leaf's vertex ids, and (kinematic flag | scene group << 1), in leaf order for
-      // the traversal
-      if (kind == kTri) {
-        const int32_t v0 = T.tris[3 * (int64_t)prim];
-        leaf_info[l] = make_int4(v0, T.tris[3 * (int64_t)prim + 1], T.tris[3 * (int64_t)prim + 2],
-                                 kin | (T.vgroup[v0] << 1));
-      } else {
-        const int32_t v0 = T.edges[2 * (int64_t)prim];
-        leaf_info[l] = make_int4(v0, T.edges[2 * (int64_t)prim + 1], -1, kin | (T.vgroup[v0] << 1));
-      }
+      kin = write_leaf_record(kind, T, prim, l, leaf_prim, leaf_info);
       for (int k = 0; k < 3; ++k) { lo[k] = leaf_box[6 * prim + k]; hi[k] = leaf_box[6 * prim + 3 + k]; }
     } else {
       const float2* b = reinterpret_cast<const float2*>(leaf_box + 6 * l);
@@ -301,9 +306,13 @@ __global__ void __launch_bounds__(kBlock) k_refit(PrimKind kind, int64_t n, Topo
 // larger nodes) with the release-acquire counters.  Box unions are exact, so the boxes
 // are those of any other refit order.
 
+// On a build refitted by treelets (leaf_prim not null) it also writes the leaf records,
+// which both refit phases read.
 __global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2* __restrict__ range,
                                                           const int32_t* __restrict__ parent, int32_t* __restrict__ tl_root,
-                                                          int32_t* __restrict__ up_start, int32_t* __restrict__ count) {
+                                                          int32_t* __restrict__ up_start, int32_t* __restrict__ count,
+                                                          PrimKind kind, Topo T, const uint32_t* __restrict__ sorted,
+                                                          int32_t* __restrict__ leaf_prim, int4* __restrict__ leaf_info) {
   pdl_entry();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 2 * n - 1; i += grid_stride()) {
     if (i < n - 1) {                              // internal node i
@@ -316,6 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_treelet_lists(int64_t n, const int2*
       }
     } else {                                      // leaf l = i - (n - 1)
       const int64_t l = i - (n - 1);
+      if (leaf_prim) write_leaf_record(kind, T, (int32_t)sorted[l], l, leaf_prim, leaf_info);
       const int32_t p = parent[i] >> 1;
       if ((int64_t)range[p].y - range[p].x + 1 > kTreelet) up_start[atomicAdd(&count[1], 1)] = ~(int32_t)l;
     }
@@ -343,12 +353,16 @@ __host__ __device__ __forceinline__ RefitView refit_view(const Bvh& t) {
 
 // Phase A of the refit of up to two trees in one launch: one warp per treelet, lane l
 // computing leaf l's box from the positions and climbing in shared memory.  The grid also
-// clears both trees' arrival counters for phase B.
+// clears both trees' arrival counters for phase B.  On a build (`first`) it also sets each
+// node's kinematic bits (bit s: every primitive under child s is kinematic), which a refit
+// leaves as they are.
+template <bool first>
 __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
   pdl_entry();
   __shared__ float sbox[kTreeletWarps][kTreelet][2][6];
   __shared__ int scnt[kTreeletWarps][kTreelet];
   __shared__ int spar[kTreeletWarps][kTreelet];
+  __shared__ int skin[kTreeletWarps][kTreelet];
   const int nA = A.n > 1 ? (int)A.n : 0, nB = B.n > 1 ? (int)B.n : 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)nA + nB; i += grid_stride()) {
     if (i < nA) A.flag[i] = 0;
@@ -368,11 +382,14 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
     // nodes are among them)
     if (lane < m && lo + lane < n - 1) spar[wib][lane] = T.parent[lo + lane];
     scnt[wib][lane] = 0;
+    if (first) skin[wib][lane] = 0;
     __syncwarp();
     if (lane < m) {
       const int32_t l = lo + lane;
       float b[6];
-      leaf_box_of(T.leaf_info[l], vbox, b, b + 3);
+      const int4 li = T.leaf_info[l];
+      leaf_box_of(li, vbox, b, b + 3);
+      int kin = li.w & 1;
       int32_t ps = T.parent[n - 1 + l];
       for (int step = 0; step < kTreelet; ++step) {  // a treelet is at most kTreelet - 1 deep
         const int32_t node = ps >> 1;
@@ -382,12 +399,18 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
         float* dh = slot ? T.nodes[node].hi1 : T.nodes[node].hi0;
         for (int k = 0; k < 3; ++k) { __stcg(&dl[k], b[k]); __stcg(&dh[k], b[3 + k]); }
         for (int k = 0; k < 6; ++k) sbox[wib][off][slot][k] = b[k];
+        if (first && kin) atomicOr(&skin[wib][off], 1 << slot);
         __threadfence_block();
         if (atomicAdd(&scnt[wib][off], 1) == 0) break;   // the sibling finishes this node
         __threadfence_block();
         for (int k = 0; k < 3; ++k) {
           b[k] = fminf(sbox[wib][off][0][k], sbox[wib][off][1][k]);
           b[3 + k] = fmaxf(sbox[wib][off][0][3 + k], sbox[wib][off][1][3 + k]);
+        }
+        if (first) {                                 // both children's bits are in
+          const int kb = skin[wib][off];
+          T.nodes[node].kin = kb;
+          kin = kb == 3;
         }
         if (node == root) break;                     // its box goes up in phase B
         ps = spar[wib][off];
@@ -399,7 +422,9 @@ __global__ void __launch_bounds__(kBlock) k_treelet_refit(RefitView A, RefitView
 
 // Phase B for up to two trees: one thread per upper start (a treelet root, or a leaf
 // directly under a larger node, its box from the positions) climbs with release-acquire
-// arrival counters; the two trees' climbs run side by side.
+// arrival counters; the two trees' climbs run side by side.  On a build (`first`) the
+// kinematic bits climb with the boxes.
+template <bool first>
 __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B, const float* __restrict__ vbox) {
   pdl_entry();
   const int64_t nuA = A.n > 1 ? A.count[1] : 0, nuB = B.n > 1 ? B.count[1] : 0;
@@ -410,17 +435,21 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
     const int32_t st = T.up_start[inA ? k : k - nuA];
     float lo[3], hi[3];
     int32_t ps;                                      // parent << 1 | slot of the climbing box
+    int kin = 0;                                     // (first) every primitive below is kinematic
     if (st >= 0) {                                   // a treelet root: its box from its children
       const BvhNode* nd = &T.nodes[st];
       for (int q = 0; q < 3; ++q) {
         lo[q] = fminf(__ldcg(&nd->lo0[q]), __ldcg(&nd->lo1[q]));
         hi[q] = fmaxf(__ldcg(&nd->hi0[q]), __ldcg(&nd->hi1[q]));
       }
+      if (first) kin = (__ldcg(&nd->kin) & 3) == 3;
       if (st == 0) continue;                         // the whole tree was one treelet
       ps = __ldg(T.parent + st);
     } else {                                         // a leaf under a larger node
       const int32_t l = ~st;
-      leaf_box_of(T.leaf_info[l], vbox, lo, hi);
+      const int4 li = T.leaf_info[l];
+      leaf_box_of(li, vbox, lo, hi);
+      if (first) kin = li.w & 1;
       ps = __ldg(T.parent + n - 1 + l);
     }
     // Per level: store this box into its slot, arrive, and (second arrival) take the union
@@ -433,6 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
       float* dl = slot ? nd->lo1 : nd->lo0;
       float* dh = slot ? nd->hi1 : nd->hi0;
       for (int q = 0; q < 3; ++q) { __stcg(&dl[q], lo[q]); __stcg(&dh[q], hi[q]); }
+      if (first && kin) atomicOr(&nd->kin, 1 << slot);
       const int32_t up = node ? __ldg(T.parent + node) : 0;
       if (arrive<false>(&T.flag[node]) == 0) break;
       const float* sl = slot ? nd->lo0 : nd->lo1;
@@ -442,6 +472,7 @@ __global__ void __launch_bounds__(kBlock) k_upper_refit(RefitView A, RefitView B
         lo[q] = slot ? fminf(a, lo[q]) : fminf(lo[q], a);
         hi[q] = slot ? fmaxf(b, hi[q]) : fmaxf(hi[q], b);
       }
+      if (first) kin = (__ldcg(&nd->kin) & 3) == 3;
       if (node == 0) break;
       ps = up;
     }
@@ -634,6 +665,19 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
   const uint32_t* sv = which ? t.vals_alt : t.vals;
   t.sorted = sv;
   if (t.n > 1) launch(k_internal, blocks_for(t.n - 1), kBlock, 0, s, sk, t.n, t.nodes, t.parent, t.range);
+  if (refit_variant == 2 && t.n > 1) {
+    // the treelet lists first (with the leaf records), then both refit phases with the
+    // kinematic bits
+    launch(k_treelet_lists, blocks_for(2 * t.n), kBlock, 0, s, t.n, static_cast<const int2*>(t.range),
+           static_cast<const int32_t*>(t.parent), t.tl_root, t.up_start, t.tl_count, kind, topo, sv, t.leaf_prim,
+           t.leaf_info);
+    const RefitView A = refit_view(t);
+    const RefitView none{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    launch(k_treelet_refit<true>, blocks_for(t.n, 8), kBlock, 0, s, A, none, vbox);
+    launch(k_upper_refit<true>, blocks_for(t.n), kBlock, 0, s, A, none, vbox);
+    t.built = true;
+    return;
+  }
   if (refit_variant == 0)
     launch(k_refit<true, true>, blocks_for(t.n), kBlock, 0, s, kind, t.n, topo, sv,
            static_cast<const float*>(t.leaf_box), t.nodes, static_cast<const int32_t*>(t.parent), t.leaf_prim,
@@ -644,7 +688,8 @@ void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const 
            t.leaf_info, t.refit_flag);
   if (t.n > 1) {
     launch(k_treelet_lists, blocks_for(2 * t.n), kBlock, 0, s, t.n, static_cast<const int2*>(t.range),
-           static_cast<const int32_t*>(t.parent), t.tl_root, t.up_start, t.tl_count);
+           static_cast<const int32_t*>(t.parent), t.tl_root, t.up_start, t.tl_count, kind, topo, sv,
+           static_cast<int32_t*>(nullptr), static_cast<int4*>(nullptr));
   }
   t.built = true;
 }
@@ -654,8 +699,8 @@ static void treelet_refit(Bvh& a, Bvh* b, const float* vbox, cudaStream_t s) {
   RefitView A = refit_view(a);
   RefitView Bv = b ? refit_view(*b) : RefitView{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   const int64_t n = a.n + (b ? b->n : 0);
-  launch(k_treelet_refit, blocks_for(n, 8), kBlock, 0, s, A, Bv, vbox);
-  launch(k_upper_refit, blocks_for(n), kBlock, 0, s, A, Bv, vbox);
+  launch(k_treelet_refit<false>, blocks_for(n, 8), kBlock, 0, s, A, Bv, vbox);
+  launch(k_upper_refit<false>, blocks_for(n), kBlock, 0, s, A, Bv, vbox);
 }
 
 void bvh_refit_pair(Bvh& a, PrimKind ka, Bvh& b, PrimKind kb, const Topo& topo, const float* vbox, cudaStream_t s,

@@ -72,7 +72,9 @@ void vertex_boxes(const Topo& topo, const double* x4, const double* dx4, double 
 // `bounds_ws` holds 6 ints of scratch.  Enqueued on stream s.
 // refit_variant: 0 = arrival counters behind full device fences, 1 = release-acquire
 // arrival counters, 2 = treelets of <= 32 leaves refitted by one warp each in shared memory,
-// then release-acquire counters above them (all give the same boxes)
+// then release-acquire counters above them (all give the same boxes).  With 2 the build's
+// own bottom-up pass is the treelet refit too: the treelet lists come first and write the
+// leaf records, and the kinematic bits climb with the boxes.
 void bvh_build(Bvh& t, PrimKind kind, const Topo& topo, const double* x4, const double* dx4, const float* vbox,
                int32_t* bounds_ws, uint32_t* sort_hist, cudaStream_t s, int refit_variant);
 
