@@ -935,7 +935,8 @@ __device__ __forceinline__ void vertex_node_weights(const int32_t v[4], const in
 }
 
 // One barrier item: distance, span Hessian (projected unless A.project is false), energy,
-// gradient records and upper-triangle Hessian records at the item's own offsets.
+// and its upper-triangle Hessian records, the diagonal ones carrying the gradient, each
+// written at its presorted position hinv[pos].
 __device__ __forceinline__ void eval_barrier_item(const EvalArgs& A, int64_t k) {
   int32_t v[4];
   const int type = A.pr.type[k];
@@ -1609,15 +1610,13 @@ __global__ void __launch_bounds__(kBlock) k_seg_sum_g(const uint64_t* __restrict
 // BSR pattern before the evaluation; the evaluation then writes every record straight to
 // its sorted position and the sums read contiguous records.
 
-// keys of item k's records in the order the evaluation emits them: gradient record u
-// (node I_u), Hessian record (u, v), u <= v (nodes (min, max)).  One warp per item, lanes
-// on consecutive records.
+// keys of item k's Hessian records in the order the evaluation emits them: record (u, v),
+// u <= v, keyed by the upper-triangle position of its nodes (min, max).  One warp per item,
+// lanes on consecutive records.
 __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__ item_nodes,
                                                      const int32_t* __restrict__ item_n, const int64_t* __restrict__ ro_h,
-                                                     const int64_t* __restrict__ ro_g, const int64_t* n_items,
-                                                     int64_t rec_cap, int64_t gcap, int64_t ns,
-                                                     uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hvals,
-                                                     uint64_t* __restrict__ gkeys, uint32_t* __restrict__ gvals) {
+                                                     const int64_t* n_items, int64_t rec_cap, int64_t ns,
+                                                     uint64_t* __restrict__ hkeys, uint32_t* __restrict__ hvals) {
   pdl_entry();
   const int64_t nit = *n_items;
   const int lane = threadIdx.x & 31;
@@ -1625,11 +1624,7 @@ __global__ void __launch_bounds__(kBlock) k_rec_keys(const int32_t* __restrict__
   for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nit; k += nw) {
     const int n = item_n[k];
     const int32_t* nodes = item_nodes + kMaxNodes * k;
-    const int64_t og = ro_g[k], oh = ro_h[k];
-    if (gkeys && lane < n && og + lane < gcap) {
-      gkeys[og + lane] = (uint64_t)nodes[lane];
-      gvals[og + lane] = (uint32_t)(og + lane);
-    }
+    const int64_t oh = ro_h[k];
     const int nrec = n * (n + 1) / 2;
     for (int l = lane; l < nrec; l += 32) {
       // row u of the upper triangle holds n - u records
@@ -1998,8 +1993,7 @@ void eval_launch(eipc_scene* sc, const double* q, const eipc_pairs& pr, const ei
   sc->timers->start(kKHReduce, s);
   launch(k_rec_keys, blocks_for(32 * item_cap, 8), kBlock, 0, s, static_cast<const int32_t*>(sc->item_nodes),
          static_cast<const int32_t*>(sc->item_n), static_cast<const int64_t*>(sc->ro_h),
-         static_cast<const int64_t*>(sc->ro_g), static_cast<const int64_t*>(cnt + kCntItems), sc->rec_cap, sc->gcap,
-         sc->ns, sc->hkeys, sc->hvals, static_cast<uint64_t*>(nullptr), static_cast<uint32_t*>(nullptr));
+         static_cast<const int64_t*>(cnt + kCntItems), sc->rec_cap, sc->ns, sc->hkeys, sc->hvals);
   const int wh = radix_sort_u64(sc->hkeys, sc->hvals, sc->hkeys_alt, sc->hvals_alt, cnt + kCntRecH, sc->rec_cap,
                                 sc->bits_h, sc->sort_hist, s);
   const uint64_t* hk = wh ? sc->hkeys_alt : sc->hkeys;
