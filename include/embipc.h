@@ -290,8 +290,8 @@ eipc_status eipc_group_alpha(eipc_scene* scene, double* alpha_groups, eipc_strea
  * registers (4 blocks of 128 per SM); traversal 2 = no register cap, 3 = at most 40
  * registers (6 blocks of 256 per SM); refit 0 = arrival counters behind full device
  * fences, 1 = release-acquire arrival counters, 2 = treelets of up to 32 leaves refitted per
- * warp in shared memory below release-acquire counters (default).  Results never depend on
- * the shape. */
+ * warp in shared memory below release-acquire counters, for the refits and for the
+ * rebuilds' own bottom-up pass (default).  Results never depend on the shape. */
 eipc_status eipc_set_launch(eipc_scene* scene, int32_t kernel, int32_t threads, int32_t blocks_per_sm,
                             int32_t variant);
 
