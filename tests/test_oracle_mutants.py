@@ -45,6 +45,7 @@ PP_HESS = ("test_oracle_potentials", "test_point_point_hessian_closed_form", [()
 PSD = ("test_oracle_potentials", "test_psd_projection_properties", [()])
 PSD_PAIR = ("test_oracle_potentials", "test_projected_barrier_hessian_is_psd_and_nearest", [()])
 FRICTION = ("test_oracle_potentials", "test_friction_derivatives_and_invariants", [()])
+FRICTION_ZERO = ("test_oracle_potentials", "test_friction_hessian_at_zero_slip_is_the_limit", [()])
 EMBED = ("test_oracle_scene", "test_embedding_reproduces_rest_positions", [()])
 REDUCE = ("test_oracle_scene", "test_reduction_equals_dense_JT_H_J_config1", [()])
 INVARIANTS = ("test_oracle_scene", "test_reduced_invariants_all_embedded", [()])
@@ -95,6 +96,8 @@ MUTANTS = [
      "return -(m * m) * log(d / T(2.0 * dhat));", [BARRIER]),
     ("f0_quadratic_term", "geometry.hpp", "+ (y * y) / T(eps) +", "+ (y * y) / T(2.0 * eps) +", [F0]),
     ("f0_constant", "geometry.hpp", "T(eps / 3.0)", "T(eps / 2.0)", [F0]),
+    ("f0_branch_point", "geometry.hpp", "if (val(y) >= eps) return y;", "if (val(y) >= 2.0 * eps) return y;",
+     [F0]),
     # forward-mode differentiation rules
     ("ad_product_cross_term", "ad.hpp", "+ a.g[i] * b.g[j] + b.g[i] * a.g[j];",
      "+ 2.0 * a.g[i] * b.g[j];", [PAIR_FD, PP_HESS]),
@@ -142,6 +145,9 @@ MUTANTS = [
     ("lag_normal", "oracle.cpp", "ln[3 * k + q] = r[q] / rn;", "ln[3 * k + q] = r[(q + 1) % 3] / rn;", [LAG]),
     ("friction_tangent_projection", "oracle.cpp", "for (int k = 0; k < 3; ++k) w[k] = v[k] - vn * AD(L.n[k]);",
      "for (int k = 0; k < 3; ++k) w[k] = v[k];", [FRICTION]),
+    ("friction_without_mu", "oracle.cpp", "double ml = mu * L.lambda;", "double ml = L.lambda;", [FRICTION]),
+    ("friction_zero_slip_curvature", "oracle.cpp", "ml * (2.0 / eps) * L.gamma[a] * L.gamma[b]",
+     "ml * (1.0 / eps) * L.gamma[a] * L.gamma[b]", [FRICTION_ZERO]),
     # the step bound (Sec. III-C)
     ("ca_no_safety_factor", "oracle.cpp", "double tn = t + (1.0 - s) * d / L;", "double tn = t + d / L;",
      [CA_PP, CA_EDGES]),

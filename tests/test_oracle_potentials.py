@@ -206,3 +206,28 @@ def test_friction_derivatives_and_invariants():
             x4b = x4.copy(); x4b[0:3] += 1e-4 * n / c[0]
             Eb, _, _ = oracle.pair_friction(v4, c, n, anchor, lam, x4b, mu, eps)
             assert np.isclose(Eb, E, rtol=1e-12)
+
+
+def test_friction_hessian_at_zero_slip_is_the_limit():
+    """At x = x^n the tangential slip u is 0 and the oracle takes the Hessian's limit
+    (Sec. III-B with Eq. 9: f1(y) / y -> 2 / eps).  Pinned against central differences of
+    the gradient around x^n, which the general branch computes (u != 0 on both sides)."""
+    mu, eps, lam = 0.5, 1e-5, 3.7
+    for ptype in (0, 1):
+        x4n, _ = _random_pair(ptype, 1e-3, "face")
+        d2, reg, c = oracle.pair_d2(ptype, x4n)
+        X = x4n.reshape(4, 3)
+        r = (c[:, None] * X).sum(0)
+        n = r / np.linalg.norm(r)
+        v4 = np.arange(4)
+        E, g, H = oracle.pair_friction(v4, c, n, r, lam, x4n, mu, eps)
+        assert np.abs(g).max() == 0
+        h = 1e-6 * eps
+        Hfd = np.zeros((12, 12))
+        for i in range(12):
+            e = np.zeros(12); e[i] = h
+            gp = oracle.pair_friction(v4, c, n, r, lam, x4n + e, mu, eps)[1]
+            gm = oracle.pair_friction(v4, c, n, r, lam, x4n - e, mu, eps)[1]
+            Hfd[:, i] = (gp - gm) / (2 * h)
+        assert np.abs(H).max() > 0
+        assert np.abs(H - Hfd).max() <= 1e-5 * np.abs(H).max()
