@@ -55,6 +55,7 @@ PAIRS = ("test_oracle_scene", "test_pair_set_properties_config1", [()])
 PAIRS_KNOWN = ("test_oracle_scene", "test_pair_set_known_configuration", [()])
 CA_PP = ("test_oracle_scene", "test_ca_point_plane_constant_velocity", [()])
 CA_EDGES = ("test_oracle_scene", "test_ca_separating_and_edges", [()])
+CA_STEPS = ("test_oracle_scene", "test_ca_advances_by_the_speed_bound_until_s_d0", [()])
 CA_CAP = ("test_oracle_scene", "test_ca_iteration_cap_returns_safe_time", [()])
 ACCD = ("test_oracle_scene", "test_accd_no_penetration_after_accepted_step_config1", [()])
 CA_REL = ("test_oracle_scene", "test_ca_bound_depends_only_on_relative_motion", [()])
@@ -124,9 +125,17 @@ MUTANTS = [
      "A[k * n + q] = s * akp - c * akq;", [PSD, PSD_PAIR]),
     ("psd_absolute_value", "oracle.cpp", "if (lam[k] > 0) s += V[i * n + k] * lam[k] * V[j * n + k];",
      "s += V[i * n + k] * std::fabs(lam[k]) * V[j * n + k];", [PSD, PSD_PAIR]),
+    ("jacobi_eigenvector_sign", "oracle.cpp", "V[k * n + q] = s * vkp + c * vkq;",
+     "V[k * n + q] = s * vkp - c * vkq;", [PSD, PSD_PAIR]),
+    ("jacobi_loose_stop", "oracle.cpp", "if (off <= 1e-34 * fro || off == 0.0) break;",
+     "if (off <= 1e-4 * fro || off == 0.0) break;", [PSD, PSD_PAIR]),
+    ("psd_eigenvector_index", "oracle.cpp", "if (lam[k] > 0) s += V[i * n + k] * lam[k] * V[j * n + k];",
+     "if (lam[k] > 0) s += V[i * n + k] * lam[k] * V[k * n + j];", [PSD, PSD_PAIR]),
     # the embedding (Eq. 14) and the reduction (Eq. 17)
     ("embed_index", "oracle.cpp", "s += w[4 * v + j] * q[3 * idx[4 * v + j] + k];",
      "s += w[4 * v + j] * q[3 * idx[4 * v + 3 - j] + k];", [EMBED]),
+    ("embed_kinematic_row", "oracle.cpp", "for (int k = 0; k < 3; ++k) x[3 * v + k] = x_kin[3 * v + k];",
+     "for (int k = 0; k < 3; ++k) x[3 * v + k] = x_kin[3 * v];", [EMBED, PAIRS_KNOWN, ACCD, NO_PENETRATION]),
     ("reduce_gradient_weight", "oracle.cpp", "R.g[3 * I + k] += wa * L.g[3 * a + k];",
      "R.g[3 * I + k] += L.g[3 * a + k];", [REDUCE, INVARIANTS]),
     ("reduce_hessian_weight", "oracle.cpp", "+= wa * wb * L.H[", "+= wa * wa * L.H[", [REDUCE, INVARIANTS]),
@@ -138,6 +147,16 @@ MUTANTS = [
     ("pairs_pt_range", "oracle.cpp", "else if (d < dhat) part[tid].push_back({0,",
      "else if (d < 1.5 * dhat) part[tid].push_back({0,", [PAIRS, PAIRS_KNOWN]),
     ("pairs_order", "oracle.cpp", "    return j < o.j;\n", "    return j > o.j;\n", [PAIRS]),
+    ("incident_ee_partial", "oracle.cpp",
+     "return v[0] == v[2] || v[0] == v[3] || v[1] == v[2] || v[1] == v[3];",
+     "return v[0] == v[2] || v[0] == v[3] || v[1] == v[2];", [PAIRS, PAIRS_KNOWN, NO_PENETRATION]),
+    ("prim_box_upper_corner", "oracle.cpp", "b.hi[k] = std::max(b.hi[k], x[3 * v[t] + k]);",
+     "b.hi[k] = std::min(b.hi[k], x[3 * v[t] + k]);", [PAIRS, PAIRS_KNOWN, PAIRS_EE_SAMPLED]),
+    ("box_overlap_pad_sign", "oracle.cpp",
+     "if (a.lo[k] - pad > b.hi[k] || b.lo[k] - pad > a.hi[k]) return false;",
+     "if (a.lo[k] + pad > b.hi[k] || b.lo[k] + pad > a.hi[k]) return false;", [PAIRS, PAIRS_KNOWN, PAIRS_EE_SAMPLED]),
+    ("enumeration_pad", "oracle.cpp", "const double pad = dhat * (1.0 + 1e-9);\n  bool ok = true;",
+     "const double pad = dhat * 0.5;\n  bool ok = true;", [PAIRS, PAIRS_KNOWN, PAIRS_EE_SAMPLED]),
     # lagged friction (Sec. III-B)
     ("lag_force_magnitude", "oracle.cpp", "llambda[k] = kappa * mk * std::fabs(bb[1]);",
      "llambda[k] = kappa * mk * std::fabs(bb[0]);", [LAG]),
@@ -155,6 +174,11 @@ MUTANTS = [
      [CA_PP, CA_EDGES, ACCD]),
     ("ca_mean_motion", "oracle.cpp", "for (int k = 0; k < 3; ++k) mean[k] /= 4.0;",
      "for (int k = 0; k < 3; ++k) mean[k] /= 2.0;", [CA_REL]),
+    ("ca_stop_threshold", "oracle.cpp", "if (d <= s * d0) return t;", "if (d <= 0.5 * s * d0) return t;",
+     [CA_PP, CA_EDGES, CA_STEPS]),
+    ("ca_cap_off_by_one", "oracle.cpp", "if (*iters >= max_iter) { *capped = true; return t; }",
+     "if (*iters > max_iter) { *capped = true; return t; }", [CA_CAP]),
+    ("ca_point_speed_dropped", "oracle.cpp", "La = norm3(0);", "La = 0.0;", [CA_PP, CA_EDGES, ACCD]),
     ("accd_unswept_boxes", "oracle.cpp",
      "Box a = prim_box(m0, type, i, side_a, x), b = prim_box(m1, type, i, side_a, x1.data());",
      "Box a = prim_box(m0, type, i, side_a, x), b = a;", [ACCD]),

@@ -267,6 +267,27 @@ def test_ca_point_plane_constant_velocity():
             assert it <= 2 and (np.isclose(t, 0.9 * tstar, rtol=1e-12) or np.isclose(t, 0.99 * tstar, rtol=1e-12))
 
 
+def test_ca_advances_by_the_speed_bound_until_s_d0():
+    """A point sliding while it falls onto a large triangle: the advancement's speed bound L
+    (Sec. III-C; with the mean displacement removed, L = |dx| of the point) exceeds the
+    closing speed v, so each advance closes the fraction (1 - s) v / L of the distance:
+    d_k = d0 r^k with r = 1 - (1 - s) v / L, and t_k = (1 - s) (d0 / L) (1 - r^k) / (1 - r).
+    The advancement stops at the first k with d_k <= s d0.  The numbers put r^2 at 0.075,
+    well between s/2 and s, so the count and the time are fixed by the stopping rule."""
+    T = np.array([[-1.0, -1.0, 0.0], [2.0, -1.0, 0.0], [-1.0, 2.0, 0.0]])
+    s, d0, v = 0.1, 1e-3, 5e-3
+    r = np.sqrt(0.075)
+    L = (1 - s) * v / (1 - r)
+    a = np.sqrt(L * L - v * v)                 # tangential speed
+    x4 = np.concatenate([[0.1, 0.2, d0], T.ravel()])
+    dx4 = np.zeros(12); dx4[0] = a; dx4[2] = -v
+    t, it, cap = oracle.ca_pair(0, x4, dx4, s=s)
+    k = 2                                      # r = 0.274 > s >= r^2 = 0.075 > s / 2
+    assert r > s >= r ** k > s / 2
+    assert it == k and not cap
+    assert np.isclose(t, (1 - s) * d0 / L * (1 - r ** k) / (1 - r), rtol=1e-12)
+
+
 def test_ca_separating_and_edges():
     T = np.array([[-1.0, -1.0, 0.0], [2.0, -1.0, 0.0], [-1.0, 2.0, 0.0]])
     x4 = np.concatenate([[0.1, 0.2, 1e-3], T.ravel()])
