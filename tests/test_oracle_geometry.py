@@ -104,6 +104,22 @@ def test_ee_closed_forms():
     assert np.isclose(d2, 0.25) and reg == 7
 
 
+def test_ee_near_parallel_interior_minimum():
+    """Segments crossing (in projection) at a small angle theta, one plane h above the
+    other: the common perpendicular of the lines joins both midpoints, so d^2 = h^2 with
+    the closest points inside both segments, while every endpoint is at least sin(theta)
+    away.  Down to theta = 1e-4 (|ea x eb|^2 / (|ea|^2 |eb|^2) = 1e-8) the pair is not
+    parallel and must take the interior minimum."""
+    h = 0.01
+    a0, a1 = np.array([-1.0, 0.0, 0.0]), np.array([1.0, 0.0, 0.0])
+    for theta in (np.radians(5.0), np.radians(2.0), 1e-2, 1e-4):
+        u = np.array([np.cos(theta), np.sin(theta), 0.0])
+        b0, b1 = np.array([0.0, 0.0, h]) - u, np.array([0.0, 0.0, h]) + u
+        d2, reg, c = oracle.pair_d2(1, np.concatenate([a0, a1, b0, b1]))
+        assert reg == 0 and np.isclose(d2, h * h, rtol=1e-10), (theta, d2)
+        assert np.allclose(c, [0.5, 0.5, -0.5, -0.5], atol=1e-8)
+
+
 def test_degenerate_primitives():
     """A triangle with collinear vertices is the segment they span, and a zero-length edge is
     its point: the distances reduce to point-segment and point-point closed forms."""

@@ -35,6 +35,7 @@ GEO_PT = ("test_oracle_geometry", "test_pt_distance_vs_sampling", [(t,) for t in
 GEO_EE = ("test_oracle_geometry", "test_ee_distance_vs_sampling", [(t,) for t in range(40)])
 GEO_PT_CF = ("test_oracle_geometry", "test_pt_closed_forms", [()])
 GEO_EE_CF = ("test_oracle_geometry", "test_ee_closed_forms", [()])
+GEO_EE_PAR = ("test_oracle_geometry", "test_ee_near_parallel_interior_minimum", [()])
 GEO_DEGEN = ("test_oracle_geometry", "test_degenerate_primitives", [()])
 GEO_EXACT = ("test_oracle_geometry", "test_intersection_test_on_exact_configurations", [()])
 BARRIER = ("test_oracle_potentials", "test_barrier_closed_form_and_boundary", [()])
@@ -120,6 +121,18 @@ MUTANTS = [
      "if (!(edges < -1.0)) {", [GEO_DEGEN]),
     ("segment_zero_length", "geometry.hpp", "if (val(dot(e, e)) == 0.0) {", "if (val(dot(e, e)) < 0.0) {",
      [GEO_DEGEN]),
+    ("pt_vertex_region", "geometry.hpp", "*region = 4 + best_k;", "*region = 4 + (best_k + 1) % 3;",
+     [GEO_PT_CF, DEDUP_APEX, DEDUP_SCENES]),
+    ("ee_corner_region", "geometry.hpp", "*region = 5 + ia * 2 + ib;", "*region = 5 + ib * 2 + ia;",
+     [GEO_EE_CF, DEDUP_SCENES]),
+    ("pt_face_stencil", "geometry.hpp",
+     "c[0] = 1.0; c[1] = -(1.0 - val(b1) - val(b2)); c[2] = -val(b1); c[3] = -val(b2);",
+     "c[0] = 1.0; c[1] = -(1.0 - val(b1)); c[2] = -val(b1); c[3] = -val(b2);", [GEO_PT_CF, LAG, FRICTION]),
+    ("ee_parallel_threshold", "geometry.hpp", "if (val(nn) > 1e-20 * val(A) * val(C)) {",
+     "if (val(nn) > 1e-2 * val(A) * val(C)) {", [GEO_EE, GEO_EE_CF, GEO_EE_PAR]),
+    ("ee_interior_weights", "geometry.hpp",
+     "c[0] = 1.0 - val(s); c[1] = val(s); c[2] = -(1.0 - val(t)); c[3] = -val(t);",
+     "c[0] = 1.0 - val(s); c[1] = val(s); c[2] = -val(t); c[3] = -(1.0 - val(t));", [GEO_EE_CF, LAG, FRICTION]),
     # projection to the nearest PSD matrix (Sec. III-C)
     ("jacobi_rotation_sign", "oracle.cpp", "A[k * n + q] = s * akp + c * akq;",
      "A[k * n + q] = s * akp - c * akq;", [PSD, PSD_PAIR]),
