@@ -9,10 +9,13 @@ the oracle that is checked only against itself.
 
 Every mutant keeps memory accesses in bounds and loops bounded (the Jacobi sweeps and the
 conservative advancement carry their own caps), so a mutant can fail a pin but not crash.
-Changes that cannot alter any output are left out.  Two examples: the second derivative
+Changes that cannot alter any output are left out.  Three examples: the second derivative
 of 1/x, which reaches the distances only through the parameters of closest points, where
-the squared distance is stationary; and where a segment clamps t above 1, since the
-closest point is then also the start of the next edge.
+the squared distance is stationary; where a segment clamps t above 1, since the closest
+point is then also the start of the next edge; and, in the coplanar case of the exact
+intersection test, the check that the segment's second endpoint lies in the triangle and
+the closed upper bounds of the collinear on-segment test, which the edge crossings and the
+same test with edge and triangle exchanged repeat.
 """
 import concurrent.futures
 import ctypes
@@ -106,6 +109,13 @@ MUTANTS = [
     ("ad_sqrt_curvature", "ad.hpp", "-0.25 / (s * a.v)", "0.25 / (s * a.v)", [PAIR_FD, PP_HESS]),
     ("ad_inverse_slope", "ad.hpp", "-1.0 / (x * x)", "-2.0 / (x * x)", [PAIR_FD, PP_HESS]),
     ("ad_log_curvature", "ad.hpp", "-1.0 / (a.v * a.v)", "1.0 / (a.v * a.v)", [BARRIER, PAIR_FD]),
+    ("ad_chain_drops_inner_hessian", "ad.hpp",
+     "for (int j = 0; j < NV; ++j) r.h[i][j] = d1 * a.h[i][j] + d2 * a.g[i] * a.g[j];",
+     "for (int j = 0; j < NV; ++j) r.h[i][j] = d2 * a.g[i] * a.g[j];", [PAIR_FD, PP_HESS]),
+    ("ad_difference_hessian", "ad.hpp", "for (int j = 0; j < NV; ++j) r.h[i][j] = a.h[i][j] - b.h[i][j];",
+     "for (int j = 0; j < NV; ++j) r.h[i][j] = a.h[i][j] + b.h[i][j];", [PAIR_FD, PP_HESS]),
+    ("ad_log_slope", "ad.hpp", "return chain(a, std::log(a.v), 1.0 / a.v, -1.0 / (a.v * a.v));",
+     "return chain(a, std::log(a.v), 2.0 / a.v, -1.0 / (a.v * a.v));", [BARRIER, PAIR_FD]),
     # distances
     ("pt_barycentric_operand", "geometry.hpp", "T b2 = (a * e - b * d) / det;",
      "T b2 = (a * e - b * e) / det;", [GEO_PT, GEO_PT_CF]),
@@ -209,6 +219,13 @@ MUTANTS = [
      [GEO_EXACT]),
     ("intersection_decision", "predicates.hpp", "return !(has_pos && has_neg);", "return has_pos && has_neg;",
      [ACCD, NO_PENETRATION]),
+    ("segment_plane_touch", "predicates.hpp", "if (sp * sq > 0) return false;", "if (sp * sq >= 0) return false;",
+     [GEO_EXACT]),
+    ("segments_meet_or", "predicates.hpp", "if (o1 * o2 < 0 && o3 * o4 < 0) return true;",
+     "if (o1 * o2 < 0 || o3 * o4 < 0) return true;", [GEO_EXACT]),
+    ("orient3d_cofactor_sign", "predicates.hpp", "Expansion cy = add(mul(bd[2], cd[0]), neg(mul(bd[0], cd[2])));",
+     "Expansion cy = add(mul(bd[0], cd[2]), neg(mul(bd[2], cd[0])));", [GEO_EXACT, ACCD]),
+    ("two_sum_error_term", "predicates.hpp", "y = (a - av) + (b - bv);", "y = (a - av);", [GEO_EXACT]),
     # the exact Hessian-vector product
     ("hvp_operand", "oracle.cpp", "acc += L.H[i * 12 + j] * u4[j];", "acc += L.H[i * 12 + j] * u4[i];",
      [HVP_FD, HVP_H]),
