@@ -164,6 +164,10 @@ MUTANTS = [
     ("reduce_hessian_weight", "oracle.cpp", "+= wa * wb * L.H[", "+= wa * wa * L.H[", [REDUCE, INVARIANTS]),
     ("reduce_drops_friction", "oracle.cpp", "      scatter(L.v, idx, w, F, res->R);\n",
      "\n", [REDUCE]),
+    ("eval_projection_switch", "oracle.cpp", "    if (project) {", "    if (!project) {",
+     [REDUCE, REDUCED_FD]),
+    ("eval_friction_energy_dropped", "oracle.cpp", "      res->R.E += F.E;", "      res->R.E += 0.0 * F.E;",
+     [REDUCE]),
     # the contact set B (Sec. III-B)
     ("pairs_ee_range", "oracle.cpp", "else if (d < dhat) part[tid].push_back({1,",
      "else if (d < 1.5 * dhat) part[tid].push_back({1,", [PAIRS, PAIRS_KNOWN]),
@@ -269,6 +273,11 @@ SIM_MUTANTS = [
     ("external_force_sign", "g = Md + h2 * (ge - m.f_ext + r[\"g\"])", "g = Md + h2 * (ge + m.f_ext + r[\"g\"])",
      [SIM_FLIGHT, SIM_NEWTON]),
     ("adjoint_second_history_term", "qbar[n - 2] -= MZ", "qbar[n - 2] += MZ", [SIM_ADJOINT]),
+    ("adjoint_first_history_term", "qbar[n - 1] += 2.0 * MZ", "qbar[n - 1] += MZ", [SIM_ADJOINT]),
+    ("adjoint_theta_partial_sign", "tbar -= h2 * float(np.sum(Z * hk))", "tbar += h2 * float(np.sum(Z * hk))",
+     [SIM_ADJOINT]),
+    ("adjoint_kappa_partial_scale", "kbar -= h2 * float(np.sum(Z * r[\"g\"])) / kappa",
+     "kbar -= h2 * float(np.sum(Z * r[\"g\"]))", [SIM_ADJOINT]),
 ]
 
 
