@@ -253,6 +253,16 @@ MUTANTS = [
      [DEDUP_RIDGE, DEDUP_SCENES]),
     ("dedup_vertex_key", "oracle.cpp", "key = {2, std::min(v[0], t), std::max(v[0], t)};",
      "key = {2, v[0], v[0]};", [DEDUP_APEX, DEDUP_SCENES]),
+    ("dedup_ee_interior_key", "oracle.cpp", "key = {3, pi[k], pj[k]};", "key = {3, pi[k], pi[k]};",
+     [DEDUP_SCENES]),
+    ("dedup_ee_endpoint_edge", "oracle.cpp",
+     "key = e < 2 ? std::array<int64_t, 3>{1, v[e], pj[k]} : std::array<int64_t, 3>{1, v[e], pi[k]};",
+     "key = e < 2 ? std::array<int64_t, 3>{1, v[e], pi[k]} : std::array<int64_t, 3>{1, v[e], pj[k]};",
+     [DEDUP_SCENES]),
+    ("dedup_ee_corner_key", "oracle.cpp", "key = {2, std::min(v[ia], v[2 + ib]), std::max(v[ia], v[2 + ib])};",
+     "key = {2, std::min(v[ia], v[2 + ia]), std::max(v[ia], v[2 + ia])};", [DEDUP_SCENES]),
+    ("mollifier_cross_operand", "oracle.cpp", "    V3<AD> n = cross(p[1] - p[0], p[3] - p[2]);",
+     "    V3<AD> n = cross(p[1] - p[0], p[2] - p[0]);", [MOLL_CF, MOLL_FD, MOLL_SCENE]),
 ]
 
 # the dense driver and adjoint (oracle/sim.py): (name, original, planted, pins)
