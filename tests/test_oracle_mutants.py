@@ -213,6 +213,10 @@ MUTANTS = [
      "++ncand; iters += n;\n      if (t < 0.0) alpha = t;", [ACCD_SAMPLED]),
     ("accd_list_update", "oracle.cpp", "iters += n;\n    if (t < alpha) alpha = t;",
      "iters += n;\n    if (t < 0.0) alpha = t;", [ACCD_SAMPLED]),
+    ("accd_min_update", "oracle.cpp", "    if (t < a) a = t;", "    if (t < 0.0) a = t;", [ACCD, ACCD_SAMPLED]),
+    ("intersection_incident_skip", "oracle.cpp",
+     "if (a == t[0] || a == t[1] || a == t[2] || b == t[0] || b == t[1] || b == t[2]) continue;",
+     "if (a == t[0] || a == t[1] || a == t[2] || b == t[0] || b == t[1]) continue;", [NO_PENETRATION, ACCD]),
     ("pairs_sampled_order", "oracle.cpp", "if (type == 1 && j < i) std::swap(i, j);\n      int32_t s[4];",
      "int32_t s[4];", [PAIRS_EE_SAMPLED]),
     ("pairs_sampled_range", "oracle.cpp", "if (d > 0.0 && d < dhat) out.push_back",
