@@ -82,6 +82,7 @@ MOLL_SCENE = ("test_oracle_mollifier", "test_scene_energy_and_lag_with_the_molli
 
 SIM_REST = ("test_oracle_sim", "test_energy_is_zero_and_stress_free_at_rest_and_rotation_invariant", [()])
 SIM_POLAR = ("test_oracle_sim", "test_polar_rotation_matches_the_svd", [()])
+SIM_LAME = ("test_oracle_sim", "test_lame_parameters_give_back_youngs_modulus_and_poissons_ratio", [()])
 SIM_SMALL_STRAIN = ("test_oracle_sim", "test_small_strain_limit_is_linear_elasticity", [()])
 SIM_STRESS = ("test_oracle_sim", "test_stress_is_the_complex_step_derivative_of_the_energy", [()])
 SIM_DSTRESS = ("test_oracle_sim", "test_stress_differential_matches_central_differences", [()])
@@ -287,6 +288,13 @@ SIM_MUTANTS = [
     ("external_force_sign", "g = Md + h2 * (ge - m.f_ext + r[\"g\"])", "g = Md + h2 * (ge + m.f_ext + r[\"g\"])",
      [SIM_FLIGHT, SIM_NEWTON]),
     ("adjoint_second_history_term", "qbar[n - 2] -= MZ", "qbar[n - 2] += MZ", [SIM_ADJOINT]),
+    ("lame_lambda", "E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))", "E * nu / ((1.0 + nu) * (1.0 - nu))",
+     [SIM_LAME]),
+    ("lame_mu", "return E / (2.0 * (1.0 + nu)),", "return E / (1.0 + nu),", [SIM_LAME]),
+    ("pk_volumetric_direction", "(np.asarray(lam) * (tr - 3.0))[..., None, None] * R",
+     "(np.asarray(lam) * (tr - 3.0))[..., None, None] * F", [SIM_STRESS, SIM_REST]),
+    ("deformation_edge_vector", "q[t[:, 3]] - q[t[:, 0]]], axis=2)", "q[t[:, 3]] - q[t[:, 1]]], axis=2)",
+     [SIM_ELASTIC, SIM_FLIGHT, SIM_NEWTON]),
     ("adjoint_first_history_term", "qbar[n - 1] += 2.0 * MZ", "qbar[n - 1] += MZ", [SIM_ADJOINT]),
     ("adjoint_theta_partial_sign", "tbar -= h2 * float(np.sum(Z * hk))", "tbar += h2 * float(np.sum(Z * hk))",
      [SIM_ADJOINT]),

@@ -40,6 +40,24 @@ def test_energy_is_zero_and_stress_free_at_rest_and_rotation_invariant():
     assert np.allclose(sim.first_pk(Q @ F, MU, LAM), Q @ sim.first_pk(F, MU, LAM), rtol=1e-10, atol=1e-9)
 
 
+def test_lame_parameters_give_back_youngs_modulus_and_poissons_ratio():
+    """Uniaxial stretch by a small e with the lateral strain t free: the energy through the
+    Lame parameters of (E, nu) is least at t = -nu e, and there it is E e^2 / 2 (the
+    definitions of Poisson's ratio and Young's modulus), up to O(e) relative terms."""
+    for E, nu in ((5e4, 0.45), (1e4, 0.3)):
+        mu, lam = sim.lame(E, nu)
+        e = 1e-5
+
+        def energy(t):
+            return sim.psi(np.diag([1.0 + e, 1.0 + t, 1.0 + t])[None], mu, lam)[0]
+
+        ts = np.array([-e, 0.0, e])
+        a, b, _ = np.polyfit(ts, [energy(t) for t in ts], 2)
+        t_min = -b / (2.0 * a)
+        assert np.isclose(-t_min / e, nu, rtol=1e-3), (E, nu, -t_min / e)
+        assert np.isclose(2.0 * energy(t_min) / e ** 2, E, rtol=1e-3), (E, nu)
+
+
 def test_polar_rotation_matches_the_svd():
     rng = np.random.default_rng(1)
     F = _F(rng, s=0.4)
