@@ -87,6 +87,7 @@ SIM_SMALL_STRAIN = ("test_oracle_sim", "test_small_strain_limit_is_linear_elasti
 SIM_STRESS = ("test_oracle_sim", "test_stress_is_the_complex_step_derivative_of_the_energy", [()])
 SIM_DSTRESS = ("test_oracle_sim", "test_stress_differential_matches_central_differences", [()])
 SIM_VOLUMES = ("test_oracle_sim", "test_volumes_mass_and_weight", [()])
+SIM_VOLUME_SPLIT = ("test_oracle_sim", "test_vertex_volumes_of_an_offset_octahedron", [()])
 SIM_MASS = ("test_oracle_sim", "test_reduced_mass_is_the_kinetic_energy_through_the_embedding", [()])
 SIM_FLIGHT = ("test_oracle_sim", "test_free_flight_of_a_rigid_translation_is_exact", [()])
 SIM_ELASTIC = ("test_oracle_sim", "test_elastic_gradient_and_hessian_match_central_differences", [()])
@@ -288,6 +289,7 @@ SIM_MUTANTS = [
     ("external_force_sign", "g = Md + h2 * (ge - m.f_ext + r[\"g\"])", "g = Md + h2 * (ge + m.f_ext + r[\"g\"])",
      [SIM_FLIGHT, SIM_NEWTON]),
     ("adjoint_second_history_term", "qbar[n - 2] -= MZ", "qbar[n - 2] += MZ", [SIM_ADJOINT]),
+    ("volume_apex_origin", "c = x[members].mean(0)", "c = np.zeros(3)", [SIM_VOLUME_SPLIT]),
     ("lame_lambda", "E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))", "E * nu / ((1.0 + nu) * (1.0 - nu))",
      [SIM_LAME]),
     ("lame_mu", "return E / (2.0 * (1.0 + nu)),", "return E / (1.0 + nu),", [SIM_LAME]),

@@ -123,6 +123,25 @@ def test_volumes_mass_and_weight():
     assert np.allclose(m.M, m.M.T) and np.linalg.eigvalsh(m.M).min() > -1e-15
 
 
+def test_vertex_volumes_of_an_offset_octahedron():
+    """The per-vertex split of the enclosed volume (one third of each incident triangle's
+    cone to the body's centroid): a regular octahedron of radius r has eight congruent
+    cones and four triangles at every vertex, so each of its six vertices takes
+    (4/3) r^3 / 6, wherever the octahedron sits.  Each vertex is its own cage node here."""
+    import types
+    r, c = 0.3, np.array([3.0, -2.0, 5.0])
+    X = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], float) * r + c
+    tris = np.array([[0, 2, 4], [2, 1, 4], [1, 3, 4], [3, 0, 4],
+                     [2, 0, 5], [1, 2, 5], [3, 1, 5], [0, 3, 5]], np.int32)
+    n = len(X)
+    sc = types.SimpleNamespace(
+        Nv=n, Ns=n, q0=X, x_kin=np.zeros((n, 3)), kinematic=np.zeros(n, bool), body=np.zeros(n, np.int64),
+        tris=tris, cage_idx=np.repeat(np.arange(n, dtype=np.int32)[:, None], 4, axis=1),
+        w=np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)))
+    Vk = sim.vertex_volumes(sc)
+    assert np.allclose(Vk, 4.0 / 3.0 * r ** 3 / 6.0, rtol=1e-12)
+
+
 def test_reduced_mass_is_the_kinetic_energy_through_the_embedding():
     """M^q = J^T M J (Sec. III-D): for any reduced velocity v, v^T M^q v equals the lumped
     full-space kinetic form sum_k rho V_k |(J v)_k|^2, with J v taken by the embedding."""
