@@ -79,3 +79,11 @@ def test_vertex_volumes_match_the_oracle(phys):
     Vo = osim.vertex_volumes(sc)
     assert np.abs(V - Vo).max() <= 1e-12 * np.abs(Vo).max()
     assert np.all(V[sc.kinematic] == 0.0)
+
+
+def test_lame_parameters_match_the_oracle():
+    """The driver's (E, nu) -> (mu, lambda) conversion against the oracle's, which is pinned
+    on Young's modulus and Poisson's ratio of a uniaxial stretch."""
+    from paper_2409_16385_gb300.elastic import lame
+    for E, nu in ((5e4, 0.45), (1e4, 0.3), (2e6, 0.0)):
+        assert np.allclose(lame(E, nu), osim.lame(E, nu), rtol=1e-15, atol=0)
