@@ -433,6 +433,10 @@ def run_reference(args, ws, rank):
         return
     import oracle
     oracle.build()
+    if ws > 1:
+        # the launcher sets OMP_NUM_THREADS=1 for every rank; only this rank works, so the
+        # oracle takes every host core it may run on, as in a one-process run
+        oracle.set_threads(len(os.sched_getaffinity(0)))
     sc = build_scene(args.quick)
     # the enumeration fraction: about 30 s of brute force per list, calibrated on 1/2000
     t_cal = time.perf_counter()
